@@ -1,0 +1,95 @@
+/*
+ * oracle.h -- plain FP64 CPU oracle of the structured-grid finite-volume hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark may load this library.  It shares no code, header, table or helper with the CUDA
+ * library; the two are checked against each other on the same seeded inputs.
+ *
+ * What it computes (arXiv 1710.09995, Sec. 2.1-2.2):
+ *   Eq. 1  compressible Navier-Stokes in curvilinear coordinates, Q = (rho, rho u, rho v, rho w, rho E);
+ *   Eq. 3  semi-discrete form dQ/dt = -R(Q);
+ *   Eqs. 4-6  third-order Runge-Kutta in Shu-Osher form with lambda read as -dt;
+ *   Sec. 2.2  cell-edge left/right states combined by a flux function, central viscous fluxes,
+ *             multi-block interfaces that preserve a uniform flow (geometric conservation).
+ * Where the paper leaves the choice open (its WCNS-E-5 interpolation is not specified beyond
+ * Eq. 2) this oracle uses cell-centred finite volume, MUSCL reconstruction of primitive
+ * variables with the minmod limiter, the Roe flux with Harten's entropy fix, second-order
+ * central viscous fluxes and SSP-RK3.
+ *
+ * Layout (the oracle's own): every field is stored with a 2-cell halo on all sides,
+ *   a[v][k+2][j+2][i+2], i in [-2, nx+1], dims (nx+4) x (ny+4) x (nz+4), no padding.
+ * Metrics: M[10][cells] = S_xi(3), S_eta(3), S_zeta(3), V; S_d of cell c is the area vector of
+ * the cell's lower face in direction d (pointing towards +d).
+ * Nodes: X[3][nz+1][ny+1][nx+1] (interior block only; halo metrics come from periodic copies).
+ *
+ * Every function returns 0 on success and a negative number on bad arguments or allocation
+ * failure.  Nothing is kept between calls.
+ */
+#ifndef CFD_ORACLE_H
+#define CFD_ORACLE_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double gamma;    /* ratio of specific heats */
+  double mu;       /* constant dynamic viscosity (0 with viscous=0) */
+  double Pr;       /* Prandtl number */
+  double cfl;      /* CFL number of the global time step */
+  double eps;      /* Harten entropy-fix fraction of (|u.n| + c); 0 disables the fix */
+  int viscous;     /* 1: add the viscous fluxes of Eq. 1 */
+  int limiter;     /* 0: minmod slopes; 1: unlimited central slope (Fromm) */
+} oracle_params;
+
+/* number of cells of one halo-padded field */
+size_t oracle_cells(int nx, int ny, int nz);
+
+/* primitive (rho,u,v,w,p) from conserved (Eq. 1 definitions, ideal gas) */
+void oracle_primitive(double gamma, const double U[5], double W[5]);
+
+/* MUSCL states at the face between w1 and w2 of the stencil w0,w1,w2,w3 (primitives) */
+void oracle_muscl(int limiter, const double w0[5], const double w1[5], const double w2[5],
+                  const double w3[5], double wl[5], double wr[5]);
+
+/* Roe flux through the area vector S (not normalised) from primitive states wl, wr */
+void oracle_roe_flux(double gamma, double eps, const double wl[5], const double wr[5],
+                     const double S[3], double F[5]);
+
+/* face area vectors and volumes of interior cells from nodes, halo cells by periodic copy */
+int oracle_metrics(int nx, int ny, int nz, const double* X, double* M);
+
+/* copy periodic images into the 2-cell halo of nvar fields */
+int oracle_fill_halo_periodic(int nx, int ny, int nz, int nvar, double* a);
+
+/* R(Q) of Eq. 3 at interior cells; Q's halo must be filled. R is [5][nz][ny][nx] compact. */
+int oracle_residual(const oracle_params* p, int nx, int ny, int nz, const double* M,
+                    const double* Q, double* R);
+
+/* global CFL time step from Q (halo filled) */
+int oracle_dt(const oracle_params* p, int nx, int ny, int nz, const double* M, const double* Q,
+              double* dt);
+
+/* RMS over interior cells of each component of a compact residual R[5][n] */
+int oracle_norms(size_t n, const double* R, double out[5]);
+
+/* one stage of Eqs. 4-6 (lambda = -dt) on flat arrays of n values */
+int oracle_rk3_stage(int stage, size_t n, const double* Qn, const double* Qs, const double* R,
+                     double dt, double* Qout);
+
+/* nsteps SSP-RK3 steps on a periodic block. Q is halo-padded, updated in place.
+ * dts[nsteps] and norms[nsteps][5] (RMS of the stage-1 residual) are written when not NULL. */
+int oracle_step(const oracle_params* p, int nx, int ny, int nz, const double* M, double* Q,
+                int nsteps, double* dts, double* norms);
+
+/* same as oracle_step with the time step fixed to dt (no CFL evaluation) */
+int oracle_step_fixed_dt(const oracle_params* p, int nx, int ny, int nz, const double* M,
+                         double* Q, int nsteps, double dt, double* norms);
+
+/* threads the oracle's OpenMP loops use (1 when built without OpenMP) */
+int oracle_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

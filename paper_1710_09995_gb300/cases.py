@@ -1,0 +1,214 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This module holds only initial conditions and grids; none of the solver's arithmetic (no
+reconstruction, flux, metric, residual or time stepping).  It imports neither the CUDA binding
+nor the oracle, and both consume what it returns.
+
+Arrays returned here:
+  state  Q[5][nz][ny][nx] float64, conserved (rho, rho u, rho v, rho w, rho E) of Eq. 1
+  nodes  X[3][nz+1][ny+1][nx+1] float64, the block's grid points (x, y, z)
+The paper's meshes (NACA0012, DeltaWing, DLR-F6, CompCorner) are not available; these seeded
+cases stand in for them with the sizes and flow regimes of the workloads the solver is built for.
+"""
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+@dataclass
+class Case:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    state: np.ndarray
+    nodes: np.ndarray = None          # None for a uniform Cartesian grid
+    spacing: tuple = (1.0, 1.0, 1.0)  # cell size of the uniform Cartesian grid
+    gamma: float = GAMMA
+    mu: float = 0.0
+    Pr: float = 0.72
+    cfl: float = 0.5
+    eps: float = 0.1
+    viscous: bool = False
+    limiter: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def grid_nodes(self) -> np.ndarray:
+        """nodes of the block (uniform Cartesian ones when the case has none)"""
+        if self.nodes is not None:
+            return self.nodes
+        return cartesian_nodes(self.nx, self.ny, self.nz, *self.spacing)
+
+
+def conserved(rho, u, v, w, p, gamma=GAMMA) -> np.ndarray:
+    """(rho, u, v, w, p) -> conserved state array (Eq. 1's Q)"""
+    rho = np.asarray(rho, dtype=np.float64)
+    shape = rho.shape
+    u, v, w, p = (np.broadcast_to(np.asarray(a, dtype=np.float64), shape) for a in (u, v, w, p))
+    q = np.empty((5,) + shape)
+    q[0] = rho
+    q[1] = rho * u
+    q[2] = rho * v
+    q[3] = rho * w
+    q[4] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return q
+
+
+def cartesian_nodes(nx, ny, nz, hx, hy, hz) -> np.ndarray:
+    x = np.arange(nx + 1, dtype=np.float64) * hx
+    y = np.arange(ny + 1, dtype=np.float64) * hy
+    z = np.arange(nz + 1, dtype=np.float64) * hz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return np.ascontiguousarray(np.stack([X, Y, Z]))
+
+
+def cell_centres(nx, ny, nz, hx, hy, hz):
+    x = (np.arange(nx) + 0.5) * hx
+    y = (np.arange(ny) + 0.5) * hy
+    z = (np.arange(nz) + 0.5) * hz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def _periodic_delta(a, a0, period):
+    d = a - a0
+    return d - period * np.round(d / period)
+
+
+# ---- 32^3 Gaussian pulse, Euler FP64 -------------------------------------------------------
+
+def gaussian_pulse(n=32, seed=0, mach=0.5, amp=1e-2, width=0.1, gamma=GAMMA, nx=None, ny=None, nz=None) -> Case:
+    """Unit periodic box, spacing 1/n, rho = 1, p = 1/gamma (so c = 1), u = Mach along x, plus
+    amp * exp(-r^2 / width^2) added to rho and p/p_inf around a seeded centre (minimum-image r)."""
+    nx, ny, nz = nx or n, ny or n, nz or n
+    h = (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x0 = rng.random(3)
+    X, Y, Z = cell_centres(nx, ny, nz, *h)
+    r2 = (_periodic_delta(X, x0[0], 1.0) ** 2 + _periodic_delta(Y, x0[1], 1.0) ** 2
+          + _periodic_delta(Z, x0[2], 1.0) ** 2)
+    g = np.exp(-r2 / width ** 2)
+    rho = 1.0 + amp * g
+    p = (1.0 / gamma) * (1.0 + amp * g)
+    q = conserved(rho, mach, 0.0, 0.0, p, gamma)
+    return Case("gaussian_pulse", nx, ny, nz, q, None, h, gamma=gamma, cfl=0.5, eps=0.1,
+                extra={"centre": x0.tolist(), "seed": seed})
+
+
+# ---- isentropic vortex (closed form), Navier-Stokes or Euler -------------------------------
+
+def vortex_fields(X, Y, t, L, beta=5.0, mach=0.5, gamma=GAMMA, centre=None):
+    """Closed-form isentropic vortex of strength beta convecting along x on a periodic box of
+    side L (free stream rho = 1, p = 1, T = p / rho, c = sqrt(gamma)); exact for Euler."""
+    uinf = mach * math.sqrt(gamma)
+    xc0, yc0 = centre if centre is not None else (0.5 * L, 0.5 * L)
+    dx = _periodic_delta(X, xc0 + uinf * t, L)
+    dy = _periodic_delta(Y, yc0, L)
+    r2 = dx * dx + dy * dy
+    e = np.exp(0.5 * (1.0 - r2))
+    u = uinf - beta / (2.0 * math.pi) * dy * e
+    v = beta / (2.0 * math.pi) * dx * e
+    T = 1.0 - (gamma - 1.0) * beta ** 2 / (8.0 * gamma * math.pi ** 2) * e * e
+    rho = T ** (1.0 / (gamma - 1.0))
+    p = rho * T
+    return rho, u, v, p
+
+
+def isentropic_vortex(n=256, L=10.0, nz=None, beta=5.0, mach=0.5, Re=1e4, Pr=0.72, viscous=True,
+                      t=0.0, gamma=GAMMA, cfl=0.5, limiter=0, eps=0.1) -> Case:
+    """z-invariant vortex on [0,L]^2 x [0, nz*h], h = L/n, periodic; mu = rho_inf |u_inf| / Re
+    with reference length 1."""
+    nz = nz or n
+    h = L / n
+    X, Y, _ = cell_centres(n, n, nz, h, h, h)
+    rho, u, v, p = vortex_fields(X, Y, t, L, beta, mach, gamma)
+    q = conserved(rho, u, v, 0.0, p, gamma)
+    uinf = mach * math.sqrt(gamma)
+    mu = uinf / Re if viscous else 0.0
+    return Case("isentropic_vortex", n, n, nz, q, None, (h, h, h), gamma=gamma, mu=mu, Pr=Pr,
+                cfl=cfl, eps=eps, viscous=viscous, limiter=limiter,
+                extra={"L": L, "beta": beta, "mach": mach, "Re": Re})
+
+
+# ---- warped curvilinear grid with broadband velocity perturbation -------------------------
+
+def warped_nodes(nx, ny, nz, amp=0.05) -> np.ndarray:
+    """[0,1]^3 mapped by x' = x + a sin(2 pi y) sin(2 pi z) and the cyclic permutations,
+    applied simultaneously; periodic-compatible (the map shifts by whole periods)."""
+    x = np.arange(nx + 1, dtype=np.float64) / nx
+    y = np.arange(ny + 1, dtype=np.float64) / ny
+    z = np.arange(nz + 1, dtype=np.float64) / nz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    s = lambda a: np.sin(2.0 * math.pi * a)
+    Xw = X + amp * s(Y) * s(Z)
+    Yw = Y + amp * s(Z) * s(X)
+    Zw = Z + amp * s(X) * s(Y)
+    return np.ascontiguousarray(np.stack([Xw, Yw, Zw]))
+
+
+def broadband_warped(nx=512, ny=512, nz=384, seed=0, mach=0.3, rms=0.05, kmax=16, Re=1e5,
+                     Pr=0.72, amp=0.05, gamma=GAMMA, viscous=True, cfl=0.5, nmodes=64) -> Case:
+    """Mean flow at Mach `mach` along x (rho = 1, p = 1/gamma, c = 1) on the warped unit box plus
+    a seeded divergence-free sum of Fourier modes with |k| <= kmax scaled to `rms` of |u_inf|."""
+    nodes = warped_nodes(nx, ny, nz, amp)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    # cell centres of the warped grid: mean of the eight corner nodes
+    c = 0.125 * (nodes[:, :-1, :-1, :-1] + nodes[:, :-1, :-1, 1:] + nodes[:, :-1, 1:, :-1]
+                 + nodes[:, :-1, 1:, 1:] + nodes[:, 1:, :-1, :-1] + nodes[:, 1:, :-1, 1:]
+                 + nodes[:, 1:, 1:, :-1] + nodes[:, 1:, 1:, 1:])
+    du = np.zeros((3,) + c.shape[1:])
+    count = 0
+    while count < nmodes:
+        k = rng.integers(-kmax, kmax + 1, size=3)
+        if not k.any() or np.dot(k, k) > kmax * kmax:
+            continue
+        a = rng.standard_normal(3)
+        a -= np.dot(a, k) / np.dot(k, k) * k      # a . k = 0: each mode is divergence-free
+        phase = rng.random() * 2.0 * math.pi
+        arg = 2.0 * math.pi * (k[0] * c[0] + k[1] * c[1] + k[2] * c[2]) + phase
+        du += a[:, None, None, None] * np.sin(arg)[None]
+        count += 1
+    uinf = mach
+    du *= rms * uinf / math.sqrt(np.mean(np.sum(du * du, axis=0)))
+    q = conserved(np.ones(c.shape[1:]), uinf + du[0], du[1], du[2], 1.0 / gamma, gamma)
+    mu = uinf / Re if viscous else 0.0
+    return Case("broadband_warped", nx, ny, nz, q, nodes, (1.0 / nx, 1.0 / ny, 1.0 / nz), gamma=gamma,
+                mu=mu, Pr=Pr, cfl=cfl, eps=0.1, viscous=viscous, extra={"seed": seed, "Re": Re})
+
+
+# ---- random smooth states for parity sweeps -------------------------------------------------
+
+def smooth_random(nx, ny, nz, seed=0, amp=0.05, mach=0.5, gamma=GAMMA, h=None, nodes=None,
+                  viscous=False, mu=0.0, limiter=0, eps=0.1, cfl=0.5, nmodes=6) -> Case:
+    """Free stream (rho = 1, p = 1/gamma, u = Mach along x) plus a few seeded periodic Fourier
+    modes of relative amplitude `amp` in every primitive variable."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = h or (1.0 / nx, 1.0 / ny, 1.0 / nz)
+    X, Y, Z = cell_centres(nx, ny, nz, *h)
+    Lx, Ly, Lz = nx * h[0], ny * h[1], nz * h[2]
+    prim = [np.ones_like(X), np.full_like(X, mach), np.zeros_like(X), np.zeros_like(X),
+            np.full_like(X, 1.0 / gamma)]
+    for m in range(5):
+        scale = amp * (1.0 if m in (0, 4) else 1.0)
+        ref = 1.0 if m in (0, 1, 2, 3) else 1.0 / gamma
+        for _ in range(nmodes):
+            k = rng.integers(-3, 4, size=3)
+            ph = rng.random() * 2 * math.pi
+            a = rng.standard_normal() / nmodes
+            prim[m] = prim[m] + scale * ref * a * np.sin(
+                2 * math.pi * (k[0] * X / Lx + k[1] * Y / Ly + k[2] * Z / Lz) + ph)
+    q = conserved(*prim, gamma=gamma)
+    return Case("smooth_random", nx, ny, nz, q, nodes, h, gamma=gamma, mu=mu, cfl=cfl, eps=eps,
+                viscous=viscous, limiter=limiter, extra={"seed": seed})
+
+
+def with_grid(case: Case, nodes: np.ndarray) -> Case:
+    case.nodes = nodes
+    return case
