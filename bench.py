@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark of the structured-grid finite-volume hot path on one GB300 (or N replicas).
+
+Workload: 256^3 isentropic vortex (strength 5, Mach 0.5, periodic [0,10]^3), compressible
+Navier-Stokes at Re 1e4, Pr 0.72; MUSCL/minmod + Roe + central viscous fluxes, SSP-RK3 at
+CFL 0.5.  A step is one full SSP-RK3 step of the block: per stage one halo exchange and one
+fused stage kernel (residual + update; stage 1 also the residual norm, stage 3 also the next
+time step).  The headline runs the mixed path (FP32 reconstruction and fluxes, FP64 state,
+update and norms); the FP64 path is timed on the same case in the same run.
+
+Prints one JSON line (rank 0).  Inputs are seeded and synthetic (the paper's meshes are not
+available).  `--impl reference` times the FP64 CPU oracle instead (the only reference there is).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 256
+PEAK_FALLBACK_GBS = 6800.0
+# algorithmic HBM bytes per interior cell for stages 1, 2, 3 (state reads/writes, halos excluded)
+ALGO_BYTES = {
+    "mixed": (40 + 20, 40 + 20 + 20, 40 + 20 + 40),   # Qn read; D read; D or Q^{n+1} written
+    "fp64": (40 + 40, 40 + 40 + 40, 40 + 40 + 40),    # stage input, Qn read; stage output written
+}
+WORKLOAD = "isentropic vortex 256^3, Navier-Stokes Re 1e4 Pr 0.72, MUSCL/minmod + Roe, SSP-RK3 CFL 0.5"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gbcfd", choices=["gbcfd", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT, help="cells per side of the cubic block")
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---- distributed plumbing (independent replicas; no data-path collective) ------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks ----------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, flag in zip(names, r[3][1:]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "power_w_max": max(r[2] for r in rows), "reasons": sorted(reasons)}
+
+
+# ---- peaks and profile evidence --------------------------------------------------------------
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1710_09995_gb300", "csrc")
+    for name in ("stage.cuh", "physics.cuh", "internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(precision):
+    """DRAM bytes per stage launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"stage_kernel_{precision}_vortex.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel source hash:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram bytes per stage launch at 256\^3:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+# ---- the GPU arm -----------------------------------------------------------------------------
+def time_path(gbcfd, torch, case, precision, steps, warmup, world, device):
+    blk = gbcfd.block_for_case(case, precision=gbcfd.MIXED if precision == "mixed" else gbcfd.FP64)
+    stream = torch.cuda.current_stream()
+
+    def one_step(evs=None):
+        for s in (1, 2, 3):
+            if evs is not None:
+                evs[s][0].record(stream)
+            gbcfd.exchange_halos([blk], stream)
+            if evs is not None:
+                evs[s][1].record(stream)
+            gbcfd.stage([blk], s, stream)
+            if evs is not None:
+                evs[s][2].record(stream)
+
+    for _ in range(warmup):
+        one_step()
+    torch.cuda.synchronize()
+    events = [{s: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for s in (1, 2, 3)}
+              for _ in range(steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(steps):
+        one_step(events[k])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(start.elapsed_time(stop), world, device)
+    stage_ms = {s: sum(e[s][1].elapsed_time(e[s][2]) for e in events) for s in (1, 2, 3)}
+    halo_ms = sum(e[s][0].elapsed_time(e[s][1]) for e in events for s in (1, 2, 3))
+    norms = blk.residual_norm()  # also surfaces any device-side error flag
+    blk.close()
+    return {"ms": ms, "stage_ms": stage_ms, "halo_ms": halo_ms, "launches": 6 * steps, "norms": norms.tolist()}
+
+
+def e2e_path(gbcfd, torch, case, precision, steps, world, device):
+    """Through the C ABI with pinned host buffers: every step uploads the state, advances one
+    SSP-RK3 step and reads back the new state and the residual norm."""
+    blk = gbcfd.block_for_case(case, precision=gbcfd.MIXED if precision == "mixed" else gbcfd.FP64)
+    host_in = torch.from_numpy(case.state).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    blk.set_state(host_in)
+    gbcfd.step([blk], 1)
+    blk.get_state(host_out)
+    blk.residual_norm()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        blk.set_state(host_in)
+        gbcfd.step([blk], 1)
+        blk.get_state(host_out)
+        blk.residual_norm()
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, world, device)
+    blk.close()
+    nbytes = case.state.nbytes
+    ctrl_bytes = 112  # the control block read by residual_norm
+    return {"value": world * case.cells * steps / dt, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + ctrl_bytes}
+
+
+def roofline(precision, res, cells, steps, peak, peak_kind):
+    nbytes = sum(ALGO_BYTES[precision][s - 1] * cells * steps for s in (1, 2, 3))
+    sec = sum(res["stage_ms"].values()) / 1e3
+    achieved = nbytes / sec / 1e9
+    traffic = profiled_traffic(precision)
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+            "traffic": traffic, "algorithmic_bytes_per_launch": nbytes / (3 * steps),
+            "kernel": "stage_kernel", "avg_launch_ms": round(sec * 1e3 / (3 * steps), 4)}
+
+
+def cpu_baseline_sample(n):
+    """The FP64 oracle on the host cores: one SSP-RK3 step of a 256 x 256 x 64 z-slab of the
+    (z-invariant) vortex -- exactly a sub-problem of the workload -- best of 2."""
+    import oracle
+    from paper_1710_09995_gb300 import cases
+    nz = 64
+    c = cases.isentropic_vortex(n=n, L=10.0, nz=nz, viscous=True)
+    M = oracle.metrics(c.grid_nodes())
+    p = oracle.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, c.limiter)
+    Q = oracle.pad(c.state)
+    best = math.inf
+    for _ in range(2):
+        t0 = time.perf_counter()
+        oracle.step(p, Q, M, 1)
+        best = min(best, time.perf_counter() - t0)
+    return {"value": c.cells / best, "unit": "cell-updates/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"1 SSP-RK3 step (FP64) of a {n}x{n}x{nz} z-slab of the z-invariant vortex, best of 2"}
+
+
+def run_gbcfd(args):
+    world, rank, local = dist_env()
+    import torch
+    if world > 1:
+        dist_init(world, "nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_1710_09995_gb300 import cases, gbcfd
+    gbcfd.lib()
+    case = cases.isentropic_vortex(n=args.n, L=10.0, viscous=True)
+    peak, peak_kind = hbm_peak()
+    paths = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    clocks = ClockSampler(local)
+    clocks.start()
+    results = {p: time_path(gbcfd, torch, case, p, args.steps, args.warmup, world, device) for p in paths}
+    clk = clocks.stop()
+    head = paths[0]
+    e2e = e2e_path(gbcfd, torch, case, head, min(args.e2e_steps, args.steps), world, device)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(args.n)
+    if rank != 0:
+        return
+    r = results[head]
+    out = {
+        "metric": "cell-updates/s",
+        "value": world * case.cells * args.steps / (r["ms"] / 1e3),
+        "unit": "cell-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": r["ms"] / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64" if head == "mixed" else "f64",
+        "data": "synthetic (seeded closed-form vortex; the paper's meshes are not available)",
+        "config": {"workload": WORKLOAD, "cells": case.cells, "precision": head,
+                   "l2": "working set > 1.4 GB >> 129 MB L2, no flush needed",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline(head, r, case.cells, args.steps, peak, peak_kind),
+        "e2e": e2e,
+        "gpu_launches": r["launches"],
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "halo_ms_per_step": r["halo_ms"] / args.steps,
+        "residual_norm": r["norms"],
+    }
+    for p in paths[1:]:
+        rp = results[p]
+        out[p] = {"value": world * case.cells * args.steps / (rp["ms"] / 1e3), "unit": "cell-updates/s",
+                  "ms_per_step": rp["ms"] / args.steps, "dtype": "f64",
+                  "roofline": roofline(p, rp, case.cells, args.steps, peak, peak_kind),
+                  "gpu_launches": rp["launches"]}
+    print(json.dumps(out))
+
+
+# ---- the reference arm: the FP64 CPU oracle ----------------------------------------------------
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1710_09995_gb300 import cases
+    nz = 8
+    c = cases.isentropic_vortex(n=args.n, L=10.0, nz=nz, viscous=True)
+    M = oracle.metrics(c.grid_nodes())
+    p = oracle.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, c.limiter)
+    Q = oracle.pad(c.state)
+    for _ in range(args.warmup):
+        Q, _, _ = oracle.step(p, Q, M, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Q, _, _ = oracle.step(p, Q, M, 1)
+    sec = time.perf_counter() - t0
+    value = c.cells * args.steps / sec
+    sample = (f"each step: 1 SSP-RK3 step (FP64 oracle) of a {args.n}x{args.n}x{nz} z-slab of the "
+              f"z-invariant {args.n}^3 vortex")
+    out = {"impl": "reference", "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "cells": c.cells, "precision": "fp64"},
+           "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": oracle.threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gbcfd(a)

@@ -1,0 +1,139 @@
+/*
+ * gbcfd.h -- C ABI of the GB300 (sm_103a) structured-grid finite-volume hot path.
+ *
+ * The operations are those of arXiv 1710.09995 Sec. 2.1-2.2 on 3D structured blocks:
+ *   the residual R(Q) of the semi-discrete form dQ/dt = -R(Q) (Eq. 3) for the curvilinear
+ *   Navier-Stokes equations (Eq. 1), with cell-edge left/right states combined by a flux
+ *   function and central viscous fluxes (Sec. 2.2), the third-order Runge-Kutta time update
+ *   (Eqs. 4-6, lambda read as -dt), the data exchange between neighbouring blocks after each
+ *   update (Sec. 3.2.5 (2)) and the residual norm of the convergence check (Sec. 2.3).
+ * The scheme where the paper leaves the choice open: cell-centred finite volume, MUSCL
+ * reconstruction of primitive variables with the minmod limiter, Roe flux with Harten's entropy
+ * fix, second-order central viscous fluxes, SSP-RK3, a 2-cell halo, a global CFL time step.
+ *
+ * Conventions
+ *  - Every function returns GBCFD_OK (0) or a negative GBCFD_ERR_* code; gbcfd_last_error()
+ *    then returns a message for the calling host thread.  Nothing throws across the ABI.
+ *  - Device memory is owned by the caller: gbcfd_required_bytes() tells how much one block
+ *    needs, gbcfd_create_block() carves it.  The library allocates no device memory.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are asynchronous on it
+ *    unless stated; a block must not be used from two streams at once.
+ *  - State arrays passed in or out are compact SoA float64, q[5][nz][ny][nx] (x fastest), the
+ *    conserved variables (rho, rho u, rho v, rho w, rho E) of Eq. 1.  Where a pointer may be
+ *    host or device memory it says so; host memory should be pinned for speed.
+ *  - Faces are numbered 0..5 = -x, +x, -y, +y, -z, +z.
+ */
+#ifndef GBCFD_H
+#define GBCFD_H
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBCFD_OK 0
+#define GBCFD_ERR_ARG (-1)          /* bad argument: null pointer, size, range, mismatch */
+#define GBCFD_ERR_CUDA (-2)         /* a CUDA runtime or driver call failed */
+#define GBCFD_ERR_NONPHYSICAL (-3)  /* rho <= 0, p <= 0 or a non-finite value was met */
+#define GBCFD_ERR_TIMEOUT (-4)      /* a bounded device wait ran out (a copy never landed) */
+#define GBCFD_ERR_STATE (-5)        /* call out of order (e.g. step before set_state) */
+#define GBCFD_ERR_MEMORY (-6)       /* caller memory too small or misaligned */
+
+#define GBCFD_FP64 0   /* everything in FP64 */
+#define GBCFD_MIXED 1  /* reconstruction, fluxes and stage increments in FP32; state, its
+                          update and the residual-norm reduction in FP64 */
+
+typedef struct gbcfd_block_s* gbcfd_block; /* opaque, host-side descriptor */
+
+typedef struct {
+  double gamma;       /* ratio of specific heats (1.4) */
+  double mu;          /* constant dynamic viscosity; used when viscous != 0 */
+  double Pr;          /* Prandtl number; heat conductivity = mu gamma / ((gamma - 1) Pr) */
+  double cfl;         /* CFL number of the global time step */
+  double entropy_eps; /* Harten entropy-fix fraction of (|u.n| + c); 0 disables the fix */
+  int viscous;        /* 0: Euler, 1: Navier-Stokes (Eq. 1 with Fv, Gv, Hv) */
+  int limiter;        /* 0: minmod, 1: unlimited central slope */
+  int precision;      /* GBCFD_FP64 or GBCFD_MIXED */
+  int reserved;       /* must be 0 */
+} gbcfd_params;
+
+/* Bytes of caller device memory one block of nx x ny x nz interior cells needs (state, stage
+ * buffers, metrics, reduction scratch), for the given precision.  Sizes must be >= 1.
+ * The halo is always 2 cells (the MUSCL stencil i-1..i+2 of Sec. 2.2's cell-edge states). */
+int gbcfd_required_bytes(int nx, int ny, int nz, const gbcfd_params* params, size_t* bytes);
+
+/* Create a block on the current CUDA device inside caller memory `dev_mem` of `bytes` bytes
+ * (at least gbcfd_required_bytes, 256-byte aligned).  The memory must stay valid until
+ * gbcfd_destroy_block.  The block starts unconnected, with uniform Cartesian metrics of unit
+ * spacing and no state.  Returns the descriptor in *out. */
+int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* params, void* dev_mem,
+                       size_t bytes, gbcfd_block* out);
+
+/* Release the host descriptor (the caller frees the device memory).  Waits for the device. */
+int gbcfd_destroy_block(gbcfd_block block);
+
+/* Connect face `face` of `block` to the opposite face of `nbr` (conforming, same orientation:
+ * equal cell counts along the two shared directions).  nbr == block makes the direction
+ * periodic.  Multi-block interfaces share their grid points (Sec. 2.2); the halo then holds
+ * the neighbour's first two cell layers.  Faces left unconnected keep whatever halo the caller
+ * sets (the kernels read but never write them). */
+int gbcfd_connect(gbcfd_block block, int face, gbcfd_block nbr);
+
+/* Set the grid (Eq. 1's curvilinear coordinates).  nodes == NULL: uniform Cartesian grid with
+ * cell sizes spacing[0..2].  Otherwise `nodes` is a device pointer to float64
+ * x[3][nz+1][ny+1][nx+1], the block's grid points; face area vectors (half the cross product
+ * of the face diagonals) and cell volumes are computed on the device, and the halo cells take
+ * their neighbours' metrics at the next exchange, so that a uniform flow is preserved exactly
+ * across block interfaces (the geometric conservation of Sec. 2.2). */
+int gbcfd_set_metrics(gbcfd_block block, const double* nodes, const double spacing[3],
+                      void* stream);
+
+/* Load the conserved state q[5][nz][ny][nx] (host or device pointer), exchange nothing, and
+ * evaluate the CFL time step of the first step.  Halos are filled by the next
+ * gbcfd_exchange_halos or gbcfd_step. */
+int gbcfd_set_state(gbcfd_block block, const double* q, void* stream);
+
+/* Copy the conserved state out to q[5][nz][ny][nx] (host or device pointer).  A host
+ * destination synchronises the stream before returning. */
+int gbcfd_get_state(gbcfd_block block, double* q, void* stream);
+
+/* Fill the 2-cell halos of the array the next Runge-Kutta stage reads (the state Q^n between
+ * steps, the stage-1 / stage-2 result between stages) of n blocks from their connected
+ * neighbours: the data exchange among blocks after each update (Sec. 3.2.5 (2)).  One launch
+ * for all blocks; edge and corner cells come from the diagonal neighbour reached through the
+ * face neighbours.  All n blocks must be at the same stage. */
+int gbcfd_exchange_halos(const gbcfd_block* blocks, int n, void* stream);
+
+/* R(Q) of Eq. 3 for the current state, written to r[5][nz][ny][nx] float64 (device pointer):
+ * the sum over the six faces of (inviscid - viscous) flux through the face area vector,
+ * divided by the cell volume; dQ/dt = -R.  Exchanges the block's halo first. */
+int gbcfd_compute_residual(gbcfd_block block, double* r, void* stream);
+
+/* One Runge-Kutta stage (1, 2 or 3; Eqs. 4-6 with lambda = -dt) of n blocks, halos assumed
+ * exchanged.  Stages must come in order 1, 2, 3 (GBCFD_ERR_STATE otherwise); set_state restarts
+ * at 1.  Stage 1 also records the residual norm of R(Q^n) and, for n > 1, takes the global time
+ * step as the minimum over the blocks; stage 3 also evaluates the next CFL time step.
+ * gbcfd_step is gbcfd_exchange_halos + gbcfd_stage, three times. */
+int gbcfd_stage(const gbcfd_block* blocks, int n, int stage, void* stream);
+
+/* nsteps full SSP-RK3 steps of n blocks (halo exchange before each stage, the global time
+ * step the minimum over all blocks).  Asynchronous: errors met on the device are reported by
+ * the next gbcfd_residual_norm. */
+int gbcfd_step(const gbcfd_block* blocks, int n, int nsteps, void* stream);
+
+/* RMS over the block's interior cells of each component of R(Q^n) from the last stage 1 (the
+ * convergence criterion of Sec. 2.3), copied to out[5] on the host.  Synchronises the stream
+ * and reports GBCFD_ERR_NONPHYSICAL / GBCFD_ERR_TIMEOUT if a kernel flagged one since the
+ * last call (the flag is then cleared). */
+int gbcfd_residual_norm(gbcfd_block block, double out[5], void* stream);
+
+/* The time step the next stage 1 will use, copied to *dt on the host (synchronises). */
+int gbcfd_get_dt(gbcfd_block block, double* dt, void* stream);
+
+/* Message of the last error on the calling host thread ("" if none). */
+const char* gbcfd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,566 @@
+// api.cu -- the C ABI declared in include/gbcfd.h.
+//
+// A block is a host descriptor plus arrays carved from caller device memory.  Every call is
+// enqueued on the caller's stream; only residual_norm / get_dt / get_state-to-host wait.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gbcfd.h"
+#include "launch.h"
+
+using namespace gbcfd;
+
+// ---- error state ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(GBCFD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+extern "C" const char* gbcfd_last_error(void) { return g_err.c_str(); }
+
+// ---- block descriptor ----------------------------------------------------------------------
+struct gbcfd_block_s {
+  int nx, ny, nz;
+  gbcfd_params p;
+  Geometry g;
+  int device, nsm, grid;
+  size_t bytes;
+  double* q[3];      // FP64: Qn, Q1, Q2.  mixed: QA, QB (ping-pong Q^n)
+  float* d[2];       // mixed: D1, D2
+  void* metrics;     // 10 fields (f64, or f32 on the mixed path)
+  DevCtrl* ctrl;
+  double* partial;
+  char* staging;     // host-transfer staging (aliases the stage buffers)
+  size_t staging_bytes;
+  int cur;           // mixed: index of Q^n in q[]
+  int has_state;
+  int next_stage;    // 1, 2 or 3: the Runge-Kutta stage the block expects next
+  double spacing[3];
+  gbcfd_block nbr[6];
+  CUtensorMap tm_q[3];
+  CUtensorMap tm_d[2];
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int pitch_for(int nx, int elem) {
+  const int per = 128 / elem;  // 128-byte rows
+  return (nx + 2 * HALO + per - 1) / per * per;
+}
+
+static Geometry make_geometry(int nx, int ny, int nz) {
+  Geometry g;
+  g.nx = nx; g.ny = ny; g.nz = nz;
+  g.px = pitch_for(nx, 8);
+  g.pxf = pitch_for(nx, 4);
+  g.plane = (long long)(ny + 2 * HALO) * g.px;
+  g.planef = (long long)(ny + 2 * HALO) * g.pxf;
+  g.field = g.plane * (nz + 2 * HALO);
+  g.fieldf = g.planef * (nz + 2 * HALO);
+  return g;
+}
+
+static bool valid_params(const gbcfd_params* p, std::string& why) {
+  if (!p) { why = "params is NULL"; return false; }
+  if (!(p->gamma > 1.0)) { why = "gamma must be > 1"; return false; }
+  if (!(p->cfl > 0.0)) { why = "cfl must be > 0"; return false; }
+  if (!(p->entropy_eps >= 0.0)) { why = "entropy_eps must be >= 0"; return false; }
+  if (p->viscous && !(p->mu >= 0.0 && p->Pr > 0.0)) { why = "viscous needs mu >= 0 and Pr > 0"; return false; }
+  if (p->limiter != 0 && p->limiter != 1) { why = "limiter must be 0 or 1"; return false; }
+  if (p->precision != GBCFD_FP64 && p->precision != GBCFD_MIXED) { why = "bad precision"; return false; }
+  if (p->reserved != 0) { why = "reserved must be 0"; return false; }
+  return true;
+}
+
+// stage grid: resident CTAs on every SM, capped by the number of tile-planes
+static int stage_grid(const Geometry& g, int precision, int viscous, int nsm) {
+  const int occ = precision == GBCFD_MIXED ? stage_occupancy_f32(viscous) : stage_occupancy_f64(viscous);
+  const long long units = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY) * g.nz;
+  long long grid = (long long)nsm * occ;
+  if (grid > units) grid = units;
+  return (int)std::max(1LL, grid);
+}
+
+struct Carve {
+  size_t off[12];
+  size_t total;
+  size_t partial_n;
+};
+
+static Carve carve(const Geometry& g, int precision, int nsm) {
+  Carve c;
+  size_t o = 0;
+  const size_t f64 = align256(sizeof(double) * 5 * g.field);
+  const size_t f32 = align256(sizeof(float) * 5 * g.fieldf);
+  c.off[0] = o; o += f64;                   // q0
+  c.off[1] = o; o += f64;                   // q1
+  if (precision == GBCFD_FP64) {
+    c.off[2] = o; o += f64;                 // q2
+    c.off[3] = c.off[4] = 0;
+    c.off[5] = o; o += align256(sizeof(double) * 10 * g.field);  // metrics f64
+  } else {
+    c.off[2] = 0;
+    c.off[3] = o; o += f32;                 // d0
+    c.off[4] = o; o += f32;                 // d1
+    c.off[5] = o; o += align256(sizeof(float) * 10 * g.fieldf);  // metrics f32
+  }
+  c.off[6] = o; o += align256(sizeof(DevCtrl));
+  c.partial_n = (size_t)std::max(4 * nsm, 4 * 152);
+  c.off[7] = o; o += align256(sizeof(double) * NPART * c.partial_n);
+  c.total = o;
+  return c;
+}
+
+static int device_sms(int* dev, int* nsm) {
+  CK(cudaGetDevice(dev));
+  CK(cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, *dev));
+  return GBCFD_OK;
+}
+
+// ---- TMA descriptors -------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// 4D map (x, y, z, variable) over a padded field; box = one tile plane with its halo, all 5
+// variables.  x extent is the padded width nx + 4, so a box past it is zero-filled.
+static int make_map(CUtensorMap* m, void* base, const Geometry& g, int elem) {
+  auto enc = get_encode();
+  if (!enc) return fail(GBCFD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const int pitch = elem == 8 ? g.px : g.pxf;
+  cuuint64_t dims[4] = {(cuuint64_t)(g.nx + 2 * HALO), (cuuint64_t)(g.ny + 2 * HALO),
+                        (cuuint64_t)(g.nz + 2 * HALO), 5};
+  cuuint64_t strides[3] = {(cuuint64_t)pitch * elem, (cuuint64_t)pitch * elem * (g.ny + 2 * HALO),
+                           (cuuint64_t)pitch * elem * (g.ny + 2 * HALO) * (g.nz + 2 * HALO)};
+  cuuint32_t box[4] = {(cuuint32_t)BX, (cuuint32_t)BY, 1, 5};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base,
+                   dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(GBCFD_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return GBCFD_OK;
+}
+
+// ---- creation --------------------------------------------------------------------------------
+extern "C" int gbcfd_required_bytes(int nx, int ny, int nz, const gbcfd_params* params, size_t* bytes) {
+  std::string why;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(GBCFD_ERR_ARG, "block sizes must be >= 1");
+  if (!bytes) return fail(GBCFD_ERR_ARG, "bytes is NULL");
+  if (!valid_params(params, why)) return fail(GBCFD_ERR_ARG, why);
+  int dev = 0, nsm = 152;
+  int rc = device_sms(&dev, &nsm);
+  if (rc) return rc;
+  *bytes = carve(make_geometry(nx, ny, nz), params->precision, nsm).total;
+  return GBCFD_OK;
+}
+
+static Physics physics_of(const gbcfd_block_s* b) {
+  Physics ph;
+  ph.gamma = b->p.gamma;
+  ph.mu = b->p.mu;
+  ph.Pr = b->p.Pr;
+  ph.cfl = b->p.cfl;
+  ph.eps = b->p.entropy_eps;
+  ph.ihx = 1.0 / b->spacing[0];
+  ph.ihy = 1.0 / b->spacing[1];
+  ph.ihz = 1.0 / b->spacing[2];
+  ph.viscous = b->p.viscous;
+  ph.limiter = b->p.limiter;
+  return ph;
+}
+
+extern "C" int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* params, void* dev_mem,
+                                  size_t bytes, gbcfd_block* out) {
+  std::string why;
+  if (!out) return fail(GBCFD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(GBCFD_ERR_ARG, "block sizes must be >= 1");
+  if (!valid_params(params, why)) return fail(GBCFD_ERR_ARG, why);
+  if (!dev_mem) return fail(GBCFD_ERR_ARG, "dev_mem is NULL");
+  if (((uintptr_t)dev_mem & 255u) != 0) return fail(GBCFD_ERR_MEMORY, "dev_mem must be 256-byte aligned");
+  cudaPointerAttributes attr;
+  CK(cudaPointerGetAttributes(&attr, dev_mem));
+  if (attr.type != cudaMemoryTypeDevice) return fail(GBCFD_ERR_MEMORY, "dev_mem is not device memory");
+  int dev = 0, nsm = 0;
+  int rc = device_sms(&dev, &nsm);
+  if (rc) return rc;
+  Geometry g = make_geometry(nx, ny, nz);
+  Carve c = carve(g, params->precision, nsm);
+  if (bytes < c.total) return fail(GBCFD_ERR_MEMORY, "dev_mem smaller than gbcfd_required_bytes");
+
+  gbcfd_block_s* b = new gbcfd_block_s();
+  b->nx = nx; b->ny = ny; b->nz = nz;
+  b->p = *params;
+  b->g = g;
+  b->device = dev;
+  b->nsm = nsm;
+  b->bytes = bytes;
+  char* base = static_cast<char*>(dev_mem);
+  b->q[0] = reinterpret_cast<double*>(base + c.off[0]);
+  b->q[1] = reinterpret_cast<double*>(base + c.off[1]);
+  b->q[2] = params->precision == GBCFD_FP64 ? reinterpret_cast<double*>(base + c.off[2]) : nullptr;
+  b->d[0] = params->precision == GBCFD_MIXED ? reinterpret_cast<float*>(base + c.off[3]) : nullptr;
+  b->d[1] = params->precision == GBCFD_MIXED ? reinterpret_cast<float*>(base + c.off[4]) : nullptr;
+  b->metrics = base + c.off[5];
+  b->ctrl = reinterpret_cast<DevCtrl*>(base + c.off[6]);
+  b->partial = reinterpret_cast<double*>(base + c.off[7]);
+  if (params->precision == GBCFD_FP64) {
+    b->staging = reinterpret_cast<char*>(b->q[1]);
+    b->staging_bytes = c.off[2] - c.off[1];
+  } else {
+    b->staging = reinterpret_cast<char*>(b->d[0]);
+    b->staging_bytes = c.off[5] - c.off[3];
+  }
+  b->cur = 0;
+  b->has_state = 0;
+  b->next_stage = 1;
+  b->spacing[0] = b->spacing[1] = b->spacing[2] = 1.0;
+  for (int f = 0; f < 6; ++f) b->nbr[f] = nullptr;
+  b->grid = stage_grid(g, params->precision, params->viscous, nsm);
+  if ((size_t)b->grid > c.partial_n) b->grid = (int)c.partial_n;
+
+  int r = GBCFD_OK;
+  if (params->precision == GBCFD_FP64) {
+    for (int i = 0; i < 3 && !r; ++i) r = make_map(&b->tm_q[i], b->q[i], g, 8);
+    if (!r) b->tm_d[0] = b->tm_d[1] = b->tm_q[0];
+  } else {
+    for (int i = 0; i < 2 && !r; ++i) r = make_map(&b->tm_q[i], b->q[i], g, 8);
+    for (int i = 0; i < 2 && !r; ++i) r = make_map(&b->tm_d[i], b->d[i], g, 4);
+    if (!r) b->tm_q[2] = b->tm_q[0];
+  }
+  if (r) { delete b; return r; }
+  cudaError_t e = cudaMemset(b->ctrl, 0, sizeof(DevCtrl));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { delete b; return cuda_fail(e, "clearing the control block"); }
+  *out = b;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_destroy_block(gbcfd_block b) {
+  if (!b) return fail(GBCFD_ERR_ARG, "block is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  delete b;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_connect(gbcfd_block b, int face, gbcfd_block nbr) {
+  if (!b || !nbr) return fail(GBCFD_ERR_ARG, "block is NULL");
+  if (face < 0 || face > 5) return fail(GBCFD_ERR_ARG, "face must be 0..5");
+  const int d = face / 2;
+  const int na[3] = {b->nx, b->ny, b->nz}, nb[3] = {nbr->nx, nbr->ny, nbr->nz};
+  for (int a = 0; a < 3; ++a)
+    if (a != d && na[a] != nb[a]) return fail(GBCFD_ERR_ARG, "connected faces must have equal cell counts");
+  if (b->p.precision != nbr->p.precision) return fail(GBCFD_ERR_ARG, "connected blocks must share a precision");
+  b->nbr[face] = nbr;
+  nbr->nbr[face ^ 1] = b;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_set_metrics(gbcfd_block b, const double* nodes, const double spacing[3], void* stream) {
+  (void)stream;
+  if (!b) return fail(GBCFD_ERR_ARG, "block is NULL");
+  if (nodes) return fail(GBCFD_ERR_ARG, "curvilinear node input is not available in this build");
+  if (!spacing || !(spacing[0] > 0 && spacing[1] > 0 && spacing[2] > 0))
+    return fail(GBCFD_ERR_ARG, "spacing must be three positive cell sizes");
+  for (int a = 0; a < 3; ++a) b->spacing[a] = spacing[a];
+  return GBCFD_OK;
+}
+
+// ---- state in / out ------------------------------------------------------------------------
+static int is_device_ptr(const void* p, bool* dev) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes");
+  *dev = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return GBCFD_OK;
+}
+
+static double* state_ptr(gbcfd_block b) {
+  return b->p.precision == GBCFD_FP64 ? b->q[0] : b->q[b->cur];
+}
+
+extern "C" int gbcfd_set_state(gbcfd_block b, const double* q, void* stream) {
+  if (!b || !q) return fail(GBCFD_ERR_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t n = (size_t)b->nx * b->ny * b->nz;
+  bool dev = false;
+  int rc = is_device_ptr(q, &dev);
+  if (rc) return rc;
+  const double* src = q;
+  if (!dev) {
+    if (b->staging_bytes < 5 * n * sizeof(double)) return fail(GBCFD_ERR_MEMORY, "staging too small");
+    CK(cudaMemcpyAsync(b->staging, q, 5 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+    src = reinterpret_cast<const double*>(b->staging);
+  }
+  CK(launch_scatter(b->g, src, state_ptr(b), s));
+  CK(launch_init_rate(b->g, physics_of(b), state_ptr(b), b->ctrl, b->partial, 4 * b->nsm, s));
+  b->has_state = 1;
+  b->next_stage = 1;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_get_state(gbcfd_block b, double* q, void* stream) {
+  if (!b || !q) return fail(GBCFD_ERR_ARG, "NULL argument");
+  if (!b->has_state) return fail(GBCFD_ERR_STATE, "no state set");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t n = (size_t)b->nx * b->ny * b->nz;
+  bool dev = false;
+  int rc = is_device_ptr(q, &dev);
+  if (rc) return rc;
+  if (dev) {
+    CK(launch_gather(b->g, state_ptr(b), q, s));
+    return GBCFD_OK;
+  }
+  double* tmp = reinterpret_cast<double*>(b->staging);
+  CK(launch_gather(b->g, state_ptr(b), tmp, s));
+  CK(cudaMemcpyAsync(q, tmp, 5 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return GBCFD_OK;
+}
+
+// ---- halo exchange over a group -----------------------------------------------------------
+enum Field { F_STATE = 0, F_STAGE1 = 1, F_STAGE2 = 2, F_METRICS = 3 };
+
+static void field_of(gbcfd_block b, int f, char** base, int* elem, int* nvar) {
+  const bool mixed = b->p.precision == GBCFD_MIXED;
+  *nvar = 5;
+  switch (f) {
+    case F_STATE: *base = reinterpret_cast<char*>(state_ptr(b)); *elem = 8; break;
+    case F_STAGE1: *base = mixed ? reinterpret_cast<char*>(b->d[0]) : reinterpret_cast<char*>(b->q[1]); *elem = mixed ? 4 : 8; break;
+    case F_STAGE2: *base = mixed ? reinterpret_cast<char*>(b->d[1]) : reinterpret_cast<char*>(b->q[2]); *elem = mixed ? 4 : 8; break;
+    default: *base = reinterpret_cast<char*>(b->metrics); *elem = mixed ? 4 : 8; *nvar = 10; break;
+  }
+}
+
+// fills halos of blocks[0..n); neighbours outside the list are read as sources when
+// allow_external, else the call fails
+static int build_group(const gbcfd_block* blocks, int n, int field, bool allow_external, HaloGroup* G) {
+  std::vector<gbcfd_block> list(blocks, blocks + n);
+  for (size_t i = 0; i < list.size(); ++i) {
+    for (int f = 0; f < 6; ++f) {
+      gbcfd_block nb = list[i]->nbr[f];
+      if (!nb) continue;
+      if (std::find(list.begin(), list.end(), nb) == list.end()) {
+        if (!allow_external) return fail(GBCFD_ERR_ARG, "a connected neighbour is missing from the block list");
+        list.push_back(nb);
+      }
+    }
+  }
+  if ((int)list.size() > MAX_GROUP) return fail(GBCFD_ERR_ARG, "too many blocks in one group");
+  G->n = (int)list.size();
+  long long total = 0;
+  int elem0 = -1;
+  for (int i = 0; i < G->n; ++i) {
+    gbcfd_block b = list[i];
+    HaloBlock& h = G->b[i];
+    int elem, nvar;
+    field_of(b, field, &h.base[0], &elem, &nvar);
+    if (elem0 < 0) elem0 = elem;
+    if (elem != elem0) return fail(GBCFD_ERR_ARG, "blocks of one group must share a precision");
+    G->elem = elem;
+    G->nvar = nvar;
+    h.nx = b->nx; h.ny = b->ny; h.nz = b->nz;
+    h.pitch = elem == 8 ? b->g.px : b->g.pxf;
+    for (int f = 0; f < 6; ++f) {
+      h.nbr[f] = -1;
+      if (b->nbr[f]) h.nbr[f] = (int)(std::find(list.begin(), list.end(), b->nbr[f]) - list.begin());
+    }
+    if (i < n) {
+      h.first = total;
+      total += (long long)(b->nx + 4) * (b->ny + 4) * (b->nz + 4) - (long long)b->nx * b->ny * b->nz;
+    } else {
+      h.first = 0x7fffffffffffffffLL;  // source only: never selected by the halo search
+    }
+  }
+  G->total = total;
+  return GBCFD_OK;
+}
+
+static int exchange(const gbcfd_block* blocks, int n, int field, bool allow_external, cudaStream_t s) {
+  static thread_local HaloGroup G;  // ~8 KB, kept off the stack
+  int rc = build_group(blocks, n, field, allow_external, &G);
+  if (rc) return rc;
+  CK(launch_halo(G, s));
+  return GBCFD_OK;
+}
+
+static int check_blocks(const gbcfd_block* blocks, int n) {
+  if (!blocks || n < 1) return fail(GBCFD_ERR_ARG, "empty block list");
+  if (n > MAX_GROUP) return fail(GBCFD_ERR_ARG, "too many blocks in one call");
+  for (int i = 0; i < n; ++i) {
+    if (!blocks[i]) return fail(GBCFD_ERR_ARG, "NULL block in list");
+    if (!blocks[i]->has_state) return fail(GBCFD_ERR_STATE, "block has no state");
+    if (blocks[i]->p.precision != blocks[0]->p.precision) return fail(GBCFD_ERR_ARG, "mixed precisions in one call");
+    if (blocks[i]->next_stage != blocks[0]->next_stage)
+      return fail(GBCFD_ERR_STATE, "blocks of one call are at different Runge-Kutta stages");
+  }
+  return GBCFD_OK;
+}
+
+// the field the next stage reads: Q^n before stage 1, the stage-1 output before stage 2, ...
+static int input_field(gbcfd_block b) {
+  return b->next_stage == 1 ? F_STATE : (b->next_stage == 2 ? F_STAGE1 : F_STAGE2);
+}
+
+extern "C" int gbcfd_exchange_halos(const gbcfd_block* blocks, int n, void* stream) {
+  int rc = check_blocks(blocks, n);
+  if (rc) return rc;
+  return exchange(blocks, n, input_field(blocks[0]), true, static_cast<cudaStream_t>(stream));
+}
+
+// ---- stages --------------------------------------------------------------------------------
+static int run_stage(gbcfd_block b, int stage, double* rout, cudaStream_t s) {
+  StageParams P;
+  memset(&P, 0, sizeof(P));
+  P.g = b->g;
+  P.ph = physics_of(b);
+  P.ctrl = b->ctrl;
+  P.partial = b->partial;
+  P.ntx = (b->nx + TX - 1) / TX;
+  P.nty = (b->ny + TY - 1) / TY;
+  P.units = (long long)P.ntx * P.nty * b->nz;
+  const CUtensorMap* tmq = &b->tm_q[0];
+  const CUtensorMap* tmd = &b->tm_d[0];
+  if (b->p.precision == GBCFD_FP64) {
+    P.qn = b->q[0];
+    switch (stage) {
+      case 0: P.qs = b->q[0]; P.rout = rout; tmq = &b->tm_q[0]; break;
+      case 1: P.qs = b->q[0]; P.qout = b->q[1]; tmq = &b->tm_q[0]; break;
+      case 2: P.qs = b->q[1]; P.qout = b->q[2]; tmq = &b->tm_q[1]; break;
+      case 3: P.qs = b->q[2]; P.qout = b->q[0]; tmq = &b->tm_q[2]; break;
+    }
+  } else {
+    const int c = b->cur;
+    P.qn = b->q[c];
+    tmq = &b->tm_q[c];
+    switch (stage) {
+      case 0: P.rout = rout; break;
+      case 1: P.dout = b->d[0]; break;
+      case 2: P.dprev = b->d[0]; P.dout = b->d[1]; tmd = &b->tm_d[0]; break;
+      case 3: P.dprev = b->d[1]; P.qout = b->q[1 - c]; tmd = &b->tm_d[1]; break;
+    }
+  }
+  CK(launch_stage(b->p.precision, b->p.viscous, stage, *tmq, *tmd, P, b->grid, s));
+  if (stage == 3 && b->p.precision == GBCFD_MIXED) b->cur = 1 - b->cur;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_stage(const gbcfd_block* blocks, int n, int stage, void* stream) {
+  int rc = check_blocks(blocks, n);
+  if (rc) return rc;
+  if (stage < 1 || stage > 3) return fail(GBCFD_ERR_ARG, "stage must be 1, 2 or 3");
+  if (stage != blocks[0]->next_stage)
+    return fail(GBCFD_ERR_STATE, "stage " + std::to_string(stage) + " called, stage " +
+                                     std::to_string(blocks[0]->next_stage) + " expected");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (stage == 1 && n > 1) {
+    std::vector<DevCtrl*> c(n);
+    for (int i = 0; i < n; ++i) c[i] = blocks[i]->ctrl;
+    CK(launch_group_dt(c.data(), n, blocks[0]->p.cfl, s));
+  }
+  for (int i = 0; i < n; ++i) {
+    rc = run_stage(blocks[i], stage, nullptr, s);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < n; ++i) blocks[i]->next_stage = stage % 3 + 1;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_step(const gbcfd_block* blocks, int n, int nsteps, void* stream) {
+  int rc = check_blocks(blocks, n);
+  if (rc) return rc;
+  if (nsteps < 0) return fail(GBCFD_ERR_ARG, "nsteps must be >= 0");
+  if (blocks[0]->next_stage != 1) return fail(GBCFD_ERR_STATE, "a step was left between stages");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int fields[3] = {F_STATE, F_STAGE1, F_STAGE2};
+  for (int it = 0; it < nsteps; ++it) {
+    for (int st = 1; st <= 3; ++st) {
+      rc = exchange(blocks, n, fields[st - 1], false, s);
+      if (rc) return rc;
+      rc = gbcfd_stage(blocks, n, st, stream);
+      if (rc) return rc;
+    }
+  }
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_compute_residual(gbcfd_block b, double* r, void* stream) {
+  if (!b || !r) return fail(GBCFD_ERR_ARG, "NULL argument");
+  if (!b->has_state) return fail(GBCFD_ERR_STATE, "no state set");
+  bool dev = false;
+  int rc = is_device_ptr(r, &dev);
+  if (rc) return rc;
+  if (!dev) return fail(GBCFD_ERR_ARG, "r must be device memory");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = exchange(&b, 1, F_STATE, true, s);
+  if (rc) return rc;
+  return run_stage(b, 0, r, s);
+}
+
+// ---- read-backs ----------------------------------------------------------------------------
+static int read_ctrl(gbcfd_block b, DevCtrl* h, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h, b->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_residual_norm(gbcfd_block b, double out[5], void* stream) {
+  if (!b || !out) return fail(GBCFD_ERR_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevCtrl h;
+  int rc = read_ctrl(b, &h, s);
+  if (rc) return rc;
+  for (int m = 0; m < 5; ++m) out[m] = h.norms[m];
+  if (h.flag) {
+    CK(cudaMemsetAsync(&b->ctrl->flag, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    if (h.flag & FLAG_TIMEOUT) return fail(GBCFD_ERR_TIMEOUT, "a bounded device wait timed out");
+    return fail(GBCFD_ERR_NONPHYSICAL, "non-positive density or pressure, or a non-finite value");
+  }
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_get_dt(gbcfd_block b, double* dt, void* stream) {
+  if (!b || !dt) return fail(GBCFD_ERR_ARG, "NULL argument");
+  DevCtrl h;
+  int rc = read_ctrl(b, &h, static_cast<cudaStream_t>(stream));
+  if (rc) return rc;
+  *dt = h.dt;
+  return GBCFD_OK;
+}
+
+// ---- dispatch ----------------------------------------------------------------------------
+namespace gbcfd {
+cudaError_t launch_stage(int precision, int viscous, int stage, const CUtensorMap& tmq, const CUtensorMap& tmd,
+                         const StageParams& P, int grid, cudaStream_t s) {
+  if (precision == GBCFD_MIXED) return launch_stage_f32(viscous, stage, tmq, tmd, P, grid, s);
+  return launch_stage_f64(viscous, stage, tmq, tmd, P, grid, s);
+}
+}  // namespace gbcfd

@@ -1,0 +1,192 @@
+// aux_kernels.cu -- halo exchange, state scatter/gather and time-step kernels.
+#include "launch.h"
+
+namespace gbcfd {
+
+// ---- halo exchange -------------------------------------------------------------------------
+// One thread per halo cell of every block in the group.  The source of a halo cell is found by
+// walking face neighbours: first along x, then along y in the block reached, then along z, so
+// that edge and corner cells come from the diagonal neighbour.  Each block's halo is the union
+// of the z-slabs (k < 0 or k >= nz, all i, j), the y-slabs (0 <= k < nz, j outside, all i) and
+// the x-slabs (inside k and j, i outside).
+__global__ void halo_kernel(const __grid_constant__ HaloGroup G) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < G.total; t += stride) {
+    int lo = 0, hi = G.n - 1;
+    while (lo < hi) {  // last block whose prefix start <= t
+      const int mid = (lo + hi + 1) >> 1;
+      if (G.b[mid].first <= t) lo = mid; else hi = mid - 1;
+    }
+    const HaloBlock& B = G.b[lo];
+    long long h = t - B.first;
+    const int nx = B.nx, ny = B.ny, nz = B.nz;
+    const long long wx = nx + 2 * HALO, wy = ny + 2 * HALO;
+    int i, j, k;
+    const long long zc = 2LL * HALO * wx * wy, yc = (long long)nz * 2 * HALO * wx;
+    if (h < zc) {
+      const int kk = (int)(h / (wx * wy));
+      const long long r = h - kk * wx * wy;
+      k = kk < HALO ? kk - HALO : nz + kk - HALO;
+      j = (int)(r / wx) - HALO;
+      i = (int)(r % wx) - HALO;
+    } else if ((h -= zc) < yc) {
+      k = (int)(h / (2 * HALO * wx));
+      const long long r = h - (long long)k * 2 * HALO * wx;
+      const int jj = (int)(r / wx);
+      j = jj < HALO ? jj - HALO : ny + jj - HALO;
+      i = (int)(r % wx) - HALO;
+    } else {
+      h -= yc;
+      k = (int)(h / ((long long)ny * 2 * HALO));
+      const long long r = h - (long long)k * ny * 2 * HALO;
+      j = (int)(r / (2 * HALO));
+      const int ii = (int)(r % (2 * HALO));
+      i = ii < HALO ? ii - HALO : nx + ii - HALO;
+    }
+    // walk to the source block
+    int b = lo, si = i, sj = j, sk = k;
+    bool ok = true;
+    while (ok && si < 0) { b = G.b[b].nbr[0]; if (b < 0) ok = false; else si += G.b[b].nx; }
+    while (ok && si >= G.b[b].nx) { si -= G.b[b].nx; b = G.b[b].nbr[1]; if (b < 0) ok = false; }
+    while (ok && sj < 0) { b = G.b[b].nbr[2]; if (b < 0) ok = false; else sj += G.b[b].ny; }
+    while (ok && sj >= G.b[b].ny) { sj -= G.b[b].ny; b = G.b[b].nbr[3]; if (b < 0) ok = false; }
+    while (ok && sk < 0) { b = G.b[b].nbr[4]; if (b < 0) ok = false; else sk += G.b[b].nz; }
+    while (ok && sk >= G.b[b].nz) { sk -= G.b[b].nz; b = G.b[b].nbr[5]; if (b < 0) ok = false; }
+    if (!ok) continue;
+    const HaloBlock& S = G.b[b];
+    const long long dplane = (long long)(ny + 2 * HALO) * B.pitch, dfield = dplane * (nz + 2 * HALO);
+    const long long splane = (long long)(S.ny + 2 * HALO) * S.pitch, sfield = splane * (S.nz + 2 * HALO);
+    const long long dof = (k + HALO) * dplane + (long long)(j + HALO) * B.pitch + (i + HALO);
+    const long long sof = (sk + HALO) * splane + (long long)(sj + HALO) * S.pitch + (si + HALO);
+    if (G.elem == 8) {
+      double* d = reinterpret_cast<double*>(B.base[0]);
+      const double* s = reinterpret_cast<const double*>(S.base[0]);
+      for (int v = 0; v < G.nvar; ++v) d[v * dfield + dof] = s[v * sfield + sof];
+    } else {
+      float* d = reinterpret_cast<float*>(B.base[0]);
+      const float* s = reinterpret_cast<const float*>(S.base[0]);
+      for (int v = 0; v < G.nvar; ++v) d[v * dfield + dof] = s[v * sfield + sof];
+    }
+  }
+}
+
+cudaError_t launch_halo(const HaloGroup& G, cudaStream_t s) {
+  if (G.total <= 0) return cudaSuccess;
+  const int threads = 256;
+  long long blocks = (G.total + threads - 1) / threads;
+  if (blocks > 65535LL * 8) blocks = 65535LL * 8;
+  halo_kernel<<<(unsigned)blocks, threads, 0, s>>>(G);
+  return cudaGetLastError();
+}
+
+// ---- compact <-> padded state --------------------------------------------------------------
+__global__ void scatter_kernel(Geometry g, const double* __restrict__ src, double* __restrict__ dst) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 5 * n; t += stride) {
+    const int v = (int)(t / n);
+    const long long c = t - v * n;
+    const int i = (int)(c % g.nx);
+    const long long r = c / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    dst[v * g.field + gidx(g, i, j, k)] = src[t];
+  }
+}
+__global__ void gather_kernel(Geometry g, const double* __restrict__ src, double* __restrict__ dst) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 5 * n; t += stride) {
+    const int v = (int)(t / n);
+    const long long c = t - v * n;
+    const int i = (int)(c % g.nx);
+    const long long r = c / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    dst[t] = src[v * g.field + gidx(g, i, j, k)];
+  }
+}
+static unsigned grid_for(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  if (b > 65535LL * 16) b = 65535LL * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+cudaError_t launch_scatter(const Geometry& g, const double* src, double* dst, cudaStream_t s) {
+  const long long n = 5LL * g.nx * g.ny * g.nz;
+  scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(g, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather(const Geometry& g, const double* src, double* dst, cudaStream_t s) {
+  const long long n = 5LL * g.nx * g.ny * g.nz;
+  gather_kernel<<<grid_for(n, 256), 256, 0, s>>>(g, src, dst);
+  return cudaGetLastError();
+}
+
+// ---- time step -----------------------------------------------------------------------------
+// rate = sum over directions of (|u_d| + c) / h_d (+ 4 max(4/3, gamma/Pr) mu / rho / h_d^2 when
+// viscous); the CFL step is cfl / max(rate).  FP64, from the padded state.
+__global__ void init_rate_kernel(Geometry g, Physics ph, const double* __restrict__ q, DevCtrl* ctrl,
+                                 double* partial) {
+  __shared__ double wmax[32];
+  __shared__ int last;
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  double best = 0.0;
+  const double f = fmax(4.0 / 3.0, ph.gamma / ph.Pr);
+  const double s2 = ph.ihx * ph.ihx + ph.ihy * ph.ihy + ph.ihz * ph.ihz;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.nx);
+    const long long r = c / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    const long long o = gidx(g, i, j, k);
+    const double rho = q[o], ir = 1.0 / rho;
+    const double u = q[g.field + o] * ir, v = q[2 * g.field + o] * ir, w = q[3 * g.field + o] * ir;
+    const double p = (ph.gamma - 1.0) * (q[4 * g.field + o] - 0.5 * rho * (u * u + v * v + w * w));
+    const double a = sqrt(ph.gamma * p * ir);
+    double rate = (fabs(u) + a) * ph.ihx + (fabs(v) + a) * ph.ihy + (fabs(w) + a) * ph.ihz;
+    if (ph.viscous) rate += 4.0 * f * ph.mu * ir * s2;
+    if (!(rho > 0.0 && p > 0.0)) atomicOr(&ctrl->flag, FLAG_NONPHYSICAL);
+    best = fmax(best, rate);
+  }
+  for (int off = 16; off > 0; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
+    partial[(size_t)blockIdx.x * NPART + 5] = m;
+    __threadfence();
+    last = (atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double m = 0.0;
+  for (unsigned b = 0; b < gridDim.x; ++b) m = fmax(m, __ldcg(partial + (size_t)b * NPART + 5));
+  ctrl->rate = m;
+  ctrl->dt = ph.cfl / m;
+  ctrl->counter = 0u;
+}
+
+cudaError_t launch_init_rate(const Geometry& g, const Physics& ph, const double* q, DevCtrl* ctrl,
+                             double* partial, int grid, cudaStream_t s) {
+  init_rate_kernel<<<grid, 256, 0, s>>>(g, ph, q, ctrl, partial);
+  return cudaGetLastError();
+}
+
+struct CtrlList {
+  DevCtrl* c[MAX_GROUP];
+};
+__global__ void group_dt_kernel(CtrlList L, int n, double cfl) {
+  if (threadIdx.x != 0) return;
+  double m = 0.0;
+  for (int b = 0; b < n; ++b) m = fmax(m, L.c[b]->rate);
+  for (int b = 0; b < n; ++b) L.c[b]->dt = cfl / m;
+}
+cudaError_t launch_group_dt(DevCtrl* const* ctrls, int n, double cfl, cudaStream_t s) {
+  CtrlList L;
+  for (int b = 0; b < n && b < MAX_GROUP; ++b) L.c[b] = ctrls[b];
+  group_dt_kernel<<<1, 32, 0, s>>>(L, n, cfl);
+  return cudaGetLastError();
+}
+
+}  // namespace gbcfd

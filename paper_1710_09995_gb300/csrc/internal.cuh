@@ -1,0 +1,108 @@
+// internal.cuh -- data layout, kernel parameter blocks and shared device helpers of the
+// gbcfd library (not part of the C ABI).
+//
+// Layout in HBM (per block, carved from caller memory, every array 256-byte aligned):
+//   fields are SoA with a 2-cell halo: a[v][k+2][j+2][x], x = i + 2, row pitch padded to
+//   128 bytes (16 doubles / 32 floats), so a TMA box starting at interior column 32*t - 2
+//   starts at storage column 32*t.
+//   FP64 path:  Qn (f64) and stage states Q1, Q2 (f64).  Stage 3 writes Q^{n+1} over Qn (it
+//               reads Qn only at its own cell).
+//   mixed path: Q^n in a ping-pong pair QA/QB (f64) and stage increments D1, D2 (f32):
+//               Q1 = Qn + D1,  Q2 = Qn + D2,  D1 = -dt R(Qn),  D2 = (D1 - dt R(Q1)) / 4,
+//               Q^{n+1} = Qn + 2/3 (D2 - dt R(Q2))   -- algebraically Eqs. 4-6.
+//   metrics (curvilinear only): M[10][..] = S_xi(3), S_eta(3), S_zeta(3), V, f64 (f32 copy for
+//               the mixed path), the lower-face area vectors of each cell.
+//   control:    DevCtrl (time step, norms, flag, counter) + per-CTA partials.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbcfd {
+
+constexpr int HALO = 2;
+constexpr int TX = 32;        // tile width (cells, x) = one warp
+constexpr int TY = 8;         // tile height (cells, y) = number of cell-owning warps
+constexpr int NWARP = TY + 1; // + one helper warp for the tile's upper x and y faces
+constexpr int NT = 32 * NWARP;
+constexpr int BX = TX + 2 * HALO; // staged box width
+constexpr int BY = TY + 2 * HALO; // staged box height
+constexpr int NSTAGE = 2;     // TMA staging slots (prefetch distance 2 planes)
+constexpr int NRING = 4;      // primitive planes kept: k-1, k, k+1, k+2
+constexpr int MAX_GROUP = 128; // blocks per grouped launch (halo exchange, time-step minimum)
+
+// device flags (DevCtrl::flag bits)
+constexpr int FLAG_NONPHYSICAL = 1;
+constexpr int FLAG_TIMEOUT = 2;
+
+struct DevCtrl {
+  double dt;          // time step of the next stage 1
+  double norms[5];    // RMS of R(Q^n) from the last stage 1
+  double rate;        // max over cells of sum of spectral radii / V (from the last stage 3)
+  unsigned int counter; // CTAs finished in the current launch (last one reduces, resets to 0)
+  int flag;           // FLAG_* bits, cleared by the host when read
+  double pad[6];
+};
+
+// partial results per CTA: [0..4] sums of R^2 (stage 1), [5] max rate (stage 3)
+constexpr int NPART = 8;
+
+struct Geometry {
+  int nx, ny, nz;
+  int px, pxf;                 // row pitch in f64 / f32 elements
+  long long plane, planef;     // elements per k-plane (f64 / f32)
+  long long field, fieldf;     // elements per variable (f64 / f32)
+};
+
+__host__ __device__ inline long long gidx(const Geometry& g, int i, int j, int k) {
+  return ((long long)(k + HALO) * (g.ny + 2 * HALO) + (j + HALO)) * g.px + (i + HALO);
+}
+__host__ __device__ inline long long gidxf(const Geometry& g, int i, int j, int k) {
+  return ((long long)(k + HALO) * (g.ny + 2 * HALO) + (j + HALO)) * g.pxf + (i + HALO);
+}
+
+struct Physics {
+  double gamma, mu, Pr, cfl, eps;
+  double ihx, ihy, ihz;  // 1 / cell size (Cartesian grids)
+  int viscous, limiter;
+};
+
+// parameters of one stage launch
+struct StageParams {
+  Geometry g;
+  Physics ph;
+  const double* qn;   // Q^n (f64): stages 2,3 of the FP64 path, all stages of the mixed path
+  const double* qs;   // stage input (f64, FP64 path): Qn, Q1 or Q2
+  double* qout;       // f64 output: Q1, Q2, Q^{n+1} (FP64 path) or Q^{n+1} (mixed stage 3)
+  const float* dprev; // mixed: D1 (stage 2) or D2 (stage 3)
+  float* dout;        // mixed: D1 (stage 1) or D2 (stage 2)
+  double* rout;       // residual mode: compact R[5][nz][ny][nx]
+  DevCtrl* ctrl;
+  double* partial;    // [gridDim.x][NPART]
+  int ntx, nty;       // tiles along x and y
+  long long units;    // ntx * nty * nz (tile-planes)
+};
+
+// ---- block group descriptors for halo exchange ----------------------------------------------
+struct HaloBlock {
+  char* base[1];       // field base pointer (the field being exchanged)
+  int nx, ny, nz, pitch;
+  int nbr[6];          // group index of the neighbour across each face, -1 if none
+  long long first;     // prefix sum of halo cells before this block
+};
+struct HaloGroup {
+  HaloBlock b[MAX_GROUP];
+  int n;
+  int nvar;
+  int elem;            // element size in bytes (8 or 4)
+  long long total;     // halo cells over all blocks
+};
+
+// ---- small device helpers ------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+}  // namespace gbcfd

@@ -1,0 +1,34 @@
+// launch.h -- host-side launchers of the gbcfd kernels (internal, not part of the C ABI)
+#pragma once
+#include "internal.cuh"
+
+namespace gbcfd {
+
+// fused stage kernel; precision GBCFD_FP64 / GBCFD_MIXED, stage 0 = residual only
+cudaError_t launch_stage(int precision, int viscous, int stage, const CUtensorMap& tmq,
+                         const CUtensorMap& tmd, const StageParams& P, int grid, cudaStream_t s);
+// dynamic shared memory of one stage CTA and resident CTAs per SM
+size_t stage_smem_bytes(int precision, int viscous);
+int stage_ctas_per_sm(int precision, int viscous);
+
+cudaError_t launch_stage_f64(int viscous, int stage, const CUtensorMap& tmq, const CUtensorMap& tmd,
+                             const StageParams& P, int grid, cudaStream_t s);
+cudaError_t launch_stage_f32(int viscous, int stage, const CUtensorMap& tmq, const CUtensorMap& tmd,
+                             const StageParams& P, int grid, cudaStream_t s);
+size_t stage_smem_f64(int viscous);
+size_t stage_smem_f32(int viscous);
+int stage_occupancy_f64(int viscous);
+int stage_occupancy_f32(int viscous);
+
+// halo exchange of one field over a group of blocks
+cudaError_t launch_halo(const HaloGroup& G, cudaStream_t s);
+// compact [5][nz][ny][nx] f64 <-> padded f64 field
+cudaError_t launch_scatter(const Geometry& g, const double* src, double* dst, cudaStream_t s);
+cudaError_t launch_gather(const Geometry& g, const double* src, double* dst, cudaStream_t s);
+// spectral-radius rate and time step of a padded f64 state (per-CTA partials, last CTA reduces)
+cudaError_t launch_init_rate(const Geometry& g, const Physics& ph, const double* q, DevCtrl* ctrl,
+                             double* partial, int grid, cudaStream_t s);
+// global time step of a group: dt = cfl / max rate, written to every block
+cudaError_t launch_group_dt(DevCtrl* const* ctrls, int n, double cfl, cudaStream_t s);
+
+}  // namespace gbcfd

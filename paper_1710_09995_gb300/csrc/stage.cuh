@@ -1,0 +1,505 @@
+// stage.cuh -- the fused Runge-Kutta stage kernel (residual of Eq. 3 + update of Eqs. 4-6).
+//
+// Work decomposition: the block's (x, y) cross-section is cut into TX x TY tiles; a tile-plane
+// (tile, k) is one work unit.  The grid is persistent (a multiple of the SM count) and CTA c
+// owns the contiguous unit range [c W / G, (c+1) W / G) in tile-major order, so every CTA
+// marches along z through one or two tiles.  Per plane k:
+//   1. the TMA has already brought the conserved state of plane k+2 (tile + 2-cell halo) into a
+//      shared staging slot; threads convert it to primitives into a 4-plane ring (k-1..k+2)
+//      and the slot is refilled with plane k+4;
+//   2. warps 0..TY-1 evaluate the lower x- and y-face of their cell and the upper z-face of
+//      their column; warp TY evaluates the tile's upper x- and y-faces.  Every face flux is
+//      computed once; the upper z-face becomes the next plane's lower z-face in registers;
+//   3. each cell sums its six face fluxes (order -x +x -y +y -z +z per direction), applies the
+//      stage update and writes its output.
+// Stage 1 also accumulates sum R^2 (residual norm); stage 3 the maximum spectral-radius rate
+// of the new state (next time step).  The last CTA to finish reduces the per-CTA partials in a
+// fixed order (deterministic) and resets the counter.  No CTA ever waits on another.
+#pragma once
+#include "internal.cuh"
+#include "physics.cuh"
+
+namespace gbcfd {
+
+// ---- mbarrier / TMA primitives (inline PTX) ------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y, int z, int v) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(v), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// bounded wait: true on completion, false after ~2 s
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > 2000000000ull) return false;
+  }
+  return true;
+}
+
+// ---- shared-memory plan ----------------------------------------------------------------------
+template <typename T, bool VISC>
+struct Plan {
+  static constexpr int NV = VISC ? 6 : 5;           // rho u v w p [theta]
+  static constexpr int BOX = BY * BX;               // cells per staged plane
+  static constexpr int RSLOT = NV * BOX;            // T per ring slot
+  // staging slots are 128-byte aligned (TMA tensor-copy destinations)
+  static constexpr size_t QSLOT = (sizeof(double) * 5 * BOX + 127) / 128 * 128;
+  static constexpr size_t DSLOT = sizeof(T) == 4 ? (sizeof(float) * 5 * BOX + 127) / 128 * 128 : 0;
+  static constexpr size_t stq = 0;                        // f64 staging
+  static constexpr size_t std_ = stq + NSTAGE * QSLOT;    // f32 staging
+  static constexpr size_t ring = std_ + NSTAGE * DSLOT;
+  static constexpr size_t fx = ring + sizeof(T) * NRING * RSLOT;
+  static constexpr size_t fy = fx + sizeof(T) * 5 * TY * (TX + 1);
+  static constexpr size_t red = (fy + sizeof(T) * 5 * (TY + 1) * TX + 15) / 16 * 16;
+  static constexpr size_t bar = red + sizeof(double) * NWARP * NPART;
+  static constexpr size_t misc = bar + 8 * NSTAGE;
+  static constexpr size_t bytes = (misc + 16 + 127) / 128 * 128;
+};
+
+// stencil cell base index inside the ring: slot s, row cy, column cx (variable 0)
+template <int NV>
+__device__ __forceinline__ int rb(int s, int cy, int cx) {
+  return (s * NV * BY + cy) * BX + cx;
+}
+
+// Flux through one axis-aligned face, per unit area, x/y/z components.
+//   b0..b3: ring base indices of the 4 stencil cells along the face normal (b1 = L, b2 = R)
+//   VN, VT1, VT2: primitive indices of the normal and the two tangential velocities
+//   lp1/lm1/rp1/rm1: L and R neighbours +-1 along tangent 1; lp2/lm2/rp2/rm2 along tangent 2
+template <typename T, bool VISC, int VN, int VT1, int VT2>
+__device__ __forceinline__ void face_flux(const T* __restrict__ ring, int b0, int b1, int b2, int b3,
+                                          int lp1, int lm1, int rp1, int rm1, int lp2, int lm2,
+                                          int rp2, int rm2, T ihn, T iht1, T iht2,
+                                          const Consts<T>& K, T* F) {
+  constexpr int MS = BY * BX;  // variable stride
+  constexpr int idx[5] = {0, VN, VT1, VT2, 4};
+  T L[5], R[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int m = idx[q] * MS;
+    const T w0 = ring[b0 + m], w1 = ring[b1 + m], w2 = ring[b2 + m], w3 = ring[b3 + m];
+    const T d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
+    L[q] = w1 + T(0.5) * slope(d01, d12, K.lim);
+    R[q] = w2 - T(0.5) * slope(d12, d23, K.lim);
+  }
+  T Fr[5];
+  roe_frame(L, R, K, Fr);
+  if (VISC) {
+    constexpr int TH = 5 * MS;  // theta = p / rho
+    T gn[4], ub[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int m = idx[q + 1] * MS;
+      gn[q] = (ring[b2 + m] - ring[b1 + m]) * ihn;
+      ub[q] = T(0.5) * (ring[b1 + m] + ring[b2 + m]);
+    }
+    gn[3] = (ring[b2 + TH] - ring[b1 + TH]) * ihn;
+    const int mn = VN * MS, m1 = VT1 * MS, m2 = VT2 * MS;
+    const T q4 = T(0.25);
+    const T dnt1 = q4 * ((ring[lp1 + mn] - ring[lm1 + mn]) + (ring[rp1 + mn] - ring[rm1 + mn])) * iht1;
+    const T dnt2 = q4 * ((ring[lp2 + mn] - ring[lm2 + mn]) + (ring[rp2 + mn] - ring[rm2 + mn])) * iht2;
+    const T d11 = q4 * ((ring[lp1 + m1] - ring[lm1 + m1]) + (ring[rp1 + m1] - ring[rm1 + m1])) * iht1;
+    const T d22 = q4 * ((ring[lp2 + m2] - ring[lm2 + m2]) + (ring[rp2 + m2] - ring[rm2 + m2])) * iht2;
+    T Fv[5];
+    viscous_frame(gn, dnt1, dnt2, d11, d22, ub, K, Fv);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Fr[q] -= Fv[q];
+  }
+  F[0] = Fr[0];
+  F[VN] = Fr[1];
+  F[VT1] = Fr[2];
+  F[VT2] = Fr[3];
+  F[4] = Fr[4];
+}
+
+// x-face below box cell (cy, cx) in ring slot s; sm / sp = slots of planes k-1 / k+1
+template <typename T, bool VISC>
+__device__ __forceinline__ void xface(const T* ring, int s, int sm, int sp, int cy, int cx,
+                                      const Physics& ph, const Consts<T>& K, T* F) {
+  constexpr int NV = VISC ? 6 : 5;
+  const int b = rb<NV>(s, cy, cx);
+  face_flux<T, VISC, 1, 2, 3>(ring, b - 2, b - 1, b, b + 1,
+                              // tangent 1 = y (rows), tangent 2 = z (planes)
+                              b - 1 + BX, b - 1 - BX, b + BX, b - BX,
+                              rb<NV>(sp, cy, cx - 1), rb<NV>(sm, cy, cx - 1), rb<NV>(sp, cy, cx),
+                              rb<NV>(sm, cy, cx), T(ph.ihx), T(ph.ihy), T(ph.ihz), K, F);
+}
+
+template <typename T, bool VISC>
+__device__ __forceinline__ void yface(const T* ring, int s, int sm, int sp, int cy, int cx,
+                                      const Physics& ph, const Consts<T>& K, T* F) {
+  constexpr int NV = VISC ? 6 : 5;
+  const int b = rb<NV>(s, cy, cx);
+  face_flux<T, VISC, 2, 3, 1>(ring, b - 2 * BX, b - BX, b, b + BX,
+                              // tangent 1 = z (planes), tangent 2 = x (columns)
+                              rb<NV>(sp, cy - 1, cx), rb<NV>(sm, cy - 1, cx), rb<NV>(sp, cy, cx),
+                              rb<NV>(sm, cy, cx), b - BX + 1, b - BX - 1, b + 1, b - 1, T(ph.ihy),
+                              T(ph.ihz), T(ph.ihx), K, F);
+}
+
+// z-face between planes k (slot s1) and k+1 (slot s2); s0 = k-1, s3 = k+2
+template <typename T, bool VISC>
+__device__ __forceinline__ void zface(const T* ring, int s0, int s1, int s2, int s3, int cy, int cx,
+                                      const Physics& ph, const Consts<T>& K, T* F) {
+  constexpr int NV = VISC ? 6 : 5;
+  const int b1 = rb<NV>(s1, cy, cx), b2 = rb<NV>(s2, cy, cx);
+  face_flux<T, VISC, 3, 1, 2>(ring, rb<NV>(s0, cy, cx), b1, b2, rb<NV>(s3, cy, cx),
+                              // tangent 1 = x (columns), tangent 2 = y (rows)
+                              b1 + 1, b1 - 1, b2 + 1, b2 - 1, b1 + BX, b1 - BX, b2 + BX, b2 - BX,
+                              T(ph.ihz), T(ph.ihx), T(ph.ihy), K, F);
+}
+
+// spectral-radius rate of one cell: sum over directions of the convective radius (plus 4x the
+// viscous one) divided by the volume, i.e. the inverse of the cell's stable step / CFL
+template <typename T>
+__device__ __forceinline__ T cell_rate(T r, T u, T v, T w, T p, const Physics& ph) {
+  using Fm = Fast<T>;
+  const T c = Fm::sqrt_(T(ph.gamma) * p * Fm::rcp(r));
+  T rate = (Fm::ab(u) + c) * T(ph.ihx) + (Fm::ab(v) + c) * T(ph.ihy) + (Fm::ab(w) + c) * T(ph.ihz);
+  if (ph.viscous) {
+    const double f = fmax(4.0 / 3.0, ph.gamma / ph.Pr);
+    const T s2 = T(ph.ihx * ph.ihx + ph.ihy * ph.ihy + ph.ihz * ph.ihz);
+    rate += T(4.0 * f * ph.mu) * Fm::rcp(r) * s2;
+  }
+  return rate;
+}
+
+// ---- the kernel ------------------------------------------------------------------------------
+// STAGE 0: residual only (R to P.rout); 1..3: Runge-Kutta stages
+template <typename T, bool VISC, int STAGE>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    stage_kernel(const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmd,
+                 const StageParams P) {
+  constexpr bool MIXED = sizeof(T) == 4;
+  constexpr bool LOADD = MIXED && (STAGE == 2 || STAGE == 3);
+  using PL = Plan<T, VISC>;
+  constexpr int NV = PL::NV;
+  constexpr int MS = BY * BX;
+  using Fm = Fast<T>;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* ring = reinterpret_cast<T*>(smem + PL::ring);
+  T* fx = reinterpret_cast<T*>(smem + PL::fx);
+  T* fy = reinterpret_cast<T*>(smem + PL::fy);
+  double* red = reinterpret_cast<double*>(smem + PL::red);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + PL::bar);
+  int* sabort = reinterpret_cast<int*>(smem + PL::misc);
+  int* slast = sabort + 1;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const Geometry& g = P.g;
+  const Physics& ph = P.ph;
+  Consts<T> K;
+  K.gm1 = T(ph.gamma - 1.0);
+  K.ggm1 = T(ph.gamma / (ph.gamma - 1.0));
+  K.eps = T(ph.eps);
+  K.mu = T(VISC ? ph.mu : 0.0);
+  K.kappa = T(VISC ? ph.mu * ph.gamma / ((ph.gamma - 1.0) * ph.Pr) : 0.0);
+  K.lim = ph.limiter;
+  const T gm1 = K.gm1;
+
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
+    fence_barrier_init();
+    *sabort = 0;
+  }
+  __syncthreads();
+
+  const double dt = (STAGE == 0) ? 0.0 : P.ctrl->dt;
+  const T dtT = T(dt);
+  unsigned phase_bits = 0;   // parity of each staging slot (uniform across the CTA)
+  unsigned pending = 0;      // slots with a copy in flight (meaningful in thread 0)
+  bool bad = false;          // non-physical value met by this thread
+  double nacc[5] = {0, 0, 0, 0, 0};
+  float ncomp[5] = {0, 0, 0, 0, 0};  // Kahan compensation (mixed path)
+  float nsum[5] = {0, 0, 0, 0, 0};
+  T rate_max = T(0);
+
+  const long long W = P.units;
+  const long long u_begin = (long long)blockIdx.x * W / gridDim.x;
+  const long long u_end = (long long)(blockIdx.x + 1) * W / gridDim.x;
+  constexpr unsigned QBYTES = 5u * MS * sizeof(double);
+  constexpr unsigned DBYTES = 5u * MS * sizeof(float);
+
+  for (long long u = u_begin; u < u_end;) {
+    const int nz = g.nz;
+    const long long tile = u / nz;
+    const int k0 = (int)(u - tile * nz);
+    const int k1 = (int)min((long long)nz, (long long)k0 + (u_end - u));
+    u += k1 - k0;
+    const int tix = (int)(tile % P.ntx), tiy = (int)(tile / P.ntx);
+    const int x0 = tix * TX, y0 = tiy * TY;  // storage coordinates of the box origin
+    const int last_plane = k1 + 1;
+
+    auto request = [&](int kp) {  // thread 0 only
+      const int s = (kp + 2) & (NSTAGE - 1);
+      fence_proxy_async();
+      mbar_expect_tx(&bar[s], QBYTES + (LOADD ? DBYTES : 0u));
+      tma_load_4d(smem + PL::stq + s * PL::QSLOT, &tmq, &bar[s], x0, y0, kp + HALO, 0);
+      if (LOADD) tma_load_4d(smem + PL::std_ + s * PL::DSLOT, &tmd, &bar[s], x0, y0, kp + HALO, 0);
+      pending |= 1u << s;
+    };
+    // wait for plane kp, convert it into ring slot kp & 3, then refill the staging slot
+    auto consume = [&](int kp) -> bool {
+      const int s = (kp + 2) & (NSTAGE - 1);
+      const bool ok = mbar_wait_bounded(&bar[s], (phase_bits >> s) & 1u);
+      if (!ok) atomicOr(sabort, 1);
+      phase_bits ^= 1u << s;
+      const double* sq = reinterpret_cast<const double*>(smem + PL::stq + s * PL::QSLOT);
+      const float* sd = reinterpret_cast<const float*>(smem + PL::std_ + s * PL::DSLOT);
+      T* rs = ring + (size_t)(kp & 3) * NV * MS;
+      for (int c = tid; c < MS; c += NT) {
+        const int cy = c / BX, cx = c - cy * BX;
+        T q[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          if constexpr (MIXED) q[v] = T((float)sq[v * MS + c] + (LOADD ? sd[v * MS + c] : 0.0f));
+          else q[v] = T(sq[v * MS + c]);
+        }
+        const bool valid = (x0 - HALO + cx < g.nx + HALO) && (y0 - HALO + cy < g.ny + HALO);
+        T r = q[0];
+        const T ir = Fm::rcp(r);
+        const T uu = q[1] * ir, vv = q[2] * ir, ww = q[3] * ir;
+        T p = gm1 * (q[4] - T(0.5) * r * (uu * uu + vv * vv + ww * ww));
+        if (valid && !(r > T(0) && p > T(0))) bad = true;
+        const bool fill = !valid || !(r > T(0) && p > T(0));
+        rs[0 * MS + c] = fill ? T(1) : r;
+        rs[1 * MS + c] = fill ? T(0) : uu;
+        rs[2 * MS + c] = fill ? T(0) : vv;
+        rs[3 * MS + c] = fill ? T(0) : ww;
+        rs[4 * MS + c] = fill ? T(1) : p;
+        if (VISC) rs[5 * MS + c] = fill ? T(1) : p * ir;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        pending &= ~(1u << s);
+        if (kp + NSTAGE <= last_plane && *sabort == 0) request(kp + NSTAGE);
+      }
+      return *sabort == 0;
+    };
+
+    if (tid == 0) {
+      request(k0 - 2);
+      request(k0 - 1);
+    }
+    bool ok = true;
+    for (int kp = k0 - 2; kp <= k0 + 1 && ok; ++kp) ok = consume(kp);
+    if (!ok) break;
+
+    // owning warps: cell (lane, warp) of the tile
+    const bool owner = warp < TY;
+    const int ci = x0 + lane, cj = y0 + warp;  // interior coordinates of the owned cell
+    const bool live = owner && ci < g.nx && cj < g.ny;
+    const int ocy = warp + HALO, ocx = lane + HALO;
+    T fzl[5], fzu[5];
+    if (owner) zface<T, VISC>(ring, (k0 - 2) & 3, (k0 - 1) & 3, k0 & 3, (k0 + 1) & 3, ocy, ocx, ph, K, fzl);
+    __syncthreads();  // the first consume below overwrites plane k0-2, read by the z-face above
+
+    for (int k = k0; k < k1; ++k) {
+      if (!consume(k + 2)) { ok = false; break; }
+      // per-cell inputs of the update (L2-resident planes), loaded before the face work
+      double qs_[5], qn_[5];
+      float dp_[5];
+      if (live) {
+        const long long o = gidx(g, ci, cj, k), of = gidxf(g, ci, cj, k);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          if constexpr (!MIXED && STAGE >= 1) qs_[v] = __ldg(P.qs + v * g.field + o);
+          if constexpr (!MIXED && STAGE >= 2) qn_[v] = __ldg(P.qn + v * g.field + o);
+          if constexpr (MIXED && STAGE == 3) qn_[v] = __ldg(P.qn + v * g.field + o);
+          if constexpr (LOADD) dp_[v] = __ldg(P.dprev + v * g.fieldf + of);
+        }
+      }
+      const int sk = k & 3, sm = (k - 1) & 3, sp = (k + 1) & 3, s2 = (k + 2) & 3;
+      if (owner) {
+        T F[5];
+        xface<T, VISC>(ring, sk, sm, sp, ocy, ocx, ph, K, F);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) fx[(m * TY + warp) * (TX + 1) + lane] = F[m];
+        yface<T, VISC>(ring, sk, sm, sp, ocy, ocx, ph, K, F);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + warp) * TX + lane] = F[m];
+        zface<T, VISC>(ring, sm, sk, sp, s2, ocy, ocx, ph, K, fzu);
+      } else {
+        T F[5];
+        yface<T, VISC>(ring, sk, sm, sp, TY + HALO, lane + HALO, ph, K, F);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + TY) * TX + lane] = F[m];
+        if (lane < TY) {
+          xface<T, VISC>(ring, sk, sm, sp, lane + HALO, TX + HALO, ph, K, F);
+#pragma unroll
+          for (int m = 0; m < 5; ++m) fx[(m * TY + lane) * (TX + 1) + TX] = F[m];
+        }
+      }
+      __syncthreads();
+      if (live) {
+        T R[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+          const T ddx = fx[(m * TY + warp) * (TX + 1) + lane + 1] - fx[(m * TY + warp) * (TX + 1) + lane];
+          const T ddy = fy[(m * (TY + 1) + warp + 1) * TX + lane] - fy[(m * (TY + 1) + warp) * TX + lane];
+          R[m] = (ddx * T(ph.ihx) + ddy * T(ph.ihy)) + (fzu[m] - fzl[m]) * T(ph.ihz);
+        }
+        const long long o = gidx(g, ci, cj, k), of = gidxf(g, ci, cj, k);
+        if constexpr (STAGE == 0) {
+          const long long oc = ((long long)k * g.ny + cj) * g.nx + ci;
+          const long long n = (long long)g.nx * g.ny * g.nz;
+#pragma unroll
+          for (int m = 0; m < 5; ++m) P.rout[m * n + oc] = double(R[m]);
+        } else if constexpr (!MIXED) {
+          double out[5];
+#pragma unroll
+          for (int m = 0; m < 5; ++m) {
+            const double adv = qs_[m] - dt * double(R[m]);
+            if constexpr (STAGE == 1) out[m] = adv;
+            else if constexpr (STAGE == 2) out[m] = 0.75 * qn_[m] + 0.25 * adv;
+            else out[m] = qn_[m] / 3.0 + (2.0 / 3.0) * adv;
+            P.qout[m * g.field + o] = out[m];
+          }
+          if constexpr (STAGE == 3) {
+            const double ir = 1.0 / out[0];
+            const double uu = out[1] * ir, vv = out[2] * ir, ww = out[3] * ir;
+            const double pp = (ph.gamma - 1.0) * (out[4] - 0.5 * out[0] * (uu * uu + vv * vv + ww * ww));
+            if (!(out[0] > 0.0 && pp > 0.0)) bad = true;
+            rate_max = Fm::mx(rate_max, T(cell_rate<double>(out[0], uu, vv, ww, pp, ph)));
+          }
+        } else {
+          float inc[5];
+#pragma unroll
+          for (int m = 0; m < 5; ++m) inc[m] = -float(dtT) * float(R[m]);
+          if constexpr (STAGE == 1) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) P.dout[m * g.fieldf + of] = inc[m];
+          } else if constexpr (STAGE == 2) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) P.dout[m * g.fieldf + of] = 0.25f * (dp_[m] + inc[m]);
+          } else {
+            float qf[5];
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+              const float d = (2.0f / 3.0f) * (dp_[m] + inc[m]);
+              P.qout[m * g.field + o] = qn_[m] + double(d);
+              qf[m] = float(qn_[m]) + d;
+            }
+            const float ir = Fast<float>::rcp(qf[0]);
+            const float uu = qf[1] * ir, vv = qf[2] * ir, ww = qf[3] * ir;
+            const float pp = float(ph.gamma - 1.0) * (qf[4] - 0.5f * qf[0] * (uu * uu + vv * vv + ww * ww));
+            if (!(qf[0] > 0.0f && pp > 0.0f)) bad = true;
+            rate_max = Fm::mx(rate_max, T(cell_rate<float>(qf[0], uu, vv, ww, pp, ph)));
+          }
+        }
+        if constexpr (STAGE == 1) {
+#pragma unroll
+          for (int m = 0; m < 5; ++m) {
+            if constexpr (MIXED) {  // compensated FP32 accumulation, folded into FP64 below
+              const float y = float(R[m]) * float(R[m]) - ncomp[m];
+              const float t = nsum[m] + y;
+              ncomp[m] = (t - nsum[m]) - y;
+              nsum[m] = t;
+            } else {
+              nacc[m] += double(R[m]) * double(R[m]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 5; ++m) fzl[m] = fzu[m];
+    }
+    if (!ok) break;
+  }
+
+  // abort path: drain copies still in flight (bounded), flag the timeout
+  if (*sabort) {
+    if (tid == 0) {
+      for (int s = 0; s < NSTAGE; ++s)
+        if (pending & (1u << s)) mbar_wait_bounded(&bar[s], (phase_bits >> s) & 1u);
+      atomicOr(&P.ctrl->flag, FLAG_TIMEOUT);
+    }
+  }
+  if (bad) atomicOr(&P.ctrl->flag, FLAG_NONPHYSICAL);
+  if constexpr (STAGE != 1 && STAGE != 3) return;
+
+  // ---- per-CTA partials, then the last CTA reduces them in a fixed order ---------------------
+  double part[6];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) part[m] = MIXED ? double(nsum[m]) - double(ncomp[m]) : nacc[m];
+  part[5] = double(rate_max);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) part[m] += __shfl_xor_sync(0xffffffffu, part[m], off);
+    part[5] = fmax(part[5], __shfl_xor_sync(0xffffffffu, part[5], off));
+  }
+  if (lane == 0)
+    for (int m = 0; m < 6; ++m) red[warp * NPART + m] = part[m];
+  __syncthreads();
+  if (tid == 0) {
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < NWARP; ++w) {
+      for (int m = 0; m < 5; ++m) s[m] += red[w * NPART + m];
+      s[5] = fmax(s[5], red[w * NPART + 5]);
+    }
+    for (int m = 0; m < 6; ++m) P.partial[(size_t)blockIdx.x * NPART + m] = s[m];
+    __threadfence();
+    const unsigned prev = atomicAdd(&P.ctrl->counter, 1u);
+    *slast = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!*slast || warp != 0) return;
+  __threadfence();
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int c = lane; c < (int)gridDim.x; c += 32) {
+    for (int m = 0; m < 5; ++m) s[m] += __ldcg(P.partial + (size_t)c * NPART + m);
+    s[5] = fmax(s[5], __ldcg(P.partial + (size_t)c * NPART + 5));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) s[m] += __shfl_xor_sync(0xffffffffu, s[m], off);
+    s[5] = fmax(s[5], __shfl_xor_sync(0xffffffffu, s[5], off));
+  }
+  if (lane == 0) {
+    const double n = (double)g.nx * g.ny * g.nz;
+    if (STAGE == 1)
+      for (int m = 0; m < 5; ++m) P.ctrl->norms[m] = sqrt(s[m] / n);
+    if (STAGE == 3) {
+      P.ctrl->rate = s[5];
+      P.ctrl->dt = ph.cfl / s[5];
+    }
+    P.ctrl->counter = 0u;
+  }
+}
+
+}  // namespace gbcfd

@@ -1,0 +1,219 @@
+"""Thin Python binding of the gbcfd C ABI (include/gbcfd.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.  PyTorch provides
+the device memory (one uint8 tensor per block) and the stream.  Importing this module loads
+libgbcfd.so (building it with nvcc if needed) and raises if that is impossible: there is no
+CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_STATE, ERR_MEMORY = -1, -2, -3, -4, -5, -6
+FP64, MIXED = 0, 1
+FACES = {"-x": 0, "+x": 1, "-y": 2, "+y": 3, "-z": 4, "+z": 5}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("gamma", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("Pr", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("entropy_eps", ctypes.c_double),
+        ("viscous", ctypes.c_int),
+        ("limiter", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("reserved", ctypes.c_int),
+    ]
+
+
+def params(gamma=1.4, mu=0.0, Pr=0.72, cfl=0.5, entropy_eps=0.1, viscous=False, limiter=0,
+           precision=FP64) -> Params:
+    return Params(gamma, mu, Pr, cfl, entropy_eps, int(bool(viscous)), int(limiter), int(precision), 0)
+
+
+class GbcfdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gbcfd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+# (name, argtypes) of every entry point declared in include/gbcfd.h
+SIGNATURES = {
+    "gbcfd_required_bytes": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params),
+                             ctypes.POINTER(ctypes.c_size_t)],
+    "gbcfd_create_block": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), _VP,
+                           ctypes.c_size_t, ctypes.POINTER(_VP)],
+    "gbcfd_destroy_block": [_VP],
+    "gbcfd_connect": [_VP, ctypes.c_int, _VP],
+    "gbcfd_set_metrics": [_VP, _VP, _D, _VP],
+    "gbcfd_set_state": [_VP, _VP, _VP],
+    "gbcfd_get_state": [_VP, _VP, _VP],
+    "gbcfd_exchange_halos": [ctypes.POINTER(_VP), ctypes.c_int, _VP],
+    "gbcfd_compute_residual": [_VP, _VP, _VP],
+    "gbcfd_stage": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP],
+    "gbcfd_step": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP],
+    "gbcfd_residual_norm": [_VP, _D, _VP],
+    "gbcfd_get_dt": [_VP, _D, _VP],
+    "gbcfd_last_error": [],
+}
+
+
+def lib():
+    """Load libgbcfd.so (built in-tree on first use); raises if it cannot be built or loaded."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        for name, argt in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = argt
+            fn.restype = ctypes.c_char_p if name == "gbcfd_last_error" else ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return os.path.abspath(_build.LIB)
+
+
+def _check(rc):
+    if rc != OK:
+        raise GbcfdError(rc, lib().gbcfd_last_error().decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return ctypes.c_void_p(t.ctypes.data)
+    raise TypeError(type(t))
+
+
+class Block:
+    """One structured block: nx x ny x nz interior cells in a torch-owned device buffer."""
+
+    def __init__(self, nx, ny, nz, prm: Params, device=None):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.params = prm
+        nbytes = ctypes.c_size_t(0)
+        _check(lib().gbcfd_required_bytes(self.nx, self.ny, self.nz, ctypes.byref(prm), ctypes.byref(nbytes)))
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.memory = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=dev)
+        base = self.memory.data_ptr()
+        off = (-base) % 256
+        h = ctypes.c_void_p(0)
+        _check(lib().gbcfd_create_block(self.nx, self.ny, self.nz, ctypes.byref(prm),
+                                        ctypes.c_void_p(base + off), nbytes.value, ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().gbcfd_destroy_block(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def connect(self, face, other: "Block"):
+        f = FACES[face] if isinstance(face, str) else int(face)
+        _check(lib().gbcfd_connect(self.handle, f, other.handle))
+
+    def periodic(self):
+        for d in range(3):
+            self.connect(2 * d + 1, self)
+        return self
+
+    def set_metrics(self, spacing=None, nodes=None, stream=None):
+        sp = (ctypes.c_double * 3)(*(spacing if spacing is not None else (1.0, 1.0, 1.0)))
+        nptr = _ptr(nodes) if nodes is not None else None
+        _check(lib().gbcfd_set_metrics(self.handle, nptr, sp, _stream(stream)))
+
+    def set_state(self, q, stream=None):
+        """q: compact [5][nz][ny][nx] float64, a CUDA tensor or a (pinned) host tensor/array"""
+        if isinstance(q, np.ndarray):
+            q = np.ascontiguousarray(q, dtype=np.float64)
+        else:
+            assert q.dtype == torch.float64 and q.is_contiguous()
+        assert tuple(q.shape) == (5, self.nz, self.ny, self.nx)
+        _check(lib().gbcfd_set_state(self.handle, _ptr(q), _stream(stream)))
+
+    def get_state(self, out=None, stream=None):
+        if out is None:
+            out = torch.empty((5, self.nz, self.ny, self.nx), dtype=torch.float64, device=self.memory.device)
+        _check(lib().gbcfd_get_state(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def compute_residual(self, out=None, stream=None):
+        if out is None:
+            out = torch.empty((5, self.nz, self.ny, self.nx), dtype=torch.float64, device=self.memory.device)
+        _check(lib().gbcfd_compute_residual(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def residual_norm(self, stream=None) -> np.ndarray:
+        out = np.zeros(5)
+        _check(lib().gbcfd_residual_norm(self.handle, out.ctypes.data_as(_D), _stream(stream)))
+        return out
+
+    def get_dt(self, stream=None) -> float:
+        out = ctypes.c_double(0.0)
+        _check(lib().gbcfd_get_dt(self.handle, ctypes.byref(out), _stream(stream)))
+        return out.value
+
+
+def _handles(blocks):
+    arr = (ctypes.c_void_p * len(blocks))(*[b.handle.value for b in blocks])
+    return arr
+
+
+def exchange_halos(blocks, stream=None):
+    _check(lib().gbcfd_exchange_halos(_handles(blocks), len(blocks), _stream(stream)))
+
+
+def stage(blocks, s, stream=None):
+    _check(lib().gbcfd_stage(_handles(blocks), len(blocks), int(s), _stream(stream)))
+
+
+def step(blocks, nsteps=1, stream=None):
+    _check(lib().gbcfd_step(_handles(blocks), len(blocks), int(nsteps), _stream(stream)))
+
+
+def create_block(nx, ny, nz, prm: Params, device=None) -> Block:
+    return Block(nx, ny, nz, prm, device)
+
+
+def block_for_case(case, precision=FP64, periodic=True, device=None) -> Block:
+    """Block configured from a cases.Case (physics, Cartesian spacing, initial state)."""
+    prm = params(case.gamma, case.mu, case.Pr, case.cfl, case.eps, case.viscous, case.limiter, precision)
+    b = Block(case.nx, case.ny, case.nz, prm, device)
+    if periodic:
+        b.periodic()
+    if case.nodes is None:
+        b.set_metrics(spacing=case.spacing)
+    else:
+        b.set_metrics(nodes=torch.from_numpy(np.ascontiguousarray(case.nodes)).to(b.memory.device))
+    b.set_state(torch.from_numpy(np.ascontiguousarray(case.state)).to(b.memory.device))
+    return b

@@ -1,0 +1,309 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on the same seeded inputs.
+
+Bars: FP64 path relative L2 <= 1e-12 per conserved variable after N steps; mixed path (FP32
+reconstruction and fluxes, FP64 state) density relative L2 <= 1e-5 after 100 steps.  Sizes span
+several 32 x 8 tiles with ragged tails; the full-size 256^3 vortex is checked through its exact
+z-invariance against the oracle run on one plane of it.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1710_09995_gb300 import cases  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_09995_gb300 import gbcfd
+    gbcfd.lib()
+    return gbcfd
+
+
+def oparams(case):
+    return oracle.params(case.gamma, case.mu, case.Pr, case.cfl, case.eps, case.viscous, case.limiter)
+
+
+def per_var(a, b):
+    """relative L2 error per conserved variable; a variable whose reference norm is below 1e-3 of
+    the density's (a momentum component at rest) is measured against 1e-3 of the density norm"""
+    floor = 1e-3 * np.linalg.norm(b[0].ravel())
+    return [np.linalg.norm((a[m] - b[m]).ravel()) / max(np.linalg.norm(b[m].ravel()), floor)
+            for m in range(5)]
+
+
+def run_oracle(case, nsteps):
+    M = oracle.metrics(case.grid_nodes())
+    Q, dts, norms = oracle.step(oparams(case), oracle.pad(case.state), M, nsteps)
+    return oracle.interior(Q), dts, norms
+
+
+def ragged_case(viscous, seed=3, nx=70, ny=19, nz=12):
+    c = cases.smooth_random(nx, ny, nz, seed=seed, amp=0.05, viscous=viscous, mu=3e-3 if viscous else 0.0)
+    c.spacing = (1.0 / 64, 1.0 / 16, 1.0 / 8)
+    return c
+
+
+# ---- residual ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_residual_fp64(gb, viscous):
+    c = ragged_case(viscous)
+    blk = gb.block_for_case(c, precision=gb.FP64)
+    R = blk.compute_residual().cpu().numpy()
+    ref = oracle.residual(oparams(c), oracle.pad(c.state), oracle.metrics(c.grid_nodes()))
+    assert max(per_var(R, ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_residual_mixed(gb, viscous):
+    """FP32 fluxes: a face-flux difference carries ~6e-8 |F| of rounding, about 1e-5 of R here."""
+    c = ragged_case(viscous)
+    blk = gb.block_for_case(c, precision=gb.MIXED)
+    R = blk.compute_residual().cpu().numpy()
+    ref = oracle.residual(oparams(c), oracle.pad(c.state), oracle.metrics(c.grid_nodes()))
+    assert max(per_var(R, ref)) <= 1e-4
+
+
+# ---- time stepping -------------------------------------------------------------------------
+
+def test_gaussian_pulse_32_fp64_10_steps(gb):
+    """32^3 Euler Gaussian pulse, CFL 0.5, MUSCL/minmod + Roe, 10 SSP-RK3 steps, FP64."""
+    c = cases.gaussian_pulse(32, seed=0)
+    ref, dts, norms = run_oracle(c, 10)
+    blk = gb.block_for_case(c, precision=gb.FP64)
+    gb.step([blk], 10)
+    got = blk.get_state().cpu().numpy()
+    assert max(per_var(got, ref)) <= 1e-12
+    change = ref - c.state
+    assert np.linalg.norm(got - ref) / np.linalg.norm(change) <= 1e-10
+    assert abs(blk.get_dt() - oracle.dt(oparams(c), oracle.pad(ref), oracle.metrics(c.grid_nodes()))) \
+        <= 1e-13 * dts[0]
+    assert np.allclose(blk.residual_norm(), norms[-1], rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_ragged_fp64_steps(gb, viscous):
+    c = ragged_case(viscous, seed=5)
+    ref, _, norms = run_oracle(c, 5)
+    blk = gb.block_for_case(c, precision=gb.FP64)
+    gb.step([blk], 5)
+    got = blk.get_state().cpu().numpy()
+    assert max(per_var(got, ref)) <= 1e-12
+    assert np.allclose(blk.residual_norm(), norms[-1], rtol=1e-11, atol=0)
+
+
+def test_vortex_mixed_100_steps(gb):
+    """Navier-Stokes isentropic vortex (Re 1e4), mixed precision: density within 1e-5 of the FP64
+    oracle after 100 steps."""
+    c = cases.isentropic_vortex(n=64, L=10.0, nz=4, viscous=True)
+    ref, _, norms = run_oracle(c, 100)
+    blk = gb.block_for_case(c, precision=gb.MIXED)
+    gb.step([blk], 100)
+    got = blk.get_state().cpu().numpy()
+    err = per_var(got, ref)
+    assert err[0] <= 1e-5, err
+    assert max(err) <= 1e-5, err
+    assert np.allclose(blk.residual_norm(), norms[-1], rtol=1e-4, atol=0)
+
+
+def test_gaussian_pulse_mixed(gb):
+    c = cases.gaussian_pulse(32, seed=0)
+    ref, _, _ = run_oracle(c, 10)
+    blk = gb.block_for_case(c, precision=gb.MIXED)
+    gb.step([blk], 10)
+    err = per_var(blk.get_state().cpu().numpy(), ref)
+    # FP32 fluxes carry ~6e-8 |F|; relative to the small transverse momenta that is ~1e-6
+    assert err[0] <= 1e-6 and max(err) <= 1e-5, err
+
+
+@pytest.mark.parametrize("shape", [(3, 1, 2), (1, 1, 1), (5, 9, 1), (33, 8, 3)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_small_and_degenerate_blocks(gb, shape, precision):
+    """Blocks narrower than the halo (periodic images wrap more than once), single planes, one
+    cell, and a size one past the tile width."""
+    nx, ny, nz = shape
+    c = cases.smooth_random(nx, ny, nz, seed=7, amp=0.05, viscous=True, mu=2e-3)
+    ref, _, _ = run_oracle(c, 3)
+    blk = gb.block_for_case(c, precision=precision)
+    gb.step([blk], 3)
+    err = per_var(blk.get_state().cpu().numpy(), ref)
+    if precision == 0:
+        assert max(err) <= 1e-12, err
+    else:
+        assert err[0] <= 1e-6 and max(err) <= 1e-5, err
+
+
+# ---- multi-block ----------------------------------------------------------------------------
+
+def split_blocks(gb, c, cuts, precision):
+    """Blocks of uneven sizes tiling the periodic domain, connected face to face."""
+    xs, ys, zs = cuts
+    grid = {}
+    for a in range(len(zs) - 1):
+        for b in range(len(ys) - 1):
+            for e in range(len(xs) - 1):
+                sub = c.state[:, zs[a]:zs[a + 1], ys[b]:ys[b + 1], xs[e]:xs[e + 1]]
+                prm = gb.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, c.limiter, precision)
+                blk = gb.Block(sub.shape[3], sub.shape[2], sub.shape[1], prm)
+                blk.set_metrics(spacing=c.spacing)
+                blk.set_state(torch.from_numpy(np.ascontiguousarray(sub)).cuda())
+                grid[(a, b, e)] = blk
+    na, nb, ne = len(zs) - 1, len(ys) - 1, len(xs) - 1
+    for (a, b, e), blk in grid.items():
+        blk.connect("+x", grid[(a, b, (e + 1) % ne)])
+        blk.connect("+y", grid[(a, (b + 1) % nb, e)])
+        blk.connect("+z", grid[((a + 1) % na, b, e)])
+    return grid
+
+
+def assemble(grid, cuts, shape):
+    xs, ys, zs = cuts
+    out = np.zeros(shape)
+    for (a, b, e), blk in grid.items():
+        out[:, zs[a]:zs[a + 1], ys[b]:ys[b + 1], xs[e]:xs[e + 1]] = blk.get_state().cpu().numpy()
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multiblock_matches_single_block(gb, precision):
+    """Eight uneven blocks of a periodic 40 x 24 x 16 domain give the single-block result
+    bitwise: the halo exchange (faces, edges, corners) and the global time step are exact."""
+    c = cases.smooth_random(40, 24, 16, seed=9, amp=0.05, viscous=True, mu=3e-3)
+    c.spacing = (1 / 32, 1 / 16, 1 / 16)
+    cuts = ([0, 27, 40], [0, 9, 24], [0, 5, 16])
+    grid = split_blocks(gb, c, cuts, precision)
+    single = gb.block_for_case(c, precision=precision)
+    blocks = list(grid.values())
+    gb.step(blocks, 4)
+    gb.step([single], 4)
+    got = assemble(grid, cuts, c.state.shape)
+    want = single.get_state().cpu().numpy()
+    assert np.array_equal(got, want), np.max(np.abs(got - want))
+    if precision == 0:
+        ref, _, _ = run_oracle(c, 4)
+        assert max(per_var(got, ref)) <= 1e-12
+
+
+def test_exchange_halos_then_residual_matches_oracle_on_blocks(gb):
+    c = cases.smooth_random(40, 24, 16, seed=10, amp=0.05, viscous=True, mu=3e-3)
+    cuts = ([0, 13, 40], [0, 16, 24], [0, 8, 16])
+    grid = split_blocks(gb, c, cuts, 0)
+    gb.exchange_halos(list(grid.values()))
+    ref = oracle.residual(oparams(c), oracle.pad(c.state), oracle.metrics(c.grid_nodes()))
+    xs, ys, zs = cuts
+    for (a, b, e), blk in grid.items():
+        R = blk.compute_residual().cpu().numpy()
+        sub = ref[:, zs[a]:zs[a + 1], ys[b]:ys[b + 1], xs[e]:xs[e + 1]]
+        assert max(per_var(R, sub)) <= 1e-12
+
+
+# ---- invariants on the device ---------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_conservation_on_device(gb, precision):
+    c = cases.smooth_random(48, 20, 10, seed=11, amp=0.1, viscous=True, mu=3e-3)
+    blk = gb.block_for_case(c, precision=precision)
+    gb.step([blk], 20)
+    got = blk.get_state().cpu().numpy()
+    for m in range(5):
+        t0, t1 = c.state[m].sum(), got[m].sum()
+        tol = 1e-13 if precision == 0 else 1e-7
+        assert abs(t1 - t0) <= tol * np.abs(c.state[m]).sum()
+
+
+def test_freestream_is_exact_on_device(gb):
+    """A uniform flow has identical fluxes on every face: R = 0 exactly.  The mixed path adds a
+    zero increment (bitwise unchanged); the FP64 path's Shu-Osher weights round at 1e-16."""
+    c = cases.smooth_random(40, 16, 8, seed=0, amp=0.0, viscous=True, mu=1e-2)
+    for precision in (0, 1):
+        blk = gb.block_for_case(c, precision=precision)
+        R = blk.compute_residual().cpu().numpy()
+        assert np.max(np.abs(R)) == 0.0
+        gb.step([blk], 3)
+        got = blk.get_state().cpu().numpy()
+        if precision == 1:
+            assert np.array_equal(got, c.state)
+        else:
+            assert np.max(np.abs(got - c.state)) <= 4e-16 * np.max(np.abs(c.state))
+
+
+# ---- the state round trip and error paths --------------------------------------------------
+
+def test_host_state_roundtrip(gb):
+    c = cases.smooth_random(35, 10, 6, seed=12)
+    for precision in (0, 1):
+        prm = gb.params(precision=precision)
+        blk = gb.Block(35, 10, 6, prm)
+        blk.periodic()
+        blk.set_state(c.state)
+        out = np.zeros_like(c.state)
+        blk.get_state(out)
+        assert np.array_equal(out, c.state)
+
+
+def test_nonphysical_state_is_reported(gb):
+    c = cases.smooth_random(16, 8, 4, seed=13)
+    bad = c.state.copy()
+    bad[4, 2, 3, 5] = -1.0   # negative total energy -> negative pressure
+    for precision in (0, 1):
+        blk = gb.Block(16, 8, 4, gb.params(precision=precision))
+        blk.periodic()
+        blk.set_state(torch.from_numpy(bad).cuda())
+        gb.step([blk], 1)
+        with pytest.raises(gb.GbcfdError) as e:
+            blk.residual_norm()
+        assert e.value.code == gb.ERR_NONPHYSICAL
+        blk.set_state(torch.from_numpy(c.state).cuda())
+        gb.step([blk], 1)
+        blk.residual_norm()   # flag was cleared; a good state passes
+
+
+def test_argument_errors(gb):
+    L = gb.lib()
+    import ctypes
+    n = ctypes.c_size_t(0)
+    prm = gb.params()
+    assert L.gbcfd_required_bytes(0, 4, 4, ctypes.byref(prm), ctypes.byref(n)) == gb.ERR_ARG
+    bad = gb.params(precision=7)
+    assert L.gbcfd_required_bytes(4, 4, 4, ctypes.byref(bad), ctypes.byref(n)) == gb.ERR_ARG
+    blk = gb.Block(8, 8, 8, prm)
+    with pytest.raises(gb.GbcfdError) as e:
+        gb.step([blk], 1)
+    assert e.value.code == gb.ERR_STATE
+    other = gb.Block(8, 9, 8, prm)
+    with pytest.raises(gb.GbcfdError) as e:
+        blk.connect("+x", other)
+    assert e.value.code == gb.ERR_ARG
+    blk.periodic()
+    blk.set_state(cases.smooth_random(8, 8, 8).state)
+    with pytest.raises(gb.GbcfdError) as e:
+        blk.compute_residual(out=np.zeros((5, 8, 8, 8)))
+    assert e.value.code == gb.ERR_ARG
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    h = ctypes.c_void_p(0)
+    assert L.gbcfd_create_block(8, 8, 8, ctypes.byref(prm), ctypes.c_void_p(small.data_ptr()), 1024,
+                                ctypes.byref(h)) == gb.ERR_MEMORY
+
+
+# ---- full size: the 256^3 vortex ------------------------------------------------------------
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_full_size_vortex_256(gb, precision, tol):
+    """The 256^3 Navier-Stokes vortex, in the launch configuration the benchmark times: the flow
+    is z-invariant, so every plane of the GPU result must equal plane 0 bitwise, and plane 0
+    must match the oracle run on a single-plane periodic slab of the same case."""
+    full = cases.isentropic_vortex(n=256, L=10.0, viscous=True)
+    blk = gb.block_for_case(full, precision=precision)
+    gb.step([blk], 2)
+    got = blk.get_state()
+    assert bool(torch.all(got == got[:, :1]).item())
+    plane = got[:, 0].cpu().numpy()
+    slab = cases.isentropic_vortex(n=256, L=10.0, nz=1, viscous=True)
+    ref, _, norms = run_oracle(slab, 2)
+    assert max(per_var(plane[:, None], ref)) <= tol
+    assert np.allclose(blk.residual_norm(), norms[-1], rtol=1e-10 if precision == 0 else 1e-4, atol=0)
