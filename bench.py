@@ -30,7 +30,7 @@ N_DEFAULT = 256
 PEAK_FALLBACK_GBS = 6800.0
 # algorithmic HBM bytes per interior cell for stages 1, 2, 3 (state reads/writes, halos excluded)
 ALGO_BYTES = {
-    "mixed": (40 + 20, 40 + 20 + 20, 40 + 20 + 40),   # Qn read; D read; D or Q^{n+1} written
+    "mixed": (20 + 20, 20 + 20 + 20, 20 + 20 + 40 + 40 + 20),  # S^n, D read; D or Q^{n+1}, S^{n+1} written
     "fp64": (40 + 40, 40 + 40 + 40, 40 + 40 + 40),    # stage input, Qn read; stage output written
 }
 WORKLOAD = "isentropic vortex 256^3, Navier-Stokes Re 1e4 Pr 0.72, MUSCL/minmod + Roe, SSP-RK3 CFL 0.5"

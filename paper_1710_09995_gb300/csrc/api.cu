@@ -42,6 +42,7 @@ struct gbcfd_block_s {
   int device, nsm, grid;
   size_t bytes;
   double* q[3];      // FP64: Qn, Q1, Q2.  mixed: QA, QB (ping-pong Q^n)
+  float* sh[2];      // mixed: SA, SB, the f32 shadows of QA, QB
   float* d[2];       // mixed: D1, D2
   void* metrics;     // 10 fields (f64, or f32 on the mixed path)
   DevCtrl* ctrl;
@@ -53,7 +54,7 @@ struct gbcfd_block_s {
   int next_stage;    // 1, 2 or 3: the Runge-Kutta stage the block expects next
   double spacing[3];
   gbcfd_block nbr[6];
-  CUtensorMap tm_q[3];
+  CUtensorMap tm_q[3];  // FP64: maps of Qn, Q1, Q2.  mixed: maps of the shadows SA, SB
   CUtensorMap tm_d[2];
 };
 
@@ -119,6 +120,8 @@ static Carve carve(const Geometry& g, int precision, int nsm) {
     c.off[3] = o; o += f32;                 // d0
     c.off[4] = o; o += f32;                 // d1
     c.off[5] = o; o += align256(sizeof(float) * 10 * g.fieldf);  // metrics f32
+    c.off[8] = o; o += f32;                 // shadow A
+    c.off[9] = o; o += f32;                 // shadow B
   }
   c.off[6] = o; o += align256(sizeof(DevCtrl));
   c.partial_n = (size_t)std::max(4 * nsm, 4 * 152);
@@ -227,6 +230,8 @@ extern "C" int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* pa
   b->q[2] = params->precision == GBCFD_FP64 ? reinterpret_cast<double*>(base + c.off[2]) : nullptr;
   b->d[0] = params->precision == GBCFD_MIXED ? reinterpret_cast<float*>(base + c.off[3]) : nullptr;
   b->d[1] = params->precision == GBCFD_MIXED ? reinterpret_cast<float*>(base + c.off[4]) : nullptr;
+  b->sh[0] = params->precision == GBCFD_MIXED ? reinterpret_cast<float*>(base + c.off[8]) : nullptr;
+  b->sh[1] = params->precision == GBCFD_MIXED ? reinterpret_cast<float*>(base + c.off[9]) : nullptr;
   b->metrics = base + c.off[5];
   b->ctrl = reinterpret_cast<DevCtrl*>(base + c.off[6]);
   b->partial = reinterpret_cast<double*>(base + c.off[7]);
@@ -250,7 +255,7 @@ extern "C" int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* pa
     for (int i = 0; i < 3 && !r; ++i) r = make_map(&b->tm_q[i], b->q[i], g, 8);
     if (!r) b->tm_d[0] = b->tm_d[1] = b->tm_q[0];
   } else {
-    for (int i = 0; i < 2 && !r; ++i) r = make_map(&b->tm_q[i], b->q[i], g, 8);
+    for (int i = 0; i < 2 && !r; ++i) r = make_map(&b->tm_q[i], b->sh[i], g, 4);
     for (int i = 0; i < 2 && !r; ++i) r = make_map(&b->tm_d[i], b->d[i], g, 4);
     if (!r) b->tm_q[2] = b->tm_q[0];
   }
@@ -319,8 +324,9 @@ extern "C" int gbcfd_set_state(gbcfd_block b, const double* q, void* stream) {
     CK(cudaMemcpyAsync(b->staging, q, 5 * n * sizeof(double), cudaMemcpyHostToDevice, s));
     src = reinterpret_cast<const double*>(b->staging);
   }
-  CK(launch_scatter(b->g, src, state_ptr(b), s));
-  CK(launch_init_rate(b->g, physics_of(b), state_ptr(b), b->ctrl, b->partial, 4 * b->nsm, s));
+  CK(launch_scatter(b->g, src, state_ptr(b), b->p.precision == GBCFD_MIXED ? b->sh[b->cur] : nullptr, s));
+  CK(launch_init_rate(b->g, physics_of(b), state_ptr(b), b->ctrl, b->partial, 4 * b->nsm,
+                      b->p.precision == GBCFD_MIXED, s));
   b->has_state = 1;
   b->next_stage = 1;
   return GBCFD_OK;
@@ -352,7 +358,10 @@ static void field_of(gbcfd_block b, int f, char** base, int* elem, int* nvar) {
   const bool mixed = b->p.precision == GBCFD_MIXED;
   *nvar = 5;
   switch (f) {
-    case F_STATE: *base = reinterpret_cast<char*>(state_ptr(b)); *elem = 8; break;
+    case F_STATE:  // the mixed path's stencils read the f32 shadow of Q^n
+      *base = mixed ? reinterpret_cast<char*>(b->sh[b->cur]) : reinterpret_cast<char*>(state_ptr(b));
+      *elem = mixed ? 4 : 8;
+      break;
     case F_STAGE1: *base = mixed ? reinterpret_cast<char*>(b->d[0]) : reinterpret_cast<char*>(b->q[1]); *elem = mixed ? 4 : 8; break;
     case F_STAGE2: *base = mixed ? reinterpret_cast<char*>(b->d[1]) : reinterpret_cast<char*>(b->q[2]); *elem = mixed ? 4 : 8; break;
     default: *base = reinterpret_cast<char*>(b->metrics); *elem = mixed ? 4 : 8; *nvar = 10; break;
@@ -464,7 +473,7 @@ static int run_stage(gbcfd_block b, int stage, double* rout, cudaStream_t s) {
       case 0: P.rout = rout; break;
       case 1: P.dout = b->d[0]; break;
       case 2: P.dprev = b->d[0]; P.dout = b->d[1]; tmd = &b->tm_d[0]; break;
-      case 3: P.dprev = b->d[1]; P.qout = b->q[1 - c]; tmd = &b->tm_d[1]; break;
+      case 3: P.dprev = b->d[1]; P.qout = b->q[1 - c]; P.sout = b->sh[1 - c]; tmd = &b->tm_d[1]; break;
     }
   }
   CK(launch_stage(b->p.precision, b->p.viscous, stage, *tmq, *tmd, P, b->grid, s));

@@ -80,7 +80,9 @@ cudaError_t launch_halo(const HaloGroup& G, cudaStream_t s) {
 }
 
 // ---- compact <-> padded state --------------------------------------------------------------
-__global__ void scatter_kernel(Geometry g, const double* __restrict__ src, double* __restrict__ dst) {
+// shadow (may be null): the f32 rounding of the state, written alongside
+__global__ void scatter_kernel(Geometry g, const double* __restrict__ src, double* __restrict__ dst,
+                               float* __restrict__ shadow) {
   const long long n = (long long)g.nx * g.ny * g.nz;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 5 * n; t += stride) {
@@ -89,7 +91,9 @@ __global__ void scatter_kernel(Geometry g, const double* __restrict__ src, doubl
     const int i = (int)(c % g.nx);
     const long long r = c / g.nx;
     const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    dst[v * g.field + gidx(g, i, j, k)] = src[t];
+    const double x = src[t];
+    dst[v * g.field + gidx(g, i, j, k)] = x;
+    if (shadow) shadow[v * g.fieldf + gidxf(g, i, j, k)] = float(x);
   }
 }
 __global__ void gather_kernel(Geometry g, const double* __restrict__ src, double* __restrict__ dst) {
@@ -110,9 +114,9 @@ static unsigned grid_for(long long work, int threads) {
   if (b < 1) b = 1;
   return (unsigned)b;
 }
-cudaError_t launch_scatter(const Geometry& g, const double* src, double* dst, cudaStream_t s) {
+cudaError_t launch_scatter(const Geometry& g, const double* src, double* dst, float* shadow, cudaStream_t s) {
   const long long n = 5LL * g.nx * g.ny * g.nz;
-  scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(g, src, dst);
+  scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(g, src, dst, shadow);
   return cudaGetLastError();
 }
 cudaError_t launch_gather(const Geometry& g, const double* src, double* dst, cudaStream_t s) {
@@ -123,29 +127,33 @@ cudaError_t launch_gather(const Geometry& g, const double* src, double* dst, cud
 
 // ---- time step -----------------------------------------------------------------------------
 // rate = sum over directions of (|u_d| + c) / h_d (+ 4 max(4/3, gamma/Pr) mu / rho / h_d^2 when
-// viscous); the CFL step is cfl / max(rate).  FP64, from the padded state.
+// viscous); the CFL step is cfl / max(rate).  From the padded f64 state, in the path's flux
+// precision T (the mixed path's time step is an f32 evaluation, like its fluxes).
+template <typename T>
 __global__ void init_rate_kernel(Geometry g, Physics ph, const double* __restrict__ q, DevCtrl* ctrl,
                                  double* partial) {
   __shared__ double wmax[32];
   __shared__ int last;
   const long long n = (long long)g.nx * g.ny * g.nz;
   double best = 0.0;
-  const double f = fmax(4.0 / 3.0, ph.gamma / ph.Pr);
-  const double s2 = ph.ihx * ph.ihx + ph.ihy * ph.ihy + ph.ihz * ph.ihz;
+  const T f = T(fmax(4.0 / 3.0, ph.gamma / ph.Pr));
+  const T s2 = T(ph.ihx * ph.ihx + ph.ihy * ph.ihy + ph.ihz * ph.ihz);
+  const T gam = T(ph.gamma), gm1 = T(ph.gamma - 1.0), mu4 = T(4.0 * ph.mu);
+  const T ihx = T(ph.ihx), ihy = T(ph.ihy), ihz = T(ph.ihz);
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.nx);
     const long long r = c / g.nx;
     const int j = (int)(r % g.ny), k = (int)(r / g.ny);
     const long long o = gidx(g, i, j, k);
-    const double rho = q[o], ir = 1.0 / rho;
-    const double u = q[g.field + o] * ir, v = q[2 * g.field + o] * ir, w = q[3 * g.field + o] * ir;
-    const double p = (ph.gamma - 1.0) * (q[4 * g.field + o] - 0.5 * rho * (u * u + v * v + w * w));
-    const double a = sqrt(ph.gamma * p * ir);
-    double rate = (fabs(u) + a) * ph.ihx + (fabs(v) + a) * ph.ihy + (fabs(w) + a) * ph.ihz;
-    if (ph.viscous) rate += 4.0 * f * ph.mu * ir * s2;
-    if (!(rho > 0.0 && p > 0.0)) atomicOr(&ctrl->flag, FLAG_NONPHYSICAL);
-    best = fmax(best, rate);
+    const T rho = T(q[o]), ir = T(1) / rho;
+    const T u = T(q[g.field + o]) * ir, v = T(q[2 * g.field + o]) * ir, w = T(q[3 * g.field + o]) * ir;
+    const T p = gm1 * (T(q[4 * g.field + o]) - T(0.5) * rho * (u * u + v * v + w * w));
+    const T a = sqrt(gam * p * ir);
+    T rate = (fabs(u) + a) * ihx + (fabs(v) + a) * ihy + (fabs(w) + a) * ihz;
+    if (ph.viscous) rate += f * mu4 * ir * s2;
+    if (!(rho > T(0) && p > T(0))) atomicOr(&ctrl->flag, FLAG_NONPHYSICAL);
+    best = fmax(best, double(rate));
   }
   for (int off = 16; off > 0; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
   if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = best;
@@ -168,8 +176,11 @@ __global__ void init_rate_kernel(Geometry g, Physics ph, const double* __restric
 }
 
 cudaError_t launch_init_rate(const Geometry& g, const Physics& ph, const double* q, DevCtrl* ctrl,
-                             double* partial, int grid, cudaStream_t s) {
-  init_rate_kernel<<<grid, 256, 0, s>>>(g, ph, q, ctrl, partial);
+                             double* partial, int grid, int mixed, cudaStream_t s) {
+  if (mixed)
+    init_rate_kernel<float><<<grid, 256, 0, s>>>(g, ph, q, ctrl, partial);
+  else
+    init_rate_kernel<double><<<grid, 256, 0, s>>>(g, ph, q, ctrl, partial);
   return cudaGetLastError();
 }
 

@@ -7,9 +7,11 @@
 //   starts at storage column 32*t.
 //   FP64 path:  Qn (f64) and stage states Q1, Q2 (f64).  Stage 3 writes Q^{n+1} over Qn (it
 //               reads Qn only at its own cell).
-//   mixed path: Q^n in a ping-pong pair QA/QB (f64) and stage increments D1, D2 (f32):
-//               Q1 = Qn + D1,  Q2 = Qn + D2,  D1 = -dt R(Qn),  D2 = (D1 - dt R(Q1)) / 4,
-//               Q^{n+1} = Qn + 2/3 (D2 - dt R(Q2))   -- algebraically Eqs. 4-6.
+//   mixed path: Q^n in a ping-pong pair QA/QB (f64), its f32 rounding S^n in a ping-pong pair
+//               SA/SB (what the flux stencils read), and stage increments D1, D2 (f32):
+//               Q1 = Sn + D1,  Q2 = Sn + D2,  D1 = -dt R(Sn),  D2 = (D1 - dt R(Q1)) / 4,
+//               Q^{n+1} = Qn + 2/3 (D2 - dt R(Q2)) in f64, S^{n+1} = f32(Q^{n+1})
+//               -- algebraically Eqs. 4-6.
 //   metrics (curvilinear only): M[10][..] = S_xi(3), S_eta(3), S_zeta(3), V, f64 (f32 copy for
 //               the mixed path), the lower-face area vectors of each cell.
 //   control:    DevCtrl (time step, norms, flag, counter) + per-CTA partials.
@@ -74,6 +76,7 @@ struct StageParams {
   const double* qn;   // Q^n (f64): stages 2,3 of the FP64 path, all stages of the mixed path
   const double* qs;   // stage input (f64, FP64 path): Qn, Q1 or Q2
   double* qout;       // f64 output: Q1, Q2, Q^{n+1} (FP64 path) or Q^{n+1} (mixed stage 3)
+  float* sout;        // mixed stage 3: f32 shadow of Q^{n+1}
   const float* dprev; // mixed: D1 (stage 2) or D2 (stage 3)
   float* dout;        // mixed: D1 (stage 1) or D2 (stage 2)
   double* rout;       // residual mode: compact R[5][nz][ny][nx]

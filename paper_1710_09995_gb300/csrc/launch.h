@@ -23,11 +23,11 @@ int stage_occupancy_f32(int viscous);
 // halo exchange of one field over a group of blocks
 cudaError_t launch_halo(const HaloGroup& G, cudaStream_t s);
 // compact [5][nz][ny][nx] f64 <-> padded f64 field
-cudaError_t launch_scatter(const Geometry& g, const double* src, double* dst, cudaStream_t s);
+cudaError_t launch_scatter(const Geometry& g, const double* src, double* dst, float* shadow, cudaStream_t s);
 cudaError_t launch_gather(const Geometry& g, const double* src, double* dst, cudaStream_t s);
 // spectral-radius rate and time step of a padded f64 state (per-CTA partials, last CTA reduces)
 cudaError_t launch_init_rate(const Geometry& g, const Physics& ph, const double* q, DevCtrl* ctrl,
-                             double* partial, int grid, cudaStream_t s);
+                             double* partial, int grid, int mixed, cudaStream_t s);
 // global time step of a group: dt = cfl / max rate, written to every block
 cudaError_t launch_group_dt(DevCtrl* const* ctrls, int n, double cfl, cudaStream_t s);
 

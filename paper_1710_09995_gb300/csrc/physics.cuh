@@ -35,14 +35,15 @@ template <typename T> struct Consts {
   int lim;   // 0 minmod, 1 central slope
 };
 
-// limited slope from the backward and forward differences
+// half the limited slope from the backward and forward differences.  minmod without compares:
+// (copysign(1/4, a) + copysign(1/4, b)) * min(|a|, |b|) is 0.5 min(a,b) when both are positive,
+// 0.5 max(a,b) when both are negative and 0 otherwise -- exactly 0.5 * minmod(a, b) (the sum is
+// 0, +-1/2 and the product by a power of two is exact).
 template <typename T>
-__device__ __forceinline__ T slope(T dm, T dp, int lim) {
+__device__ __forceinline__ T half_slope(T dm, T dp, int lim) {
   using F = Fast<T>;
-  if (lim) return T(0.5) * (dm + dp);
-  T s = (dm > T(0) && dp > T(0)) ? F::mn(dm, dp) : T(0);
-  s = (dm < T(0) && dp < T(0)) ? F::mx(dm, dp) : s;
-  return s;
+  if (lim) return T(0.25) * (dm + dp);
+  return (copysign(T(0.25), dm) + copysign(T(0.25), dp)) * F::mn(F::ab(dm), F::ab(dp));
 }
 
 // Roe flux per unit area in the face frame.  L, R: (rho, u_n, u_t1, u_t2, p).

@@ -74,10 +74,11 @@ struct Plan {
   static constexpr int NV = VISC ? 6 : 5;           // rho u v w p [theta]
   static constexpr int BOX = BY * BX;               // cells per staged plane
   static constexpr int RSLOT = NV * BOX;            // T per ring slot
-  // staging slots are 128-byte aligned (TMA tensor-copy destinations)
-  static constexpr size_t QSLOT = (sizeof(double) * 5 * BOX + 127) / 128 * 128;
+  // staging slots are 128-byte aligned (TMA tensor-copy destinations); the state is staged in
+  // f64 on the FP64 path and as its f32 shadow on the mixed path
+  static constexpr size_t QSLOT = (sizeof(T) * 5 * BOX + 127) / 128 * 128;
   static constexpr size_t DSLOT = sizeof(T) == 4 ? (sizeof(float) * 5 * BOX + 127) / 128 * 128 : 0;
-  static constexpr size_t stq = 0;                        // f64 staging
+  static constexpr size_t stq = 0;                        // state staging
   static constexpr size_t std_ = stq + NSTAGE * QSLOT;    // f32 staging
   static constexpr size_t ring = std_ + NSTAGE * DSLOT;
   static constexpr size_t fx = ring + sizeof(T) * NRING * RSLOT;
@@ -111,8 +112,8 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ ring, int b0, in
     const int m = idx[q] * MS;
     const T w0 = ring[b0 + m], w1 = ring[b1 + m], w2 = ring[b2 + m], w3 = ring[b3 + m];
     const T d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
-    L[q] = w1 + T(0.5) * slope(d01, d12, K.lim);
-    R[q] = w2 - T(0.5) * slope(d12, d23, K.lim);
+    L[q] = w1 + half_slope(d01, d12, K.lim);
+    R[q] = w2 - half_slope(d12, d23, K.lim);
   }
   T Fr[5];
   roe_frame(L, R, K, Fr);
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
   const long long W = P.units;
   const long long u_begin = (long long)blockIdx.x * W / gridDim.x;
   const long long u_end = (long long)(blockIdx.x + 1) * W / gridDim.x;
-  constexpr unsigned QBYTES = 5u * MS * sizeof(double);
+  constexpr unsigned QBYTES = 5u * MS * sizeof(T);
   constexpr unsigned DBYTES = 5u * MS * sizeof(float);
 
   for (long long u = u_begin; u < u_end;) {
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
       const bool ok = mbar_wait_bounded(&bar[s], (phase_bits >> s) & 1u);
       if (!ok) atomicOr(sabort, 1);
       phase_bits ^= 1u << s;
-      const double* sq = reinterpret_cast<const double*>(smem + PL::stq + s * PL::QSLOT);
+      const T* sq = reinterpret_cast<const T*>(smem + PL::stq + s * PL::QSLOT);
       const float* sd = reinterpret_cast<const float*>(smem + PL::std_ + s * PL::DSLOT);
       T* rs = ring + (size_t)(kp & 3) * NV * MS;
       for (int c = tid; c < MS; c += NT) {
@@ -285,8 +286,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
         T q[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          if constexpr (MIXED) q[v] = T((float)sq[v * MS + c] + (LOADD ? sd[v * MS + c] : 0.0f));
-          else q[v] = T(sq[v * MS + c]);
+          if constexpr (LOADD) q[v] = sq[v * MS + c] + sd[v * MS + c];
+          else q[v] = sq[v * MS + c];
         }
         const bool valid = (x0 - HALO + cx < g.nx + HALO) && (y0 - HALO + cy < g.ny + HALO);
         T r = q[0];
@@ -410,8 +411,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
               const float d = (2.0f / 3.0f) * (dp_[m] + inc[m]);
-              P.qout[m * g.field + o] = qn_[m] + double(d);
-              qf[m] = float(qn_[m]) + d;
+              const double qnew = qn_[m] + double(d);
+              P.qout[m * g.field + o] = qnew;
+              qf[m] = float(qnew);
+              P.sout[m * g.fieldf + of] = qf[m];
             }
             const float ir = Fast<float>::rcp(qf[0]);
             const float uu = qf[1] * ir, vv = qf[2] * ir, ww = qf[3] * ir;
