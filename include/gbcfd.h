@@ -130,6 +130,23 @@ int gbcfd_residual_norm(gbcfd_block block, double out[5], void* stream);
 /* The time step the next stage 1 will use, copied to *dt on the host (synchronises). */
 int gbcfd_get_dt(gbcfd_block block, double* dt, void* stream);
 
+/* The CFL time step of a state, with no device memory allocated by anyone: for callers that
+ * cannot call cudaMalloc -- code running where the device allocator is off limits (inside a
+ * pre-sized memory pool or a fixed-footprint service) or that holds no block.  The paper has no
+ * counterpart; it is the same time step gbcfd_set_state evaluates (cfl / max over cells of the
+ * summed spectral-radius rate, in the precision params->precision selects), on a uniform
+ * Cartesian grid with cell sizes spacing[0..2].
+ *   q:  device pointer, compact q[5][nz][ny][nx] float64 (caller-owned, read only)
+ *   dt: device pointer to one float64 (caller-owned), written asynchronously on `stream`; a
+ *       negative value means a cell had rho <= 0 or p <= 0.
+ * Scratch: a fixed 64 KB array in the library's device image (one per GPU that loads the
+ * library, kept until exit), so at most 134,217,728 cells (GBCFD_ERR_ARG beyond).  The first call
+ * on each device looks up that array's device address (cudaGetSymbolAddress), so make it before
+ * any stream capture.  Every call shares the array and the previous call's contents remain there:
+ * two calls that overlap on the GPU (different streams, or devices sharing nothing else) race. */
+int gbcfd_time_step_noalloc(const double* q, int nx, int ny, int nz, const gbcfd_params* params,
+                            const double spacing[3], double* dt, void* stream);
+
 /* Message of the last error on the calling host thread ("" if none). */
 const char* gbcfd_last_error(void);
 

@@ -34,6 +34,8 @@ static int cuda_fail(cudaError_t e, const char* what) {
 
 extern "C" const char* gbcfd_last_error(void) { return g_err.c_str(); }
 
+int gbcfd::set_error(int code, const std::string& msg) { return fail(code, msg); }
+
 // ---- block descriptor ----------------------------------------------------------------------
 struct gbcfd_block_s {
   int nx, ny, nz;

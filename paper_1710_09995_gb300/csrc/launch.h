@@ -1,8 +1,13 @@
 // launch.h -- host-side launchers of the gbcfd kernels (internal, not part of the C ABI)
 #pragma once
+#include <string>
+
 #include "internal.cuh"
 
 namespace gbcfd {
+
+// record an error for gbcfd_last_error() on this host thread and return `code`
+int set_error(int code, const std::string& msg);
 
 // fused stage kernel; precision GBCFD_FP64 / GBCFD_MIXED, stage 0 = residual only
 cudaError_t launch_stage(int precision, int viscous, int stage, const CUtensorMap& tmq,

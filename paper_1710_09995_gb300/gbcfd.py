@@ -65,6 +65,8 @@ SIGNATURES = {
     "gbcfd_step": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP],
     "gbcfd_residual_norm": [_VP, _D, _VP],
     "gbcfd_get_dt": [_VP, _D, _VP],
+    "gbcfd_time_step_noalloc": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), _D, _VP,
+                                _VP],
     "gbcfd_last_error": [],
 }
 
@@ -217,3 +219,15 @@ def block_for_case(case, precision=FP64, periodic=True, device=None) -> Block:
         b.set_metrics(nodes=torch.from_numpy(np.ascontiguousarray(case.nodes)).to(b.memory.device))
     b.set_state(torch.from_numpy(np.ascontiguousarray(case.state)).to(b.memory.device))
     return b
+
+
+def time_step_noalloc(q, prm: Params, spacing, out=None, stream=None):
+    """CFL time step of a compact CUDA state q[5][nz][ny][nx] without any device allocation in the
+    library; `out` is a caller-owned one-element float64 CUDA tensor (allocated here if None)."""
+    assert q.is_cuda and q.dtype == torch.float64 and q.is_contiguous()
+    _, nz, ny, nx = q.shape
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=q.device)
+    sp = (ctypes.c_double * 3)(*spacing)
+    _check(lib().gbcfd_time_step_noalloc(_ptr(q), nx, ny, nz, ctypes.byref(prm), sp, _ptr(out), _stream(stream)))
+    return out
