@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/gbcfd.h"
+#include "gbcfd.h"
 #include "launch.h"
 
 using namespace gbcfd;

@@ -10,7 +10,7 @@
 #include <mutex>
 #include <string>
 
-#include "../../include/gbcfd.h"
+#include "gbcfd.h"
 #include "launch.h"
 
 namespace gbcfd {

@@ -95,110 +95,119 @@ __device__ __forceinline__ int rb(int s, int cy, int cx) {
   return (s * NV * BY + cy) * BX + cx;
 }
 
-// Flux through one axis-aligned face, per unit area, x/y/z components.
-//   b0..b3: ring base indices of the 4 stencil cells along the face normal (b1 = L, b2 = R)
-//   VN, VT1, VT2: primitive indices of the normal and the two tangential velocities
-//   lp1/lm1/rp1/rm1: L and R neighbours +-1 along tangent 1; lp2/lm2/rp2/rm2 along tangent 2
-template <typename T, bool VISC, int VN, int VT1, int VT2>
-__device__ __forceinline__ void face_flux(const T* __restrict__ ring, int b0, int b1, int b2, int b3,
-                                          int lp1, int lm1, int rp1, int rm1, int lp2, int lm2,
-                                          int rp2, int rm2, T ihn, T iht1, T iht2,
-                                          const Consts<T>& K, T* F) {
-  constexpr int MS = BY * BX;  // variable stride
-  constexpr int idx[5] = {0, VN, VT1, VT2, 4};
-  T L[5], R[5];
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    const int m = idx[q] * MS;
-    const T w0 = ring[b0 + m], w1 = ring[b1 + m], w2 = ring[b2 + m], w3 = ring[b3 + m];
-    const T d01 = w1 - w0, d12 = w2 - w1, d23 = w3 - w2;
-    L[q] = w1 + half_slope(d01, d12, K.lim);
-    R[q] = w2 - half_slope(d12, d23, K.lim);
-  }
-  T Fr[5];
-  roe_frame(L, R, K, Fr);
-  if (VISC) {
-    constexpr int TH = 5 * MS;  // theta = p / rho
-    T gn[4], ub[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int m = idx[q + 1] * MS;
-      gn[q] = (ring[b2 + m] - ring[b1 + m]) * ihn;
-      ub[q] = T(0.5) * (ring[b1 + m] + ring[b2 + m]);
-    }
-    gn[3] = (ring[b2 + TH] - ring[b1 + TH]) * ihn;
-    const int mn = VN * MS, m1 = VT1 * MS, m2 = VT2 * MS;
-    const T q4 = T(0.25);
-    const T dnt1 = q4 * ((ring[lp1 + mn] - ring[lm1 + mn]) + (ring[rp1 + mn] - ring[rm1 + mn])) * iht1;
-    const T dnt2 = q4 * ((ring[lp2 + mn] - ring[lm2 + mn]) + (ring[rp2 + mn] - ring[rm2 + mn])) * iht2;
-    const T d11 = q4 * ((ring[lp1 + m1] - ring[lm1 + m1]) + (ring[rp1 + m1] - ring[rm1 + m1])) * iht1;
-    const T d22 = q4 * ((ring[lp2 + m2] - ring[lm2 + m2]) + (ring[rp2 + m2] - ring[rm2 + m2])) * iht2;
-    T Fv[5];
-    viscous_frame(gn, dnt1, dnt2, d11, d22, ub, K, Fv);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) Fr[q] -= Fv[q];
-  }
-  F[0] = Fr[0];
-  F[VN] = Fr[1];
-  F[VT1] = Fr[2];
-  F[VT2] = Fr[3];
-  F[4] = Fr[4];
-}
+// Ring indices of one face's stencil: b[0..3] the 4 cells along the normal (b[1] = L, b[2] = R);
+// L and R neighbours +-1 along tangent 1 (lp1, lm1, rp1, rm1) and tangent 2 (lp2 ... rm2).
+struct FaceIdx {
+  int b[4];
+  int lp1, lm1, rp1, rm1, lp2, lm2, rp2, rm2;
+};
+
+// face frames: primitive index of the normal velocity and of tangents 1 and 2 per direction
+template <int D> struct Frame;
+template <> struct Frame<0> { static constexpr int N = 1, T1 = 2, T2 = 3; };  // x: (u | v, w)
+template <> struct Frame<1> { static constexpr int N = 2, T1 = 3, T2 = 1; };  // y: (v | w, u)
+template <> struct Frame<2> { static constexpr int N = 3, T1 = 1, T2 = 2; };  // z: (w | u, v)
 
 // x-face below box cell (cy, cx) in ring slot s; sm / sp = slots of planes k-1 / k+1
-template <typename T, bool VISC>
-__device__ __forceinline__ void xface(const T* ring, int s, int sm, int sp, int cy, int cx,
-                                      const Physics& ph, const Consts<T>& K, T* F) {
-  constexpr int NV = VISC ? 6 : 5;
+template <int NV>
+__device__ __forceinline__ FaceIdx xface_idx(int s, int sm, int sp, int cy, int cx) {
   const int b = rb<NV>(s, cy, cx);
-  face_flux<T, VISC, 1, 2, 3>(ring, b - 2, b - 1, b, b + 1,
-                              // tangent 1 = y (rows), tangent 2 = z (planes)
-                              b - 1 + BX, b - 1 - BX, b + BX, b - BX,
-                              rb<NV>(sp, cy, cx - 1), rb<NV>(sm, cy, cx - 1), rb<NV>(sp, cy, cx),
-                              rb<NV>(sm, cy, cx), T(ph.ihx), T(ph.ihy), T(ph.ihz), K, F);
+  // tangent 1 = y (rows), tangent 2 = z (planes)
+  return {{b - 2, b - 1, b, b + 1}, b - 1 + BX, b - 1 - BX, b + BX, b - BX,
+          rb<NV>(sp, cy, cx - 1), rb<NV>(sm, cy, cx - 1), rb<NV>(sp, cy, cx), rb<NV>(sm, cy, cx)};
 }
-
-template <typename T, bool VISC>
-__device__ __forceinline__ void yface(const T* ring, int s, int sm, int sp, int cy, int cx,
-                                      const Physics& ph, const Consts<T>& K, T* F) {
-  constexpr int NV = VISC ? 6 : 5;
+template <int NV>
+__device__ __forceinline__ FaceIdx yface_idx(int s, int sm, int sp, int cy, int cx) {
   const int b = rb<NV>(s, cy, cx);
-  face_flux<T, VISC, 2, 3, 1>(ring, b - 2 * BX, b - BX, b, b + BX,
-                              // tangent 1 = z (planes), tangent 2 = x (columns)
-                              rb<NV>(sp, cy - 1, cx), rb<NV>(sm, cy - 1, cx), rb<NV>(sp, cy, cx),
-                              rb<NV>(sm, cy, cx), b - BX + 1, b - BX - 1, b + 1, b - 1, T(ph.ihy),
-                              T(ph.ihz), T(ph.ihx), K, F);
+  // tangent 1 = z (planes), tangent 2 = x (columns)
+  return {{b - 2 * BX, b - BX, b, b + BX}, rb<NV>(sp, cy - 1, cx), rb<NV>(sm, cy - 1, cx),
+          rb<NV>(sp, cy, cx), rb<NV>(sm, cy, cx), b - BX + 1, b - BX - 1, b + 1, b - 1};
 }
-
 // z-face between planes k (slot s1) and k+1 (slot s2); s0 = k-1, s3 = k+2
-template <typename T, bool VISC>
-__device__ __forceinline__ void zface(const T* ring, int s0, int s1, int s2, int s3, int cy, int cx,
-                                      const Physics& ph, const Consts<T>& K, T* F) {
-  constexpr int NV = VISC ? 6 : 5;
+template <int NV>
+__device__ __forceinline__ FaceIdx zface_idx(int s0, int s1, int s2, int s3, int cy, int cx) {
   const int b1 = rb<NV>(s1, cy, cx), b2 = rb<NV>(s2, cy, cx);
-  face_flux<T, VISC, 3, 1, 2>(ring, rb<NV>(s0, cy, cx), b1, b2, rb<NV>(s3, cy, cx),
-                              // tangent 1 = x (columns), tangent 2 = y (rows)
-                              b1 + 1, b1 - 1, b2 + 1, b2 - 1, b1 + BX, b1 - BX, b2 + BX, b2 - BX,
-                              T(ph.ihz), T(ph.ihx), T(ph.ihy), K, F);
+  // tangent 1 = x (columns), tangent 2 = y (rows)
+  return {{rb<NV>(s0, cy, cx), b1, b2, rb<NV>(s3, cy, cx)}, b1 + 1, b1 - 1, b2 + 1, b2 - 1,
+          b1 + BX, b1 - BX, b2 + BX, b2 - BX};
+}
+
+// the per-face arithmetic once the stencil is in registers: w[cell][frame variable]
+template <typename V, bool VISC>
+__device__ __forceinline__ void flux_core(const V (&w)[4][5], const V* gn, V dnt1, V dnt2, V d11, V d22,
+                                          const V* ub, const Consts<V>& K, V* Fr) {
+  V L[5], R[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) muscl(w[0][q], w[1][q], w[2][q], w[3][q], K.lim, L[q], R[q]);
+  roe_frame(L, R, K, Fr);
+  if constexpr (VISC) {
+    V Fv[5];
+    viscous_frame(gn, dnt1, dnt2, d11, d22, ub, K, Fv);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Fr[q] = Fr[q] - Fv[q];
+  }
+}
+
+// stencil gather of one face, then flux_core.  ih = inverse spacings along (normal, tangent 1,
+// tangent 2).
+template <typename T, bool VISC, int D>
+__device__ __forceinline__ void face_flux(const T* __restrict__ ring, const FaceIdx& f, const T* ih,
+                                          const Consts<T>& K, T* F) {
+  constexpr int MS = BY * BX;
+  using Fr_ = Frame<D>;
+  constexpr int idx[5] = {0, Fr_::N, Fr_::T1, Fr_::T2, 4};
+  T w[4][5];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) w[c][q] = ring[f.b[c] + idx[q] * MS];
+  T gn[4], ub[3], dnt1 = T(0), dnt2 = T(0), d11 = T(0), d22 = T(0);
+  if constexpr (VISC) {
+    const int L = f.b[1], R = f.b[2];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      gn[q] = (w[2][q + 1] - w[1][q + 1]) * ih[0];
+      ub[q] = T(0.5) * (w[1][q + 1] + w[2][q + 1]);
+    }
+    constexpr int TH = 5 * MS, mn = Fr_::N * MS, m1 = Fr_::T1 * MS, m2 = Fr_::T2 * MS;
+    gn[3] = (ring[R + TH] - ring[L + TH]) * ih[0];
+    const T q4 = T(0.25);
+    dnt1 = q4 * ((ring[f.lp1 + mn] - ring[f.lm1 + mn]) + (ring[f.rp1 + mn] - ring[f.rm1 + mn])) * ih[1];
+    dnt2 = q4 * ((ring[f.lp2 + mn] - ring[f.lm2 + mn]) + (ring[f.rp2 + mn] - ring[f.rm2 + mn])) * ih[2];
+    d11 = q4 * ((ring[f.lp1 + m1] - ring[f.lm1 + m1]) + (ring[f.rp1 + m1] - ring[f.rm1 + m1])) * ih[1];
+    d22 = q4 * ((ring[f.lp2 + m2] - ring[f.lm2 + m2]) + (ring[f.rp2 + m2] - ring[f.rm2 + m2])) * ih[2];
+  }
+  T Fr[5];
+  flux_core<T, VISC>(w, gn, dnt1, dnt2, d11, d22, ub, K, Fr);
+  F[0] = Fr[0];
+  F[Fr_::N] = Fr[1];
+  F[Fr_::T1] = Fr[2];
+  F[Fr_::T2] = Fr[3];
+  F[4] = Fr[4];
 }
 
 // spectral-radius rate of one cell: sum over directions of the convective radius (plus 4x the
 // viscous one) divided by the volume, i.e. the inverse of the cell's stable step / CFL
 template <typename T>
 __device__ __forceinline__ T cell_rate(T r, T u, T v, T w, T p, const Physics& ph) {
-  using Fm = Fast<T>;
-  const T c = Fm::sqrt_(T(ph.gamma) * p * Fm::rcp(r));
-  T rate = (Fm::ab(u) + c) * T(ph.ihx) + (Fm::ab(v) + c) * T(ph.ihy) + (Fm::ab(w) + c) * T(ph.ihz);
+  using O = VM<T>;
+  const T ir = O::rcp(r);
+  const T c2 = T(ph.gamma) * p * ir;
+  const T c = c2 * O::rsqrt(c2);
+  T rate = (O::ab(u) + c) * T(ph.ihx) + (O::ab(v) + c) * T(ph.ihy) + (O::ab(w) + c) * T(ph.ihz);
   if (ph.viscous) {
     const double f = fmax(4.0 / 3.0, ph.gamma / ph.Pr);
     const T s2 = T(ph.ihx * ph.ihx + ph.ihy * ph.ihy + ph.ihz * ph.ihz);
-    rate += T(4.0 * f * ph.mu) * Fm::rcp(r) * s2;
+    rate += T(4.0 * f * ph.mu) * ir * s2;
   }
   return rate;
 }
 
 // ---- the kernel ------------------------------------------------------------------------------
 // STAGE 0: residual only (R to P.rout); 1..3: Runge-Kutta stages
+// registers: the register file is split over the SM's four sub-partitions (16K each) and warps
+// are spread round-robin, so two 9-warp CTAs (5 warps on one sub-partition) allow 96 registers
+// per thread on the mixed path, one CTA (3 warps) 168 on the FP64 path
 template <typename T, bool VISC, int STAGE>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     stage_kernel(const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmd,
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
   using PL = Plan<T, VISC>;
   constexpr int NV = PL::NV;
   constexpr int MS = BY * BX;
-  using Fm = Fast<T>;
+  using Fm = VM<T>;
 
   extern __shared__ __align__(128) unsigned char smem[];
   T* ring = reinterpret_cast<T*>(smem + PL::ring);
@@ -222,14 +231,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Geometry& g = P.g;
   const Physics& ph = P.ph;
-  Consts<T> K;
-  K.gm1 = T(ph.gamma - 1.0);
-  K.ggm1 = T(ph.gamma / (ph.gamma - 1.0));
-  K.eps = T(ph.eps);
-  K.mu = T(VISC ? ph.mu : 0.0);
-  K.kappa = T(VISC ? ph.mu * ph.gamma / ((ph.gamma - 1.0) * ph.Pr) : 0.0);
-  K.lim = ph.limiter;
-  const T gm1 = K.gm1;
+  const Consts<T> K = make_consts<T>(ph.gamma, ph.eps, VISC ? ph.mu : 0.0, ph.Pr, ph.limiter);
+  const T gm1 = T(ph.gamma - 1.0);
+  // inverse spacings along (normal, tangent 1, tangent 2) of x-, y- and z-faces
+  const T ihX[3] = {T(ph.ihx), T(ph.ihy), T(ph.ihz)};
+  const T ihY[3] = {T(ph.ihy), T(ph.ihz), T(ph.ihx)};
+  const T ihZ[3] = {T(ph.ihz), T(ph.ihx), T(ph.ihy)};
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
@@ -325,7 +332,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     const bool live = owner && ci < g.nx && cj < g.ny;
     const int ocy = warp + HALO, ocx = lane + HALO;
     T fzl[5], fzu[5];
-    if (owner) zface<T, VISC>(ring, (k0 - 2) & 3, (k0 - 1) & 3, k0 & 3, (k0 + 1) & 3, ocy, ocx, ph, K, fzl);
+    if (owner)
+      face_flux<T, VISC, 2>(ring, zface_idx<NV>((k0 - 2) & 3, (k0 - 1) & 3, k0 & 3, (k0 + 1) & 3, ocy, ocx), ihZ,
+                            K, fzl);
     __syncthreads();  // the first consume below overwrites plane k0-2, read by the z-face above
 
     for (int k = k0; k < k1; ++k) {
@@ -345,23 +354,27 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
       }
       const int sk = k & 3, sm = (k - 1) & 3, sp = (k + 1) & 3, s2 = (k + 2) & 3;
       if (owner) {
-        T F[5];
-        xface<T, VISC>(ring, sk, sm, sp, ocy, ocx, ph, K, F);
+        T Fa[5], Fb[5];
+        const FaceIdx ix = xface_idx<NV>(sk, sm, sp, ocy, ocx), iy = yface_idx<NV>(sk, sm, sp, ocy, ocx);
+        face_flux<T, VISC, 0>(ring, ix, ihX, K, Fa);
+        face_flux<T, VISC, 1>(ring, iy, ihY, K, Fb);
 #pragma unroll
-        for (int m = 0; m < 5; ++m) fx[(m * TY + warp) * (TX + 1) + lane] = F[m];
-        yface<T, VISC>(ring, sk, sm, sp, ocy, ocx, ph, K, F);
+        for (int m = 0; m < 5; ++m) fx[(m * TY + warp) * (TX + 1) + lane] = Fa[m];
 #pragma unroll
-        for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + warp) * TX + lane] = F[m];
-        zface<T, VISC>(ring, sm, sk, sp, s2, ocy, ocx, ph, K, fzu);
+        for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + warp) * TX + lane] = Fb[m];
+        face_flux<T, VISC, 2>(ring, zface_idx<NV>(sm, sk, sp, s2, ocy, ocx), ihZ, K, fzu);
       } else {
-        T F[5];
-        yface<T, VISC>(ring, sk, sm, sp, TY + HALO, lane + HALO, ph, K, F);
+        // the tile's upper y-faces (all lanes) and upper x-faces (lanes < TY)
+        T Fa[5], Fb[5];
+        const FaceIdx iy = yface_idx<NV>(sk, sm, sp, TY + HALO, lane + HALO);
+        const FaceIdx ix = xface_idx<NV>(sk, sm, sp, (lane % TY) + HALO, TX + HALO);
+        face_flux<T, VISC, 1>(ring, iy, ihY, K, Fa);
+        if (lane < TY) face_flux<T, VISC, 0>(ring, ix, ihX, K, Fb);
 #pragma unroll
-        for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + TY) * TX + lane] = F[m];
+        for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + TY) * TX + lane] = Fa[m];
         if (lane < TY) {
-          xface<T, VISC>(ring, sk, sm, sp, lane + HALO, TX + HALO, ph, K, F);
 #pragma unroll
-          for (int m = 0; m < 5; ++m) fx[(m * TY + lane) * (TX + 1) + TX] = F[m];
+          for (int m = 0; m < 5; ++m) fx[(m * TY + lane) * (TX + 1) + TX] = Fb[m];
         }
       }
       __syncthreads();
@@ -394,7 +407,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
             const double uu = out[1] * ir, vv = out[2] * ir, ww = out[3] * ir;
             const double pp = (ph.gamma - 1.0) * (out[4] - 0.5 * out[0] * (uu * uu + vv * vv + ww * ww));
             if (!(out[0] > 0.0 && pp > 0.0)) bad = true;
-            rate_max = Fm::mx(rate_max, T(cell_rate<double>(out[0], uu, vv, ww, pp, ph)));
+            rate_max = fmax(rate_max, T(cell_rate<double>(out[0], uu, vv, ww, pp, ph)));
           }
         } else {
           float inc[5];
@@ -411,16 +424,16 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
               const float d = (2.0f / 3.0f) * (dp_[m] + inc[m]);
-              const double qnew = qn_[m] + double(d);
+              const double qnew = qn_[m] + f32_to_f64_bits(d);
               P.qout[m * g.field + o] = qnew;
-              qf[m] = float(qnew);
+              qf[m] = f64_to_f32_bits(qnew);
               P.sout[m * g.fieldf + of] = qf[m];
             }
-            const float ir = Fast<float>::rcp(qf[0]);
+            const float ir = VM<float>::rcp(qf[0]);
             const float uu = qf[1] * ir, vv = qf[2] * ir, ww = qf[3] * ir;
             const float pp = float(ph.gamma - 1.0) * (qf[4] - 0.5f * qf[0] * (uu * uu + vv * vv + ww * ww));
             if (!(qf[0] > 0.0f && pp > 0.0f)) bad = true;
-            rate_max = Fm::mx(rate_max, T(cell_rate<float>(qf[0], uu, vv, ww, pp, ph)));
+            rate_max = fmax(rate_max, T(cell_rate<float>(qf[0], uu, vv, ww, pp, ph)));
           }
         }
         if constexpr (STAGE == 1) {
@@ -452,56 +465,57 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     }
   }
   if (bad) atomicOr(&P.ctrl->flag, FLAG_NONPHYSICAL);
-  if constexpr (STAGE != 1 && STAGE != 3) return;
+  if constexpr (STAGE == 1 || STAGE == 3) {
 
-  // ---- per-CTA partials, then the last CTA reduces them in a fixed order ---------------------
-  double part[6];
-#pragma unroll
-  for (int m = 0; m < 5; ++m) part[m] = MIXED ? double(nsum[m]) - double(ncomp[m]) : nacc[m];
-  part[5] = double(rate_max);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int m = 0; m < 5; ++m) part[m] += __shfl_xor_sync(0xffffffffu, part[m], off);
-    part[5] = fmax(part[5], __shfl_xor_sync(0xffffffffu, part[5], off));
-  }
-  if (lane == 0)
-    for (int m = 0; m < 6; ++m) red[warp * NPART + m] = part[m];
-  __syncthreads();
-  if (tid == 0) {
-    double s[6] = {0, 0, 0, 0, 0, 0};
-    for (int w = 0; w < NWARP; ++w) {
-      for (int m = 0; m < 5; ++m) s[m] += red[w * NPART + m];
-      s[5] = fmax(s[5], red[w * NPART + 5]);
+    // ---- per-CTA partials, then the last CTA reduces them in a fixed order ---------------------
+    double part[6];
+  #pragma unroll
+    for (int m = 0; m < 5; ++m) part[m] = MIXED ? double(nsum[m]) - double(ncomp[m]) : nacc[m];
+    part[5] = double(rate_max);
+  #pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+  #pragma unroll
+      for (int m = 0; m < 5; ++m) part[m] += __shfl_xor_sync(0xffffffffu, part[m], off);
+      part[5] = fmax(part[5], __shfl_xor_sync(0xffffffffu, part[5], off));
     }
-    for (int m = 0; m < 6; ++m) P.partial[(size_t)blockIdx.x * NPART + m] = s[m];
+    if (lane == 0)
+      for (int m = 0; m < 6; ++m) red[warp * NPART + m] = part[m];
+    __syncthreads();
+    if (tid == 0) {
+      double s[6] = {0, 0, 0, 0, 0, 0};
+      for (int w = 0; w < NWARP; ++w) {
+        for (int m = 0; m < 5; ++m) s[m] += red[w * NPART + m];
+        s[5] = fmax(s[5], red[w * NPART + 5]);
+      }
+      for (int m = 0; m < 6; ++m) P.partial[(size_t)blockIdx.x * NPART + m] = s[m];
+      __threadfence();
+      const unsigned prev = atomicAdd(&P.ctrl->counter, 1u);
+      *slast = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!*slast || warp != 0) return;
     __threadfence();
-    const unsigned prev = atomicAdd(&P.ctrl->counter, 1u);
-    *slast = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!*slast || warp != 0) return;
-  __threadfence();
-  double s[6] = {0, 0, 0, 0, 0, 0};
-  for (int c = lane; c < (int)gridDim.x; c += 32) {
-    for (int m = 0; m < 5; ++m) s[m] += __ldcg(P.partial + (size_t)c * NPART + m);
-    s[5] = fmax(s[5], __ldcg(P.partial + (size_t)c * NPART + 5));
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int m = 0; m < 5; ++m) s[m] += __shfl_xor_sync(0xffffffffu, s[m], off);
-    s[5] = fmax(s[5], __shfl_xor_sync(0xffffffffu, s[5], off));
-  }
-  if (lane == 0) {
-    const double n = (double)g.nx * g.ny * g.nz;
-    if (STAGE == 1)
-      for (int m = 0; m < 5; ++m) P.ctrl->norms[m] = sqrt(s[m] / n);
-    if (STAGE == 3) {
-      P.ctrl->rate = s[5];
-      P.ctrl->dt = ph.cfl / s[5];
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int c = lane; c < (int)gridDim.x; c += 32) {
+      for (int m = 0; m < 5; ++m) s[m] += __ldcg(P.partial + (size_t)c * NPART + m);
+      s[5] = fmax(s[5], __ldcg(P.partial + (size_t)c * NPART + 5));
     }
-    P.ctrl->counter = 0u;
+  #pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+  #pragma unroll
+      for (int m = 0; m < 5; ++m) s[m] += __shfl_xor_sync(0xffffffffu, s[m], off);
+      s[5] = fmax(s[5], __shfl_xor_sync(0xffffffffu, s[5], off));
+    }
+    if (lane == 0) {
+      const double n = (double)g.nx * g.ny * g.nz;
+      if (STAGE == 1)
+        for (int m = 0; m < 5; ++m) P.ctrl->norms[m] = sqrt(s[m] / n);
+      if (STAGE == 3) {
+        P.ctrl->rate = s[5];
+        P.ctrl->dt = ph.cfl / s[5];
+      }
+      P.ctrl->counter = 0u;
+    }
   }
 }
 
