@@ -58,7 +58,13 @@ struct gbcfd_block_s {
   gbcfd_block nbr[6];
   CUtensorMap tm_q[3];  // FP64: maps of Qn, Q1, Q2.  mixed: maps of the shadows SA, SB
   CUtensorMap tm_d[2];
+  CUtensorMap tm_m;     // metric planes (10 fields)
+  int curvi;            // metrics from nodes (curvilinear) rather than a uniform spacing
+  int metrics_dirty;    // metric halos not exchanged since the metrics were set
 };
+
+static int prepare_metrics(const gbcfd_block* blocks, int n, cudaStream_t s);
+static int init_rate(gbcfd_block b, cudaStream_t s);
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -92,8 +98,9 @@ static bool valid_params(const gbcfd_params* p, std::string& why) {
 }
 
 // stage grid: resident CTAs on every SM, capped by the number of tile-planes
-static int stage_grid(const Geometry& g, int precision, int viscous, int nsm) {
-  const int occ = precision == GBCFD_MIXED ? stage_occupancy_f32(viscous) : stage_occupancy_f64(viscous);
+static int stage_grid(const Geometry& g, int precision, int viscous, int curvi, int nsm) {
+  const int occ = precision == GBCFD_MIXED ? (curvi ? stage_occupancy_f32c(viscous) : stage_occupancy_f32(viscous))
+                                           : (curvi ? stage_occupancy_f64c(viscous) : stage_occupancy_f64(viscous));
   const long long units = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY) * g.nz;
   long long grid = (long long)nsm * occ;
   if (grid > units) grid = units;
@@ -153,17 +160,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// 4D map (x, y, z, variable) over a padded field; box = one tile plane with its halo, all 5
+// 4D map (x, y, z, variable) over a padded field; box = one tile plane with its halo, all nvar
 // variables.  x extent is the padded width nx + 4, so a box past it is zero-filled.
-static int make_map(CUtensorMap* m, void* base, const Geometry& g, int elem) {
+static int make_map(CUtensorMap* m, void* base, const Geometry& g, int elem, int nvar = 5) {
   auto enc = get_encode();
   if (!enc) return fail(GBCFD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const int pitch = elem == 8 ? g.px : g.pxf;
   cuuint64_t dims[4] = {(cuuint64_t)(g.nx + 2 * HALO), (cuuint64_t)(g.ny + 2 * HALO),
-                        (cuuint64_t)(g.nz + 2 * HALO), 5};
+                        (cuuint64_t)(g.nz + 2 * HALO), (cuuint64_t)nvar};
   cuuint64_t strides[3] = {(cuuint64_t)pitch * elem, (cuuint64_t)pitch * elem * (g.ny + 2 * HALO),
                            (cuuint64_t)pitch * elem * (g.ny + 2 * HALO) * (g.nz + 2 * HALO)};
-  cuuint32_t box[4] = {(cuuint32_t)BX, (cuuint32_t)BY, 1, 5};
+  cuuint32_t box[4] = {(cuuint32_t)BX, (cuuint32_t)BY, 1, (cuuint32_t)nvar};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = enc(m, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base,
                    dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -249,7 +256,9 @@ extern "C" int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* pa
   b->next_stage = 1;
   b->spacing[0] = b->spacing[1] = b->spacing[2] = 1.0;
   for (int f = 0; f < 6; ++f) b->nbr[f] = nullptr;
-  b->grid = stage_grid(g, params->precision, params->viscous, nsm);
+  b->curvi = 0;
+  b->metrics_dirty = 0;
+  b->grid = stage_grid(g, params->precision, params->viscous, 0, nsm);
   if ((size_t)b->grid > c.partial_n) b->grid = (int)c.partial_n;
 
   int r = GBCFD_OK;
@@ -261,6 +270,7 @@ extern "C" int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* pa
     for (int i = 0; i < 2 && !r; ++i) r = make_map(&b->tm_d[i], b->d[i], g, 4);
     if (!r) b->tm_q[2] = b->tm_q[0];
   }
+  if (!r) r = make_map(&b->tm_m, b->metrics, g, params->precision == GBCFD_MIXED ? 4 : 8, 10);
   if (r) { delete b; return r; }
   cudaError_t e = cudaMemset(b->ctrl, 0, sizeof(DevCtrl));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -291,12 +301,27 @@ extern "C" int gbcfd_connect(gbcfd_block b, int face, gbcfd_block nbr) {
 }
 
 extern "C" int gbcfd_set_metrics(gbcfd_block b, const double* nodes, const double spacing[3], void* stream) {
-  (void)stream;
   if (!b) return fail(GBCFD_ERR_ARG, "block is NULL");
-  if (nodes) return fail(GBCFD_ERR_ARG, "curvilinear node input is not available in this build");
-  if (!spacing || !(spacing[0] > 0 && spacing[1] > 0 && spacing[2] > 0))
-    return fail(GBCFD_ERR_ARG, "spacing must be three positive cell sizes");
-  for (int a = 0; a < 3; ++a) b->spacing[a] = spacing[a];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!nodes) {
+    if (!spacing || !(spacing[0] > 0 && spacing[1] > 0 && spacing[2] > 0))
+      return fail(GBCFD_ERR_ARG, "spacing must be three positive cell sizes");
+    for (int a = 0; a < 3; ++a) b->spacing[a] = spacing[a];
+    if (b->curvi) {
+      b->curvi = 0;
+      b->metrics_dirty = 0;
+      b->grid = stage_grid(b->g, b->p.precision, b->p.viscous, 0, b->nsm);
+    }
+    return GBCFD_OK;
+  }
+  cudaPointerAttributes attr;
+  CK(cudaPointerGetAttributes(&attr, nodes));
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return fail(GBCFD_ERR_ARG, "nodes must be device memory");
+  CK(launch_metrics(b->g, nodes, b->metrics, b->p.precision == GBCFD_MIXED ? 4 : 8, s));
+  b->curvi = 1;
+  b->metrics_dirty = 1;
+  b->grid = stage_grid(b->g, b->p.precision, b->p.viscous, 1, b->nsm);
   return GBCFD_OK;
 }
 
@@ -327,10 +352,10 @@ extern "C" int gbcfd_set_state(gbcfd_block b, const double* q, void* stream) {
     src = reinterpret_cast<const double*>(b->staging);
   }
   CK(launch_scatter(b->g, src, state_ptr(b), b->p.precision == GBCFD_MIXED ? b->sh[b->cur] : nullptr, s));
-  CK(launch_init_rate(b->g, physics_of(b), state_ptr(b), b->ctrl, b->partial, 4 * b->nsm,
-                      b->p.precision == GBCFD_MIXED, s));
   b->has_state = 1;
   b->next_stage = 1;
+  if (b->metrics_dirty) return prepare_metrics(&b, 1, s);  // also evaluates the time step
+  return init_rate(b, s);
   return GBCFD_OK;
 }
 
@@ -422,6 +447,35 @@ static int exchange(const gbcfd_block* blocks, int n, int field, bool allow_exte
   return GBCFD_OK;
 }
 
+// metric halos and, for blocks holding a state, the time step evaluated on the full metrics;
+// run before anything reads metrics after gbcfd_set_metrics
+static int init_rate(gbcfd_block b, cudaStream_t s) {
+  if (b->curvi)
+    CK(launch_init_rate_curvi(b->g, physics_of(b), state_ptr(b), b->metrics, b->ctrl, b->partial, 4 * b->nsm,
+                              b->p.precision == GBCFD_MIXED, s));
+  else
+    CK(launch_init_rate(b->g, physics_of(b), state_ptr(b), b->ctrl, b->partial, 4 * b->nsm,
+                        b->p.precision == GBCFD_MIXED, s));
+  return GBCFD_OK;
+}
+
+static int prepare_metrics(const gbcfd_block* blocks, int n, cudaStream_t s) {
+  bool dirty = false;
+  for (int i = 0; i < n; ++i) dirty = dirty || blocks[i]->metrics_dirty;
+  if (!dirty) return GBCFD_OK;
+  int rc = exchange(blocks, n, F_METRICS, true, s);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    if (!blocks[i]->metrics_dirty) continue;
+    blocks[i]->metrics_dirty = 0;
+    if (blocks[i]->has_state) {
+      rc = init_rate(blocks[i], s);
+      if (rc) return rc;
+    }
+  }
+  return GBCFD_OK;
+}
+
 static int check_blocks(const gbcfd_block* blocks, int n) {
   if (!blocks || n < 1) return fail(GBCFD_ERR_ARG, "empty block list");
   if (n > MAX_GROUP) return fail(GBCFD_ERR_ARG, "too many blocks in one call");
@@ -442,6 +496,8 @@ static int input_field(gbcfd_block b) {
 
 extern "C" int gbcfd_exchange_halos(const gbcfd_block* blocks, int n, void* stream) {
   int rc = check_blocks(blocks, n);
+  if (rc) return rc;
+  rc = prepare_metrics(blocks, n, static_cast<cudaStream_t>(stream));
   if (rc) return rc;
   return exchange(blocks, n, input_field(blocks[0]), true, static_cast<cudaStream_t>(stream));
 }
@@ -478,7 +534,8 @@ static int run_stage(gbcfd_block b, int stage, double* rout, cudaStream_t s) {
       case 3: P.dprev = b->d[1]; P.qout = b->q[1 - c]; P.sout = b->sh[1 - c]; tmd = &b->tm_d[1]; break;
     }
   }
-  CK(launch_stage(b->p.precision, b->p.viscous, stage, *tmq, *tmd, P, b->grid, s));
+  const StageMaps maps = {tmq, tmd, &b->tm_m};
+  CK(launch_stage(b->p.precision, b->p.viscous, b->curvi, stage, maps, P, b->grid, s));
   if (stage == 3 && b->p.precision == GBCFD_MIXED) b->cur = 1 - b->cur;
   return GBCFD_OK;
 }
@@ -510,6 +567,8 @@ extern "C" int gbcfd_step(const gbcfd_block* blocks, int n, int nsteps, void* st
   if (nsteps < 0) return fail(GBCFD_ERR_ARG, "nsteps must be >= 0");
   if (blocks[0]->next_stage != 1) return fail(GBCFD_ERR_STATE, "a step was left between stages");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = prepare_metrics(blocks, n, s);
+  if (rc) return rc;
   const int fields[3] = {F_STATE, F_STAGE1, F_STAGE2};
   for (int it = 0; it < nsteps; ++it) {
     for (int st = 1; st <= 3; ++st) {
@@ -530,6 +589,8 @@ extern "C" int gbcfd_compute_residual(gbcfd_block b, double* r, void* stream) {
   if (rc) return rc;
   if (!dev) return fail(GBCFD_ERR_ARG, "r must be device memory");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = prepare_metrics(&b, 1, s);
+  if (rc) return rc;
   rc = exchange(&b, 1, F_STATE, true, s);
   if (rc) return rc;
   return run_stage(b, 0, r, s);
@@ -569,9 +630,10 @@ extern "C" int gbcfd_get_dt(gbcfd_block b, double* dt, void* stream) {
 
 // ---- dispatch ----------------------------------------------------------------------------
 namespace gbcfd {
-cudaError_t launch_stage(int precision, int viscous, int stage, const CUtensorMap& tmq, const CUtensorMap& tmd,
+cudaError_t launch_stage(int precision, int viscous, int curvi, int stage, const StageMaps& M,
                          const StageParams& P, int grid, cudaStream_t s) {
-  if (precision == GBCFD_MIXED) return launch_stage_f32(viscous, stage, tmq, tmd, P, grid, s);
-  return launch_stage_f64(viscous, stage, tmq, tmd, P, grid, s);
+  if (precision == GBCFD_MIXED)
+    return curvi ? launch_stage_f32c(viscous, stage, M, P, grid, s) : launch_stage_f32(viscous, stage, M, P, grid, s);
+  return curvi ? launch_stage_f64c(viscous, stage, M, P, grid, s) : launch_stage_f64(viscous, stage, M, P, grid, s);
 }
 }  // namespace gbcfd

@@ -184,6 +184,141 @@ cudaError_t launch_init_rate(const Geometry& g, const Physics& ph, const double*
   return cudaGetLastError();
 }
 
+// ---- curvilinear metrics -------------------------------------------------------------------
+// Per interior cell: the area vectors of its lower xi, eta, zeta faces, S = 1/2 (d1 x d2) over
+// the face diagonals, oriented towards +xi, +eta, +zeta, and the volume by the divergence
+// theorem, V = 1/3 sum over the six faces of (face centroid - first corner) . outward S.
+// nodes: x[3][nz+1][ny+1][nx+1] (f64).  M: 10 padded fields, f64 or f32 (elem bytes).
+__device__ __forceinline__ void vsub(const double* a, const double* b, double* c) {
+  c[0] = a[0] - b[0]; c[1] = a[1] - b[1]; c[2] = a[2] - b[2];
+}
+__device__ __forceinline__ void half_cross(const double* a, const double* b, double* c) {
+  c[0] = 0.5 * (a[1] * b[2] - a[2] * b[1]);
+  c[1] = 0.5 * (a[2] * b[0] - a[0] * b[2]);
+  c[2] = 0.5 * (a[0] * b[1] - a[1] * b[0]);
+}
+
+__global__ void metrics_kernel(Geometry g, const double* __restrict__ X, void* M, int elem) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long nn = (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.nx);
+    const long long r = c / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    double p[8][3];  // corner (di, dj, dk) at index di + 2 dj + 4 dk
+    for (int q = 0; q < 8; ++q) {
+      const long long o = ((long long)(k + (q >> 2)) * (g.ny + 1) + (j + ((q >> 1) & 1))) * (g.nx + 1) + i + (q & 1);
+      p[q][0] = X[o]; p[q][1] = X[nn + o]; p[q][2] = X[2 * nn + o];
+    }
+    // quadrilateral a, b, c, d in counter-clockwise order seen from the side S points to:
+    // S = 1/2 (c - a) x (d - b)
+    auto face = [&](int a, int b, int cc, int d, double* S, double* cen) {
+      double d1[3], d2[3];
+      vsub(p[cc], p[a], d1);
+      vsub(p[d], p[b], d2);
+      half_cross(d1, d2, S);
+      for (int x = 0; x < 3; ++x) cen[x] = 0.25 * (p[a][x] + p[b][x] + p[cc][x] + p[d][x]) - p[0][x];
+    };
+    double S[6][3], C[6][3];
+    face(0, 2, 6, 4, S[0], C[0]);  // lower xi   (eta, zeta plane at di = 0)
+    face(1, 3, 7, 5, S[1], C[1]);  // upper xi
+    face(0, 4, 5, 1, S[2], C[2]);  // lower eta  (zeta, xi plane at dj = 0)
+    face(2, 6, 7, 3, S[3], C[3]);  // upper eta
+    face(0, 1, 3, 2, S[4], C[4]);  // lower zeta (xi, eta plane at dk = 0)
+    face(4, 5, 7, 6, S[5], C[5]);  // upper zeta
+    double vol = 0.0;
+    for (int f = 0; f < 6; ++f) {
+      const double sgn = (f & 1) ? 1.0 : -1.0;
+      vol += sgn * (C[f][0] * S[f][0] + C[f][1] * S[f][1] + C[f][2] * S[f][2]);
+    }
+    vol *= 1.0 / 3.0;
+    const double out[10] = {S[0][0], S[0][1], S[0][2], S[2][0], S[2][1], S[2][2],
+                            S[4][0], S[4][1], S[4][2], vol};
+    if (elem == 8) {
+      double* m = static_cast<double*>(M);
+      const long long o = gidx(g, i, j, k);
+      for (int v = 0; v < 10; ++v) m[v * g.field + o] = out[v];
+    } else {
+      float* m = static_cast<float*>(M);
+      const long long o = gidxf(g, i, j, k);
+      for (int v = 0; v < 10; ++v) m[v * g.fieldf + o] = float(out[v]);
+    }
+  }
+}
+
+cudaError_t launch_metrics(const Geometry& g, const double* nodes, void* M, int elem, cudaStream_t s) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  metrics_kernel<<<grid_for(n, 128), 128, 0, s>>>(g, nodes, M, elem);
+  return cudaGetLastError();
+}
+
+// spectral-radius rate on a curvilinear grid: sum over directions of |u.Sb| + c |Sb| (+ 4 max(4/3,
+// gamma/Pr) mu/rho |Sb|^2 / V), divided by V, with Sb the mean of a cell's two faces in a direction
+template <typename T>
+__global__ void init_rate_curvi_kernel(Geometry g, Physics ph, const double* __restrict__ q,
+                                       const T* __restrict__ M, DevCtrl* ctrl, double* partial) {
+  __shared__ double wmax[32];
+  __shared__ int last;
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long fm = sizeof(T) == 8 ? g.field : g.fieldf;
+  const double f = fmax(4.0 / 3.0, ph.gamma / ph.Pr);
+  double best = 0.0;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.nx);
+    const long long r = c / g.nx;
+    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    const long long o = gidx(g, i, j, k);
+    const long long om = sizeof(T) == 8 ? o : gidxf(g, i, j, k);
+    const long long up[3] = {1, sizeof(T) == 8 ? g.px : g.pxf, sizeof(T) == 8 ? g.plane : g.planef};
+    const T rho = T(q[o]), ir = T(1) / rho;
+    const T u = T(q[g.field + o]) * ir, v = T(q[2 * g.field + o]) * ir, w = T(q[3 * g.field + o]) * ir;
+    const T p = T(ph.gamma - 1.0) * (T(q[4 * g.field + o]) - T(0.5) * rho * (u * u + v * v + w * w));
+    const T a = sqrt(T(ph.gamma) * p * ir);
+    const T vol = M[9 * fm + om], iv = T(1) / vol;
+    T rate = T(0);
+    for (int d = 0; d < 3; ++d) {
+      T sb[3];
+      for (int x = 0; x < 3; ++x) sb[x] = T(0.5) * (M[(3 * d + x) * fm + om] + M[(3 * d + x) * fm + om + up[d]]);
+      const T s2 = sb[0] * sb[0] + sb[1] * sb[1] + sb[2] * sb[2];
+      T lam = fabs(u * sb[0] + v * sb[1] + w * sb[2]) + a * sqrt(s2);
+      if (ph.viscous) lam += T(4.0 * f * ph.mu) * ir * s2 * iv;
+      rate += lam;
+    }
+    rate *= iv;
+    if (!(rho > T(0) && p > T(0))) atomicOr(&ctrl->flag, FLAG_NONPHYSICAL);
+    best = fmax(best, double(rate));
+  }
+  for (int off = 16; off > 0; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
+    partial[(size_t)blockIdx.x * NPART + 5] = m;
+    __threadfence();
+    last = (atomicAdd(&ctrl->counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double m = 0.0;
+  for (unsigned b = 0; b < gridDim.x; ++b) m = fmax(m, __ldcg(partial + (size_t)b * NPART + 5));
+  ctrl->rate = m;
+  ctrl->dt = ph.cfl / m;
+  ctrl->counter = 0u;
+}
+
+cudaError_t launch_init_rate_curvi(const Geometry& g, const Physics& ph, const double* q, const void* M,
+                                   DevCtrl* ctrl, double* partial, int grid, int mixed, cudaStream_t s) {
+  if (mixed)
+    init_rate_curvi_kernel<float><<<grid, 256, 0, s>>>(g, ph, q, static_cast<const float*>(M), ctrl, partial);
+  else
+    init_rate_curvi_kernel<double><<<grid, 256, 0, s>>>(g, ph, q, static_cast<const double*>(M), ctrl, partial);
+  return cudaGetLastError();
+}
+
 struct CtrlList {
   DevCtrl* c[MAX_GROUP];
 };

@@ -9,21 +9,25 @@ namespace gbcfd {
 // record an error for gbcfd_last_error() on this host thread and return `code`
 int set_error(int code, const std::string& msg);
 
-// fused stage kernel; precision GBCFD_FP64 / GBCFD_MIXED, stage 0 = residual only
-cudaError_t launch_stage(int precision, int viscous, int stage, const CUtensorMap& tmq,
-                         const CUtensorMap& tmd, const StageParams& P, int grid, cudaStream_t s);
-// dynamic shared memory of one stage CTA and resident CTAs per SM
-size_t stage_smem_bytes(int precision, int viscous);
-int stage_ctas_per_sm(int precision, int viscous);
+// tensor maps of one stage launch: staged state, staged increment, metric planes
+struct StageMaps {
+  const CUtensorMap* q;
+  const CUtensorMap* d;
+  const CUtensorMap* m;
+};
 
-cudaError_t launch_stage_f64(int viscous, int stage, const CUtensorMap& tmq, const CUtensorMap& tmd,
-                             const StageParams& P, int grid, cudaStream_t s);
-cudaError_t launch_stage_f32(int viscous, int stage, const CUtensorMap& tmq, const CUtensorMap& tmd,
-                             const StageParams& P, int grid, cudaStream_t s);
-size_t stage_smem_f64(int viscous);
-size_t stage_smem_f32(int viscous);
+// fused stage kernel; precision GBCFD_FP64 / GBCFD_MIXED, stage 0 = residual only
+cudaError_t launch_stage(int precision, int viscous, int curvi, int stage, const StageMaps& M,
+                         const StageParams& P, int grid, cudaStream_t s);
+
+cudaError_t launch_stage_f64(int viscous, int stage, const StageMaps& M, const StageParams& P, int grid, cudaStream_t s);
+cudaError_t launch_stage_f64c(int viscous, int stage, const StageMaps& M, const StageParams& P, int grid, cudaStream_t s);
+cudaError_t launch_stage_f32(int viscous, int stage, const StageMaps& M, const StageParams& P, int grid, cudaStream_t s);
+cudaError_t launch_stage_f32c(int viscous, int stage, const StageMaps& M, const StageParams& P, int grid, cudaStream_t s);
 int stage_occupancy_f64(int viscous);
+int stage_occupancy_f64c(int viscous);
 int stage_occupancy_f32(int viscous);
+int stage_occupancy_f32c(int viscous);
 
 // halo exchange of one field over a group of blocks
 cudaError_t launch_halo(const HaloGroup& G, cudaStream_t s);
@@ -33,6 +37,10 @@ cudaError_t launch_gather(const Geometry& g, const double* src, double* dst, cud
 // spectral-radius rate and time step of a padded f64 state (per-CTA partials, last CTA reduces)
 cudaError_t launch_init_rate(const Geometry& g, const Physics& ph, const double* q, DevCtrl* ctrl,
                              double* partial, int grid, int mixed, cudaStream_t s);
+// curvilinear metrics of the interior cells from the block's nodes (10 padded fields)
+cudaError_t launch_metrics(const Geometry& g, const double* nodes, void* M, int elem, cudaStream_t s);
+cudaError_t launch_init_rate_curvi(const Geometry& g, const Physics& ph, const double* q, const void* M,
+                                   DevCtrl* ctrl, double* partial, int grid, int mixed, cudaStream_t s);
 // global time step of a group: dt = cfl / max rate, written to every block
 cudaError_t launch_group_dt(DevCtrl* const* ctrls, int n, double cfl, cudaStream_t s);
 

@@ -16,6 +16,7 @@
 // of the new state (next time step).  The last CTA to finish reduces the per-CTA partials in a
 // fixed order (deterministic) and resets the counter.  No CTA ever waits on another.
 #pragma once
+#include "curvi.cuh"
 #include "internal.cuh"
 #include "physics.cuh"
 
@@ -69,7 +70,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 }
 
 // ---- shared-memory plan ----------------------------------------------------------------------
-template <typename T, bool VISC>
+template <typename T, bool VISC, bool CURVI = false>
 struct Plan {
   static constexpr int NV = VISC ? 6 : 5;           // rho u v w p [theta]
   static constexpr int BOX = BY * BX;               // cells per staged plane
@@ -83,9 +84,13 @@ struct Plan {
   static constexpr size_t ring = std_ + NSTAGE * DSLOT;
   static constexpr size_t fx = ring + sizeof(T) * NRING * RSLOT;
   static constexpr size_t fy = fx + sizeof(T) * 5 * TY * (TX + 1);
-  static constexpr size_t red = (fy + sizeof(T) * 5 * (TY + 1) * TX + 15) / 16 * 16;
+  // curvilinear: a ring of metric planes (10 fields, k and k+1 in use, the next one landing)
+  static constexpr int NMS = CURVI ? (sizeof(T) == 4 ? 3 : 2) : 0;
+  static constexpr size_t MSLOT = (sizeof(T) * 10 * BOX + 127) / 128 * 128;
+  static constexpr size_t mring = (fy + sizeof(T) * 5 * (TY + 1) * TX + 127) / 128 * 128;
+  static constexpr size_t red = (mring + NMS * MSLOT + 15) / 16 * 16;
   static constexpr size_t bar = red + sizeof(double) * NWARP * NPART;
-  static constexpr size_t misc = bar + 8 * NSTAGE;
+  static constexpr size_t misc = bar + 8 * (NSTAGE + NMS);
   static constexpr size_t bytes = (misc + 16 + 127) / 128 * 128;
 };
 
@@ -186,6 +191,23 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ ring, const Face
   F[4] = Fr[4];
 }
 
+// tangential neighbour indices of a face as one array (lp1, lm1, rp1, rm1, lp2, lm2, rp2, rm2)
+__device__ __forceinline__ const int (&tg_of(const FaceIdx& f))[8] {
+  return *reinterpret_cast<const int(*)[8]>(&f.lp1);
+}
+
+// a cell's mean face vector per direction (lower and upper face), from the metric ring
+template <typename T>
+__device__ __forceinline__ void cell_face_means(const T* mring, int mk, int mk1, int cy, int cx, T* sb) {
+  constexpr int MS = BY * BX;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    sb[x] = T(0.5) * (mring[mb(mk, cy, cx) + x * MS] + mring[mb(mk, cy, cx + 1) + x * MS]);
+    sb[3 + x] = T(0.5) * (mring[mb(mk, cy, cx) + (3 + x) * MS] + mring[mb(mk, cy + 1, cx) + (3 + x) * MS]);
+    sb[6 + x] = T(0.5) * (mring[mb(mk, cy, cx) + (6 + x) * MS] + mring[mb(mk1, cy, cx) + (6 + x) * MS]);
+  }
+}
+
 // spectral-radius rate of one cell: sum over directions of the convective radius (plus 4x the
 // viscous one) divided by the volume, i.e. the inverse of the cell's stable step / CFL
 template <typename T>
@@ -208,13 +230,14 @@ __device__ __forceinline__ T cell_rate(T r, T u, T v, T w, T p, const Physics& p
 // registers: the register file is split over the SM's four sub-partitions (16K each) and warps
 // are spread round-robin, so two 9-warp CTAs (5 warps on one sub-partition) allow 96 registers
 // per thread on the mixed path, one CTA (3 warps) 168 on the FP64 path
-template <typename T, bool VISC, int STAGE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+template <typename T, bool VISC, int STAGE, bool CURVI>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
     stage_kernel(const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmd,
-                 const StageParams P) {
+                 const __grid_constant__ CUtensorMap tmm, const StageParams P) {
   constexpr bool MIXED = sizeof(T) == 4;
   constexpr bool LOADD = MIXED && (STAGE == 2 || STAGE == 3);
-  using PL = Plan<T, VISC>;
+  using PL = Plan<T, VISC, CURVI>;
+  constexpr int NMS = PL::NMS;
   constexpr int NV = PL::NV;
   constexpr int MS = BY * BX;
   using Fm = VM<T>;
@@ -223,6 +246,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
   T* ring = reinterpret_cast<T*>(smem + PL::ring);
   T* fx = reinterpret_cast<T*>(smem + PL::fx);
   T* fy = reinterpret_cast<T*>(smem + PL::fy);
+  T* mring = reinterpret_cast<T*>(smem + PL::mring);
   double* red = reinterpret_cast<double*>(smem + PL::red);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + PL::bar);
   int* sabort = reinterpret_cast<int*>(smem + PL::misc);
@@ -239,7 +263,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
   const T ihZ[3] = {T(ph.ihz), T(ph.ihx), T(ph.ihy)};
 
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < NSTAGE + NMS; ++s) mbar_init(&bar[s], 1);
     fence_barrier_init();
     *sabort = 0;
   }
@@ -249,6 +273,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
   const T dtT = T(dt);
   unsigned phase_bits = 0;   // parity of each staging slot (uniform across the CTA)
   unsigned pending = 0;      // slots with a copy in flight (meaningful in thread 0)
+  unsigned mphase = 0;       // parity of each metric slot
+  unsigned mpending = 0;     // metric slots with a copy in flight (thread 0)
   bool bad = false;          // non-physical value met by this thread
   double nacc[5] = {0, 0, 0, 0, 0};
   float ncomp[5] = {0, 0, 0, 0, 0};  // Kahan compensation (mixed path)
@@ -318,13 +344,43 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
       return *sabort == 0;
     };
 
+    // metric planes (curvilinear): plane kp in slot (kp + 1) % NMS; iteration k reads k and k+1
+    int m_req = k0 - 2, m_wait = k0 - 2;
+    auto mslot = [](int kp) { return NMS ? (kp + 1) % (NMS ? NMS : 1) : 0; };
+    auto mrequest_upto = [&](int upto) {  // thread 0 only
+      if constexpr (CURVI) {
+        upto = min(upto, k1);
+        while (m_req < upto) {
+          ++m_req;
+          const int s = mslot(m_req);
+          fence_proxy_async();
+          mbar_expect_tx(&bar[NSTAGE + s], 10u * MS * sizeof(T));
+          tma_load_4d(smem + PL::mring + s * PL::MSLOT, &tmm, &bar[NSTAGE + s], x0, y0, m_req + HALO, 0);
+          mpending |= 1u << s;
+        }
+      }
+    };
+    auto mwait_upto = [&](int upto) {  // all threads
+      if constexpr (CURVI) {
+        while (m_wait < upto) {
+          ++m_wait;
+          const int s = mslot(m_wait);
+          if (!mbar_wait_bounded(&bar[NSTAGE + s], (mphase >> s) & 1u)) atomicOr(sabort, 1);
+          mphase ^= 1u << s;
+        }
+      }
+    };
+
     if (tid == 0) {
       request(k0 - 2);
       request(k0 - 1);
+      mrequest_upto(k0 - 2 + NMS);
     }
     bool ok = true;
     for (int kp = k0 - 2; kp <= k0 + 1 && ok; ++kp) ok = consume(kp);
     if (!ok) break;
+    mwait_upto(k0);
+    if (*sabort) break;
 
     // owning warps: cell (lane, warp) of the tile
     const bool owner = warp < TY;
@@ -332,13 +388,20 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     const bool live = owner && ci < g.nx && cj < g.ny;
     const int ocy = warp + HALO, ocx = lane + HALO;
     T fzl[5], fzu[5];
-    if (owner)
-      face_flux<T, VISC, 2>(ring, zface_idx<NV>((k0 - 2) & 3, (k0 - 1) & 3, k0 & 3, (k0 + 1) & 3, ocy, ocx), ihZ,
-                            K, fzl);
+    if (owner) {
+      const FaceIdx iz = zface_idx<NV>((k0 - 2) & 3, (k0 - 1) & 3, k0 & 3, (k0 + 1) & 3, ocy, ocx);
+      if constexpr (CURVI)
+        face_flux_curvi<T, VISC>(ring, mring, NV * MS, iz.b, tg_of(iz), zface_met(mslot(k0 - 1), mslot(k0), ocy, ocx),
+                                 K, fzl);
+      else
+        face_flux<T, VISC, 2>(ring, iz, ihZ, K, fzl);
+    }
     __syncthreads();  // the first consume below overwrites plane k0-2, read by the z-face above
 
     for (int k = k0; k < k1; ++k) {
       if (!consume(k + 2)) { ok = false; break; }
+      if (tid == 0) mrequest_upto(k - 1 + NMS);  // the slot of plane k-1 is free
+      mwait_upto(k + 1);
       // per-cell inputs of the update (L2-resident planes), loaded before the face work
       double qs_[5], qn_[5];
       float dp_[5];
@@ -353,23 +416,41 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
         }
       }
       const int sk = k & 3, sm = (k - 1) & 3, sp = (k + 1) & 3, s2 = (k + 2) & 3;
+      const int mk = mslot(k), mk1 = mslot(k + 1);
       if (owner) {
         T Fa[5], Fb[5];
         const FaceIdx ix = xface_idx<NV>(sk, sm, sp, ocy, ocx), iy = yface_idx<NV>(sk, sm, sp, ocy, ocx);
-        face_flux<T, VISC, 0>(ring, ix, ihX, K, Fa);
-        face_flux<T, VISC, 1>(ring, iy, ihY, K, Fb);
+        if constexpr (CURVI) {
+          face_flux_curvi<T, VISC>(ring, mring, NV * MS, ix.b, tg_of(ix), xface_met(mk, mk1, ocy, ocx), K, Fa);
+          face_flux_curvi<T, VISC>(ring, mring, NV * MS, iy.b, tg_of(iy), yface_met(mk, mk1, ocy, ocx), K, Fb);
+        } else {
+          face_flux<T, VISC, 0>(ring, ix, ihX, K, Fa);
+          face_flux<T, VISC, 1>(ring, iy, ihY, K, Fb);
+        }
 #pragma unroll
         for (int m = 0; m < 5; ++m) fx[(m * TY + warp) * (TX + 1) + lane] = Fa[m];
 #pragma unroll
         for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + warp) * TX + lane] = Fb[m];
-        face_flux<T, VISC, 2>(ring, zface_idx<NV>(sm, sk, sp, s2, ocy, ocx), ihZ, K, fzu);
+        const FaceIdx iz = zface_idx<NV>(sm, sk, sp, s2, ocy, ocx);
+        if constexpr (CURVI)
+          face_flux_curvi<T, VISC>(ring, mring, NV * MS, iz.b, tg_of(iz), zface_met(mk, mk1, ocy, ocx), K, fzu);
+        else
+          face_flux<T, VISC, 2>(ring, iz, ihZ, K, fzu);
       } else {
         // the tile's upper y-faces (all lanes) and upper x-faces (lanes < TY)
         T Fa[5], Fb[5];
         const FaceIdx iy = yface_idx<NV>(sk, sm, sp, TY + HALO, lane + HALO);
         const FaceIdx ix = xface_idx<NV>(sk, sm, sp, (lane % TY) + HALO, TX + HALO);
-        face_flux<T, VISC, 1>(ring, iy, ihY, K, Fa);
-        if (lane < TY) face_flux<T, VISC, 0>(ring, ix, ihX, K, Fb);
+        if constexpr (CURVI) {
+          face_flux_curvi<T, VISC>(ring, mring, NV * MS, iy.b, tg_of(iy),
+                                   yface_met(mk, mk1, TY + HALO, lane + HALO), K, Fa);
+          if (lane < TY)
+            face_flux_curvi<T, VISC>(ring, mring, NV * MS, ix.b, tg_of(ix),
+                                     xface_met(mk, mk1, lane + HALO, TX + HALO), K, Fb);
+        } else {
+          face_flux<T, VISC, 1>(ring, iy, ihY, K, Fa);
+          if (lane < TY) face_flux<T, VISC, 0>(ring, ix, ihX, K, Fb);
+        }
 #pragma unroll
         for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + TY) * TX + lane] = Fa[m];
         if (lane < TY) {
@@ -384,7 +465,15 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
         for (int m = 0; m < 5; ++m) {
           const T ddx = fx[(m * TY + warp) * (TX + 1) + lane + 1] - fx[(m * TY + warp) * (TX + 1) + lane];
           const T ddy = fy[(m * (TY + 1) + warp + 1) * TX + lane] - fy[(m * (TY + 1) + warp) * TX + lane];
-          R[m] = (ddx * T(ph.ihx) + ddy * T(ph.ihy)) + (fzu[m] - fzl[m]) * T(ph.ihz);
+          if constexpr (CURVI)
+            R[m] = (ddx + ddy) + (fzu[m] - fzl[m]);  // face fluxes carry |S|; divided by V below
+          else
+            R[m] = (ddx * T(ph.ihx) + ddy * T(ph.ihy)) + (fzu[m] - fzl[m]) * T(ph.ihz);
+        }
+        if constexpr (CURVI) {
+          const T iv = Fm::rcp(mring[mb(mk, ocy, ocx) + 9 * MS]);
+#pragma unroll
+          for (int m = 0; m < 5; ++m) R[m] = R[m] * iv;
         }
         const long long o = gidx(g, ci, cj, k), of = gidxf(g, ci, cj, k);
         if constexpr (STAGE == 0) {
@@ -407,7 +496,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
             const double uu = out[1] * ir, vv = out[2] * ir, ww = out[3] * ir;
             const double pp = (ph.gamma - 1.0) * (out[4] - 0.5 * out[0] * (uu * uu + vv * vv + ww * ww));
             if (!(out[0] > 0.0 && pp > 0.0)) bad = true;
-            rate_max = fmax(rate_max, T(cell_rate<double>(out[0], uu, vv, ww, pp, ph)));
+            if constexpr (CURVI) {
+              T sb[9];
+              cell_face_means(mring, mk, mk1, ocy, ocx, sb);
+              rate_max = fmax(rate_max, T(cell_rate_curvi<double>(out[0], uu, vv, ww, pp, sb,
+                                                                  mring[mb(mk, ocy, ocx) + 9 * MS], ph)));
+            } else {
+              rate_max = fmax(rate_max, T(cell_rate<double>(out[0], uu, vv, ww, pp, ph)));
+            }
           }
         } else {
           float inc[5];
@@ -433,7 +529,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
             const float uu = qf[1] * ir, vv = qf[2] * ir, ww = qf[3] * ir;
             const float pp = float(ph.gamma - 1.0) * (qf[4] - 0.5f * qf[0] * (uu * uu + vv * vv + ww * ww));
             if (!(qf[0] > 0.0f && pp > 0.0f)) bad = true;
-            rate_max = fmax(rate_max, T(cell_rate<float>(qf[0], uu, vv, ww, pp, ph)));
+            if constexpr (CURVI) {
+              T sb[9];
+              cell_face_means(mring, mk, mk1, ocy, ocx, sb);
+              rate_max = fmax(rate_max, T(cell_rate_curvi<float>(qf[0], uu, vv, ww, pp, sb,
+                                                                 mring[mb(mk, ocy, ocx) + 9 * MS], ph)));
+            } else {
+              rate_max = fmax(rate_max, T(cell_rate<float>(qf[0], uu, vv, ww, pp, ph)));
+            }
           }
         }
         if constexpr (STAGE == 1) {
@@ -461,6 +564,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     if (tid == 0) {
       for (int s = 0; s < NSTAGE; ++s)
         if (pending & (1u << s)) mbar_wait_bounded(&bar[s], (phase_bits >> s) & 1u);
+      for (int s = 0; s < NMS; ++s)
+        if (mpending & (1u << s)) mbar_wait_bounded(&bar[NSTAGE + s], (mphase >> s) & 1u);
       atomicOr(&P.ctrl->flag, FLAG_TIMEOUT);
     }
   }
