@@ -231,7 +231,27 @@ def e2e_path(gbcfd, torch, case, precision, steps, world, device):
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + ctrl_bytes}
 
 
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64, nominal (the profiling recipe's figure; 1.20 measured by FMA probe)
+ISSUE_PER_CLK = 152 * 4 * 32  # SMs x schedulers x lanes: thread instructions issued per clock
+
+
+def profiled_numbers(precision, key):
+    """numbers of a `key: a b c` line in the committed ncu summary, if it was taken on the current
+    kernel source (else None)"""
+    path = os.path.join(ROOT, "profiles", f"stage_kernel_{precision}_vortex.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel source hash:\s*([0-9a-f]+)", text)
+    m = re.search(re.escape(key) + r":\s*([0-9.eE+ ]+)", text)
+    if not m_hash or not m or m_hash.group(1) != kernel_source_hash():
+        return None
+    return [float(x) for x in m.group(1).split()]
+
+
 def roofline(precision, res, cells, steps, peak, peak_kind):
+    """HBM roofline of the stage kernel: algorithmic bytes per launch / mean launch time"""
     nbytes = sum(ALGO_BYTES[precision][s - 1] * cells * steps for s in (1, 2, 3))
     sec = sum(res["stage_ms"].values()) / 1e3
     achieved = nbytes / sec / 1e9
@@ -240,6 +260,36 @@ def roofline(precision, res, cells, steps, peak, peak_kind):
             "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
             "traffic": traffic, "algorithmic_bytes_per_launch": nbytes / (3 * steps),
             "kernel": "stage_kernel", "avg_launch_ms": round(sec * 1e3 / (3 * steps), 4)}
+
+
+def fp64_alu_roofline(res, cells, steps, hbm):
+    """FP64-pipe roofline of the FP64 stage kernel: its FP64 flops per cell (2 DFMA + DADD + DMUL,
+    counted by ncu per stage) over the launch time, against the part's FP64 peak"""
+    flops = profiled_numbers("fp64", "fp64 flops per cell and stage")
+    out = {"bound": "alu", "kernel": "stage_kernel", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+           "peak_kind": "nominal FP64 (profiling recipe)", "avg_launch_ms": hbm["avg_launch_ms"],
+           "traffic": hbm["traffic"], "hbm_frac": hbm["frac"]}
+    if flops:
+        total = sum(flops[s - 1] * cells * steps for s in (1, 2, 3))
+        achieved = total / (sum(res["stage_ms"].values()) / 1e3) / 1e12
+        out.update({"achieved": round(achieved, 4), "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                    "flops_per_cell": flops})
+    else:
+        out.update({"achieved": None, "frac": None})
+    return out
+
+
+def issue_estimate(precision, res, cells, steps, sm_mhz):
+    """instruction-issue utilisation of the stage kernel: ncu's thread instructions per cell over
+    the launch time, against 152 SMs x 4 schedulers x 32 lanes per clock at the sampled clock"""
+    inst = profiled_numbers(precision, "thread instructions per cell and stage")
+    if not inst or not sm_mhz:
+        return None
+    total = sum(inst[s - 1] * cells * steps for s in (1, 2, 3))
+    rate = total / (sum(res["stage_ms"].values()) / 1e3)
+    peak = ISSUE_PER_CLK * sm_mhz * 1e6
+    return {"achieved_tinst_per_s": round(rate / 1e12, 3), "peak_tinst_per_s": round(peak / 1e12, 3),
+            "frac": round(rate / peak, 4), "instructions_per_cell": inst}
 
 
 def cpu_baseline_sample(n):
@@ -302,6 +352,7 @@ def run_gbcfd(args):
                    "l2": "working set > 1.4 GB >> 129 MB L2, no flush needed",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline(head, r, case.cells, args.steps, peak, peak_kind),
+        "issue": issue_estimate(head, r, case.cells, args.steps, clk.get("sm_mhz")),
         "e2e": e2e,
         "gpu_launches": r["launches"],
         "clocks": clk,
@@ -311,9 +362,10 @@ def run_gbcfd(args):
     }
     for p in paths[1:]:
         rp = results[p]
+        hbm = roofline(p, rp, case.cells, args.steps, peak, peak_kind)
         out[p] = {"value": world * case.cells * args.steps / (rp["ms"] / 1e3), "unit": "cell-updates/s",
-                  "ms_per_step": rp["ms"] / args.steps, "dtype": "f64",
-                  "roofline": roofline(p, rp, case.cells, args.steps, peak, peak_kind),
+                  "ms_per_step": rp["ms"] / args.steps, "dtype": "f64" if p == "fp64" else "f32+f64",
+                  "roofline": fp64_alu_roofline(rp, case.cells, args.steps, hbm) if p == "fp64" else hbm,
                   "gpu_launches": rp["launches"]}
     print(json.dumps(out))
 
