@@ -33,7 +33,13 @@ ALGO_BYTES = {
     "mixed": (20 + 20, 20 + 20 + 20, 20 + 20 + 40 + 40 + 20),  # S^n, D read; D or Q^{n+1}, S^{n+1} written
     "fp64": (40 + 40, 40 + 40 + 40, 40 + 40 + 40),    # stage input, Qn read; stage output written
 }
-WORKLOAD = "isentropic vortex 256^3, Navier-Stokes Re 1e4 Pr 0.72, MUSCL/minmod + Roe, SSP-RK3 CFL 0.5"
+WORKLOADS = {
+    "vortex256": "isentropic vortex 256^3, Navier-Stokes Re 1e4 Pr 0.72, MUSCL/minmod + Roe, SSP-RK3 CFL 0.5",
+    "warped512": ("warped curvilinear block 512x512x384, Navier-Stokes Re 1e5, 5% broadband velocity on Mach 0.3, "
+                  "MUSCL/minmod + Roe, SSP-RK3 CFL 0.5"),
+}
+# metric bytes read per cell and stage on curvilinear blocks (10 fields)
+METRIC_BYTES = {"mixed": 40, "fp64": 80}
 
 
 def parse():
@@ -42,8 +48,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbcfd", choices=["gbcfd", "reference"])
-    ap.add_argument("--n", type=int, default=N_DEFAULT, help="cells per side of the cubic block")
-    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT, help="cells per side of the cubic vortex block")
+    ap.add_argument("--workload", default="vortex256", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["both", "mixed", "fp64"],
+                    help="default: both for vortex256, mixed for warped512")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -142,28 +150,23 @@ def hbm_peak():
         return PEAK_FALLBACK_GBS, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(curvi=False):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1710_09995_gb300", "csrc")
-    for name in ("stage.cuh", "physics.cuh", "internal.cuh"):
+    for name in ("stage.cuh", "physics.cuh", "internal.cuh") + (("curvi.cuh",) if curvi else ()):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(precision):
+PROFILE_TAG = {"vortex256": "vortex", "warped512": "warped"}
+
+
+def profiled_traffic(precision, workload="vortex256"):
     """DRAM bytes per stage launch from the committed ncu summary, if it was taken on the
     current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"stage_kernel_{precision}_vortex.md")
-    try:
-        text = open(path).read()
-    except OSError:
-        return None
-    m_hash = re.search(r"kernel source hash:\s*([0-9a-f]+)", text)
-    m_bytes = re.search(r"dram bytes per stage launch at 256\^3:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
-        return None
-    return float(m_bytes.group(1))
+    v = profiled_numbers(precision, "dram bytes per stage launch at full size", workload)
+    return v[0] if v else None
 
 
 # ---- the GPU arm -----------------------------------------------------------------------------
@@ -235,37 +238,38 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 FP64, nominal (the profiling recipe's figure; 1
 ISSUE_PER_CLK = 152 * 4 * 32  # SMs x schedulers x lanes: thread instructions issued per clock
 
 
-def profiled_numbers(precision, key):
+def profiled_numbers(precision, key, workload="vortex256"):
     """numbers of a `key: a b c` line in the committed ncu summary, if it was taken on the current
     kernel source (else None)"""
-    path = os.path.join(ROOT, "profiles", f"stage_kernel_{precision}_vortex.md")
+    path = os.path.join(ROOT, "profiles", f"stage_kernel_{precision}_{PROFILE_TAG[workload]}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
     m_hash = re.search(r"kernel source hash:\s*([0-9a-f]+)", text)
     m = re.search(re.escape(key) + r":\s*([0-9.eE+ ]+)", text)
-    if not m_hash or not m or m_hash.group(1) != kernel_source_hash():
+    if not m_hash or not m or m_hash.group(1) != kernel_source_hash(workload == "warped512"):
         return None
     return [float(x) for x in m.group(1).split()]
 
 
-def roofline(precision, res, cells, steps, peak, peak_kind):
+def roofline(precision, res, cells, steps, peak, peak_kind, workload="vortex256"):
     """HBM roofline of the stage kernel: algorithmic bytes per launch / mean launch time"""
-    nbytes = sum(ALGO_BYTES[precision][s - 1] * cells * steps for s in (1, 2, 3))
+    extra = METRIC_BYTES[precision] if workload == "warped512" else 0
+    nbytes = sum((ALGO_BYTES[precision][s - 1] + extra) * cells * steps for s in (1, 2, 3))
     sec = sum(res["stage_ms"].values()) / 1e3
     achieved = nbytes / sec / 1e9
-    traffic = profiled_traffic(precision)
+    traffic = profiled_traffic(precision, workload)
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
             "traffic": traffic, "algorithmic_bytes_per_launch": nbytes / (3 * steps),
             "kernel": "stage_kernel", "avg_launch_ms": round(sec * 1e3 / (3 * steps), 4)}
 
 
-def fp64_alu_roofline(res, cells, steps, hbm):
+def fp64_alu_roofline(res, cells, steps, hbm, workload="vortex256"):
     """FP64-pipe roofline of the FP64 stage kernel: its FP64 flops per cell (2 DFMA + DADD + DMUL,
     counted by ncu per stage) over the launch time, against the part's FP64 peak"""
-    flops = profiled_numbers("fp64", "fp64 flops per cell and stage")
+    flops = profiled_numbers("fp64", "fp64 flops per cell and stage", workload)
     out = {"bound": "alu", "kernel": "stage_kernel", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
            "peak_kind": "nominal FP64 (profiling recipe)", "avg_launch_ms": hbm["avg_launch_ms"],
            "traffic": hbm["traffic"], "hbm_frac": hbm["frac"]}
@@ -279,10 +283,10 @@ def fp64_alu_roofline(res, cells, steps, hbm):
     return out
 
 
-def issue_estimate(precision, res, cells, steps, sm_mhz):
+def issue_estimate(precision, res, cells, steps, sm_mhz, workload="vortex256"):
     """instruction-issue utilisation of the stage kernel: ncu's thread instructions per cell over
     the launch time, against 152 SMs x 4 schedulers x 32 lanes per clock at the sampled clock"""
-    inst = profiled_numbers(precision, "thread instructions per cell and stage")
+    inst = profiled_numbers(precision, "thread instructions per cell and stage", workload)
     if not inst or not sm_mhz:
         return None
     total = sum(inst[s - 1] * cells * steps for s in (1, 2, 3))
@@ -311,6 +315,25 @@ def cpu_baseline_sample(n):
             "sample": f"1 SSP-RK3 step (FP64) of a {n}x{n}x{nz} z-slab of the z-invariant vortex, best of 2"}
 
 
+def cpu_baseline_warped():
+    """The FP64 oracle on the host cores on a bounded sample of the warped 512x512x384 case: one
+    SSP-RK3 step of a periodic 128 x 128 x 96 block with the same grid map, perturbation recipe
+    and physics (1/16 of the cells), best of 2."""
+    import oracle
+    from paper_1710_09995_gb300 import cases
+    c = cases.broadband_warped(128, 128, 96, seed=0)
+    M = oracle.metrics(c.nodes)
+    p = oracle.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, c.limiter)
+    Q = oracle.pad(c.state)
+    best = math.inf
+    for _ in range(2):
+        t0 = time.perf_counter()
+        oracle.step(p, Q, M, 1)
+        best = min(best, time.perf_counter() - t0)
+    return {"value": c.cells / best, "unit": "cell-updates/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "1 SSP-RK3 step (FP64) of a periodic 128x128x96 warped block, same recipe, best of 2"}
+
+
 def run_gbcfd(args):
     world, rank, local = dist_env()
     import torch
@@ -320,9 +343,14 @@ def run_gbcfd(args):
     device = torch.device("cuda", local)
     from paper_1710_09995_gb300 import cases, gbcfd
     gbcfd.lib()
-    case = cases.isentropic_vortex(n=args.n, L=10.0, viscous=True)
+    if args.workload == "warped512":
+        case = cases.broadband_warped(512, 512, 384, seed=0, device=device)
+        prec = args.precision or "mixed"
+    else:
+        case = cases.isentropic_vortex(n=args.n, L=10.0, viscous=True)
+        prec = args.precision or "both"
     peak, peak_kind = hbm_peak()
-    paths = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    paths = ["mixed", "fp64"] if prec == "both" else [prec]
     clocks = ClockSampler(local)
     clocks.start()
     results = {p: time_path(gbcfd, torch, case, p, args.steps, args.warmup, world, device) for p in paths}
@@ -331,7 +359,7 @@ def run_gbcfd(args):
     e2e = e2e_path(gbcfd, torch, case, head, min(args.e2e_steps, args.steps), world, device)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(args.n)
+        cpu = cpu_baseline_sample(args.n) if args.workload == "vortex256" else cpu_baseline_warped()
     if rank != 0:
         return
     r = results[head]
@@ -347,12 +375,14 @@ def run_gbcfd(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32+f64" if head == "mixed" else "f64",
-        "data": "synthetic (seeded closed-form vortex; the paper's meshes are not available)",
-        "config": {"workload": WORKLOAD, "cells": case.cells, "precision": head,
+        "data": ("synthetic (seeded closed-form vortex; the paper's meshes are not available)"
+                 if args.workload == "vortex256" else
+                 "synthetic (seeded warped grid and Fourier-mode perturbation; the paper's meshes are not available)"),
+        "config": {"workload": WORKLOADS[args.workload], "cells": case.cells, "precision": head,
                    "l2": "working set > 1.4 GB >> 129 MB L2, no flush needed",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roofline(head, r, case.cells, args.steps, peak, peak_kind),
-        "issue": issue_estimate(head, r, case.cells, args.steps, clk.get("sm_mhz")),
+        "roofline": roofline(head, r, case.cells, args.steps, peak, peak_kind, args.workload),
+        "issue": issue_estimate(head, r, case.cells, args.steps, clk.get("sm_mhz"), args.workload),
         "e2e": e2e,
         "gpu_launches": r["launches"],
         "clocks": clk,
@@ -362,10 +392,10 @@ def run_gbcfd(args):
     }
     for p in paths[1:]:
         rp = results[p]
-        hbm = roofline(p, rp, case.cells, args.steps, peak, peak_kind)
+        hbm = roofline(p, rp, case.cells, args.steps, peak, peak_kind, args.workload)
         out[p] = {"value": world * case.cells * args.steps / (rp["ms"] / 1e3), "unit": "cell-updates/s",
                   "ms_per_step": rp["ms"] / args.steps, "dtype": "f64" if p == "fp64" else "f32+f64",
-                  "roofline": fp64_alu_roofline(rp, case.cells, args.steps, hbm) if p == "fp64" else hbm,
+                  "roofline": fp64_alu_roofline(rp, case.cells, args.steps, hbm, args.workload) if p == "fp64" else hbm,
                   "gpu_launches": rp["launches"]}
     print(json.dumps(out))
 
@@ -394,7 +424,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "cells": c.cells, "precision": "fp64"},
+           "data": "synthetic", "config": {"workload": WORKLOADS["vortex256"], "cells": c.cells, "precision": "fp64"},
            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": oracle.threads(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
