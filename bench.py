@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbcfd", choices=["gbcfd", "reference"])
-    ap.add_argument("--n", type=int, default=N_DEFAULT, help="cells per side of the cubic vortex block")
+    ap.add_argument("--side", type=int, default=N_DEFAULT, help="cells per side of the cubic vortex block")
     ap.add_argument("--workload", default="vortex256", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["both", "mixed", "fp64"],
                     help="default: both for vortex256, mixed for warped512")
@@ -347,7 +347,7 @@ def run_gbcfd(args):
         case = cases.broadband_warped(512, 512, 384, seed=0, device=device)
         prec = args.precision or "mixed"
     else:
-        case = cases.isentropic_vortex(n=args.n, L=10.0, viscous=True)
+        case = cases.isentropic_vortex(n=args.side, L=10.0, viscous=True)
         prec = args.precision or "both"
     peak, peak_kind = hbm_peak()
     paths = ["mixed", "fp64"] if prec == "both" else [prec]
@@ -359,7 +359,7 @@ def run_gbcfd(args):
     e2e = e2e_path(gbcfd, torch, case, head, min(args.e2e_steps, args.steps), world, device)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(args.n) if args.workload == "vortex256" else cpu_baseline_warped()
+        cpu = cpu_baseline_sample(args.side) if args.workload == "vortex256" else cpu_baseline_warped()
     if rank != 0:
         return
     r = results[head]
@@ -408,7 +408,7 @@ def run_reference(args):
     import oracle
     from paper_1710_09995_gb300 import cases
     nz = 8
-    c = cases.isentropic_vortex(n=args.n, L=10.0, nz=nz, viscous=True)
+    c = cases.isentropic_vortex(n=args.side, L=10.0, nz=nz, viscous=True)
     M = oracle.metrics(c.grid_nodes())
     p = oracle.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, c.limiter)
     Q = oracle.pad(c.state)
@@ -419,8 +419,8 @@ def run_reference(args):
         Q, _, _ = oracle.step(p, Q, M, 1)
     sec = time.perf_counter() - t0
     value = c.cells * args.steps / sec
-    sample = (f"each step: 1 SSP-RK3 step (FP64 oracle) of a {args.n}x{args.n}x{nz} z-slab of the "
-              f"z-invariant {args.n}^3 vortex")
+    sample = (f"each step: 1 SSP-RK3 step (FP64 oracle) of a {args.side}x{args.side}x{nz} z-slab of the "
+              f"z-invariant {args.side}^3 vortex")
     out = {"impl": "reference", "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
