@@ -32,7 +32,7 @@ def test_max_over_ranks_and_barrier_gloo(tmp_path):
         t = bench.max_over_ranks(1.5 + rank, world, torch.device("cpu"))
         assert t == 2.5, t
         bench.barrier(world)
-        print(f"rank {rank} ok {t}", flush=True)
+        print(f"rank {{rank}} ok {{t}}", flush=True)
     """))
     r = torchrun([str(script)], 29611)
     assert r.returncode == 0, r.stderr[-3000:]
