@@ -37,6 +37,9 @@ WORKLOADS = {
     "vortex256": "isentropic vortex 256^3, Navier-Stokes Re 1e4 Pr 0.72, MUSCL/minmod + Roe, SSP-RK3 CFL 0.5",
     "warped512": ("warped curvilinear block 512x512x384, Navier-Stokes Re 1e5, 5% broadband velocity on Mach 0.3, "
                   "MUSCL/minmod + Roe, SSP-RK3 CFL 0.5"),
+    "lattice96": ("96 uneven Cartesian blocks (4x4x6 lattice, sides 16..160, seed 4: 506x492x550 = 1.37e8 cells), "
+                  "Euler, Mach 0.8 + 1e-2 Fourier perturbation, MUSCL/minmod + Roe, SSP-RK3 CFL 0.5, "
+                  "one group: one launch per stage, CUDA graph per step, autotuned grid split"),
 }
 # metric bytes read per cell and stage on curvilinear blocks (10 fields)
 METRIC_BYTES = {"mixed": 40, "fp64": 80}
@@ -51,7 +54,7 @@ def parse():
     ap.add_argument("--side", type=int, default=N_DEFAULT, help="cells per side of the cubic vortex block")
     ap.add_argument("--workload", default="vortex256", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["both", "mixed", "fp64"],
-                    help="default: both for vortex256, mixed for warped512")
+                    help="default: both for vortex256, mixed for warped512 and lattice96")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -159,7 +162,7 @@ def kernel_source_hash(curvi=False):
     return h.hexdigest()[:16]
 
 
-PROFILE_TAG = {"vortex256": "vortex", "warped512": "warped"}
+PROFILE_TAG = {"vortex256": "vortex", "warped512": "warped", "lattice96": "lattice"}
 
 
 def profiled_traffic(precision, workload="vortex256"):
@@ -205,6 +208,76 @@ def time_path(gbcfd, torch, case, precision, steps, warmup, world, device):
     norms = blk.residual_norm()  # also surfaces any device-side error flag
     blk.close()
     return {"ms": ms, "stage_ms": stage_ms, "halo_ms": halo_ms, "launches": 6 * steps, "norms": norms.tolist()}
+
+
+def time_group_path(gbcfd, torch, lat, precision, steps, warmup, world, device):
+    """The lattice as one group: per step one CUDA graph (time step, then halo exchange and one
+    stage launch for all blocks, three times).  Seven events recorded inside the graph time each
+    stage kernel; the stream is synchronised after every step to read them (the host gap this
+    leaves is inside the timed region)."""
+    blocks = gbcfd.blocks_for_lattice(lat, gbcfd.MIXED if precision == "mixed" else gbcfd.FP64, device)
+    g = gbcfd.Group(blocks)
+    ctas_per_sm = g.tune()
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+    g.set_timing(marks)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        g.step(1, stream)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_ms = {1: 0.0, 2: 0.0, 3: 0.0}
+    halo_ms = 0.0
+    barrier(world)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(steps):
+        g.step(1, stream)
+        stream.synchronize()
+        for st in (1, 2, 3):
+            stage_ms[st] += marks[2 * st - 1].elapsed_time(marks[2 * st])
+            halo_ms += marks[2 * st - 2].elapsed_time(marks[2 * st - 1])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(start.elapsed_time(stop), world, device)
+    norms = [b.residual_norm().tolist() for b in blocks]
+    g.close()
+    for b in blocks:
+        b.close()
+    return {"ms": ms, "stage_ms": stage_ms, "halo_ms": halo_ms, "launches": 7 * steps, "norms": norms[0],
+            "ctas_per_sm": ctas_per_sm, "blocks": len(blocks)}
+
+
+def e2e_group_path(gbcfd, torch, lat, precision, steps, world, device):
+    """Through the C ABI with pinned host buffers: every step uploads each block's state, advances
+    the group one SSP-RK3 step and reads back every block's state and residual norm."""
+    blocks = gbcfd.blocks_for_lattice(lat, gbcfd.MIXED if precision == "mixed" else gbcfd.FP64, device)
+    g = gbcfd.Group(blocks)
+    g.tune()
+    host_in = [lat.state[:, zs, ys, xs].contiguous().cpu().pin_memory() for zs, ys, xs in lat.block_slices().values()]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+
+    def one():
+        for b, h in zip(blocks, host_in):
+            b.set_state(h)
+        g.step(1)
+        for b, h in zip(blocks, host_out):
+            b.get_state(h)
+        for b in blocks:
+            b.residual_norm()
+
+    one()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, world, device)
+    g.close()
+    nbytes = sum(h.numel() * 8 for h in host_in)
+    return {"value": world * lat.cells * steps / dt, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 112 * len(blocks)}
 
 
 def e2e_path(gbcfd, torch, case, precision, steps, world, device):
@@ -334,6 +407,24 @@ def cpu_baseline_warped():
             "sample": "1 SSP-RK3 step (FP64) of a periodic 128x128x96 warped block, same recipe, best of 2"}
 
 
+def cpu_baseline_lattice():
+    """The FP64 oracle on the host cores on a bounded sample of the lattice workload: one SSP-RK3
+    step of a periodic 128 x 128 x 96 block with the same state recipe and physics, best of 2."""
+    import oracle
+    from paper_1710_09995_gb300 import cases
+    lat = cases.lattice_case(sizes=([128], [128], [96]), seed=4)
+    M = oracle.metrics(cases.cartesian_nodes(128, 128, 96, *lat.spacing))
+    p = oracle.params(lat.gamma, 0.0, 0.72, lat.cfl, lat.eps, False, 0)
+    Q = oracle.pad(lat.state.numpy())
+    best = math.inf
+    for _ in range(2):
+        t0 = time.perf_counter()
+        oracle.step(p, Q, M, 1)
+        best = min(best, time.perf_counter() - t0)
+    return {"value": lat.cells / best, "unit": "cell-updates/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "1 SSP-RK3 step (FP64, Euler) of a periodic 128x128x96 block, same recipe, best of 2"}
+
+
 def run_gbcfd(args):
     world, rank, local = dist_env()
     import torch
@@ -343,6 +434,8 @@ def run_gbcfd(args):
     device = torch.device("cuda", local)
     from paper_1710_09995_gb300 import cases, gbcfd
     gbcfd.lib()
+    if args.workload == "lattice96":
+        return run_lattice(args, world, rank, local, device, torch, cases, gbcfd)
     if args.workload == "warped512":
         case = cases.broadband_warped(512, 512, 384, seed=0, device=device)
         prec = args.precision or "mixed"
@@ -396,6 +489,57 @@ def run_gbcfd(args):
         out[p] = {"value": world * case.cells * args.steps / (rp["ms"] / 1e3), "unit": "cell-updates/s",
                   "ms_per_step": rp["ms"] / args.steps, "dtype": "f64" if p == "fp64" else "f32+f64",
                   "roofline": fp64_alu_roofline(rp, case.cells, args.steps, hbm, args.workload) if p == "fp64" else hbm,
+                  "gpu_launches": rp["launches"]}
+    print(json.dumps(out))
+
+
+def run_lattice(args, world, rank, local, device, torch, cases, gbcfd):
+    lat = cases.lattice_case(device=device)
+    prec = args.precision or "mixed"
+    paths = ["mixed", "fp64"] if prec == "both" else [prec]
+    peak, peak_kind = hbm_peak()
+    clocks = ClockSampler(local)
+    clocks.start()
+    results = {p: time_group_path(gbcfd, torch, lat, p, args.steps, args.warmup, world, device) for p in paths}
+    clk = clocks.stop()
+    head = paths[0]
+    e2e = e2e_group_path(gbcfd, torch, lat, head, min(args.e2e_steps, args.steps), world, device)
+    cpu = cpu_baseline_lattice() if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    if rank != 0:
+        return
+    r = results[head]
+    out = {
+        "metric": "cell-updates/s",
+        "value": world * lat.cells * args.steps / (r["ms"] / 1e3),
+        "unit": "cell-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": r["ms"] / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64" if head == "mixed" else "f64",
+        "data": "synthetic (seeded lattice sizes and Fourier-mode phases; the paper's meshes are not available)",
+        "config": {"workload": WORKLOADS["lattice96"], "cells": lat.cells, "blocks": r["blocks"], "precision": head,
+                   "ctas_per_sm": r["ctas_per_sm"],
+                   "l2": "working set > 20 GB >> 129 MB L2, no flush needed",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline(head, r, lat.cells, args.steps, peak, peak_kind, "lattice96"),
+        "issue": issue_estimate(head, r, lat.cells, args.steps, clk.get("sm_mhz"), "lattice96"),
+        "e2e": e2e,
+        "gpu_launches": r["launches"],
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "halo_ms_per_step": r["halo_ms"] / args.steps,
+        "residual_norm": r["norms"],
+    }
+    for p in paths[1:]:
+        rp = results[p]
+        hbm = roofline(p, rp, lat.cells, args.steps, peak, peak_kind, "lattice96")
+        out[p] = {"value": world * lat.cells * args.steps / (rp["ms"] / 1e3), "unit": "cell-updates/s",
+                  "ms_per_step": rp["ms"] / args.steps, "dtype": "f64" if p == "fp64" else "f32+f64",
+                  "roofline": fp64_alu_roofline(rp, lat.cells, args.steps, hbm, "lattice96") if p == "fp64" else hbm,
                   "gpu_launches": rp["launches"]}
     print(json.dumps(out))
 

@@ -147,6 +147,43 @@ int gbcfd_get_dt(gbcfd_block block, double* dt, void* stream);
 int gbcfd_time_step_noalloc(const double* q, int nx, int ny, int nz, const gbcfd_params* params,
                             const double spacing[3], double* dt, void* stream);
 
+/* ---- batched groups of blocks --------------------------------------------------------------
+ * A group advances many blocks with one kernel launch per Runge-Kutta stage (the multi-zone
+ * parallelism of Sec. 3.1.1 (1) on one GPU): the persistent grid is split between the blocks in
+ * proportion to their cells, every stage of every block is one launch, the halos of all blocks
+ * one launch, and a whole step is replayed from a CUDA graph captured on the first step.  The
+ * blocks must share precision, physics and grid kind (Cartesian or curvilinear); every block a
+ * member connects to must be a member.  Results equal gbcfd_step on the same blocks bitwise. */
+typedef struct gbcfd_group_s* gbcfd_group;
+
+/* Device bytes a group of n blocks needs (descriptor table, control block, partial sums). */
+int gbcfd_group_required_bytes(int n, size_t* bytes);
+
+/* Create a group of n blocks in caller memory dev_mem (256-byte aligned, at least
+ * gbcfd_group_required_bytes).  The blocks must outlive the group; their connections and grids
+ * must not change while it exists (the captured graphs hold their halo tables). */
+int gbcfd_group_create(const gbcfd_block* blocks, int n, void* dev_mem, size_t bytes, gbcfd_group* out);
+
+/* Release the group's host objects (graphs, capture stream).  Waits for the device. */
+int gbcfd_group_destroy(gbcfd_group group);
+
+/* nsteps SSP-RK3 steps of all member blocks (global time step over the group).  Members must
+ * hold a state and be between steps.  Asynchronous on `stream`; errors met on the device are
+ * reported per block by gbcfd_residual_norm. */
+int gbcfd_group_step(gbcfd_group group, int nsteps, void* stream);
+
+/* Autotuner: times stage-1 launches (which write only scratch and norms) for several grid
+ * splits (CTAs per SM) and keeps the fastest for this group.  Synchronises the stream; drops
+ * the captured graphs.  The chosen CTAs per SM are returned in *ctas_per_sm when not NULL. */
+int gbcfd_group_tune(gbcfd_group group, void* stream, int* ctas_per_sm);
+
+/* Timing marks inside each step of the group: events[0..6] are CUDA events (cudaEvent_t) the
+ * caller created with timing enabled and owns.  Each step records events[0] before the time-step
+ * kernel, events[2s-1] after the halo exchange of stage s and events[2s] after its stage kernel,
+ * so elapsed(events[2s-1], events[2s]) is the stage-s kernel's duration.  events NULL removes
+ * them.  Drops the captured graphs; the events of one step are overwritten by the next. */
+int gbcfd_group_set_timing(gbcfd_group group, void* const* events, int n);
+
 /* Message of the last error on the calling host thread ("" if none). */
 const char* gbcfd_last_error(void);
 

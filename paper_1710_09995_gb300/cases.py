@@ -219,3 +219,104 @@ def smooth_random(nx, ny, nz, seed=0, amp=0.05, mach=0.5, gamma=GAMMA, h=None, n
 def with_grid(case: Case, nodes: np.ndarray) -> Case:
     case.nodes = nodes
     return case
+
+
+# ---- conforming lattice of uneven blocks, Euler at Mach 0.8 ---------------------------------
+
+def lattice_sizes(seed, shape=(4, 4, 6), lo=16, hi=160):
+    """per-slab cell counts of a shape[0] x shape[1] x shape[2] lattice of blocks, each drawn
+    uniformly from lo..hi: block (i, j, k) has sx[i] x sy[j] x sz[k] cells, so every face is
+    shared whole with exactly one neighbour (periodic wrap included)"""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return tuple(rng.integers(lo, hi + 1, size=n).tolist() for n in shape)
+
+
+def lattice_seed(shape=(4, 4, 6), lo=16, hi=160, total=(100_000_000, 140_000_000)):
+    """the first seed 0, 1, 2, ... whose lattice holds between total[0] and total[1] cells"""
+    s = 0
+    while True:
+        sx, sy, sz = lattice_sizes(s, shape, lo, hi)
+        if total[0] <= sum(sx) * sum(sy) * sum(sz) <= total[1]:
+            return s
+        s += 1
+
+
+@dataclass
+class Lattice:
+    sx: list
+    sy: list
+    sz: list
+    state: object            # global state [5][Nz][Ny][Nx] float64 (torch tensor)
+    spacing: tuple
+    gamma: float = GAMMA
+    mach: float = 0.8
+    cfl: float = 0.5
+    eps: float = 0.1
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def shape(self):
+        return len(self.sx), len(self.sy), len(self.sz)
+
+    @property
+    def cells(self) -> int:
+        return sum(self.sx) * sum(self.sy) * sum(self.sz)
+
+    def offsets(self):
+        c = lambda s: np.concatenate([[0], np.cumsum(s)]).astype(int).tolist()
+        return c(self.sx), c(self.sy), c(self.sz)
+
+    def block_slices(self):
+        """(i, j, k) -> (z slice, y slice, x slice) of block (i, j, k) in the global arrays, in
+        block order k (slowest), j, i"""
+        ox, oy, oz = self.offsets()
+        out = {}
+        for k in range(len(self.sz)):
+            for j in range(len(self.sy)):
+                for i in range(len(self.sx)):
+                    out[(i, j, k)] = (slice(oz[k], oz[k + 1]), slice(oy[j], oy[j + 1]), slice(ox[i], ox[i + 1]))
+        return out
+
+
+def lattice_case(sizes=None, seed=None, shape=(4, 4, 6), lo=16, hi=160, mach=0.8, amp=1e-2, gamma=GAMMA,
+                 device=None) -> Lattice:
+    """Periodic lattice of uneven Cartesian blocks, Euler: free stream rho = 1, p = 1/gamma (c = 1),
+    u = Mach along x, with rho and p each perturbed by a sum of the 27 Fourier modes k in
+    {1,2,3}^3 of the global box with seeded phases, scaled to a largest relative change of `amp`.
+    Cells are cubes of side 1/Nx (Nx = sum of sx).  Without `sizes`, the lattice is the first seed
+    whose total lies in 1.0e8..1.4e8 cells (`seed` picks the phases and defaults to that seed)."""
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cpu")
+    if sizes is None:
+        lseed = lattice_seed(shape, lo, hi)
+        sizes = lattice_sizes(lseed, shape, lo, hi)
+        seed = lseed if seed is None else seed
+    seed = 0 if seed is None else seed
+    sx, sy, sz = (list(map(int, s)) for s in sizes)
+    Nx, Ny, Nz = sum(sx), sum(sy), sum(sz)
+    h = 1.0 / Nx
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xi = [(torch.arange(n, dtype=torch.float64, device=dev) + 0.5) / n for n in (Nx, Ny, Nz)]
+    fields = []
+    for _ in range(2):  # rho, then p
+        ph = rng.random((3, 3, 3)) * 2.0 * math.pi
+        d = torch.zeros((Nz, Ny, Nx), dtype=torch.float64, device=dev)
+        for kz in range(1, 4):
+            ez0 = torch.exp(1j * 2.0 * math.pi * kz * xi[2])
+            for ky in range(1, 4):
+                ey = torch.exp(1j * 2.0 * math.pi * ky * xi[1])
+                for kx in range(1, 4):
+                    ex = torch.exp(1j * 2.0 * math.pi * kx * xi[0])
+                    ez = ez0 * complex(math.cos(ph[kz - 1, ky - 1, kx - 1]), math.sin(ph[kz - 1, ky - 1, kx - 1]))
+                    d.add_((ez[:, None, None] * ey[None, :, None] * ex[None, None, :]).imag)
+        d.mul_(amp / float(d.abs().max()))
+        fields.append(d)
+    q = torch.empty((5, Nz, Ny, Nx), dtype=torch.float64, device=dev)
+    rho = fields[0].add_(1.0)
+    q[0] = rho
+    q[1] = rho * mach
+    q[2] = 0.0
+    q[3] = 0.0
+    q[4] = fields[1].add_(1.0).mul_(1.0 / (gamma * (gamma - 1.0))).add_(rho * (0.5 * mach * mach))
+    return Lattice(sx, sy, sz, q, (h, h, h), gamma=gamma, mach=mach,
+                   extra={"seed": seed, "shape": list(shape), "lo": lo, "hi": hi})

@@ -59,6 +59,8 @@ struct gbcfd_block_s {
   CUtensorMap tm_q[3];  // FP64: maps of Qn, Q1, Q2.  mixed: maps of the shadows SA, SB
   CUtensorMap tm_d[2];
   CUtensorMap tm_m;     // metric planes (10 fields)
+  BlockDesc* desc;      // the block's descriptor in device memory (a group of one)
+  BlockDesc desc_host;  // host copy
   int curvi;            // metrics from nodes (curvilinear) rather than a uniform spacing
   int metrics_dirty;    // metric halos not exchanged since the metrics were set
 };
@@ -133,6 +135,7 @@ static Carve carve(const Geometry& g, int precision, int nsm) {
     c.off[9] = o; o += f32;                 // shadow B
   }
   c.off[6] = o; o += align256(sizeof(DevCtrl));
+  c.off[10] = o; o += align256(sizeof(BlockDesc));
   c.partial_n = (size_t)std::max(4 * nsm, 4 * 152);
   c.off[7] = o; o += align256(sizeof(double) * NPART * c.partial_n);
   c.total = o;
@@ -207,6 +210,27 @@ static Physics physics_of(const gbcfd_block_s* b) {
   return ph;
 }
 
+// the block as the stage kernel sees it
+static void fill_desc(gbcfd_block_s* b) {
+  BlockDesc& D = b->desc_host;
+  memset(&D, 0, sizeof(D));
+  for (int i = 0; i < 3; ++i) D.tq[i] = b->tm_q[i];
+  for (int i = 0; i < 2; ++i) D.td[i] = b->tm_d[i];
+  D.tm = b->tm_m;
+  D.g = b->g;
+  D.ihx = 1.0 / b->spacing[0];
+  D.ihy = 1.0 / b->spacing[1];
+  D.ihz = 1.0 / b->spacing[2];
+  for (int i = 0; i < 3; ++i) D.q[i] = b->q[i];
+  for (int i = 0; i < 2; ++i) { D.sh[i] = b->sh[i]; D.d[i] = b->d[i]; }
+  D.ctrl = b->ctrl;
+  D.ntx = (b->nx + TX - 1) / TX;
+  D.nty = (b->ny + TY - 1) / TY;
+  D.units = (long long)D.ntx * D.nty * b->nz;
+  D.cta0 = 0;
+  D.ctas = b->grid;
+}
+
 extern "C" int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* params, void* dev_mem,
                                   size_t bytes, gbcfd_block* out) {
   std::string why;
@@ -272,9 +296,12 @@ extern "C" int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* pa
   }
   if (!r) r = make_map(&b->tm_m, b->metrics, g, params->precision == GBCFD_MIXED ? 4 : 8, 10);
   if (r) { delete b; return r; }
+  b->desc = reinterpret_cast<BlockDesc*>(base + c.off[10]);
+  fill_desc(b);
   cudaError_t e = cudaMemset(b->ctrl, 0, sizeof(DevCtrl));
+  if (e == cudaSuccess) e = cudaMemcpy(b->desc, &b->desc_host, sizeof(BlockDesc), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) { delete b; return cuda_fail(e, "clearing the control block"); }
+  if (e != cudaSuccess) { delete b; return cuda_fail(e, "initialising the block"); }
   *out = b;
   return GBCFD_OK;
 }
@@ -312,6 +339,8 @@ extern "C" int gbcfd_set_metrics(gbcfd_block b, const double* nodes, const doubl
       b->metrics_dirty = 0;
       b->grid = stage_grid(b->g, b->p.precision, b->p.viscous, 0, b->nsm);
     }
+    fill_desc(b);
+    CK(cudaMemcpy(b->desc, &b->desc_host, sizeof(BlockDesc), cudaMemcpyHostToDevice));
     return GBCFD_OK;
   }
   cudaPointerAttributes attr;
@@ -322,6 +351,8 @@ extern "C" int gbcfd_set_metrics(gbcfd_block b, const double* nodes, const doubl
   b->curvi = 1;
   b->metrics_dirty = 1;
   b->grid = stage_grid(b->g, b->p.precision, b->p.viscous, 1, b->nsm);
+  fill_desc(b);
+  CK(cudaMemcpy(b->desc, &b->desc_host, sizeof(BlockDesc), cudaMemcpyHostToDevice));
   return GBCFD_OK;
 }
 
@@ -504,38 +535,16 @@ extern "C" int gbcfd_exchange_halos(const gbcfd_block* blocks, int n, void* stre
 
 // ---- stages --------------------------------------------------------------------------------
 static int run_stage(gbcfd_block b, int stage, double* rout, cudaStream_t s) {
-  StageParams P;
+  GroupParams P;
   memset(&P, 0, sizeof(P));
-  P.g = b->g;
+  P.table = b->desc;
+  P.nblocks = 1;
+  P.cur = b->cur;
   P.ph = physics_of(b);
-  P.ctrl = b->ctrl;
+  P.gctrl = b->ctrl;
   P.partial = b->partial;
-  P.ntx = (b->nx + TX - 1) / TX;
-  P.nty = (b->ny + TY - 1) / TY;
-  P.units = (long long)P.ntx * P.nty * b->nz;
-  const CUtensorMap* tmq = &b->tm_q[0];
-  const CUtensorMap* tmd = &b->tm_d[0];
-  if (b->p.precision == GBCFD_FP64) {
-    P.qn = b->q[0];
-    switch (stage) {
-      case 0: P.qs = b->q[0]; P.rout = rout; tmq = &b->tm_q[0]; break;
-      case 1: P.qs = b->q[0]; P.qout = b->q[1]; tmq = &b->tm_q[0]; break;
-      case 2: P.qs = b->q[1]; P.qout = b->q[2]; tmq = &b->tm_q[1]; break;
-      case 3: P.qs = b->q[2]; P.qout = b->q[0]; tmq = &b->tm_q[2]; break;
-    }
-  } else {
-    const int c = b->cur;
-    P.qn = b->q[c];
-    tmq = &b->tm_q[c];
-    switch (stage) {
-      case 0: P.rout = rout; break;
-      case 1: P.dout = b->d[0]; break;
-      case 2: P.dprev = b->d[0]; P.dout = b->d[1]; tmd = &b->tm_d[0]; break;
-      case 3: P.dprev = b->d[1]; P.qout = b->q[1 - c]; P.sout = b->sh[1 - c]; tmd = &b->tm_d[1]; break;
-    }
-  }
-  const StageMaps maps = {tmq, tmd, &b->tm_m};
-  CK(launch_stage(b->p.precision, b->p.viscous, b->curvi, stage, maps, P, b->grid, s));
+  P.rout = rout;
+  CK(launch_stage(b->p.precision, b->p.viscous, b->curvi, stage, P, b->grid, s));
   if (stage == 3 && b->p.precision == GBCFD_MIXED) b->cur = 1 - b->cur;
   return GBCFD_OK;
 }
@@ -556,6 +565,11 @@ extern "C" int gbcfd_stage(const gbcfd_block* blocks, int n, int stage, void* st
   for (int i = 0; i < n; ++i) {
     rc = run_stage(blocks[i], stage, nullptr, s);
     if (rc) return rc;
+  }
+  if (stage == 3 && n > 1) {  // every block then holds the global step the next stage 1 takes
+    std::vector<DevCtrl*> c(n);
+    for (int i = 0; i < n; ++i) c[i] = blocks[i]->ctrl;
+    CK(launch_group_dt(c.data(), n, blocks[0]->p.cfl, s));
   }
   for (int i = 0; i < n; ++i) blocks[i]->next_stage = stage % 3 + 1;
   return GBCFD_OK;
@@ -596,6 +610,256 @@ extern "C" int gbcfd_compute_residual(gbcfd_block b, double* r, void* stream) {
   return run_stage(b, 0, r, s);
 }
 
+// ---- batched groups ------------------------------------------------------------------------
+struct gbcfd_group_s {
+  std::vector<gbcfd_block> blocks;
+  std::vector<BlockDesc> table_host;
+  BlockDesc* table;
+  DevCtrl* gctrl;
+  double* partial;
+  size_t partial_n;
+  int ctas_per_sm;        // grid = SMs x this (split between the blocks)
+  int grid;
+  cudaStream_t cap;       // private stream the step graphs are captured on
+  cudaGraphExec_t exec[2];  // one step, for each parity of the mixed path's ping-pong
+  cudaEvent_t marks[7];     // caller's timing events (or none)
+  bool timed;
+};
+
+static int max_group_ctas(int nsm) { return 8 * nsm; }
+
+extern "C" int gbcfd_group_required_bytes(int n, size_t* bytes) {
+  if (n < 1 || n > MAX_GROUP) return fail(GBCFD_ERR_ARG, "a group holds 1.." + std::to_string(MAX_GROUP) + " blocks");
+  if (!bytes) return fail(GBCFD_ERR_ARG, "bytes is NULL");
+  int dev = 0, nsm = 0;
+  int rc = device_sms(&dev, &nsm);
+  if (rc) return rc;
+  *bytes = align256(sizeof(BlockDesc) * n) + align256(sizeof(DevCtrl)) +
+           align256(sizeof(double) * NPART * (size_t)(max_group_ctas(nsm) + n));
+  return GBCFD_OK;
+}
+
+// split SMs x ctas_per_sm CTAs between the blocks in proportion to their tile-planes (each gets
+// at least one) and write the descriptor table
+static int group_split(gbcfd_group g, int ctas_per_sm, cudaStream_t s) {
+  const int nsm = g->blocks[0]->nsm;
+  const long long target = (long long)nsm * ctas_per_sm;
+  long long W = 0;
+  for (auto& d : g->table_host) W += d.units;
+  int c0 = 0;
+  for (size_t i = 0; i < g->table_host.size(); ++i) {
+    BlockDesc& d = g->table_host[i];
+    long long c = (target * d.units + W / 2) / W;
+    c = std::max(1LL, std::min(c, d.units));
+    d.cta0 = c0;
+    d.ctas = (int)c;
+    c0 += (int)c;
+  }
+  if ((size_t)c0 > g->partial_n) return fail(GBCFD_ERR_ARG, "too many CTAs for the group's partial sums");
+  g->grid = c0;
+  g->ctas_per_sm = ctas_per_sm;
+  CK(cudaMemcpyAsync(g->table, g->table_host.data(), sizeof(BlockDesc) * g->table_host.size(),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // the host table is reused
+  for (int p = 0; p < 2; ++p)
+    if (g->exec[p]) { cudaGraphExecDestroy(g->exec[p]); g->exec[p] = nullptr; }
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_group_create(const gbcfd_block* blocks, int n, void* dev_mem, size_t bytes, gbcfd_group* out) {
+  if (!out) return fail(GBCFD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  size_t need = 0;
+  int rc = gbcfd_group_required_bytes(n, &need);
+  if (rc) return rc;
+  if (!blocks || !dev_mem) return fail(GBCFD_ERR_ARG, "NULL argument");
+  if (((uintptr_t)dev_mem & 255u) != 0) return fail(GBCFD_ERR_MEMORY, "dev_mem must be 256-byte aligned");
+  if (bytes < need) return fail(GBCFD_ERR_MEMORY, "dev_mem smaller than gbcfd_group_required_bytes");
+  for (int i = 0; i < n; ++i) {
+    gbcfd_block b = blocks[i];
+    if (!b) return fail(GBCFD_ERR_ARG, "NULL block");
+    const gbcfd_params &p = b->p, &q = blocks[0]->p;
+    if (p.precision != q.precision || p.viscous != q.viscous || p.limiter != q.limiter || p.gamma != q.gamma ||
+        p.mu != q.mu || p.Pr != q.Pr || p.cfl != q.cfl || p.entropy_eps != q.entropy_eps ||
+        b->curvi != blocks[0]->curvi)
+      return fail(GBCFD_ERR_ARG, "group members must share precision, physics and grid kind");
+    for (int j = 0; j < i; ++j)
+      if (blocks[j] == b) return fail(GBCFD_ERR_ARG, "a block appears twice in the group");
+    for (int f = 0; f < 6; ++f)
+      if (b->nbr[f] && std::find(blocks, blocks + n, b->nbr[f]) == blocks + n)
+        return fail(GBCFD_ERR_ARG, "a connected neighbour is not a member of the group");
+  }
+  gbcfd_group g = new gbcfd_group_s();
+  g->blocks.assign(blocks, blocks + n);
+  char* base = static_cast<char*>(dev_mem);
+  g->table = reinterpret_cast<BlockDesc*>(base);
+  g->gctrl = reinterpret_cast<DevCtrl*>(base + align256(sizeof(BlockDesc) * n));
+  g->partial = reinterpret_cast<double*>(base + align256(sizeof(BlockDesc) * n) + align256(sizeof(DevCtrl)));
+  g->partial_n = (size_t)max_group_ctas(blocks[0]->nsm) + n;
+  g->exec[0] = g->exec[1] = nullptr;
+  g->cap = nullptr;
+  g->timed = false;
+  for (int i = 0; i < n; ++i) g->table_host.push_back(blocks[i]->desc_host);
+  const int mixed = blocks[0]->p.precision == GBCFD_MIXED, vis = blocks[0]->p.viscous, cv = blocks[0]->curvi;
+  cudaError_t e = mixed ? (cv ? stage_prepare_f32c(vis) : stage_prepare_f32(vis))
+                        : (cv ? stage_prepare_f64c(vis) : stage_prepare_f64(vis));
+  if (e == cudaSuccess) e = cudaMemset(g->gctrl, 0, sizeof(DevCtrl));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete g; return cuda_fail(e, "group set-up"); }
+  const int occ = blocks[0]->p.precision == GBCFD_MIXED
+                      ? (blocks[0]->curvi ? stage_occupancy_f32c(blocks[0]->p.viscous) : stage_occupancy_f32(blocks[0]->p.viscous))
+                      : (blocks[0]->curvi ? stage_occupancy_f64c(blocks[0]->p.viscous) : stage_occupancy_f64(blocks[0]->p.viscous));
+  rc = group_split(g, occ, g->cap);
+  if (rc) { cudaStreamDestroy(g->cap); delete g; return rc; }
+  *out = g;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_group_destroy(gbcfd_group g) {
+  if (!g) return fail(GBCFD_ERR_ARG, "group is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  for (int p = 0; p < 2; ++p)
+    if (g->exec[p]) cudaGraphExecDestroy(g->exec[p]);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  delete g;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  return GBCFD_OK;
+}
+
+static GroupParams group_params(gbcfd_group g) {
+  GroupParams P;
+  memset(&P, 0, sizeof(P));
+  P.table = g->table;
+  P.nblocks = (int)g->blocks.size();
+  P.cur = g->blocks[0]->cur;
+  P.ph = physics_of(g->blocks[0]);
+  P.gctrl = g->gctrl;
+  P.partial = g->partial;
+  return P;
+}
+
+// one step of the group enqueued on s: time step, then halo exchange and one batched stage
+// launch, three times
+static int group_step_launches(gbcfd_group g, cudaStream_t s) {
+  const int n = (int)g->blocks.size();
+  gbcfd_block b0 = g->blocks[0];
+  std::vector<DevCtrl*> ctrls(n);
+  for (int i = 0; i < n; ++i) ctrls[i] = g->blocks[i]->ctrl;
+  auto mark = [&](int i) { return g->timed ? cudaEventRecordWithFlags(g->marks[i], s, cudaEventRecordExternal)
+                                            : cudaSuccess; };
+  CK(mark(0));
+  CK(launch_group_dt(ctrls.data(), n, b0->p.cfl, s, g->gctrl));
+  GroupParams P = group_params(g);
+  const int fields[3] = {F_STATE, F_STAGE1, F_STAGE2};
+  for (int st = 1; st <= 3; ++st) {
+    int rc = exchange(g->blocks.data(), n, fields[st - 1], false, s);
+    if (rc) return rc;
+    CK(mark(2 * st - 1));
+    CK(launch_stage(b0->p.precision, b0->p.viscous, b0->curvi, st, P, g->grid, s));
+    CK(mark(2 * st));
+  }
+  return GBCFD_OK;
+}
+
+static int group_check(gbcfd_group g) {
+  int rc = check_blocks(g->blocks.data(), (int)g->blocks.size());
+  if (rc) return rc;
+  for (auto b : g->blocks) {
+    if (b->next_stage != 1) return fail(GBCFD_ERR_STATE, "a group member was left between stages");
+    if (b->cur != g->blocks[0]->cur) return fail(GBCFD_ERR_STATE, "group members are at different step parities");
+  }
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_group_step(gbcfd_group g, int nsteps, void* stream) {
+  if (!g) return fail(GBCFD_ERR_ARG, "group is NULL");
+  if (nsteps < 0) return fail(GBCFD_ERR_ARG, "nsteps must be >= 0");
+  int rc = group_check(g);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = prepare_metrics(g->blocks.data(), (int)g->blocks.size(), s);
+  if (rc) return rc;
+  const bool mixed = g->blocks[0]->p.precision == GBCFD_MIXED;
+  for (int it = 0; it < nsteps; ++it) {
+    const int par = mixed ? g->blocks[0]->cur : 0;
+    if (!g->exec[par]) {  // capture one step on the private stream
+      CK(cudaStreamSynchronize(s));
+      CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+      rc = group_step_launches(g, g->cap);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(g->cap, &graph);
+      if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&g->exec[par], graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    CK(cudaGraphLaunch(g->exec[par], s));
+    if (mixed)
+      for (auto b : g->blocks) b->cur = 1 - b->cur;
+  }
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_group_set_timing(gbcfd_group g, void* const* events, int n) {
+  if (!g) return fail(GBCFD_ERR_ARG, "group is NULL");
+  if (events && n != 7) return fail(GBCFD_ERR_ARG, "timing needs exactly 7 events");
+  if (events)
+    for (int i = 0; i < 7; ++i)
+      if (!events[i]) return fail(GBCFD_ERR_ARG, "NULL event");
+  g->timed = events != nullptr;
+  for (int i = 0; i < 7; ++i) g->marks[i] = events ? static_cast<cudaEvent_t>(events[i]) : nullptr;
+  for (int p = 0; p < 2; ++p)
+    if (g->exec[p]) { cudaGraphExecDestroy(g->exec[p]); g->exec[p] = nullptr; }
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_group_tune(gbcfd_group g, void* stream, int* ctas_per_sm) {
+  if (!g) return fail(GBCFD_ERR_ARG, "group is NULL");
+  int rc = group_check(g);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = prepare_metrics(g->blocks.data(), (int)g->blocks.size(), s);
+  if (rc) return rc;
+  gbcfd_block b0 = g->blocks[0];
+  const int occ = b0->p.precision == GBCFD_MIXED
+                      ? (b0->curvi ? stage_occupancy_f32c(b0->p.viscous) : stage_occupancy_f32(b0->p.viscous))
+                      : (b0->curvi ? stage_occupancy_f64c(b0->p.viscous) : stage_occupancy_f64(b0->p.viscous));
+  // candidates: one resident wave (occ per SM) and finer splits of 2x and 4x that
+  const int cand[3] = {occ, 2 * occ, 4 * occ};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_c = occ;
+  rc = exchange(g->blocks.data(), (int)g->blocks.size(), F_STATE, false, s);
+  for (int ci = 0; ci < 3 && !rc; ++ci) {
+    if ((long long)b0->nsm * cand[ci] > max_group_ctas(b0->nsm)) continue;
+    rc = group_split(g, cand[ci], s);
+    if (rc) break;
+    GroupParams P = group_params(g);
+    float t = 0.f;
+    for (int rep = 0; rep < 4 && !rc; ++rep) {  // the first launch warms up, three are timed
+      cudaEventRecord(e0, s);
+      if (launch_stage(b0->p.precision, b0->p.viscous, b0->curvi, 1, P, g->grid, s) != cudaSuccess)
+        rc = fail(GBCFD_ERR_CUDA, "tuning launch failed");
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) t += ms;
+    }
+    if (!rc && t < best) { best = t; best_c = cand[ci]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  rc = group_split(g, best_c, s);
+  if (rc) return rc;
+  if (ctas_per_sm) *ctas_per_sm = best_c;
+  return GBCFD_OK;
+}
+
 // ---- read-backs ----------------------------------------------------------------------------
 static int read_ctrl(gbcfd_block b, DevCtrl* h, cudaStream_t s) {
   CK(cudaMemcpyAsync(h, b->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
@@ -630,10 +894,10 @@ extern "C" int gbcfd_get_dt(gbcfd_block b, double* dt, void* stream) {
 
 // ---- dispatch ----------------------------------------------------------------------------
 namespace gbcfd {
-cudaError_t launch_stage(int precision, int viscous, int curvi, int stage, const StageMaps& M,
-                         const StageParams& P, int grid, cudaStream_t s) {
+cudaError_t launch_stage(int precision, int viscous, int curvi, int stage, const GroupParams& P, int grid,
+                         cudaStream_t s) {
   if (precision == GBCFD_MIXED)
-    return curvi ? launch_stage_f32c(viscous, stage, M, P, grid, s) : launch_stage_f32(viscous, stage, M, P, grid, s);
-  return curvi ? launch_stage_f64c(viscous, stage, M, P, grid, s) : launch_stage_f64(viscous, stage, M, P, grid, s);
+    return curvi ? launch_stage_f32c(viscous, stage, P, grid, s) : launch_stage_f32(viscous, stage, P, grid, s);
+  return curvi ? launch_stage_f64c(viscous, stage, P, grid, s) : launch_stage_f64(viscous, stage, P, grid, s);
 }
 }  // namespace gbcfd

@@ -322,16 +322,22 @@ cudaError_t launch_init_rate_curvi(const Geometry& g, const Physics& ph, const d
 struct CtrlList {
   DevCtrl* c[MAX_GROUP];
 };
-__global__ void group_dt_kernel(CtrlList L, int n, double cfl) {
+// global time step of a group: cfl / max rate over the blocks, to every block (and to `extra`,
+// the group's own control block, when given)
+__global__ void group_dt_kernel(CtrlList L, int n, double cfl, DevCtrl* extra) {
   if (threadIdx.x != 0) return;
   double m = 0.0;
   for (int b = 0; b < n; ++b) m = fmax(m, L.c[b]->rate);
   for (int b = 0; b < n; ++b) L.c[b]->dt = cfl / m;
+  if (extra) {
+    extra->rate = m;
+    extra->dt = cfl / m;
+  }
 }
-cudaError_t launch_group_dt(DevCtrl* const* ctrls, int n, double cfl, cudaStream_t s) {
+cudaError_t launch_group_dt(DevCtrl* const* ctrls, int n, double cfl, cudaStream_t s, DevCtrl* extra) {
   CtrlList L;
   for (int b = 0; b < n && b < MAX_GROUP; ++b) L.c[b] = ctrls[b];
-  group_dt_kernel<<<1, 32, 0, s>>>(L, n, cfl);
+  group_dt_kernel<<<1, 32, 0, s>>>(L, n, cfl, extra);
   return cudaGetLastError();
 }
 

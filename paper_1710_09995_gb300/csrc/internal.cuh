@@ -69,21 +69,36 @@ struct Physics {
   int viscous, limiter;
 };
 
-// parameters of one stage launch
-struct StageParams {
+// ---- one block as the stage kernel sees it (device-resident descriptor table) --------------
+// The TMA descriptors live in global memory (written by the host before any launch that reads
+// them); the kernel selects the arrays of a stage from `stage` and the mixed path's parity `cur`.
+struct BlockDesc {
+  CUtensorMap tq[3];   // FP64: Qn, Q1, Q2 (stage inputs).  mixed: shadows SA, SB ([2] unused)
+  CUtensorMap td[2];   // mixed: D1, D2
+  CUtensorMap tm;      // metric planes (curvilinear)
   Geometry g;
-  Physics ph;
-  const double* qn;   // Q^n (f64): stages 2,3 of the FP64 path, all stages of the mixed path
-  const double* qs;   // stage input (f64, FP64 path): Qn, Q1 or Q2
-  double* qout;       // f64 output: Q1, Q2, Q^{n+1} (FP64 path) or Q^{n+1} (mixed stage 3)
-  float* sout;        // mixed stage 3: f32 shadow of Q^{n+1}
-  const float* dprev; // mixed: D1 (stage 2) or D2 (stage 3)
-  float* dout;        // mixed: D1 (stage 1) or D2 (stage 2)
-  double* rout;       // residual mode: compact R[5][nz][ny][nx]
+  double ihx, ihy, ihz;      // 1 / cell size (Cartesian)
+  double* q[3];              // FP64: Qn, Q1, Q2.  mixed: QA, QB
+  float* sh[2];              // mixed: shadows
+  float* d[2];               // mixed: increments
   DevCtrl* ctrl;
-  double* partial;    // [gridDim.x][NPART]
-  int ntx, nty;       // tiles along x and y
-  long long units;    // ntx * nty * nz (tile-planes)
+  int ntx, nty;              // tiles along x and y
+  long long units;           // work units (tile-planes) = ntx * nty * nz
+  int cta0, ctas;            // the CTAs of a group launch that work on this block
+  long long pad_[2];
+};
+
+// parameters of one stage launch over a group of blocks.  The grid is split between the blocks
+// (block b owns CTAs cta0 .. cta0 + ctas - 1, about in proportion to its work), so each CTA works
+// on one block and its partial sums go to slot blockIdx.x.
+struct GroupParams {
+  const BlockDesc* table;    // nblocks descriptors
+  int nblocks;
+  int cur;                   // mixed path: which of QA/QB, SA/SB holds Q^n
+  Physics ph;                // shared physics (gamma, mu, Pr, cfl, eps, viscous, limiter)
+  DevCtrl* gctrl;            // group control: counter, time step (read at stage start)
+  double* partial;           // [gridDim.x * NPART]
+  double* rout;              // residual mode (one block): compact R[5][nz][ny][nx]
 };
 
 // ---- block group descriptors for halo exchange ----------------------------------------------

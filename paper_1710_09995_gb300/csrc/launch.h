@@ -9,21 +9,17 @@ namespace gbcfd {
 // record an error for gbcfd_last_error() on this host thread and return `code`
 int set_error(int code, const std::string& msg);
 
-// tensor maps of one stage launch: staged state, staged increment, metric planes
-struct StageMaps {
-  const CUtensorMap* q;
-  const CUtensorMap* d;
-  const CUtensorMap* m;
-};
-
-// fused stage kernel; precision GBCFD_FP64 / GBCFD_MIXED, stage 0 = residual only
-cudaError_t launch_stage(int precision, int viscous, int curvi, int stage, const StageMaps& M,
-                         const StageParams& P, int grid, cudaStream_t s);
-
-cudaError_t launch_stage_f64(int viscous, int stage, const StageMaps& M, const StageParams& P, int grid, cudaStream_t s);
-cudaError_t launch_stage_f64c(int viscous, int stage, const StageMaps& M, const StageParams& P, int grid, cudaStream_t s);
-cudaError_t launch_stage_f32(int viscous, int stage, const StageMaps& M, const StageParams& P, int grid, cudaStream_t s);
-cudaError_t launch_stage_f32c(int viscous, int stage, const StageMaps& M, const StageParams& P, int grid, cudaStream_t s);
+// fused stage kernel over a group of blocks; precision GBCFD_FP64 / GBCFD_MIXED, stage 0 = residual
+cudaError_t launch_stage(int precision, int viscous, int curvi, int stage, const GroupParams& P, int grid,
+                         cudaStream_t s);
+cudaError_t launch_stage_f64(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s);
+cudaError_t launch_stage_f64c(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s);
+cudaError_t launch_stage_f32(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s);
+cudaError_t launch_stage_f32c(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s);
+cudaError_t stage_prepare_f64(int viscous);
+cudaError_t stage_prepare_f64c(int viscous);
+cudaError_t stage_prepare_f32(int viscous);
+cudaError_t stage_prepare_f32c(int viscous);
 int stage_occupancy_f64(int viscous);
 int stage_occupancy_f64c(int viscous);
 int stage_occupancy_f32(int viscous);
@@ -42,6 +38,6 @@ cudaError_t launch_metrics(const Geometry& g, const double* nodes, void* M, int 
 cudaError_t launch_init_rate_curvi(const Geometry& g, const Physics& ph, const double* q, const void* M,
                                    DevCtrl* ctrl, double* partial, int grid, int mixed, cudaStream_t s);
 // global time step of a group: dt = cfl / max rate, written to every block
-cudaError_t launch_group_dt(DevCtrl* const* ctrls, int n, double cfl, cudaStream_t s);
+cudaError_t launch_group_dt(DevCtrl* const* ctrls, int n, double cfl, cudaStream_t s, DevCtrl* extra = nullptr);
 
 }  // namespace gbcfd

@@ -208,32 +208,38 @@ __device__ __forceinline__ void cell_face_means(const T* mring, int mk, int mk1,
   }
 }
 
+// inverse spacings along (normal, tangent 1, tangent 2) of x-, y- and z-faces
+template <typename T> struct Tri { T v[3]; };
+template <typename T> __device__ __forceinline__ Tri<T> ihx3(T x, T y, T z) { return {{x, y, z}}; }
+template <typename T> __device__ __forceinline__ Tri<T> ihy3(T x, T y, T z) { return {{y, z, x}}; }
+template <typename T> __device__ __forceinline__ Tri<T> ihz3(T x, T y, T z) { return {{z, x, y}}; }
+
 // spectral-radius rate of one cell: sum over directions of the convective radius (plus 4x the
 // viscous one) divided by the volume, i.e. the inverse of the cell's stable step / CFL
 template <typename T>
-__device__ __forceinline__ T cell_rate(T r, T u, T v, T w, T p, const Physics& ph) {
+__device__ __forceinline__ T cell_rate(T r, T u, T v, T w, T p, const Physics& ph, T ihx, T ihy, T ihz) {
   using O = VM<T>;
   const T ir = O::rcp(r);
   const T c2 = T(ph.gamma) * p * ir;
   const T c = c2 * O::rsqrt(c2);
-  T rate = (O::ab(u) + c) * T(ph.ihx) + (O::ab(v) + c) * T(ph.ihy) + (O::ab(w) + c) * T(ph.ihz);
+  T rate = (O::ab(u) + c) * ihx + (O::ab(v) + c) * ihy + (O::ab(w) + c) * ihz;
   if (ph.viscous) {
-    const double f = fmax(4.0 / 3.0, ph.gamma / ph.Pr);
-    const T s2 = T(ph.ihx * ph.ihx + ph.ihy * ph.ihy + ph.ihz * ph.ihz);
-    rate += T(4.0 * f * ph.mu) * ir * s2;
+    const T f = T(fmax(4.0 / 3.0, ph.gamma / ph.Pr));
+    const T s2 = ihx * ihx + ihy * ihy + ihz * ihz;
+    rate += T(4.0 * ph.mu) * f * ir * s2;
   }
   return rate;
 }
 
 // ---- the kernel ------------------------------------------------------------------------------
-// STAGE 0: residual only (R to P.rout); 1..3: Runge-Kutta stages
+// One launch advances one Runge-Kutta stage of a group of blocks (a single block is a group of
+// one).  STAGE 0: residual only (one block, R to P.rout); 1..3: the stages of Eqs. 4-6.
 // registers: the register file is split over the SM's four sub-partitions (16K each) and warps
 // are spread round-robin, so two 9-warp CTAs (5 warps on one sub-partition) allow 96 registers
-// per thread on the mixed path, one CTA (3 warps) 168 on the FP64 path
+// per thread on the mixed path, one CTA (3 warps) 168 on the FP64 and curvilinear paths
 template <typename T, bool VISC, int STAGE, bool CURVI>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
-    stage_kernel(const __grid_constant__ CUtensorMap tmq, const __grid_constant__ CUtensorMap tmd,
-                 const __grid_constant__ CUtensorMap tmm, const StageParams P) {
+    stage_kernel(const GroupParams P) {
   constexpr bool MIXED = sizeof(T) == 4;
   constexpr bool LOADD = MIXED && (STAGE == 2 || STAGE == 3);
   using PL = Plan<T, VISC, CURVI>;
@@ -253,14 +259,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
   int* slast = sabort + 1;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const Geometry& g = P.g;
   const Physics& ph = P.ph;
   const Consts<T> K = make_consts<T>(ph.gamma, ph.eps, VISC ? ph.mu : 0.0, ph.Pr, ph.limiter);
   const T gm1 = T(ph.gamma - 1.0);
-  // inverse spacings along (normal, tangent 1, tangent 2) of x-, y- and z-faces
-  const T ihX[3] = {T(ph.ihx), T(ph.ihy), T(ph.ihz)};
-  const T ihY[3] = {T(ph.ihy), T(ph.ihz), T(ph.ihx)};
-  const T ihZ[3] = {T(ph.ihz), T(ph.ihx), T(ph.ihy)};
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE + NMS; ++s) mbar_init(&bar[s], 1);
@@ -269,23 +270,75 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
   }
   __syncthreads();
 
-  const double dt = (STAGE == 0) ? 0.0 : P.ctrl->dt;
+  const double dt = (STAGE == 0) ? 0.0 : P.gctrl->dt;
   const T dtT = T(dt);
   unsigned phase_bits = 0;   // parity of each staging slot (uniform across the CTA)
   unsigned pending = 0;      // slots with a copy in flight (meaningful in thread 0)
   unsigned mphase = 0;       // parity of each metric slot
   unsigned mpending = 0;     // metric slots with a copy in flight (thread 0)
   bool bad = false;          // non-physical value met by this thread
+  // per-thread sums for the current block: R^2 (stage 1), max rate (stage 3)
   double nacc[5] = {0, 0, 0, 0, 0};
   float ncomp[5] = {0, 0, 0, 0, 0};  // Kahan compensation (mixed path)
   float nsum[5] = {0, 0, 0, 0, 0};
   T rate_max = T(0);
 
-  const long long W = P.units;
-  const long long u_begin = (long long)blockIdx.x * W / gridDim.x;
-  const long long u_end = (long long)(blockIdx.x + 1) * W / gridDim.x;
+  // the block of this CTA and the CTA's contiguous share of its tile-planes
+  int bsel;
+  {
+    int lo = 0, hi = P.nblocks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.table[mid].cta0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    bsel = lo;
+  }
+  const BlockDesc* D = P.table + bsel;
+  const int lcta = (int)blockIdx.x - D->cta0, nctas = D->ctas;
+  const long long W = D->units;
+  const long long u_begin = (long long)lcta * W / nctas;
+  const long long u_end = (long long)(lcta + 1) * W / nctas;
   constexpr unsigned QBYTES = 5u * MS * sizeof(T);
   constexpr unsigned DBYTES = 5u * MS * sizeof(float);
+
+  // this CTA's sums -> partial slot blockIdx.x; all threads call it together
+  auto flush = [&]() {
+    if constexpr (STAGE == 1 || STAGE == 3) {
+      double part[6];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        part[m] = MIXED ? double(nsum[m]) - double(ncomp[m]) : nacc[m];
+        nacc[m] = 0.0;
+        nsum[m] = 0.f;
+        ncomp[m] = 0.f;
+      }
+      part[5] = double(rate_max);
+      rate_max = T(0);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) part[m] += __shfl_xor_sync(0xffffffffu, part[m], off);
+        part[5] = fmax(part[5], __shfl_xor_sync(0xffffffffu, part[5], off));
+      }
+      __syncthreads();
+      if (lane == 0)
+        for (int m = 0; m < 6; ++m) red[warp * NPART + m] = part[m];
+      __syncthreads();
+      if (tid == 0) {
+        double sum[6] = {0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < NWARP; ++w) {
+          for (int m = 0; m < 5; ++m) sum[m] += red[w * NPART + m];
+          sum[5] = fmax(sum[5], red[w * NPART + 5]);
+        }
+        for (int m = 0; m < 6; ++m) P.partial[(size_t)blockIdx.x * NPART + m] = sum[m];
+      }
+    }
+  };
+
+  // ring slot of plane kp (kp >= -2)
+  auto rslot = [](int kp) { return kp & 3; };
+  const bool owner = warp < TY;  // warps 0..TY-1 own row `warp` of the tile; warp TY helps
+  const Geometry g = D->g;
 
   for (long long u = u_begin; u < u_end;) {
     const int nz = g.nz;
@@ -293,16 +346,38 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
     const int k0 = (int)(u - tile * nz);
     const int k1 = (int)min((long long)nz, (long long)k0 + (u_end - u));
     u += k1 - k0;
-    const int tix = (int)(tile % P.ntx), tiy = (int)(tile / P.ntx);
+    const int tix = (int)(tile % D->ntx), tiy = (int)(tile / D->ntx);
     const int x0 = tix * TX, y0 = tiy * TY;  // storage coordinates of the box origin
     const int last_plane = k1 + 1;
+    // arrays of this stage
+    const CUtensorMap* tmq;
+    const CUtensorMap* tmd = &D->td[0];
+    const double *qs = nullptr, *qn = nullptr;
+    double* qout = nullptr;
+    float *sout = nullptr, *dout = nullptr;
+    const float* dprev = nullptr;
+    if constexpr (!MIXED) {
+      const int in = STAGE == 0 ? 0 : STAGE - 1;
+      tmq = &D->tq[in];
+      qs = D->q[in];
+      qn = D->q[0];
+      qout = D->q[STAGE % 3];
+    } else {
+      const int c = P.cur;
+      tmq = &D->tq[c];
+      qn = D->q[c];
+      if (STAGE == 1) dout = D->d[0];
+      if (STAGE == 2) { dprev = D->d[0]; dout = D->d[1]; tmd = &D->td[0]; }
+      if (STAGE == 3) { dprev = D->d[1]; qout = D->q[1 - c]; sout = D->sh[1 - c]; tmd = &D->td[1]; }
+    }
+    const T hx = T(D->ihx), hy = T(D->ihy), hz = T(D->ihz);  // inverse cell sizes
 
     auto request = [&](int kp) {  // thread 0 only
       const int s = (kp + 2) & (NSTAGE - 1);
       fence_proxy_async();
       mbar_expect_tx(&bar[s], QBYTES + (LOADD ? DBYTES : 0u));
-      tma_load_4d(smem + PL::stq + s * PL::QSLOT, &tmq, &bar[s], x0, y0, kp + HALO, 0);
-      if (LOADD) tma_load_4d(smem + PL::std_ + s * PL::DSLOT, &tmd, &bar[s], x0, y0, kp + HALO, 0);
+      tma_load_4d(smem + PL::stq + s * PL::QSLOT, tmq, &bar[s], x0, y0, kp + HALO, 0);
+      if (LOADD) tma_load_4d(smem + PL::std_ + s * PL::DSLOT, tmd, &bar[s], x0, y0, kp + HALO, 0);
       pending |= 1u << s;
     };
     // wait for plane kp, convert it into ring slot kp & 3, then refill the staging slot
@@ -313,7 +388,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
       phase_bits ^= 1u << s;
       const T* sq = reinterpret_cast<const T*>(smem + PL::stq + s * PL::QSLOT);
       const float* sd = reinterpret_cast<const float*>(smem + PL::std_ + s * PL::DSLOT);
-      T* rs = ring + (size_t)(kp & 3) * NV * MS;
+      T* rs = ring + (size_t)rslot(kp) * NV * MS;
       for (int c = tid; c < MS; c += NT) {
         const int cy = c / BX, cx = c - cy * BX;
         T q[5];
@@ -355,7 +430,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
           const int s = mslot(m_req);
           fence_proxy_async();
           mbar_expect_tx(&bar[NSTAGE + s], 10u * MS * sizeof(T));
-          tma_load_4d(smem + PL::mring + s * PL::MSLOT, &tmm, &bar[NSTAGE + s], x0, y0, m_req + HALO, 0);
+          tma_load_4d(smem + PL::mring + s * PL::MSLOT, &D->tm, &bar[NSTAGE + s], x0, y0, m_req + HALO, 0);
           mpending |= 1u << s;
         }
       }
@@ -383,18 +458,17 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
     if (*sabort) break;
 
     // owning warps: cell (lane, warp) of the tile
-    const bool owner = warp < TY;
     const int ci = x0 + lane, cj = y0 + warp;  // interior coordinates of the owned cell
     const bool live = owner && ci < g.nx && cj < g.ny;
     const int ocy = warp + HALO, ocx = lane + HALO;
     T fzl[5], fzu[5];
     if (owner) {
-      const FaceIdx iz = zface_idx<NV>((k0 - 2) & 3, (k0 - 1) & 3, k0 & 3, (k0 + 1) & 3, ocy, ocx);
+      const FaceIdx iz = zface_idx<NV>(rslot(k0 - 2), rslot(k0 - 1), rslot(k0), rslot(k0 + 1), ocy, ocx);
       if constexpr (CURVI)
         face_flux_curvi<T, VISC>(ring, mring, NV * MS, iz.b, tg_of(iz), zface_met(mslot(k0 - 1), mslot(k0), ocy, ocx),
                                  K, fzl);
       else
-        face_flux<T, VISC, 2>(ring, iz, ihZ, K, fzl);
+        face_flux<T, VISC, 2>(ring, iz, ihz3(hx, hy, hz).v, K, fzl);
     }
     __syncthreads();  // the first consume below overwrites plane k0-2, read by the z-face above
 
@@ -409,13 +483,13 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
         const long long o = gidx(g, ci, cj, k), of = gidxf(g, ci, cj, k);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          if constexpr (!MIXED && STAGE >= 1) qs_[v] = __ldg(P.qs + v * g.field + o);
-          if constexpr (!MIXED && STAGE >= 2) qn_[v] = __ldg(P.qn + v * g.field + o);
-          if constexpr (MIXED && STAGE == 3) qn_[v] = __ldg(P.qn + v * g.field + o);
-          if constexpr (LOADD) dp_[v] = __ldg(P.dprev + v * g.fieldf + of);
+          if constexpr (!MIXED && STAGE >= 1) qs_[v] = __ldg(qs + v * g.field + o);
+          if constexpr (!MIXED && STAGE >= 2) qn_[v] = __ldg(qn + v * g.field + o);
+          if constexpr (MIXED && STAGE == 3) qn_[v] = __ldg(qn + v * g.field + o);
+          if constexpr (LOADD) dp_[v] = __ldg(dprev + v * g.fieldf + of);
         }
       }
-      const int sk = k & 3, sm = (k - 1) & 3, sp = (k + 1) & 3, s2 = (k + 2) & 3;
+      const int sk = rslot(k), sm = rslot(k - 1), sp = rslot(k + 1), s2 = rslot(k + 2);
       const int mk = mslot(k), mk1 = mslot(k + 1);
       if (owner) {
         T Fa[5], Fb[5];
@@ -424,8 +498,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
           face_flux_curvi<T, VISC>(ring, mring, NV * MS, ix.b, tg_of(ix), xface_met(mk, mk1, ocy, ocx), K, Fa);
           face_flux_curvi<T, VISC>(ring, mring, NV * MS, iy.b, tg_of(iy), yface_met(mk, mk1, ocy, ocx), K, Fb);
         } else {
-          face_flux<T, VISC, 0>(ring, ix, ihX, K, Fa);
-          face_flux<T, VISC, 1>(ring, iy, ihY, K, Fb);
+          face_flux<T, VISC, 0>(ring, ix, ihx3(hx, hy, hz).v, K, Fa);
+          face_flux<T, VISC, 1>(ring, iy, ihy3(hx, hy, hz).v, K, Fb);
         }
 #pragma unroll
         for (int m = 0; m < 5; ++m) fx[(m * TY + warp) * (TX + 1) + lane] = Fa[m];
@@ -435,7 +509,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
         if constexpr (CURVI)
           face_flux_curvi<T, VISC>(ring, mring, NV * MS, iz.b, tg_of(iz), zface_met(mk, mk1, ocy, ocx), K, fzu);
         else
-          face_flux<T, VISC, 2>(ring, iz, ihZ, K, fzu);
+          face_flux<T, VISC, 2>(ring, iz, ihz3(hx, hy, hz).v, K, fzu);
       } else {
         // the tile's upper y-faces (all lanes) and upper x-faces (lanes < TY)
         T Fa[5], Fb[5];
@@ -448,8 +522,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
             face_flux_curvi<T, VISC>(ring, mring, NV * MS, ix.b, tg_of(ix),
                                      xface_met(mk, mk1, lane + HALO, TX + HALO), K, Fb);
         } else {
-          face_flux<T, VISC, 1>(ring, iy, ihY, K, Fa);
-          if (lane < TY) face_flux<T, VISC, 0>(ring, ix, ihX, K, Fb);
+          face_flux<T, VISC, 1>(ring, iy, ihy3(hx, hy, hz).v, K, Fa);
+          if (lane < TY) face_flux<T, VISC, 0>(ring, ix, ihx3(hx, hy, hz).v, K, Fb);
         }
 #pragma unroll
         for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + TY) * TX + lane] = Fa[m];
@@ -468,7 +542,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
           if constexpr (CURVI)
             R[m] = (ddx + ddy) + (fzu[m] - fzl[m]);  // face fluxes carry |S|; divided by V below
           else
-            R[m] = (ddx * T(ph.ihx) + ddy * T(ph.ihy)) + (fzu[m] - fzl[m]) * T(ph.ihz);
+            R[m] = (ddx * hx + ddy * hy) + (fzu[m] - fzl[m]) * hz;
         }
         if constexpr (CURVI) {
           const T iv = Fm::rcp(mring[mb(mk, ocy, ocx) + 9 * MS]);
@@ -489,7 +563,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
             if constexpr (STAGE == 1) out[m] = adv;
             else if constexpr (STAGE == 2) out[m] = 0.75 * qn_[m] + 0.25 * adv;
             else out[m] = qn_[m] / 3.0 + (2.0 / 3.0) * adv;
-            P.qout[m * g.field + o] = out[m];
+            qout[m * g.field + o] = out[m];
           }
           if constexpr (STAGE == 3) {
             const double ir = 1.0 / out[0];
@@ -502,7 +576,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
               rate_max = fmax(rate_max, T(cell_rate_curvi<double>(out[0], uu, vv, ww, pp, sb,
                                                                   mring[mb(mk, ocy, ocx) + 9 * MS], ph)));
             } else {
-              rate_max = fmax(rate_max, T(cell_rate<double>(out[0], uu, vv, ww, pp, ph)));
+              rate_max = fmax(rate_max, T(cell_rate<double>(out[0], uu, vv, ww, pp, ph, hx, hy, hz)));
             }
           }
         } else {
@@ -511,19 +585,19 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
           for (int m = 0; m < 5; ++m) inc[m] = -float(dtT) * float(R[m]);
           if constexpr (STAGE == 1) {
 #pragma unroll
-            for (int m = 0; m < 5; ++m) P.dout[m * g.fieldf + of] = inc[m];
+            for (int m = 0; m < 5; ++m) dout[m * g.fieldf + of] = inc[m];
           } else if constexpr (STAGE == 2) {
 #pragma unroll
-            for (int m = 0; m < 5; ++m) P.dout[m * g.fieldf + of] = 0.25f * (dp_[m] + inc[m]);
+            for (int m = 0; m < 5; ++m) dout[m * g.fieldf + of] = 0.25f * (dp_[m] + inc[m]);
           } else {
             float qf[5];
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
               const float d = (2.0f / 3.0f) * (dp_[m] + inc[m]);
               const double qnew = qn_[m] + f32_to_f64_bits(d);
-              P.qout[m * g.field + o] = qnew;
+              qout[m * g.field + o] = qnew;
               qf[m] = f64_to_f32_bits(qnew);
-              P.sout[m * g.fieldf + of] = qf[m];
+              sout[m * g.fieldf + of] = qf[m];
             }
             const float ir = VM<float>::rcp(qf[0]);
             const float uu = qf[1] * ir, vv = qf[2] * ir, ww = qf[3] * ir;
@@ -535,7 +609,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
               rate_max = fmax(rate_max, T(cell_rate_curvi<float>(qf[0], uu, vv, ww, pp, sb,
                                                                  mring[mb(mk, ocy, ocx) + 9 * MS], ph)));
             } else {
-              rate_max = fmax(rate_max, T(cell_rate<float>(qf[0], uu, vv, ww, pp, ph)));
+              rate_max = fmax(rate_max, T(cell_rate<float>(qf[0], uu, vv, ww, pp, ph, hx, hy, hz)));
             }
           }
         }
@@ -566,60 +640,53 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
         if (pending & (1u << s)) mbar_wait_bounded(&bar[s], (phase_bits >> s) & 1u);
       for (int s = 0; s < NMS; ++s)
         if (mpending & (1u << s)) mbar_wait_bounded(&bar[NSTAGE + s], (mphase >> s) & 1u);
-      atomicOr(&P.ctrl->flag, FLAG_TIMEOUT);
+      atomicOr(&D->ctrl->flag, FLAG_TIMEOUT);
     }
   }
-  if (bad) atomicOr(&P.ctrl->flag, FLAG_NONPHYSICAL);
-  if constexpr (STAGE == 1 || STAGE == 3) {
+  if (bad) atomicOr(&D->ctrl->flag, FLAG_NONPHYSICAL);
 
-    // ---- per-CTA partials, then the last CTA reduces them in a fixed order ---------------------
-    double part[6];
-  #pragma unroll
-    for (int m = 0; m < 5; ++m) part[m] = MIXED ? double(nsum[m]) - double(ncomp[m]) : nacc[m];
-    part[5] = double(rate_max);
-  #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-  #pragma unroll
-      for (int m = 0; m < 5; ++m) part[m] += __shfl_xor_sync(0xffffffffu, part[m], off);
-      part[5] = fmax(part[5], __shfl_xor_sync(0xffffffffu, part[5], off));
-    }
-    if (lane == 0)
-      for (int m = 0; m < 6; ++m) red[warp * NPART + m] = part[m];
-    __syncthreads();
+  if constexpr (STAGE == 1 || STAGE == 3) {
+    flush();
+    // the last CTA to finish reduces, per block, the slots of the CTAs that worked on it (in CTA
+    // order: deterministic), and for stage 3 takes the group's time step from the largest rate
     if (tid == 0) {
-      double s[6] = {0, 0, 0, 0, 0, 0};
-      for (int w = 0; w < NWARP; ++w) {
-        for (int m = 0; m < 5; ++m) s[m] += red[w * NPART + m];
-        s[5] = fmax(s[5], red[w * NPART + 5]);
-      }
-      for (int m = 0; m < 6; ++m) P.partial[(size_t)blockIdx.x * NPART + m] = s[m];
       __threadfence();
-      const unsigned prev = atomicAdd(&P.ctrl->counter, 1u);
+      const unsigned prev = atomicAdd(&P.gctrl->counter, 1u);
       *slast = (prev == gridDim.x - 1);
     }
     __syncthreads();
     if (!*slast || warp != 0) return;
     __threadfence();
-    double s[6] = {0, 0, 0, 0, 0, 0};
-    for (int c = lane; c < (int)gridDim.x; c += 32) {
-      for (int m = 0; m < 5; ++m) s[m] += __ldcg(P.partial + (size_t)c * NPART + m);
-      s[5] = fmax(s[5], __ldcg(P.partial + (size_t)c * NPART + 5));
-    }
-  #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-  #pragma unroll
-      for (int m = 0; m < 5; ++m) s[m] += __shfl_xor_sync(0xffffffffu, s[m], off);
-      s[5] = fmax(s[5], __shfl_xor_sync(0xffffffffu, s[5], off));
+    double gmax = 0.0;
+    for (int b = 0; b < P.nblocks; ++b) {
+      const BlockDesc* Db = P.table + b;
+      double s[6] = {0, 0, 0, 0, 0, 0};
+      for (int c = lane; c < Db->ctas; c += 32) {
+        const double* src = P.partial + (size_t)(Db->cta0 + c) * NPART;
+        for (int m = 0; m < 5; ++m) s[m] += __ldcg(src + m);
+        s[5] = fmax(s[5], __ldcg(src + 5));
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) s[m] += __shfl_xor_sync(0xffffffffu, s[m], off);
+        s[5] = fmax(s[5], __shfl_xor_sync(0xffffffffu, s[5], off));
+      }
+      gmax = fmax(gmax, s[5]);
+      if (lane == 0) {
+        const double n = (double)Db->g.nx * Db->g.ny * Db->g.nz;
+        if (STAGE == 1)
+          for (int m = 0; m < 5; ++m) Db->ctrl->norms[m] = sqrt(s[m] / n);
+        if (STAGE == 3) Db->ctrl->rate = s[5];
+      }
     }
     if (lane == 0) {
-      const double n = (double)g.nx * g.ny * g.nz;
-      if (STAGE == 1)
-        for (int m = 0; m < 5; ++m) P.ctrl->norms[m] = sqrt(s[m] / n);
       if (STAGE == 3) {
-        P.ctrl->rate = s[5];
-        P.ctrl->dt = ph.cfl / s[5];
+        P.gctrl->rate = gmax;
+        P.gctrl->dt = ph.cfl / gmax;
+        for (int b = 0; b < P.nblocks; ++b) P.table[b].ctrl->dt = ph.cfl / gmax;
       }
-      P.ctrl->counter = 0u;
+      P.gctrl->counter = 0u;
     }
   }
 }

@@ -5,32 +5,60 @@
 
 namespace gbcfd {
 
+// the kernel's dynamic shared-memory limit, set once per device (before any graph capture)
 template <typename T, bool VISC, int STAGE, bool CURVI>
-cudaError_t stage_go(const StageMaps& M, const StageParams& P, int grid, cudaStream_t s) {
-  auto k = stage_kernel<T, VISC, STAGE, CURVI>;
-  const size_t bytes = Plan<T, VISC, CURVI>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t stage_attr() {
+  static unsigned long long done = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  k<<<grid, NT, bytes, s>>>(*M.q, *M.d, *M.m, P);
+  if (dev < 64 && ((done >> dev) & 1ull)) return cudaSuccess;
+  e = cudaFuncSetAttribute(stage_kernel<T, VISC, STAGE, CURVI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Plan<T, VISC, CURVI>::bytes);
+  if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+  return e;
+}
+
+template <typename T, bool VISC, int STAGE, bool CURVI>
+cudaError_t stage_go(const GroupParams& P, int grid, cudaStream_t s) {
+  cudaError_t e = stage_attr<T, VISC, STAGE, CURVI>();
+  if (e != cudaSuccess) return e;
+  stage_kernel<T, VISC, STAGE, CURVI><<<grid, NT, Plan<T, VISC, CURVI>::bytes, s>>>(P);
   return cudaGetLastError();
 }
 
 template <typename T, bool CURVI>
-cudaError_t stage_dispatch(int viscous, int stage, const StageMaps& M, const StageParams& P, int grid,
-                           cudaStream_t s) {
+cudaError_t stage_prepare(int viscous) {
+  cudaError_t e = cudaSuccess;
+  if (viscous) {
+    if (e == cudaSuccess) e = stage_attr<T, true, 0, CURVI>();
+    if (e == cudaSuccess) e = stage_attr<T, true, 1, CURVI>();
+    if (e == cudaSuccess) e = stage_attr<T, true, 2, CURVI>();
+    if (e == cudaSuccess) e = stage_attr<T, true, 3, CURVI>();
+  } else {
+    if (e == cudaSuccess) e = stage_attr<T, false, 0, CURVI>();
+    if (e == cudaSuccess) e = stage_attr<T, false, 1, CURVI>();
+    if (e == cudaSuccess) e = stage_attr<T, false, 2, CURVI>();
+    if (e == cudaSuccess) e = stage_attr<T, false, 3, CURVI>();
+  }
+  return e;
+}
+
+template <typename T, bool CURVI>
+cudaError_t stage_dispatch(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s) {
   if (viscous) {
     switch (stage) {
-      case 0: return stage_go<T, true, 0, CURVI>(M, P, grid, s);
-      case 1: return stage_go<T, true, 1, CURVI>(M, P, grid, s);
-      case 2: return stage_go<T, true, 2, CURVI>(M, P, grid, s);
-      case 3: return stage_go<T, true, 3, CURVI>(M, P, grid, s);
+      case 0: return stage_go<T, true, 0, CURVI>(P, grid, s);
+      case 1: return stage_go<T, true, 1, CURVI>(P, grid, s);
+      case 2: return stage_go<T, true, 2, CURVI>(P, grid, s);
+      case 3: return stage_go<T, true, 3, CURVI>(P, grid, s);
     }
   } else {
     switch (stage) {
-      case 0: return stage_go<T, false, 0, CURVI>(M, P, grid, s);
-      case 1: return stage_go<T, false, 1, CURVI>(M, P, grid, s);
-      case 2: return stage_go<T, false, 2, CURVI>(M, P, grid, s);
-      case 3: return stage_go<T, false, 3, CURVI>(M, P, grid, s);
+      case 0: return stage_go<T, false, 0, CURVI>(P, grid, s);
+      case 1: return stage_go<T, false, 1, CURVI>(P, grid, s);
+      case 2: return stage_go<T, false, 2, CURVI>(P, grid, s);
+      case 3: return stage_go<T, false, 3, CURVI>(P, grid, s);
     }
   }
   return cudaErrorInvalidValue;

@@ -67,6 +67,12 @@ SIGNATURES = {
     "gbcfd_get_dt": [_VP, _D, _VP],
     "gbcfd_time_step_noalloc": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), _D, _VP,
                                 _VP],
+    "gbcfd_group_required_bytes": [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+    "gbcfd_group_create": [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.c_size_t, ctypes.POINTER(_VP)],
+    "gbcfd_group_destroy": [_VP],
+    "gbcfd_group_step": [_VP, ctypes.c_int, _VP],
+    "gbcfd_group_tune": [_VP, _VP, ctypes.POINTER(ctypes.c_int)],
+    "gbcfd_group_set_timing": [_VP, ctypes.POINTER(_VP), ctypes.c_int],
     "gbcfd_last_error": [],
 }
 
@@ -230,4 +236,85 @@ def time_step_noalloc(q, prm: Params, spacing, out=None, stream=None):
         out = torch.empty(1, dtype=torch.float64, device=q.device)
     sp = (ctypes.c_double * 3)(*spacing)
     _check(lib().gbcfd_time_step_noalloc(_ptr(q), nx, ny, nz, ctypes.byref(prm), sp, _ptr(out), _stream(stream)))
+    return out
+
+
+class Group:
+    """Many blocks advanced with one launch per stage and a CUDA graph per step (gbcfd_group_*)."""
+
+    def __init__(self, blocks):
+        self.blocks = list(blocks)
+        nbytes = ctypes.c_size_t(0)
+        _check(lib().gbcfd_group_required_bytes(len(self.blocks), ctypes.byref(nbytes)))
+        dev = self.blocks[0].memory.device
+        self.memory = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=dev)
+        base = self.memory.data_ptr()
+        off = (-base) % 256
+        h = ctypes.c_void_p(0)
+        _check(lib().gbcfd_group_create(_handles(self.blocks), len(self.blocks), ctypes.c_void_p(base + off),
+                                        nbytes.value, ctypes.byref(h)))
+        self.handle = h
+
+    def step(self, nsteps=1, stream=None):
+        _check(lib().gbcfd_group_step(self.handle, int(nsteps), _stream(stream)))
+
+    def tune(self, stream=None) -> int:
+        c = ctypes.c_int(0)
+        _check(lib().gbcfd_group_tune(self.handle, _stream(stream), ctypes.byref(c)))
+        return c.value
+
+    def set_timing(self, events):
+        """events: 7 torch.cuda.Event(enable_timing=True) recorded inside every step (or None)"""
+        self._events = events
+        if events is None:
+            _check(lib().gbcfd_group_set_timing(self.handle, None, 0))
+            return
+        for e in events:
+            e.record()  # creates the underlying CUDA event
+        torch.cuda.current_stream().synchronize()
+        arr = (ctypes.c_void_p * 7)(*[e.cuda_event for e in events])
+        _check(lib().gbcfd_group_set_timing(self.handle, arr, 7))
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().gbcfd_group_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def blocks_for_lattice(lat, precision=MIXED, device=None):
+    """The blocks of a cases.Lattice, connected face to face with periodic wrap and holding their
+    part of the global state; returned in the lattice's block order (k slowest, then j, i)."""
+    prm = params(lat.gamma, 0.0, 0.72, lat.cfl, lat.eps, False, 0, precision)
+    nx, ny, nz = lat.shape
+    sl = lat.block_slices()
+    blk = {}
+    for (i, j, k), (zs, ys, xs) in sl.items():
+        b = Block(lat.sx[i], lat.sy[j], lat.sz[k], prm, device)
+        b.set_metrics(spacing=lat.spacing)
+        blk[(i, j, k)] = b
+    for (i, j, k), b in blk.items():
+        b.connect("+x", blk[((i + 1) % nx, j, k)])
+        b.connect("+y", blk[(i, (j + 1) % ny, k)])
+        b.connect("+z", blk[(i, j, (k + 1) % nz)])
+    for key, b in blk.items():
+        zs, ys, xs = sl[key]
+        part = lat.state[:, zs, ys, xs]
+        part = part.contiguous() if isinstance(part, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(part))
+        b.set_state(part.to(b.memory.device))
+    return [blk[key] for key in sl]
+
+
+def gather_lattice(lat, blocks, out=None):
+    """global state [5][Nz][Ny][Nx] float64 assembled from the lattice's blocks"""
+    ox, oy, oz = lat.offsets()
+    if out is None:
+        out = torch.empty((5, oz[-1], oy[-1], ox[-1]), dtype=torch.float64, device=blocks[0].memory.device)
+    for b, (zs, ys, xs) in zip(blocks, lat.block_slices().values()):
+        out[:, zs, ys, xs] = b.get_state()
     return out

@@ -78,3 +78,82 @@ def test_fullsize_warped_mixed_step(gb, case):
     assert 0 < dq < 0.1
     assert dt0 > 0
     blk.close()
+
+
+# ---- the 96-block lattice (4 x 4 x 6, sides 16..160, 1.37e8 cells), Euler at Mach 0.8 ----------
+
+@pytest.fixture(scope="module")
+def lattice():
+    return cases.lattice_case(device="cuda")
+
+
+def lattice_windows(lat, nbox=6, size=8, seed=2):
+    """sample corners, each box placed across a block interface (and some across the periodic
+    wrap): the corner is drawn within 4 cells before a block boundary"""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ox, oy, oz = lat.offsets()
+    out = []
+    for i in range(nbox):
+        c = []
+        for off in (oz, oy, ox):
+            b = off[int(rng.integers(0, len(off) - 1))]
+            c.append((b - int(rng.integers(1, 5))) % off[-1])
+        out.append(tuple(c))
+    out[0] = (oz[-1] - 4, oy[-1] - 4, ox[-1] - 4)  # the corner where the wrap meets in all three
+    return out
+
+
+def window(lat, z0, y0, x0, size, margin):
+    N = lat.state.shape[1:]
+    idx = [torch.arange(a - margin, a + size + margin, device=lat.state.device) % n for a, n in zip((z0, y0, x0), N)]
+    return lat.state[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]].cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fullsize_lattice_group_step(gb, lattice, precision):
+    """One group step of the full lattice equals the FP64 oracle on sampled 8^3 boxes.  Each
+    sample is an exact sub-problem: the oracle steps the box with a 6-cell margin (2 halo cells
+    per stage, 3 stages) at the group's time step, and only the box is compared.  The time step is
+    the minimum of the blocks' CFL steps; the FP64 ones are checked against the oracle's on
+    sampled blocks.  Bars: FP64 1e-12, mixed 1e-6 density and 1e-5 others (relative L2 per
+    variable, floor 1e-3 of density's norm)."""
+    lat = lattice
+    blocks = gb.blocks_for_lattice(lat, precision)
+    dts = [b.get_dt() for b in blocks]
+    p = oracle.params(lat.gamma, 0.0, 0.72, lat.cfl, lat.eps, False, 0)
+    if precision == 0:
+        sl = list(lat.block_slices().values())
+        for bi in (0, 37, 95):
+            zs, ys, xs = sl[bi]
+            q = lat.state[:, zs, ys, xs].cpu().numpy()
+            nz_, ny_, nx_ = q.shape[1:]
+            M = oracle.metrics(cases.cartesian_nodes(nx_, ny_, nz_, *lat.spacing))
+            want = oracle.dt(p, oracle.pad(q), M)
+            assert abs(dts[bi] - want) <= 1e-13 * want
+    dt = min(dts)
+    g = gb.Group(blocks)
+    g.tune()
+    g.step(1)
+    out = gb.gather_lattice(lat, blocks)
+    assert abs(blocks[0].get_dt() - blocks[-1].get_dt()) == 0.0
+    size, margin = 8, 6
+    for z0, y0, x0 in lattice_windows(lat):
+        w = window(lat, z0, y0, x0, size, margin)
+        n = size + 2 * margin
+        M = oracle.metrics(cases.cartesian_nodes(n, n, n, *lat.spacing))
+        ref, _, _ = oracle.step(p, oracle.pad(w), M, 1, dt_fixed=dt)
+        want = oracle.interior(ref)[:, margin:margin + size, margin:margin + size, margin:margin + size]
+        N = out.shape[1:]
+        idx = [torch.arange(a, a + size, device=out.device) % m for a, m in zip((z0, y0, x0), N)]
+        got = out[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]].cpu().numpy()
+        floor = 1e-3 * np.linalg.norm(want[0])
+        err = [np.linalg.norm(got[m] - want[m]) / max(np.linalg.norm(want[m]), floor) for m in range(5)]
+        if precision == 0:
+            assert max(err) <= 1e-12, ((z0, y0, x0), err)
+        else:
+            assert err[0] <= 1e-6 and max(err) <= 1e-5, ((z0, y0, x0), err)
+    g.close()
+    for b in blocks:
+        b.close()
+    del out, blocks
+    torch.cuda.empty_cache()
