@@ -28,6 +28,23 @@ def params(gamma=1.4, mu=0.0, Pr=0.72, cfl=0.5, eps=0.1, viscous=False, limiter=
     return Params(gamma, mu, Pr, cfl, eps, int(bool(viscous)), int(limiter))
 
 
+PERIODIC, SLIP_WALL, FARFIELD = 0, 1, 2
+FACES = {"-x": 0, "+x": 1, "-y": 2, "+y": 3, "-z": 4, "+z": 5}
+
+
+class BC(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int * 6), ("inf", ctypes.c_double * 5)]
+
+
+def bc(kinds=None, inf=(1.0, 0.0, 0.0, 0.0, 1.0 / 1.4)) -> BC:
+    """kinds: {face name or index: kind} (faces not named stay periodic); inf: free-stream
+    (rho, u, v, w, p) of FARFIELD faces"""
+    k = [PERIODIC] * 6
+    for f, v in (kinds or {}).items():
+        k[FACES[f] if isinstance(f, str) else int(f)] = int(v)
+    return BC((ctypes.c_int * 6)(*k), (ctypes.c_double * 5)(*inf))
+
+
 _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
 
@@ -55,6 +72,11 @@ def lib():
         L.oracle_rk3_stage.argtypes = [i, sz, _D, _D, _D, ctypes.c_double, _D]
         L.oracle_step.argtypes = [P, i, i, i, _D, _D, i, _D, _D]
         L.oracle_step_fixed_dt.argtypes = [P, i, i, i, _D, _D, i, ctypes.c_double, _D]
+        B = ctypes.POINTER(BC)
+        L.oracle_metrics_bc.argtypes = [i, i, i, _D, B, _D]
+        L.oracle_fill_halo_bc.argtypes = [ctypes.c_double, i, i, i, _D, B, _D]
+        L.oracle_dt_local.argtypes = [P, i, i, i, _D, _D, _D]
+        L.oracle_step_ex.argtypes = [P, i, i, i, _D, B, i, ctypes.c_double, _D, i, _D, _D]
         L.oracle_threads.argtypes = []
         _lib = L
     return _lib
@@ -174,4 +196,48 @@ def step(p: Params, Qp: np.ndarray, M: np.ndarray, nsteps: int, dt_fixed=None):
         dts = np.full(max(nsteps, 1), float(dt_fixed))
         _check(lib().oracle_step_fixed_dt(ctypes.byref(p), nx, ny, nz, _ptr(M), _ptr(Q), nsteps,
                                           float(dt_fixed), _ptr(norms_)), "step_fixed_dt")
+    return Q, dts[:nsteps], norms_[:nsteps]
+
+
+# ---- boundary conditions and local time stepping ---------------------------------------------
+
+def metrics_bc(nodes: np.ndarray, bcs: BC = None) -> np.ndarray:
+    """metrics as metrics(); halo cells of non-periodic directions from reflected nodes"""
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    _, nz1, ny1, nx1 = nodes.shape
+    nx, ny, nz = nx1 - 1, ny1 - 1, nz1 - 1
+    M = np.zeros((10, nz + 2 * HALO, ny + 2 * HALO, nx + 2 * HALO))
+    _check(lib().oracle_metrics_bc(nx, ny, nz, _ptr(nodes), ctypes.byref(bcs) if bcs else None, _ptr(M)),
+           "metrics_bc")
+    return M
+
+
+def fill_halo_bc(Qp: np.ndarray, M: np.ndarray, bcs: BC = None, gamma=1.4) -> np.ndarray:
+    """copy of the halo-padded state with its halo filled (periodic, then boundary ghosts)"""
+    Q = np.array(Qp, dtype=np.float64, order="C", copy=True)
+    nx, ny, nz = _dims(Q)
+    _check(lib().oracle_fill_halo_bc(gamma, nx, ny, nz, _ptr(M), ctypes.byref(bcs) if bcs else None, _ptr(Q)),
+           "fill_halo_bc")
+    return Q
+
+
+def dt_local(p: Params, Qp: np.ndarray, M: np.ndarray) -> np.ndarray:
+    """per-cell CFL time step [nz][ny][nx]"""
+    nx, ny, nz = _dims(Qp)
+    out = np.zeros((nz, ny, nx))
+    _check(lib().oracle_dt_local(ctypes.byref(p), nx, ny, nz, _ptr(M), _ptr(np.ascontiguousarray(Qp)), _ptr(out)),
+           "dt_local")
+    return out
+
+
+def step_ex(p: Params, Qp: np.ndarray, M: np.ndarray, nsteps: int, bcs: BC = None, local_dt=False, dt_fixed=None):
+    """nsteps SSP-RK3 steps with boundary conditions (None: periodic) and optionally local time
+    steps or a fixed step; returns (Q padded, smallest dt per step, stage-1 norms)"""
+    Q = np.array(Qp, dtype=np.float64, order="C", copy=True)
+    nx, ny, nz = _dims(Q)
+    norms_ = np.zeros((max(nsteps, 1), 5))
+    dts = np.zeros(max(nsteps, 1))
+    _check(lib().oracle_step_ex(ctypes.byref(p), nx, ny, nz, _ptr(M), ctypes.byref(bcs) if bcs else None,
+                                int(bool(local_dt)), float(dt_fixed or 0.0), _ptr(Q), nsteps, _ptr(dts),
+                                _ptr(norms_)), "step_ex")
     return Q, dts[:nsteps], norms_[:nsteps]

@@ -200,59 +200,115 @@ static void quad_area(const double p00[3], const double p10[3], const double p11
   S[2] = 0.5 * c[2];
 }
 
+/* node (i, j, k) of the block, for indices beyond the block's nodes extended by reflecting
+ * through the boundary node along the grid line: X(-m) = 2 X(0) - X(m), X(n + m) = 2 X(n) - X(n - m),
+ * one dimension after the other */
+static void node_ext(const double* X, int nx, int ny, int nz, int i, int j, int k, double x[3]) {
+  double a[3], b[3];
+  if (i < 0 || i > nx) {
+    int e = i < 0 ? 0 : nx;
+    node_ext(X, nx, ny, nz, e, j, k, a);
+    node_ext(X, nx, ny, nz, 2 * e - i, j, k, b);
+  } else if (j < 0 || j > ny) {
+    int e = j < 0 ? 0 : ny;
+    node_ext(X, nx, ny, nz, i, e, k, a);
+    node_ext(X, nx, ny, nz, i, 2 * e - j, k, b);
+  } else if (k < 0 || k > nz) {
+    int e = k < 0 ? 0 : nz;
+    node_ext(X, nx, ny, nz, i, j, e, a);
+    node_ext(X, nx, ny, nz, i, j, 2 * e - k, b);
+  } else {
+    node_at(X, nx, ny, nz, i, j, k, x);
+    return;
+  }
+  for (int c = 0; c < 3; ++c) x[c] = 2.0 * a[c] - b[c];
+}
+
+/* metrics of cell (i, j, k): lower-face area vectors S_xi, S_eta, S_zeta and the volume */
+static void cell_metrics(const double* X, int nx, int ny, int nz, int i, int j, int k, double out[10]) {
+  double c[2][2][2][3]; /* corner nodes c[dk][dj][di] */
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) node_ext(X, nx, ny, nz, i + di, j + dj, k + dk, c[dk][dj][di]);
+  /* lower faces (towards +d) and upper faces (towards +d) of this cell */
+  double sxl[3], sxu[3], syl[3], syu[3], szl[3], szu[3];
+  /* xi faces: corners in the (eta, zeta) plane; eta x zeta = +xi */
+  quad_area(c[0][0][0], c[0][1][0], c[1][1][0], c[1][0][0], sxl);
+  quad_area(c[0][0][1], c[0][1][1], c[1][1][1], c[1][0][1], sxu);
+  /* eta faces: corners in the (zeta, xi) plane; zeta x xi = +eta */
+  quad_area(c[0][0][0], c[1][0][0], c[1][0][1], c[0][0][1], syl);
+  quad_area(c[0][1][0], c[1][1][0], c[1][1][1], c[0][1][1], syu);
+  /* zeta faces: corners in the (xi, eta) plane; xi x eta = +zeta */
+  quad_area(c[0][0][0], c[0][0][1], c[0][1][1], c[0][1][0], szl);
+  quad_area(c[1][0][0], c[1][0][1], c[1][1][1], c[1][1][0], szu);
+
+  /* V = (1/3) sum over faces of (face centroid - corner 000) . outward area vector */
+  double o[3] = {c[0][0][0][0], c[0][0][0][1], c[0][0][0][2]};
+  double cen[6][3];
+  const double* faces[6][4] = {
+      {c[0][0][0], c[0][1][0], c[1][1][0], c[1][0][0]},
+      {c[0][0][1], c[0][1][1], c[1][1][1], c[1][0][1]},
+      {c[0][0][0], c[1][0][0], c[1][0][1], c[0][0][1]},
+      {c[0][1][0], c[1][1][0], c[1][1][1], c[0][1][1]},
+      {c[0][0][0], c[0][0][1], c[0][1][1], c[0][1][0]},
+      {c[1][0][0], c[1][0][1], c[1][1][1], c[1][1][0]}};
+  for (int f = 0; f < 6; ++f)
+    for (int a = 0; a < 3; ++a)
+      cen[f][a] = 0.25 * (faces[f][0][a] + faces[f][1][a] + faces[f][2][a] + faces[f][3][a]) - o[a];
+  const double* outward[6] = {sxl, sxu, syl, syu, szl, szu};
+  double sign[6] = {-1.0, 1.0, -1.0, 1.0, -1.0, 1.0};
+  double vol = 0.0;
+  for (int f = 0; f < 6; ++f)
+    vol += sign[f] * (cen[f][0] * outward[f][0] + cen[f][1] * outward[f][1] + cen[f][2] * outward[f][2]);
+  vol /= 3.0;
+  for (int a = 0; a < 3; ++a) {
+    out[0 + a] = sxl[a];
+    out[3 + a] = syl[a];
+    out[6 + a] = szl[a];
+  }
+  out[9] = vol;
+}
+
 int oracle_metrics(int nx, int ny, int nz, const double* X, double* M) {
-  if (bad_dims(nx, ny, nz) || !X || !M) return -1;
+  return oracle_metrics_bc(nx, ny, nz, X, NULL, M);
+}
+
+static int periodic_dim(const oracle_bc* bc, int d) {
+  return !bc || (bc->kind[2 * d] == ORACLE_BC_PERIODIC && bc->kind[2 * d + 1] == ORACLE_BC_PERIODIC);
+}
+
+static int bad_bc(const oracle_bc* bc) {
+  if (!bc) return 0;
+  for (int d = 0; d < 3; ++d) {
+    int a = bc->kind[2 * d], b = bc->kind[2 * d + 1];
+    if (a < 0 || a > 2 || b < 0 || b > 2) return 1;
+    if ((a == ORACLE_BC_PERIODIC) != (b == ORACLE_BC_PERIODIC)) return 1; /* periodic pairs only */
+  }
+  return 0;
+}
+
+static int wrap(int i, int n);
+
+int oracle_metrics_bc(int nx, int ny, int nz, const double* X, const oracle_bc* bc, double* M) {
+  if (bad_dims(nx, ny, nz) || !X || !M || bad_bc(bc)) return -1;
+  if (bc && ((!periodic_dim(bc, 0) && nx < 2) || (!periodic_dim(bc, 1) && ny < 2) ||
+             (!periodic_dim(bc, 2) && nz < 2)))
+    return -1; /* the reflected halo nodes need two cells */
   grid_t g = make_grid(nx, ny, nz);
   memset(M, 0, 10 * g.ncell * sizeof(double));
-  for (int k = 0; k < nz; ++k)
-    for (int j = 0; j < ny; ++j)
-      for (int i = 0; i < nx; ++i) {
-        double c[2][2][2][3]; /* corner nodes c[dk][dj][di] */
-        for (int dk = 0; dk < 2; ++dk)
-          for (int dj = 0; dj < 2; ++dj)
-            for (int di = 0; di < 2; ++di) node_at(X, nx, ny, nz, i + di, j + dj, k + dk, c[dk][dj][di]);
-        /* lower faces (towards +d) and upper faces (towards +d) of this cell */
-        double sxl[3], sxu[3], syl[3], syu[3], szl[3], szu[3];
-        /* xi faces: corners in the (eta, zeta) plane; eta x zeta = +xi */
-        quad_area(c[0][0][0], c[0][1][0], c[1][1][0], c[1][0][0], sxl);
-        quad_area(c[0][0][1], c[0][1][1], c[1][1][1], c[1][0][1], sxu);
-        /* eta faces: corners in the (zeta, xi) plane; zeta x xi = +eta */
-        quad_area(c[0][0][0], c[1][0][0], c[1][0][1], c[0][0][1], syl);
-        quad_area(c[0][1][0], c[1][1][0], c[1][1][1], c[0][1][1], syu);
-        /* zeta faces: corners in the (xi, eta) plane; xi x eta = +zeta */
-        quad_area(c[0][0][0], c[0][0][1], c[0][1][1], c[0][1][0], szl);
-        quad_area(c[1][0][0], c[1][0][1], c[1][1][1], c[1][1][0], szu);
-
-        /* V = (1/3) sum over faces of (face centroid - corner 000) . outward area vector */
-        double o[3] = {c[0][0][0][0], c[0][0][0][1], c[0][0][0][2]};
-        double cen[6][3];
-        const double* faces[6][4] = {
-            {c[0][0][0], c[0][1][0], c[1][1][0], c[1][0][0]},
-            {c[0][0][1], c[0][1][1], c[1][1][1], c[1][0][1]},
-            {c[0][0][0], c[1][0][0], c[1][0][1], c[0][0][1]},
-            {c[0][1][0], c[1][1][0], c[1][1][1], c[0][1][1]},
-            {c[0][0][0], c[0][0][1], c[0][1][1], c[0][1][0]},
-            {c[1][0][0], c[1][0][1], c[1][1][1], c[1][1][0]}};
-        for (int f = 0; f < 6; ++f)
-          for (int a = 0; a < 3; ++a)
-            cen[f][a] = 0.25 * (faces[f][0][a] + faces[f][1][a] + faces[f][2][a] + faces[f][3][a]) - o[a];
-        const double* outward[6] = {sxl, sxu, syl, syu, szl, szu};
-        double sign[6] = {-1.0, 1.0, -1.0, 1.0, -1.0, 1.0};
-        double vol = 0.0;
-        for (int f = 0; f < 6; ++f)
-          vol += sign[f] * (cen[f][0] * outward[f][0] + cen[f][1] * outward[f][1] +
-                            cen[f][2] * outward[f][2]);
-        vol /= 3.0;
-
+  for (int k = -HALO; k < nz + HALO; ++k)
+    for (int j = -HALO; j < ny + HALO; ++j)
+      for (int i = -HALO; i < nx + HALO; ++i) {
+        /* periodic dimensions: the periodic image (metrics are translation invariant) */
+        int ii = periodic_dim(bc, 0) ? wrap(i, nx) : i;
+        int jj = periodic_dim(bc, 1) ? wrap(j, ny) : j;
+        int kk = periodic_dim(bc, 2) ? wrap(k, nz) : k;
+        double out[10];
+        cell_metrics(X, nx, ny, nz, ii, jj, kk, out);
         size_t ci = cell(&g, i, j, k);
-        for (int a = 0; a < 3; ++a) {
-          M[(0 + a) * g.ncell + ci] = sxl[a];
-          M[(3 + a) * g.ncell + ci] = syl[a];
-          M[(6 + a) * g.ncell + ci] = szl[a];
-        }
-        M[9 * g.ncell + ci] = vol;
+        for (int a = 0; a < 10; ++a) M[(size_t)a * g.ncell + ci] = out[a];
       }
-  return oracle_fill_halo_periodic(nx, ny, nz, 10, M);
+  return 0;
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -275,6 +331,111 @@ int oracle_fill_halo_periodic(int nx, int ny, int nz, int nvar, double* a) {
           if (inside) continue;
           f[cell(&g, i, j, k)] = f[cell(&g, wrap(i, nx), wrap(j, ny), wrap(k, nz))];
         }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* boundary ghost cells (not in the paper: the usual inviscid slip wall and characteristic     */
+/* far field)                                                                                  */
+
+/* unit normal of the boundary face of direction d at the face slab point (a, b), pointing
+ * towards +d; hi selects the upper face of the block */
+static void face_normal(const grid_t* g, const double* M, int d, int hi, int i, int j, int k, double n[3]) {
+  int idx[3] = {i, j, k};
+  int nd = d == 0 ? g->nx : (d == 1 ? g->ny : g->nz);
+  idx[d] = hi ? nd : 0; /* the face is the lower face of this cell */
+  size_t c = cell(g, idx[0], idx[1], idx[2]);
+  double S[3];
+  for (int a = 0; a < 3; ++a) S[a] = M[(size_t)(3 * d + a) * g->ncell + c];
+  double len = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+  for (int a = 0; a < 3; ++a) n[a] = S[a] / len;
+}
+
+/* boundary state of a FARFIELD face from the interior primitive state wi, the free stream winf
+ * and the outward unit normal n */
+static void farfield_state(double gamma, const double wi[5], const double winf[5], const double n[3],
+                           double wb[5]) {
+  double ci = sqrt(gamma * wi[4] / wi[0]), cinf = sqrt(gamma * winf[4] / winf[0]);
+  double uni = wi[1] * n[0] + wi[2] * n[1] + wi[3] * n[2];
+  double uninf = winf[1] * n[0] + winf[2] * n[1] + winf[3] * n[2];
+  if (uninf <= -cinf) { /* supersonic inflow */
+    for (int m = 0; m < 5; ++m) wb[m] = winf[m];
+    return;
+  }
+  if (uni >= ci) { /* supersonic outflow */
+    for (int m = 0; m < 5; ++m) wb[m] = wi[m];
+    return;
+  }
+  double rplus = uni + 2.0 * ci / (gamma - 1.0);
+  double rminus = uninf - 2.0 * cinf / (gamma - 1.0);
+  double unb = 0.5 * (rplus + rminus);
+  double cb = 0.25 * (gamma - 1.0) * (rplus - rminus);
+  const double* src = unb < 0.0 ? winf : wi; /* upwind side: entropy and tangential velocity */
+  double un_src = src[1] * n[0] + src[2] * n[1] + src[3] * n[2];
+  double entropy = src[4] / pow(src[0], gamma);
+  double rho = pow(cb * cb / (gamma * entropy), 1.0 / (gamma - 1.0));
+  wb[0] = rho;
+  for (int a = 0; a < 3; ++a) wb[1 + a] = src[1 + a] + (unb - un_src) * n[a];
+  wb[4] = rho * cb * cb / gamma;
+}
+
+static void prim_at(double gamma, const grid_t* g, const double* Q, size_t c, double w[5]) {
+  double U[5];
+  for (int m = 0; m < 5; ++m) U[m] = Q[(size_t)m * g->ncell + c];
+  oracle_primitive(gamma, U, w);
+}
+
+static void store_prim(double gamma, const grid_t* g, double* Q, size_t c, const double w[5]) {
+  Q[c] = w[0];
+  Q[g->ncell + c] = w[0] * w[1];
+  Q[2 * g->ncell + c] = w[0] * w[2];
+  Q[3 * g->ncell + c] = w[0] * w[3];
+  Q[4 * g->ncell + c] = w[4] / (gamma - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+}
+
+int oracle_fill_halo_bc(double gamma, int nx, int ny, int nz, const double* M, const oracle_bc* bc,
+                        double* Q) {
+  if (bad_dims(nx, ny, nz) || !Q || bad_bc(bc) || (bc && !M)) return -1;
+  int rc = oracle_fill_halo_periodic(nx, ny, nz, 5, Q);
+  if (rc || !bc) return rc;
+  grid_t g = make_grid(nx, ny, nz);
+  int n[3] = {nx, ny, nz};
+  for (int d = 0; d < 3; ++d) {
+    if (periodic_dim(bc, d)) continue;
+    int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    for (int hi = 0; hi < 2; ++hi) {
+      int kind = bc->kind[2 * d + hi];
+      for (int b = 0; b < n[d2]; ++b)
+        for (int a = 0; a < n[d1]; ++a) {
+          int idx[3];
+          idx[d1] = a;
+          idx[d2] = b;
+          idx[d] = 0;
+          double nrm[3];
+          face_normal(&g, M, d, hi, idx[0], idx[1], idx[2], nrm);
+          for (int m = 0; m < HALO; ++m) {
+            int gi[3] = {idx[0], idx[1], idx[2]}, ii[3] = {idx[0], idx[1], idx[2]};
+            gi[d] = hi ? n[d] + m : -1 - m;  /* ghost cell */
+            ii[d] = hi ? n[d] - 1 - m : m;   /* its mirror image inside */
+            double wi[5], wb[5];
+            if (kind == ORACLE_BC_SLIP_WALL) {
+              prim_at(gamma, &g, Q, cell(&g, ii[0], ii[1], ii[2]), wi);
+              double un = wi[1] * nrm[0] + wi[2] * nrm[1] + wi[3] * nrm[2];
+              wb[0] = wi[0];
+              for (int x = 0; x < 3; ++x) wb[1 + x] = wi[1 + x] - 2.0 * un * nrm[x];
+              wb[4] = wi[4];
+            } else {
+              double out[3] = {hi ? nrm[0] : -nrm[0], hi ? nrm[1] : -nrm[1], hi ? nrm[2] : -nrm[2]};
+              int adj[3] = {idx[0], idx[1], idx[2]};
+              adj[d] = hi ? n[d] - 1 : 0;  /* the interior cell next to the face */
+              prim_at(gamma, &g, Q, cell(&g, adj[0], adj[1], adj[2]), wi);
+              farfield_state(gamma, wi, bc->inf, out, wb);
+            }
+            store_prim(gamma, &g, Q, cell(&g, gi[0], gi[1], gi[2]), wb);
+          }
+        }
+    }
   }
   return 0;
 }
@@ -463,36 +624,51 @@ int oracle_residual(const oracle_params* p, int nx, int ny, int nz, const double
 /* ------------------------------------------------------------------------------------------ */
 /* time step: dt = CFL * min over cells of V / sum_d (convective + 4 * viscous spectral radius) */
 
+/* the CFL time step of one cell: CFL V / sum over directions of the spectral radius with the
+ * cell-averaged area vector (mean of its lower and upper faces) */
+static double cell_dt(const oracle_params* p, const grid_t* g, const double* M, const double* Q, size_t c) {
+  double visc_factor = 4.0 / 3.0 > p->gamma / p->Pr ? 4.0 / 3.0 : p->gamma / p->Pr;
+  double U[5], w[5];
+  for (int m = 0; m < 5; ++m) U[m] = Q[(size_t)m * g->ncell + c];
+  oracle_primitive(p->gamma, U, w);
+  double a = sqrt(p->gamma * w[4] / w[0]);
+  double vol = M[9 * g->ncell + c];
+  double sum = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    size_t up = c + stride(g, d);
+    double Sb[3];
+    for (int x = 0; x < 3; ++x)
+      Sb[x] = 0.5 * (M[(size_t)(3 * d + x) * g->ncell + c] + M[(size_t)(3 * d + x) * g->ncell + up]);
+    double s2 = Sb[0] * Sb[0] + Sb[1] * Sb[1] + Sb[2] * Sb[2];
+    double lam = fabs(w[1] * Sb[0] + w[2] * Sb[1] + w[3] * Sb[2]) + a * sqrt(s2);
+    if (p->viscous) lam += 4.0 * visc_factor * (p->mu / w[0]) * s2 / vol;
+    sum += lam;
+  }
+  return p->cfl * vol / sum;
+}
+
 int oracle_dt(const oracle_params* p, int nx, int ny, int nz, const double* M, const double* Q,
               double* dt) {
   if (!p || bad_dims(nx, ny, nz) || !M || !Q || !dt) return -1;
   grid_t g = make_grid(nx, ny, nz);
   double best = INFINITY;
-  double visc_factor = 4.0 / 3.0 > p->gamma / p->Pr ? 4.0 / 3.0 : p->gamma / p->Pr;
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
-        size_t c = cell(&g, i, j, k);
-        double U[5], w[5];
-        for (int m = 0; m < 5; ++m) U[m] = Q[(size_t)m * g.ncell + c];
-        oracle_primitive(p->gamma, U, w);
-        double a = sqrt(p->gamma * w[4] / w[0]);
-        double vol = M[9 * g.ncell + c];
-        double sum = 0.0;
-        for (int d = 0; d < 3; ++d) {
-          size_t up = c + stride(&g, d);
-          double Sb[3];
-          for (int x = 0; x < 3; ++x)
-            Sb[x] = 0.5 * (M[(size_t)(3 * d + x) * g.ncell + c] + M[(size_t)(3 * d + x) * g.ncell + up]);
-          double s2 = Sb[0] * Sb[0] + Sb[1] * Sb[1] + Sb[2] * Sb[2];
-          double lam = fabs(w[1] * Sb[0] + w[2] * Sb[1] + w[3] * Sb[2]) + a * sqrt(s2);
-          if (p->viscous) lam += 4.0 * visc_factor * (p->mu / w[0]) * s2 / vol;
-          sum += lam;
-        }
-        double local = p->cfl * vol / sum;
+        double local = cell_dt(p, &g, M, Q, cell(&g, i, j, k));
         if (local < best) best = local;
       }
   *dt = best;
+  return 0;
+}
+
+int oracle_dt_local(const oracle_params* p, int nx, int ny, int nz, const double* M, const double* Q,
+                    double* dt) {
+  if (!p || bad_dims(nx, ny, nz) || !M || !Q || !dt) return -1;
+  grid_t g = make_grid(nx, ny, nz);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) dt[((size_t)k * ny + j) * nx + i] = cell_dt(p, &g, M, Q, cell(&g, i, j, k));
   return 0;
 }
 
@@ -513,16 +689,23 @@ int oracle_norms(size_t n, const double* R, double out[5]) {
  *   stage 1: Q1 = Qn - dt R(Qn)
  *   stage 2: Q2 = 3/4 Qn + 1/4 (Q1 - dt R(Q1))
  *   stage 3: Q  = 1/3 Qn + 2/3 (Q2 - dt R(Q2)) */
-int oracle_rk3_stage(int stage, size_t n, const double* Qn, const double* Qs, const double* R,
-                     double dt, double* Qout) {
+/* one stage with the time step dtc[c % ncell] of every cell when dtc is not NULL, else dt */
+static int rk3_stage_impl(int stage, size_t n, const double* Qn, const double* Qs, const double* R,
+                          double dt, const double* dtc, size_t ncell, double* Qout) {
   if (stage < 1 || stage > 3 || !Qn || !Qs || !R || !Qout) return -1;
   for (size_t c = 0; c < n; ++c) {
-    double advanced = Qs[c] - dt * R[c];
+    double h = dtc ? dtc[c % ncell] : dt;
+    double advanced = Qs[c] - h * R[c];
     if (stage == 1) Qout[c] = advanced;
     else if (stage == 2) Qout[c] = 0.75 * Qn[c] + 0.25 * advanced;
     else Qout[c] = Qn[c] / 3.0 + 2.0 / 3.0 * advanced;
   }
   return 0;
+}
+
+int oracle_rk3_stage(int stage, size_t n, const double* Qn, const double* Qs, const double* R,
+                     double dt, double* Qout) {
+  return rk3_stage_impl(stage, n, Qn, Qs, R, dt, NULL, 1, Qout);
 }
 
 /* scatter a compact interior residual into a halo-padded array (halo entries zero) */
@@ -537,9 +720,10 @@ static void pad_residual(const grid_t* g, const double* R, double* Rp) {
               R[(size_t)m * nint + ((size_t)k * g->ny + j) * g->nx + i];
 }
 
-static int step_impl(const oracle_params* p, int nx, int ny, int nz, const double* M, double* Q,
-                     int nsteps, int cfl_dt, double fixed_dt, double* dts, double* norms) {
-  if (!p || bad_dims(nx, ny, nz) || !M || !Q || nsteps < 0) return -1;
+static int step_impl(const oracle_params* p, int nx, int ny, int nz, const double* M, const oracle_bc* bc,
+                     int local_dt, double* Q, int nsteps, int cfl_dt, double fixed_dt, double* dts,
+                     double* norms) {
+  if (!p || bad_dims(nx, ny, nz) || !M || !Q || nsteps < 0 || bad_bc(bc)) return -1;
   grid_t g = make_grid(nx, ny, nz);
   size_t nint = (size_t)nx * ny * nz;
   size_t nall = 5 * g.ncell;
@@ -547,44 +731,66 @@ static int step_impl(const oracle_params* p, int nx, int ny, int nz, const doubl
   double* Rp = (double*)malloc(nall * sizeof(double));
   double* Q1 = (double*)malloc(nall * sizeof(double));
   double* Q2 = (double*)malloc(nall * sizeof(double));
+  double* dl = local_dt ? (double*)malloc(nint * sizeof(double)) : NULL;
+  double* dlp = local_dt ? (double*)calloc(g.ncell, sizeof(double)) : NULL;  /* halo entries 0 */
   int rc = 0;
-  if (!R || !Rp || !Q1 || !Q2) { rc = -2; goto done; }
+  if (!R || !Rp || !Q1 || !Q2 || (local_dt && (!dl || !dlp))) { rc = -2; goto done; }
   for (int s = 0; s < nsteps; ++s) {
     double dt = fixed_dt;
-    oracle_fill_halo_periodic(nx, ny, nz, 5, Q);
-    if (cfl_dt) oracle_dt(p, nx, ny, nz, M, Q, &dt);
+    oracle_fill_halo_bc(p->gamma, nx, ny, nz, M, bc, Q);
+    if (local_dt) {
+      oracle_dt_local(p, nx, ny, nz, M, Q, dl);
+      dt = INFINITY;
+      for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+          for (int i = 0; i < nx; ++i) {
+            double v = dl[((size_t)k * ny + j) * nx + i];
+            dlp[cell(&g, i, j, k)] = v;
+            if (v < dt) dt = v;
+          }
+    } else if (cfl_dt) {
+      oracle_dt(p, nx, ny, nz, M, Q, &dt);
+    }
     if (dts) dts[s] = dt;
 
     oracle_residual(p, nx, ny, nz, M, Q, R);
     if (norms) oracle_norms(nint, R, norms + 5 * (size_t)s);
     pad_residual(&g, R, Rp);
-    oracle_rk3_stage(1, nall, Q, Q, Rp, dt, Q1);
+    rk3_stage_impl(1, nall, Q, Q, Rp, dt, dlp, g.ncell, Q1);
 
-    oracle_fill_halo_periodic(nx, ny, nz, 5, Q1);
+    oracle_fill_halo_bc(p->gamma, nx, ny, nz, M, bc, Q1);
     oracle_residual(p, nx, ny, nz, M, Q1, R);
     pad_residual(&g, R, Rp);
-    oracle_rk3_stage(2, nall, Q, Q1, Rp, dt, Q2);
+    rk3_stage_impl(2, nall, Q, Q1, Rp, dt, dlp, g.ncell, Q2);
 
-    oracle_fill_halo_periodic(nx, ny, nz, 5, Q2);
+    oracle_fill_halo_bc(p->gamma, nx, ny, nz, M, bc, Q2);
     oracle_residual(p, nx, ny, nz, M, Q2, R);
     pad_residual(&g, R, Rp);
-    oracle_rk3_stage(3, nall, Q, Q2, Rp, dt, Q);
+    rk3_stage_impl(3, nall, Q, Q2, Rp, dt, dlp, g.ncell, Q);
   }
-  oracle_fill_halo_periodic(nx, ny, nz, 5, Q);
+  oracle_fill_halo_bc(p->gamma, nx, ny, nz, M, bc, Q);
 done:
   free(R);
   free(Rp);
   free(Q1);
   free(Q2);
+  free(dl);
+  free(dlp);
   return rc;
 }
 
 int oracle_step(const oracle_params* p, int nx, int ny, int nz, const double* M, double* Q,
                 int nsteps, double* dts, double* norms) {
-  return step_impl(p, nx, ny, nz, M, Q, nsteps, 1, 0.0, dts, norms);
+  return step_impl(p, nx, ny, nz, M, NULL, 0, Q, nsteps, 1, 0.0, dts, norms);
 }
 
 int oracle_step_fixed_dt(const oracle_params* p, int nx, int ny, int nz, const double* M,
                          double* Q, int nsteps, double dt, double* norms) {
-  return step_impl(p, nx, ny, nz, M, Q, nsteps, 0, dt, NULL, norms);
+  return step_impl(p, nx, ny, nz, M, NULL, 0, Q, nsteps, 0, dt, NULL, norms);
+}
+
+int oracle_step_ex(const oracle_params* p, int nx, int ny, int nz, const double* M, const oracle_bc* bc,
+                   int local_dt, double fixed_dt, double* Q, int nsteps, double* dts, double* norms) {
+  if (local_dt && fixed_dt > 0.0) return -1;
+  return step_impl(p, nx, ny, nz, M, bc, local_dt, Q, nsteps, fixed_dt > 0.0 ? 0 : 1, fixed_dt, dts, norms);
 }

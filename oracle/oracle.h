@@ -42,6 +42,28 @@ typedef struct {
   int limiter;     /* 0: minmod slopes; 1: unlimited central slope (Fromm) */
 } oracle_params;
 
+/* Boundary conditions of the six block faces (-x, +x, -y, +y, -z, +z).  Not in the paper,
+ * which gives no boundary treatment: these are the usual inviscid ones.
+ *   PERIODIC  the opposite face's interior (both faces of a direction must be periodic)
+ *   SLIP_WALL ghost cell m (m = 0, 1 away from the face) mirrors interior cell m: same density
+ *             and pressure, velocity reflected about the face's unit normal, u - 2 (u.n) n
+ *   FARFIELD  characteristic (Riemann-invariant) subsonic inflow/outflow against the free
+ *             stream inf[]: with n the outward unit normal, R+ = u.n + 2c/(gamma-1) from the
+ *             adjacent interior cell and R- = u_inf.n - 2c_inf/(gamma-1) give u_b.n and c_b;
+ *             entropy p/rho^gamma and tangential velocity come from the free stream where
+ *             u_b.n < 0 (inflow), else from the interior cell; supersonic inflow takes the free
+ *             stream, supersonic outflow the interior cell.  Both ghost layers get that state.
+ * Ghost cells are filled on the face slabs only (the other two indices interior); the inviscid
+ * stencil reads nothing else there.  Metrics of halo cells on non-periodic faces come from the
+ * block's nodes reflected through the boundary node along each grid line. */
+#define ORACLE_BC_PERIODIC 0
+#define ORACLE_BC_SLIP_WALL 1
+#define ORACLE_BC_FARFIELD 2
+typedef struct {
+  int kind[6];     /* per face -x, +x, -y, +y, -z, +z */
+  double inf[5];   /* free-stream primitive state rho, u, v, w, p (FARFIELD faces) */
+} oracle_bc;
+
 /* number of cells of one halo-padded field */
 size_t oracle_cells(int nx, int ny, int nz);
 
@@ -58,6 +80,26 @@ void oracle_roe_flux(double gamma, double eps, const double wl[5], const double 
 
 /* face area vectors and volumes of interior cells from nodes, halo cells by periodic copy */
 int oracle_metrics(int nx, int ny, int nz, const double* X, double* M);
+
+/* metrics as oracle_metrics; halo cells of non-periodic directions from reflected nodes
+ * (bc NULL: all periodic) */
+int oracle_metrics_bc(int nx, int ny, int nz, const double* X, const oracle_bc* bc, double* M);
+
+/* fill the halo of the state Q: periodic images in periodic directions, then the ghost cells
+ * of the SLIP_WALL and FARFIELD faces (x faces, then y, then z) */
+int oracle_fill_halo_bc(double gamma, int nx, int ny, int nz, const double* M, const oracle_bc* bc,
+                        double* Q);
+
+/* local CFL time step of every interior cell, compact [nz][ny][nx] (Q's halo filled) */
+int oracle_dt_local(const oracle_params* p, int nx, int ny, int nz, const double* M, const double* Q,
+                    double* dt);
+
+/* nsteps SSP-RK3 steps with boundary conditions bc (NULL: periodic); local_dt != 0 advances
+ * every cell with its own CFL time step (pseudo-time marching to a steady state), evaluated
+ * from Q^n at the start of each step; fixed_dt > 0 (with local_dt 0) takes that step instead of
+ * the CFL one.  dts[s] gets the smallest time step of step s. */
+int oracle_step_ex(const oracle_params* p, int nx, int ny, int nz, const double* M, const oracle_bc* bc,
+                   int local_dt, double fixed_dt, double* Q, int nsteps, double* dts, double* norms);
 
 /* copy periodic images into the 2-cell halo of nvar fields */
 int oracle_fill_halo_periodic(int nx, int ny, int nz, int nvar, double* a);

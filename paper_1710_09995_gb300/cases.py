@@ -320,3 +320,63 @@ def lattice_case(sizes=None, seed=None, shape=(4, 4, 6), lo=16, hi=160, mach=0.8
     q[4] = fields[1].add_(1.0).mul_(1.0 / (gamma * (gamma - 1.0))).add_(rho * (0.5 * mach * mach))
     return Lattice(sx, sy, sz, q, (h, h, h), gamma=gamma, mach=mach,
                    extra={"seed": seed, "shape": list(shape), "lo": lo, "hi": hi})
+
+
+# ---- steady channel with a bump on the lower wall (inviscid) --------------------------------
+
+def stretched_unit(n, ratio=1.1, cap=None) -> np.ndarray:
+    """n + 1 points on [0, 1]: spacings h0 ratio^j from 0, each capped at `cap` (default 1.5 / n),
+    with h0 found by bisection so that they sum to 1"""
+    cap = 1.5 / n if cap is None else cap
+
+    def total(h0):
+        return sum(min(h0 * ratio ** j, cap) for j in range(n))
+
+    lo, hi = 0.0, 1.0 / n
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if total(mid) < 1.0:
+            lo = mid
+        else:
+            hi = mid
+    h0 = 0.5 * (lo + hi)
+    s = np.array([min(h0 * ratio ** j, cap) for j in range(n)])
+    eta = np.concatenate([[0.0], np.cumsum(s)])
+    eta /= eta[-1]
+    return eta
+
+
+def bump_wall(x, height):
+    """lower wall y_w = height sin^2(pi x) on 0 <= x <= 1, flat elsewhere"""
+    x = np.asarray(x, dtype=np.float64)
+    return np.where((x >= 0.0) & (x <= 1.0), height * np.sin(math.pi * x) ** 2, 0.0)
+
+
+def channel_nodes(nx=192, ny=96, nz=64, height=0.1, x0=-1.0, x1=2.0, lz=0.5, ratio=1.1) -> np.ndarray:
+    """nodes of the channel x in [x0, x1], y from the bump wall to 1, z in [0, lz]: uniform in x
+    and z, geometric from the lower wall in y (ratio `ratio`, capped at 1.5 / ny of the local
+    height)"""
+    x = x0 + (x1 - x0) * np.arange(nx + 1, dtype=np.float64) / nx
+    z = lz * np.arange(nz + 1, dtype=np.float64) / nz
+    eta = stretched_unit(ny, ratio)
+    yw = bump_wall(x, height)
+    out = np.empty((3, nz + 1, ny + 1, nx + 1))
+    out[0] = x[None, None, :]
+    out[1] = (yw[None, :] + (1.0 - yw[None, :]) * eta[:, None])[None, :, :]
+    out[2] = z[:, None, None]
+    return out
+
+
+CHANNEL_BC = {"-x": 2, "+x": 2, "-y": 1, "+y": 1}   # far field in/out, slip walls, z periodic
+
+
+def channel_case(nx=192, ny=96, nz=64, height=0.1, mach=0.6, gamma=GAMMA, cfl=0.9, ratio=1.1) -> Case:
+    """Inviscid channel over a bump: the free stream (rho = 1, p = 1/gamma, c = 1, u = Mach along
+    x) everywhere at the start; characteristic far field at x = -1 and x = 2, slip walls at the
+    bump and at y = 1, periodic in z.  extra["bc"] names each face's condition (1 slip wall,
+    2 far field) and extra["inf"] the free stream (rho, u, v, w, p)."""
+    nodes = channel_nodes(nx, ny, nz, height, ratio=ratio)
+    q = conserved(np.ones((nz, ny, nx)), mach, 0.0, 0.0, 1.0 / gamma, gamma)
+    return Case("bump_channel", nx, ny, nz, q, nodes, (3.0 / nx, 1.0 / ny, 0.5 / nz), gamma=gamma, cfl=cfl,
+                eps=0.1, extra={"bc": dict(CHANNEL_BC), "inf": (1.0, mach, 0.0, 0.0, 1.0 / gamma),
+                                "height": height, "mach": mach})
