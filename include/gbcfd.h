@@ -54,7 +54,9 @@ typedef struct {
   int viscous;        /* 0: Euler, 1: Navier-Stokes (Eq. 1 with Fv, Gv, Hv) */
   int limiter;        /* 0: minmod, 1: unlimited central slope */
   int precision;      /* GBCFD_FP64 or GBCFD_MIXED */
-  int reserved;       /* must be 0 */
+  int local_dt;       /* 0: one global CFL time step; 1: every cell advances with its own CFL step
+                         (pseudo-time marching to a steady state; the residual norm is unchanged);
+                         inviscid blocks only (viscous = 0) */
 } gbcfd_params;
 
 /* Bytes of caller device memory one block of nx x ny x nz interior cells needs (state, stage
@@ -75,9 +77,33 @@ int gbcfd_destroy_block(gbcfd_block block);
 /* Connect face `face` of `block` to the opposite face of `nbr` (conforming, same orientation:
  * equal cell counts along the two shared directions).  nbr == block makes the direction
  * periodic.  Multi-block interfaces share their grid points (Sec. 2.2); the halo then holds
- * the neighbour's first two cell layers.  Faces left unconnected keep whatever halo the caller
- * sets (the kernels read but never write them). */
+ * the neighbour's first two cell layers.  A face with a boundary condition cannot be connected
+ * (GBCFD_ERR_ARG).  Faces with neither keep whatever their halo holds. */
 int gbcfd_connect(gbcfd_block block, int face, gbcfd_block nbr);
+
+/* Boundary conditions of unconnected faces (the paper gives none; these are the usual inviscid
+ * ones, for steady internal flows such as a channel).  Every halo fill of a stage input (the
+ * stage's exchange) then also fills the face's two ghost layers:
+ *   GBCFD_BC_SLIP_WALL  ghost layer m mirrors interior layer m about the face's unit normal n:
+ *                       same density and pressure, velocity u - 2 (u.n) n
+ *   GBCFD_BC_FARFIELD   characteristic subsonic inflow/outflow against the free stream
+ *                       inf[5] = (rho, u, v, w, p): with n the outward unit normal, the
+ *                       outgoing invariant u.n + 2c/(gamma-1) of the adjacent interior cell and
+ *                       the incoming u.n - 2c/(gamma-1) of the free stream give the boundary
+ *                       u.n and c; entropy p/rho^gamma and tangential velocity come from the
+ *                       upwind side; supersonic inflow takes the free stream, supersonic
+ *                       outflow the interior cell.  Both ghost layers get that state.
+ *   GBCFD_BC_NONE       removes the condition.
+ * Face slabs are filled over the padded extent of the other two directions (x faces, then y,
+ * then z), so edges and corners hold physical states.  Halo metrics of such faces come from
+ * the block's nodes reflected through the boundary node along each grid line (computed by
+ * gbcfd_set_metrics for every halo cell; connected faces take the neighbour's).
+ * Errors: GBCFD_ERR_ARG for a connected face, a viscous block, fewer than 2 cells across the
+ * face's direction, an unknown kind, or a far-field free stream without rho > 0, p > 0. */
+#define GBCFD_BC_NONE 0
+#define GBCFD_BC_SLIP_WALL 1
+#define GBCFD_BC_FARFIELD 2
+int gbcfd_set_boundary(gbcfd_block block, int face, int kind, const double inf[5]);
 
 /* Set the grid (Eq. 1's curvilinear coordinates).  nodes == NULL: uniform Cartesian grid with
  * cell sizes spacing[0..2].  Otherwise `nodes` is a device pointer to float64

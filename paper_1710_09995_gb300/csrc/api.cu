@@ -63,6 +63,9 @@ struct gbcfd_block_s {
   BlockDesc desc_host;  // host copy
   int curvi;            // metrics from nodes (curvilinear) rather than a uniform spacing
   int metrics_dirty;    // metric halos not exchanged since the metrics were set
+  void* dtl;            // local time steps (local_dt), one padded field of the path's flux type
+  int bc_kind[6];       // GBCFD_BC_* per face (faces without a neighbour)
+  double bc_inf[5];     // free stream of GBCFD_BC_FARFIELD faces
 };
 
 static int prepare_metrics(const gbcfd_block* blocks, int n, cudaStream_t s);
@@ -95,7 +98,8 @@ static bool valid_params(const gbcfd_params* p, std::string& why) {
   if (p->viscous && !(p->mu >= 0.0 && p->Pr > 0.0)) { why = "viscous needs mu >= 0 and Pr > 0"; return false; }
   if (p->limiter != 0 && p->limiter != 1) { why = "limiter must be 0 or 1"; return false; }
   if (p->precision != GBCFD_FP64 && p->precision != GBCFD_MIXED) { why = "bad precision"; return false; }
-  if (p->reserved != 0) { why = "reserved must be 0"; return false; }
+  if (p->local_dt != 0 && p->local_dt != 1) { why = "local_dt must be 0 or 1"; return false; }
+  if (p->local_dt && p->viscous) { why = "local time steps are for inviscid blocks (viscous = 0)"; return false; }
   return true;
 }
 
@@ -115,7 +119,7 @@ struct Carve {
   size_t partial_n;
 };
 
-static Carve carve(const Geometry& g, int precision, int nsm) {
+static Carve carve(const Geometry& g, int precision, int local_dt, int nsm) {
   Carve c;
   size_t o = 0;
   const size_t f64 = align256(sizeof(double) * 5 * g.field);
@@ -138,6 +142,11 @@ static Carve carve(const Geometry& g, int precision, int nsm) {
   c.off[10] = o; o += align256(sizeof(BlockDesc));
   c.partial_n = (size_t)std::max(4 * nsm, 4 * 152);
   c.off[7] = o; o += align256(sizeof(double) * NPART * c.partial_n);
+  c.off[11] = 0;
+  if (local_dt) {  // one padded field of local time steps
+    c.off[11] = o;
+    o += precision == GBCFD_FP64 ? align256(sizeof(double) * g.field) : align256(sizeof(float) * g.fieldf);
+  }
   c.total = o;
   return c;
 }
@@ -191,7 +200,7 @@ extern "C" int gbcfd_required_bytes(int nx, int ny, int nz, const gbcfd_params* 
   int dev = 0, nsm = 152;
   int rc = device_sms(&dev, &nsm);
   if (rc) return rc;
-  *bytes = carve(make_geometry(nx, ny, nz), params->precision, nsm).total;
+  *bytes = carve(make_geometry(nx, ny, nz), params->precision, params->local_dt, nsm).total;
   return GBCFD_OK;
 }
 
@@ -207,6 +216,7 @@ static Physics physics_of(const gbcfd_block_s* b) {
   ph.ihz = 1.0 / b->spacing[2];
   ph.viscous = b->p.viscous;
   ph.limiter = b->p.limiter;
+  ph.local_dt = b->p.local_dt;
   return ph;
 }
 
@@ -224,6 +234,7 @@ static void fill_desc(gbcfd_block_s* b) {
   for (int i = 0; i < 3; ++i) D.q[i] = b->q[i];
   for (int i = 0; i < 2; ++i) { D.sh[i] = b->sh[i]; D.d[i] = b->d[i]; }
   D.ctrl = b->ctrl;
+  D.dtl = b->dtl;
   D.ntx = (b->nx + TX - 1) / TX;
   D.nty = (b->ny + TY - 1) / TY;
   D.units = (long long)D.ntx * D.nty * b->nz;
@@ -247,7 +258,7 @@ extern "C" int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* pa
   int rc = device_sms(&dev, &nsm);
   if (rc) return rc;
   Geometry g = make_geometry(nx, ny, nz);
-  Carve c = carve(g, params->precision, nsm);
+  Carve c = carve(g, params->precision, params->local_dt, nsm);
   if (bytes < c.total) return fail(GBCFD_ERR_MEMORY, "dev_mem smaller than gbcfd_required_bytes");
 
   gbcfd_block_s* b = new gbcfd_block_s();
@@ -268,6 +279,9 @@ extern "C" int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* pa
   b->metrics = base + c.off[5];
   b->ctrl = reinterpret_cast<DevCtrl*>(base + c.off[6]);
   b->partial = reinterpret_cast<double*>(base + c.off[7]);
+  b->dtl = params->local_dt ? static_cast<void*>(base + c.off[11]) : nullptr;
+  for (int f = 0; f < 6; ++f) b->bc_kind[f] = GBCFD_BC_NONE;
+  for (int v = 0; v < 5; ++v) b->bc_inf[v] = 0.0;
   if (params->precision == GBCFD_FP64) {
     b->staging = reinterpret_cast<char*>(b->q[1]);
     b->staging_bytes = c.off[2] - c.off[1];
@@ -322,8 +336,31 @@ extern "C" int gbcfd_connect(gbcfd_block b, int face, gbcfd_block nbr) {
   for (int a = 0; a < 3; ++a)
     if (a != d && na[a] != nb[a]) return fail(GBCFD_ERR_ARG, "connected faces must have equal cell counts");
   if (b->p.precision != nbr->p.precision) return fail(GBCFD_ERR_ARG, "connected blocks must share a precision");
+  if (b->bc_kind[face] != GBCFD_BC_NONE || nbr->bc_kind[face ^ 1] != GBCFD_BC_NONE)
+    return fail(GBCFD_ERR_ARG, "a face with a boundary condition cannot be connected");
   b->nbr[face] = nbr;
   nbr->nbr[face ^ 1] = b;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_set_boundary(gbcfd_block b, int face, int kind, const double inf[5]) {
+  if (!b) return fail(GBCFD_ERR_ARG, "block is NULL");
+  if (face < 0 || face > 5) return fail(GBCFD_ERR_ARG, "face must be 0..5");
+  if (kind != GBCFD_BC_NONE && kind != GBCFD_BC_SLIP_WALL && kind != GBCFD_BC_FARFIELD)
+    return fail(GBCFD_ERR_ARG, "unknown boundary kind");
+  if (kind != GBCFD_BC_NONE) {
+    if (b->nbr[face]) return fail(GBCFD_ERR_ARG, "the face is connected to a neighbour");
+    if (b->p.viscous) return fail(GBCFD_ERR_ARG, "boundary conditions are inviscid: the block must have viscous = 0");
+    const int n[3] = {b->nx, b->ny, b->nz};
+    if (n[face / 2] < 2) return fail(GBCFD_ERR_ARG, "a boundary face needs at least 2 cells across the block");
+  }
+  if (kind == GBCFD_BC_FARFIELD) {
+    if (!inf) return fail(GBCFD_ERR_ARG, "a far-field face needs the free stream");
+    if (!(inf[0] > 0.0 && inf[4] > 0.0) || !std::isfinite(inf[1]) || !std::isfinite(inf[2]) || !std::isfinite(inf[3]))
+      return fail(GBCFD_ERR_ARG, "the free stream needs rho > 0, p > 0 and a finite velocity");
+    for (int v = 0; v < 5; ++v) b->bc_inf[v] = inf[v];
+  }
+  b->bc_kind[face] = kind;
   return GBCFD_OK;
 }
 
@@ -470,11 +507,45 @@ static int build_group(const gbcfd_block* blocks, int n, int field, bool allow_e
   return GBCFD_OK;
 }
 
+// ghost cells of the physical faces of blocks[0..n) for `field` (a stage input), one launch per
+// direction that has such faces, x before y before z (edges read the earlier directions' ghosts)
+static int apply_bc(const gbcfd_block* blocks, int n, int field, cudaStream_t s) {
+  for (int i = 0; i < n; ++i) {
+    gbcfd_block b = blocks[i];
+    const bool mixed = b->p.precision == GBCFD_MIXED;
+    BcBlock B;
+    memset(&B, 0, sizeof(B));
+    B.g = b->g;
+    for (int f = 0; f < 6; ++f) B.kind[f] = b->nbr[f] ? GBCFD_BC_NONE : b->bc_kind[f];
+    for (int v = 0; v < 5; ++v) B.inf[v] = b->bc_inf[v];
+    B.gamma = b->p.gamma;
+    B.metrics = b->curvi ? b->metrics : nullptr;
+    if (!mixed) {
+      B.mode = BC_F64;
+      B.field = field == F_STATE ? b->q[0] : (field == F_STAGE1 ? b->q[1] : b->q[2]);
+    } else if (field == F_STATE) {
+      B.mode = BC_F32;
+      B.field = b->sh[b->cur];
+    } else {
+      B.mode = BC_F32_INC;
+      B.field = field == F_STAGE1 ? b->d[0] : b->d[1];
+      B.shadow = b->sh[b->cur];
+    }
+    for (int d = 0; d < 3; ++d) {
+      if (B.kind[2 * d] == GBCFD_BC_NONE && B.kind[2 * d + 1] == GBCFD_BC_NONE) continue;
+      B.dim = d;
+      CK(launch_bc(B, s));
+    }
+  }
+  return GBCFD_OK;
+}
+
 static int exchange(const gbcfd_block* blocks, int n, int field, bool allow_external, cudaStream_t s) {
   static thread_local HaloGroup G;  // ~8 KB, kept off the stack
   int rc = build_group(blocks, n, field, allow_external, &G);
   if (rc) return rc;
   CK(launch_halo(G, s));
+  if (field != F_METRICS) return apply_bc(blocks, n, field, s);
   return GBCFD_OK;
 }
 
@@ -483,10 +554,10 @@ static int exchange(const gbcfd_block* blocks, int n, int field, bool allow_exte
 static int init_rate(gbcfd_block b, cudaStream_t s) {
   if (b->curvi)
     CK(launch_init_rate_curvi(b->g, physics_of(b), state_ptr(b), b->metrics, b->ctrl, b->partial, 4 * b->nsm,
-                              b->p.precision == GBCFD_MIXED, s));
+                              b->p.precision == GBCFD_MIXED, b->dtl, s));
   else
     CK(launch_init_rate(b->g, physics_of(b), state_ptr(b), b->ctrl, b->partial, 4 * b->nsm,
-                        b->p.precision == GBCFD_MIXED, s));
+                        b->p.precision == GBCFD_MIXED, b->dtl, s));
   return GBCFD_OK;
 }
 
@@ -680,6 +751,7 @@ extern "C" int gbcfd_group_create(const gbcfd_block* blocks, int n, void* dev_me
     if (!b) return fail(GBCFD_ERR_ARG, "NULL block");
     const gbcfd_params &p = b->p, &q = blocks[0]->p;
     if (p.precision != q.precision || p.viscous != q.viscous || p.limiter != q.limiter || p.gamma != q.gamma ||
+        p.local_dt != q.local_dt ||
         p.mu != q.mu || p.Pr != q.Pr || p.cfl != q.cfl || p.entropy_eps != q.entropy_eps ||
         b->curvi != blocks[0]->curvi)
       return fail(GBCFD_ERR_ARG, "group members must share precision, physics and grid kind");

@@ -6,9 +6,12 @@ namespace gbcfd {
 // ---- halo exchange -------------------------------------------------------------------------
 // One thread per halo cell of every block in the group.  The source of a halo cell is found by
 // walking face neighbours: first along x, then along y in the block reached, then along z, so
-// that edge and corner cells come from the diagonal neighbour.  Each block's halo is the union
-// of the z-slabs (k < 0 or k >= nz, all i, j), the y-slabs (0 <= k < nz, j outside, all i) and
-// the x-slabs (inside k and j, i outside).
+// that edge and corner cells come from the diagonal neighbour.  A direction without a neighbour
+// (a physical boundary) is skipped and its index stays outside: an edge cell next to a boundary
+// face then copies the neighbour's boundary ghost, and a cell of the boundary face slab itself
+// (no move at all) is left to the boundary kernel.  Each block's halo is the union of the
+// z-slabs (k < 0 or k >= nz, all i, j), the y-slabs (0 <= k < nz, j outside, all i) and the
+// x-slabs (inside k and j, i outside).
 __global__ void halo_kernel(const __grid_constant__ HaloGroup G) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < G.total; t += stride) {
@@ -43,16 +46,19 @@ __global__ void halo_kernel(const __grid_constant__ HaloGroup G) {
       const int ii = (int)(r % (2 * HALO));
       i = ii < HALO ? ii - HALO : nx + ii - HALO;
     }
-    // walk to the source block
+    // walk to the source block (a missing neighbour leaves that index outside)
     int b = lo, si = i, sj = j, sk = k;
-    bool ok = true;
-    while (ok && si < 0) { b = G.b[b].nbr[0]; if (b < 0) ok = false; else si += G.b[b].nx; }
-    while (ok && si >= G.b[b].nx) { si -= G.b[b].nx; b = G.b[b].nbr[1]; if (b < 0) ok = false; }
-    while (ok && sj < 0) { b = G.b[b].nbr[2]; if (b < 0) ok = false; else sj += G.b[b].ny; }
-    while (ok && sj >= G.b[b].ny) { sj -= G.b[b].ny; b = G.b[b].nbr[3]; if (b < 0) ok = false; }
-    while (ok && sk < 0) { b = G.b[b].nbr[4]; if (b < 0) ok = false; else sk += G.b[b].nz; }
-    while (ok && sk >= G.b[b].nz) { sk -= G.b[b].nz; b = G.b[b].nbr[5]; if (b < 0) ok = false; }
-    if (!ok) continue;
+    bool moved = false;
+    while (si < 0 && G.b[b].nbr[0] >= 0) { b = G.b[b].nbr[0]; si += G.b[b].nx; moved = true; }
+    while (si >= G.b[b].nx && G.b[b].nbr[1] >= 0) { si -= G.b[b].nx; b = G.b[b].nbr[1]; moved = true; }
+    while (sj < 0 && G.b[b].nbr[2] >= 0) { b = G.b[b].nbr[2]; sj += G.b[b].ny; moved = true; }
+    while (sj >= G.b[b].ny && G.b[b].nbr[3] >= 0) { sj -= G.b[b].ny; b = G.b[b].nbr[3]; moved = true; }
+    while (sk < 0 && G.b[b].nbr[4] >= 0) { b = G.b[b].nbr[4]; sk += G.b[b].nz; moved = true; }
+    while (sk >= G.b[b].nz && G.b[b].nbr[5] >= 0) { sk -= G.b[b].nz; b = G.b[b].nbr[5]; moved = true; }
+    // a source left outside a smaller neighbour's halo (only with blocks narrower than the halo)
+    if (!moved || si < -HALO || si >= G.b[b].nx + HALO || sj < -HALO || sj >= G.b[b].ny + HALO ||
+        sk < -HALO || sk >= G.b[b].nz + HALO)
+      continue;
     const HaloBlock& S = G.b[b];
     const long long dplane = (long long)(ny + 2 * HALO) * B.pitch, dfield = dplane * (nz + 2 * HALO);
     const long long splane = (long long)(S.ny + 2 * HALO) * S.pitch, sfield = splane * (S.nz + 2 * HALO);
@@ -131,7 +137,7 @@ cudaError_t launch_gather(const Geometry& g, const double* src, double* dst, cud
 // precision T (the mixed path's time step is an f32 evaluation, like its fluxes).
 template <typename T>
 __global__ void init_rate_kernel(Geometry g, Physics ph, const double* __restrict__ q, DevCtrl* ctrl,
-                                 double* partial) {
+                                 double* partial, T* dtl) {
   __shared__ double wmax[32];
   __shared__ int last;
   const long long n = (long long)g.nx * g.ny * g.nz;
@@ -152,6 +158,7 @@ __global__ void init_rate_kernel(Geometry g, Physics ph, const double* __restric
     const T a = sqrt(gam * p * ir);
     T rate = (fabs(u) + a) * ihx + (fabs(v) + a) * ihy + (fabs(w) + a) * ihz;
     if (ph.viscous) rate += f * mu4 * ir * s2;
+    if (dtl) dtl[sizeof(T) == 8 ? o : gidxf(g, i, j, k)] = T(ph.cfl) / rate;
     if (!(rho > T(0) && p > T(0))) atomicOr(&ctrl->flag, FLAG_NONPHYSICAL);
     best = fmax(best, double(rate));
   }
@@ -176,11 +183,11 @@ __global__ void init_rate_kernel(Geometry g, Physics ph, const double* __restric
 }
 
 cudaError_t launch_init_rate(const Geometry& g, const Physics& ph, const double* q, DevCtrl* ctrl,
-                             double* partial, int grid, int mixed, cudaStream_t s) {
+                             double* partial, int grid, int mixed, void* dtl, cudaStream_t s) {
   if (mixed)
-    init_rate_kernel<float><<<grid, 256, 0, s>>>(g, ph, q, ctrl, partial);
+    init_rate_kernel<float><<<grid, 256, 0, s>>>(g, ph, q, ctrl, partial, static_cast<float*>(dtl));
   else
-    init_rate_kernel<double><<<grid, 256, 0, s>>>(g, ph, q, ctrl, partial);
+    init_rate_kernel<double><<<grid, 256, 0, s>>>(g, ph, q, ctrl, partial, static_cast<double*>(dtl));
   return cudaGetLastError();
 }
 
@@ -198,19 +205,64 @@ __device__ __forceinline__ void half_cross(const double* a, const double* b, dou
   c[2] = 0.5 * (a[0] * b[1] - a[1] * b[0]);
 }
 
+// node (i, j, k); indices beyond the block's nodes are extended by reflection through the
+// boundary node along the grid line, X(-m) = 2 X(0) - X(m), X(n + m) = 2 X(n) - X(n - m), the
+// x index first, then y, then z
+__device__ __forceinline__ void node_in(const Geometry& g, const double* X, long long nn, int i, int j, int k,
+                                        double* x) {
+  const long long o = ((long long)k * (g.ny + 1) + j) * (g.nx + 1) + i;
+  x[0] = X[o]; x[1] = X[nn + o]; x[2] = X[2 * nn + o];
+}
+__device__ __forceinline__ void node_k(const Geometry& g, const double* X, long long nn, int i, int j, int k,
+                                       double* x) {
+  if (k < 0 || k > g.nz) {
+    const int e = k < 0 ? 0 : g.nz;
+    double a[3], b[3];
+    node_in(g, X, nn, i, j, e, a);
+    node_in(g, X, nn, i, j, min(max(2 * e - k, 0), g.nz), b);  // clamp: blocks thinner than 2 cells
+    for (int c = 0; c < 3; ++c) x[c] = __dsub_rn(2.0 * a[c], b[c]);
+  } else {
+    node_in(g, X, nn, i, j, k, x);
+  }
+}
+__device__ __forceinline__ void node_jk(const Geometry& g, const double* X, long long nn, int i, int j, int k,
+                                        double* x) {
+  if (j < 0 || j > g.ny) {
+    const int e = j < 0 ? 0 : g.ny;
+    double a[3], b[3];
+    node_k(g, X, nn, i, e, k, a);
+    node_k(g, X, nn, i, min(max(2 * e - j, 0), g.ny), k, b);
+    for (int c = 0; c < 3; ++c) x[c] = __dsub_rn(2.0 * a[c], b[c]);
+  } else {
+    node_k(g, X, nn, i, j, k, x);
+  }
+}
+__device__ __forceinline__ void node_ext(const Geometry& g, const double* X, long long nn, int i, int j, int k,
+                                         double* x) {
+  if (i < 0 || i > g.nx) {
+    const int e = i < 0 ? 0 : g.nx;
+    double a[3], b[3];
+    node_jk(g, X, nn, e, j, k, a);
+    node_jk(g, X, nn, min(max(2 * e - i, 0), g.nx), j, k, b);
+    for (int c = 0; c < 3; ++c) x[c] = __dsub_rn(2.0 * a[c], b[c]);
+  } else {
+    node_jk(g, X, nn, i, j, k, x);
+  }
+}
+
+// every padded cell, halo included (halo nodes by reflection; the halo exchange then replaces
+// the halo cells of connected faces with the neighbour's)
 __global__ void metrics_kernel(Geometry g, const double* __restrict__ X, void* M, int elem) {
-  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long wx = g.nx + 2 * HALO, wy = g.ny + 2 * HALO;
+  const long long n = wx * wy * (g.nz + 2 * HALO);
   const long long nn = (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(c % g.nx);
-    const long long r = c / g.nx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+    const int i = (int)(c % wx) - HALO;
+    const long long r = c / wx;
+    const int j = (int)(r % wy) - HALO, k = (int)(r / wy) - HALO;
     double p[8][3];  // corner (di, dj, dk) at index di + 2 dj + 4 dk
-    for (int q = 0; q < 8; ++q) {
-      const long long o = ((long long)(k + (q >> 2)) * (g.ny + 1) + (j + ((q >> 1) & 1))) * (g.nx + 1) + i + (q & 1);
-      p[q][0] = X[o]; p[q][1] = X[nn + o]; p[q][2] = X[2 * nn + o];
-    }
+    for (int q = 0; q < 8; ++q) node_ext(g, X, nn, i + (q & 1), j + ((q >> 1) & 1), k + (q >> 2), p[q]);
     // quadrilateral a, b, c, d in counter-clockwise order seen from the side S points to:
     // S = 1/2 (c - a) x (d - b)
     auto face = [&](int a, int b, int cc, int d, double* S, double* cen) {
@@ -248,7 +300,7 @@ __global__ void metrics_kernel(Geometry g, const double* __restrict__ X, void* M
 }
 
 cudaError_t launch_metrics(const Geometry& g, const double* nodes, void* M, int elem, cudaStream_t s) {
-  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long n = (long long)(g.nx + 2 * HALO) * (g.ny + 2 * HALO) * (g.nz + 2 * HALO);
   metrics_kernel<<<grid_for(n, 128), 128, 0, s>>>(g, nodes, M, elem);
   return cudaGetLastError();
 }
@@ -257,7 +309,7 @@ cudaError_t launch_metrics(const Geometry& g, const double* nodes, void* M, int 
 // gamma/Pr) mu/rho |Sb|^2 / V), divided by V, with Sb the mean of a cell's two faces in a direction
 template <typename T>
 __global__ void init_rate_curvi_kernel(Geometry g, Physics ph, const double* __restrict__ q,
-                                       const T* __restrict__ M, DevCtrl* ctrl, double* partial) {
+                                       const T* __restrict__ M, DevCtrl* ctrl, double* partial, T* dtl) {
   __shared__ double wmax[32];
   __shared__ int last;
   const long long n = (long long)g.nx * g.ny * g.nz;
@@ -287,6 +339,7 @@ __global__ void init_rate_curvi_kernel(Geometry g, Physics ph, const double* __r
       rate += lam;
     }
     rate *= iv;
+    if (dtl) dtl[om] = T(ph.cfl) / rate;
     if (!(rho > T(0) && p > T(0))) atomicOr(&ctrl->flag, FLAG_NONPHYSICAL);
     best = fmax(best, double(rate));
   }
@@ -311,11 +364,146 @@ __global__ void init_rate_curvi_kernel(Geometry g, Physics ph, const double* __r
 }
 
 cudaError_t launch_init_rate_curvi(const Geometry& g, const Physics& ph, const double* q, const void* M,
-                                   DevCtrl* ctrl, double* partial, int grid, int mixed, cudaStream_t s) {
+                                   DevCtrl* ctrl, double* partial, int grid, int mixed, void* dtl, cudaStream_t s) {
   if (mixed)
-    init_rate_curvi_kernel<float><<<grid, 256, 0, s>>>(g, ph, q, static_cast<const float*>(M), ctrl, partial);
+    init_rate_curvi_kernel<float><<<grid, 256, 0, s>>>(g, ph, q, static_cast<const float*>(M), ctrl, partial,
+                                                       static_cast<float*>(dtl));
   else
-    init_rate_curvi_kernel<double><<<grid, 256, 0, s>>>(g, ph, q, static_cast<const double*>(M), ctrl, partial);
+    init_rate_curvi_kernel<double><<<grid, 256, 0, s>>>(g, ph, q, static_cast<const double*>(M), ctrl, partial,
+                                                        static_cast<double*>(dtl));
+  return cudaGetLastError();
+}
+
+// ---- boundary ghost cells ---------------------------------------------------------------------
+// One thread per (side, ghost layer m, face-slab point) of the physical faces of direction
+// B.dim, over the full padded extent of the other two directions so that edges and corners get
+// physical values too (directions are filled one launch after the other: x, y, z).
+//   slip wall: ghost m mirrors interior cell m about the wall face's unit normal n,
+//              u_g = u - 2 (u.n) n, same density and pressure
+//   far field: characteristic boundary state from the adjacent interior cell and the free
+//              stream (outgoing invariant u.n + 2c/(gamma-1) from inside, incoming one from the
+//              free stream; entropy and tangential velocity from the upwind side; supersonic
+//              inflow takes the free stream, supersonic outflow the interior), both layers
+// On the mixed path the state is f32; for stages 2 and 3 the field is the f32 increment D over
+// the f32 state S^n (the stencil adds them): the ghost increment is f32(Q_ghost - S_ghost).
+__device__ __forceinline__ void bc_load(const BcBlock& B, long long o, long long of, double* q) {
+  if (B.mode == BC_F64) {
+    const double* f = static_cast<const double*>(B.field);
+    for (int v = 0; v < 5; ++v) q[v] = f[v * B.g.field + o];
+  } else if (B.mode == BC_F32) {
+    const float* f = static_cast<const float*>(B.field);
+    for (int v = 0; v < 5; ++v) q[v] = double(f[v * B.g.fieldf + of]);
+  } else {
+    const float* f = static_cast<const float*>(B.field);
+    for (int v = 0; v < 5; ++v) q[v] = double(B.shadow[v * B.g.fieldf + of] + f[v * B.g.fieldf + of]);
+  }
+}
+__device__ __forceinline__ void bc_store(const BcBlock& B, long long o, long long of, const double* w) {
+  const double gm = B.gamma;
+  double q[5];
+  q[0] = w[0];
+  q[1] = w[0] * w[1];
+  q[2] = w[0] * w[2];
+  q[3] = w[0] * w[3];
+  q[4] = w[4] / (gm - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+  if (B.mode == BC_F64) {
+    double* f = static_cast<double*>(B.field);
+    for (int v = 0; v < 5; ++v) f[v * B.g.field + o] = q[v];
+  } else if (B.mode == BC_F32) {
+    float* f = static_cast<float*>(B.field);
+    for (int v = 0; v < 5; ++v) f[v * B.g.fieldf + of] = float(q[v]);
+  } else {
+    float* f = static_cast<float*>(B.field);
+    for (int v = 0; v < 5; ++v) f[v * B.g.fieldf + of] = float(q[v] - double(B.shadow[v * B.g.fieldf + of]));
+  }
+}
+__device__ __forceinline__ void bc_prim(double gm, const double* q, double* w) {
+  w[0] = q[0];
+  w[1] = q[1] / q[0];
+  w[2] = q[2] / q[0];
+  w[3] = q[3] / q[0];
+  w[4] = (gm - 1.0) * (q[4] - 0.5 * q[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]));
+}
+
+__global__ void bc_kernel(const BcBlock B) {
+  const Geometry& g = B.g;
+  const int d = B.dim, d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const long long w1 = n[d1] + 2 * HALO, w2 = n[d2] + 2 * HALO;
+  const long long total = 2LL * HALO * w1 * w2;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(t % w1) - HALO;
+    long long r = t / w1;
+    const int b = (int)(r % w2) - HALO;
+    r /= w2;
+    const int m = (int)(r % HALO), hi = (int)(r / HALO);
+    const int kind = B.kind[2 * d + hi];
+    if (kind == BC_NONE) continue;
+    int idx[3], gi[3], ii[3];
+    idx[d1] = a; idx[d2] = b; idx[d] = hi ? n[d] : 0;  // the boundary face is this cell's lower face
+    for (int x = 0; x < 3; ++x) { gi[x] = idx[x]; ii[x] = idx[x]; }
+    gi[d] = hi ? n[d] + m : -1 - m;
+    // unit normal (towards +d) of the boundary face
+    double nrm[3] = {0.0, 0.0, 0.0};
+    if (B.metrics) {
+      double S[3];
+      if (B.mode == BC_F64) {
+        const double* M = static_cast<const double*>(B.metrics);
+        const long long oc = gidx(g, idx[0], idx[1], idx[2]);
+        for (int x = 0; x < 3; ++x) S[x] = M[(3 * d + x) * g.field + oc];
+      } else {
+        const float* M = static_cast<const float*>(B.metrics);
+        const long long oc = gidxf(g, idx[0], idx[1], idx[2]);
+        for (int x = 0; x < 3; ++x) S[x] = double(M[(3 * d + x) * g.fieldf + oc]);
+      }
+      const double len = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+      for (int x = 0; x < 3; ++x) nrm[x] = S[x] / len;
+    } else {
+      nrm[d] = 1.0;
+    }
+    double q[5], wi[5], wb[5];
+    if (kind == BC_SLIP_WALL) {
+      ii[d] = hi ? n[d] - 1 - m : m;  // the mirror image inside
+      bc_load(B, gidx(g, ii[0], ii[1], ii[2]), gidxf(g, ii[0], ii[1], ii[2]), q);
+      bc_prim(B.gamma, q, wi);
+      const double un = wi[1] * nrm[0] + wi[2] * nrm[1] + wi[3] * nrm[2];
+      wb[0] = wi[0];
+      for (int x = 0; x < 3; ++x) wb[1 + x] = wi[1 + x] - 2.0 * un * nrm[x];
+      wb[4] = wi[4];
+    } else {
+      ii[d] = hi ? n[d] - 1 : 0;  // the interior cell next to the face
+      bc_load(B, gidx(g, ii[0], ii[1], ii[2]), gidxf(g, ii[0], ii[1], ii[2]), q);
+      bc_prim(B.gamma, q, wi);
+      const double gm = B.gamma;
+      const double out[3] = {hi ? nrm[0] : -nrm[0], hi ? nrm[1] : -nrm[1], hi ? nrm[2] : -nrm[2]};
+      const double ci = sqrt(gm * wi[4] / wi[0]), cinf = sqrt(gm * B.inf[4] / B.inf[0]);
+      const double uni = wi[1] * out[0] + wi[2] * out[1] + wi[3] * out[2];
+      const double uninf = B.inf[1] * out[0] + B.inf[2] * out[1] + B.inf[3] * out[2];
+      if (uninf <= -cinf) {
+        for (int v = 0; v < 5; ++v) wb[v] = B.inf[v];
+      } else if (uni >= ci) {
+        for (int v = 0; v < 5; ++v) wb[v] = wi[v];
+      } else {
+        const double rp = uni + 2.0 * ci / (gm - 1.0), rm = uninf - 2.0 * cinf / (gm - 1.0);
+        const double unb = 0.5 * (rp + rm), cb = 0.25 * (gm - 1.0) * (rp - rm);
+        const double* src = unb < 0.0 ? B.inf : wi;
+        const double un_src = src[1] * out[0] + src[2] * out[1] + src[3] * out[2];
+        const double ent = src[4] / pow(src[0], gm);
+        const double rho = pow(cb * cb / (gm * ent), 1.0 / (gm - 1.0));
+        wb[0] = rho;
+        for (int x = 0; x < 3; ++x) wb[1 + x] = src[1 + x] + (unb - un_src) * out[x];
+        wb[4] = rho * cb * cb / gm;
+      }
+    }
+    bc_store(B, gidx(g, gi[0], gi[1], gi[2]), gidxf(g, gi[0], gi[1], gi[2]), wb);
+  }
+}
+
+cudaError_t launch_bc(const BcBlock& B, cudaStream_t s) {
+  const int n[3] = {B.g.nx, B.g.ny, B.g.nz};
+  const long long total = 2LL * HALO * (n[(B.dim + 1) % 3] + 2 * HALO) * (n[(B.dim + 2) % 3] + 2 * HALO);
+  bc_kernel<<<grid_for(total, 128), 128, 0, s>>>(B);
   return cudaGetLastError();
 }
 

@@ -67,6 +67,7 @@ struct Physics {
   double gamma, mu, Pr, cfl, eps;
   double ihx, ihy, ihz;  // 1 / cell size (Cartesian grids)
   int viscous, limiter;
+  int local_dt;          // 1: every cell advances with its own CFL step (BlockDesc::dtl)
 };
 
 // ---- one block as the stage kernel sees it (device-resident descriptor table) --------------
@@ -85,7 +86,8 @@ struct BlockDesc {
   int ntx, nty;              // tiles along x and y
   long long units;           // work units (tile-planes) = ntx * nty * nz
   int cta0, ctas;            // the CTAs of a group launch that work on this block
-  long long pad_[2];
+  void* dtl;                 // local time steps, one padded field (f64 FP64 path, f32 mixed)
+  long long pad_;
 };
 
 // parameters of one stage launch over a group of blocks.  The grid is split between the blocks
@@ -99,6 +101,21 @@ struct GroupParams {
   DevCtrl* gctrl;            // group control: counter, time step (read at stage start)
   double* partial;           // [gridDim.x * NPART]
   double* rout;              // residual mode (one block): compact R[5][nz][ny][nx]
+};
+
+// ---- boundary ghost cells of one block, one direction per launch ------------------------------
+enum BcKind { BC_NONE = 0, BC_SLIP_WALL = 1, BC_FARFIELD = 2 };
+enum BcMode { BC_F64 = 0, BC_F32 = 1, BC_F32_INC = 2 };
+struct BcBlock {
+  Geometry g;
+  int kind[6];          // per face -x, +x, -y, +y, -z, +z
+  double inf[5];        // free stream (rho, u, v, w, p)
+  double gamma;
+  int dim;              // the direction this launch fills
+  int mode;             // BC_F64: f64 state; BC_F32: f32 state; BC_F32_INC: f32 increment over `shadow`
+  void* field;
+  const float* shadow;  // BC_F32_INC: the f32 state the increment is added to
+  const void* metrics;  // curvilinear metrics (f64 on the FP64 path, f32 mixed) or null (Cartesian)
 };
 
 // ---- block group descriptors for halo exchange ----------------------------------------------

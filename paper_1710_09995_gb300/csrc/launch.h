@@ -30,13 +30,17 @@ cudaError_t launch_halo(const HaloGroup& G, cudaStream_t s);
 // compact [5][nz][ny][nx] f64 <-> padded f64 field
 cudaError_t launch_scatter(const Geometry& g, const double* src, double* dst, float* shadow, cudaStream_t s);
 cudaError_t launch_gather(const Geometry& g, const double* src, double* dst, cudaStream_t s);
-// spectral-radius rate and time step of a padded f64 state (per-CTA partials, last CTA reduces)
+// ghost cells of a block's physical faces in one direction
+cudaError_t launch_bc(const BcBlock& B, cudaStream_t s);
+// spectral-radius rate and time step of a padded f64 state (per-CTA partials, last CTA reduces);
+// dtl (may be null): every cell's own CFL step, f64 (FP64 path) or f32 (mixed) padded field
 cudaError_t launch_init_rate(const Geometry& g, const Physics& ph, const double* q, DevCtrl* ctrl,
-                             double* partial, int grid, int mixed, cudaStream_t s);
-// curvilinear metrics of the interior cells from the block's nodes (10 padded fields)
+                             double* partial, int grid, int mixed, void* dtl, cudaStream_t s);
+// curvilinear metrics of every padded cell from the block's nodes (10 padded fields)
 cudaError_t launch_metrics(const Geometry& g, const double* nodes, void* M, int elem, cudaStream_t s);
 cudaError_t launch_init_rate_curvi(const Geometry& g, const Physics& ph, const double* q, const void* M,
-                                   DevCtrl* ctrl, double* partial, int grid, int mixed, cudaStream_t s);
+                                   DevCtrl* ctrl, double* partial, int grid, int mixed, void* dtl,
+                                   cudaStream_t s);
 // global time step of a group: dt = cfl / max rate, written to every block
 cudaError_t launch_group_dt(DevCtrl* const* ctrls, int n, double cfl, cudaStream_t s, DevCtrl* extra = nullptr);
 

@@ -479,8 +479,11 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
       // per-cell inputs of the update (L2-resident planes), loaded before the face work
       double qs_[5], qn_[5];
       float dp_[5];
+      T dtc = dtT;  // this cell's time step (its own one under local time stepping)
       if (live) {
         const long long o = gidx(g, ci, cj, k), of = gidxf(g, ci, cj, k);
+        if constexpr (STAGE >= 1 && !VISC)  // local time steps: inviscid blocks only
+          if (ph.local_dt) dtc = __ldg(static_cast<const T*>(D->dtl) + (MIXED ? of : o));
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           if constexpr (!MIXED && STAGE >= 1) qs_[v] = __ldg(qs + v * g.field + o);
@@ -559,7 +562,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
           double out[5];
 #pragma unroll
           for (int m = 0; m < 5; ++m) {
-            const double adv = qs_[m] - dt * double(R[m]);
+            const double adv = qs_[m] - double(dtc) * double(R[m]);
             if constexpr (STAGE == 1) out[m] = adv;
             else if constexpr (STAGE == 2) out[m] = 0.75 * qn_[m] + 0.25 * adv;
             else out[m] = qn_[m] / 3.0 + (2.0 / 3.0) * adv;
@@ -570,19 +573,22 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
             const double uu = out[1] * ir, vv = out[2] * ir, ww = out[3] * ir;
             const double pp = (ph.gamma - 1.0) * (out[4] - 0.5 * out[0] * (uu * uu + vv * vv + ww * ww));
             if (!(out[0] > 0.0 && pp > 0.0)) bad = true;
+            double rate;
             if constexpr (CURVI) {
               T sb[9];
               cell_face_means(mring, mk, mk1, ocy, ocx, sb);
-              rate_max = fmax(rate_max, T(cell_rate_curvi<double>(out[0], uu, vv, ww, pp, sb,
-                                                                  mring[mb(mk, ocy, ocx) + 9 * MS], ph)));
+              rate = cell_rate_curvi<double>(out[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], ph);
             } else {
-              rate_max = fmax(rate_max, T(cell_rate<double>(out[0], uu, vv, ww, pp, ph, hx, hy, hz)));
+              rate = cell_rate<double>(out[0], uu, vv, ww, pp, ph, hx, hy, hz);
             }
+            rate_max = fmax(rate_max, T(rate));
+            if constexpr (!VISC)
+              if (ph.local_dt) static_cast<double*>(D->dtl)[o] = ph.cfl / rate;
           }
         } else {
           float inc[5];
 #pragma unroll
-          for (int m = 0; m < 5; ++m) inc[m] = -float(dtT) * float(R[m]);
+          for (int m = 0; m < 5; ++m) inc[m] = -float(dtc) * float(R[m]);
           if constexpr (STAGE == 1) {
 #pragma unroll
             for (int m = 0; m < 5; ++m) dout[m * g.fieldf + of] = inc[m];
@@ -603,14 +609,17 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
             const float uu = qf[1] * ir, vv = qf[2] * ir, ww = qf[3] * ir;
             const float pp = float(ph.gamma - 1.0) * (qf[4] - 0.5f * qf[0] * (uu * uu + vv * vv + ww * ww));
             if (!(qf[0] > 0.0f && pp > 0.0f)) bad = true;
+            float rate;
             if constexpr (CURVI) {
               T sb[9];
               cell_face_means(mring, mk, mk1, ocy, ocx, sb);
-              rate_max = fmax(rate_max, T(cell_rate_curvi<float>(qf[0], uu, vv, ww, pp, sb,
-                                                                 mring[mb(mk, ocy, ocx) + 9 * MS], ph)));
+              rate = cell_rate_curvi<float>(qf[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], ph);
             } else {
-              rate_max = fmax(rate_max, T(cell_rate<float>(qf[0], uu, vv, ww, pp, ph, hx, hy, hz)));
+              rate = cell_rate<float>(qf[0], uu, vv, ww, pp, ph, hx, hy, hz);
             }
+            rate_max = fmax(rate_max, T(rate));
+            if constexpr (!VISC)
+              if (ph.local_dt) static_cast<float*>(D->dtl)[of] = float(ph.cfl) / rate;
           }
         }
         if constexpr (STAGE == 1) {

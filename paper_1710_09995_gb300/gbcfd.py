@@ -17,6 +17,7 @@ OK = 0
 ERR_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_STATE, ERR_MEMORY = -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
 FACES = {"-x": 0, "+x": 1, "-y": 2, "+y": 3, "-z": 4, "+z": 5}
+BC_NONE, BC_SLIP_WALL, BC_FARFIELD = 0, 1, 2
 
 
 class Params(ctypes.Structure):
@@ -29,13 +30,14 @@ class Params(ctypes.Structure):
         ("viscous", ctypes.c_int),
         ("limiter", ctypes.c_int),
         ("precision", ctypes.c_int),
-        ("reserved", ctypes.c_int),
+        ("local_dt", ctypes.c_int),
     ]
 
 
 def params(gamma=1.4, mu=0.0, Pr=0.72, cfl=0.5, entropy_eps=0.1, viscous=False, limiter=0,
-           precision=FP64) -> Params:
-    return Params(gamma, mu, Pr, cfl, entropy_eps, int(bool(viscous)), int(limiter), int(precision), 0)
+           precision=FP64, local_dt=False) -> Params:
+    return Params(gamma, mu, Pr, cfl, entropy_eps, int(bool(viscous)), int(limiter), int(precision),
+                  int(bool(local_dt)))
 
 
 class GbcfdError(RuntimeError):
@@ -67,6 +69,7 @@ SIGNATURES = {
     "gbcfd_get_dt": [_VP, _D, _VP],
     "gbcfd_time_step_noalloc": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), _D, _VP,
                                 _VP],
+    "gbcfd_set_boundary": [_VP, ctypes.c_int, ctypes.c_int, _D],
     "gbcfd_group_required_bytes": [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
     "gbcfd_group_create": [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.c_size_t, ctypes.POINTER(_VP)],
     "gbcfd_group_destroy": [_VP],
@@ -150,6 +153,11 @@ class Block:
         f = FACES[face] if isinstance(face, str) else int(face)
         _check(lib().gbcfd_connect(self.handle, f, other.handle))
 
+    def set_boundary(self, face, kind, inf=None):
+        f = FACES[face] if isinstance(face, str) else int(face)
+        arr = (ctypes.c_double * 5)(*inf) if inf is not None else None
+        _check(lib().gbcfd_set_boundary(self.handle, f, int(kind), arr))
+
     def periodic(self):
         for d in range(3):
             self.connect(2 * d + 1, self)
@@ -213,11 +221,22 @@ def create_block(nx, ny, nz, prm: Params, device=None) -> Block:
     return Block(nx, ny, nz, prm, device)
 
 
-def block_for_case(case, precision=FP64, periodic=True, device=None) -> Block:
-    """Block configured from a cases.Case (physics, Cartesian spacing, initial state)."""
-    prm = params(case.gamma, case.mu, case.Pr, case.cfl, case.eps, case.viscous, case.limiter, precision)
+def block_for_case(case, precision=FP64, periodic=True, device=None, local_dt=None) -> Block:
+    """Block configured from a cases.Case (physics, grid, initial state).  A case with boundary
+    conditions (extra["bc"]: face -> kind, extra["inf"]: free stream) gets them on those faces,
+    is periodic in the other directions and steps with local time steps unless told otherwise."""
+    bcs = case.extra.get("bc") if case.extra else None
+    if local_dt is None:
+        local_dt = bool(bcs)
+    prm = params(case.gamma, case.mu, case.Pr, case.cfl, case.eps, case.viscous, case.limiter, precision, local_dt)
     b = Block(case.nx, case.ny, case.nz, prm, device)
-    if periodic:
+    if bcs:
+        for f, kind in bcs.items():
+            b.set_boundary(f, kind, case.extra.get("inf"))
+        for d, (lo, hi) in enumerate((("-x", "+x"), ("-y", "+y"), ("-z", "+z"))):
+            if lo not in bcs and hi not in bcs:
+                b.connect(2 * d + 1, b)
+    elif periodic:
         b.periodic()
     if case.nodes is None:
         b.set_metrics(spacing=case.spacing)
