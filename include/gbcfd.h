@@ -210,6 +210,58 @@ int gbcfd_group_tune(gbcfd_group group, void* stream, int* ctas_per_sm);
  * them.  Drops the captured graphs; the events of one step are overwritten by the next. */
 int gbcfd_group_set_timing(gbcfd_group group, void* const* events, int n);
 
+/* ---- learned convergence accelerator (not in the paper: the project's addition) --------------
+ * A 3-layer 3D convolutional network (channels 10 -> 32 -> 32 -> 5, 3x3x3 taps, SiLU, zero
+ * padding in x and y, periodic in z) predicts the change of a block's state over K = 20
+ * pseudo-time steps from the state and its residual; a prediction is kept only if the RMS of
+ * the density residual then drops (the plain iteration decides).  Features per cell:
+ * 10 (Q - Q_inf) / ref and (-dt_cell R) / ref / s, with ref = (rho, rho c, rho c, rho c, rho c^2)
+ * of the free stream and s the RMS of (-dt_cell R) / ref over the block; prediction
+ * Q + 20 s ref y.  The free stream is the block's far-field one (gbcfd_set_boundary).
+ * Tensors are channels-last: features bfloat16 [cell][16] (10 used), outputs and targets float
+ * [cell][8] (5 used); cell = ((b nz + k) ny + j) nx + i.  Weights are bfloat16 with FP32
+ * accumulation on the tensor cores; FP32 master weights and Adam moments.
+ * Parameters (host float, GBCFD_ACCEL_NPARAM): per layer W[out][in][tap] then b[out], tap
+ * t = 9 (dz+1) + 3 (dy+1) + (dx+1). */
+#define GBCFD_ACCEL_NPARAM 40677
+typedef struct gbcfd_accel_s* gbcfd_accel;
+
+/* Device bytes of an accelerator over `batch` volumes of nx x ny x nz cells. */
+int gbcfd_accel_required_bytes(int nx, int ny, int nz, int batch, size_t* bytes);
+
+/* Create it in caller memory (256-byte aligned).  zperiodic: the volume wraps in z. */
+int gbcfd_accel_create(int nx, int ny, int nz, int batch, int zperiodic, void* dev_mem, size_t bytes,
+                       gbcfd_accel* out);
+int gbcfd_accel_destroy(gbcfd_accel accel);
+
+/* Load / read the parameters (host, GBCFD_ACCEL_NPARAM floats).  Loading resets Adam. */
+int gbcfd_accel_set_params(gbcfd_accel accel, const float* params, void* stream);
+int gbcfd_accel_get_params(gbcfd_accel accel, float* params, void* stream);
+
+/* Network output y (device float [batch cells][8]) for features x (device bf16 [batch cells][16]). */
+int gbcfd_accel_forward(gbcfd_accel accel, const void* x, float* y, void* stream);
+
+/* One Adam step (learning rate lr, step counts from 1) on the mean squared error between the
+ * network's output for x and target t (device float [batch cells][8]); *loss (host) gets the
+ * loss before the step.  Synchronises the stream. */
+int gbcfd_accel_train_step(gbcfd_accel accel, const void* x, const float* t, float lr, int step, double* loss,
+                           void* stream);
+
+/* Features of a block (its size must be the accelerator's volume) into x (device bf16
+ * [cells][16], NULL: the accelerator's own buffer); remembers the state and s for
+ * gbcfd_accel_target.  The block must hold a state, be between steps and have a far-field face. */
+int gbcfd_accel_features(gbcfd_accel accel, gbcfd_block block, void* x, void* stream);
+
+/* Training target of the block's state now against the one remembered by the last
+ * gbcfd_accel_features: (Q_now - Q_then) / ref / (20 s), into t (device float [cells][8]). */
+int gbcfd_accel_target(gbcfd_accel accel, gbcfd_block block, float* t, void* stream);
+
+/* One accelerated update: residual and features at Q, prediction Q' = Q + 20 s ref y, residual at
+ * Q'; Q' is kept when RMS(R_rho(Q')) < RMS(R_rho(Q)), else Q is restored.  *accepted (host) tells
+ * which; norms[0], norms[1] (host, may be NULL) get the two RMS values.  The time steps are then
+ * re-evaluated from the block's state.  Synchronises the stream. */
+int gbcfd_accel_try(gbcfd_accel accel, gbcfd_block block, void* stream, int* accepted, double norms[2]);
+
 /* Message of the last error on the calling host thread ("" if none). */
 const char* gbcfd_last_error(void);
 

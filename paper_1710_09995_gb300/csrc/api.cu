@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -13,6 +14,7 @@
 
 #include "gbcfd.h"
 #include "launch.h"
+#include "learn.cuh"
 
 using namespace gbcfd;
 
@@ -961,6 +963,316 @@ extern "C" int gbcfd_get_dt(gbcfd_block b, double* dt, void* stream) {
   int rc = read_ctrl(b, &h, static_cast<cudaStream_t>(stream));
   if (rc) return rc;
   *dt = h.dt;
+  return GBCFD_OK;
+}
+
+// ---- learned convergence accelerator ------------------------------------------------------------
+using bf16 = __nv_bfloat16;
+struct gbcfd_accel_s {
+  int nx, ny, nz, batch, zper;
+  long long cells;            // batch x nx x ny x nz
+  learn::Net net;
+  bf16 *x, *a1, *a2, *dy, *dz1, *dz2;
+  float *z1, *z2, *y;
+  double *R, *qsave, *partial, *stats;
+  int pgrid;
+  int step_count;
+};
+
+static const size_t kAccelParts = 1024;  // rows of the per-CTA reduction partials
+
+static size_t accel_carve(int nx, int ny, int nz, int batch, int nsm, size_t* off) {
+  const long long cells = (long long)nx * ny * nz * batch, vol = (long long)nx * ny * nz;
+  const int wgrid = 2 * nsm;
+  size_t o = 0;
+  auto take = [&](int i, size_t bytes) { off[i] = o; o += align256(bytes); };
+  take(0, sizeof(float) * learn::NPARAM);                              // w
+  take(1, sizeof(float) * learn::NPARAM);                              // m
+  take(2, sizeof(float) * learn::NPARAM);                              // v
+  take(3, sizeof(float) * learn::NPARAM);                              // grad
+  take(4, sizeof(bf16) * learn::NTAP * learn::P1 * learn::P0);         // w1
+  take(5, sizeof(bf16) * learn::NTAP * learn::P2 * learn::P1);         // w2
+  take(6, sizeof(bf16) * learn::NTAP * learn::P3 * learn::P2);         // w3
+  take(7, sizeof(bf16) * learn::NTAP * learn::P2 * 16);                // w3b
+  take(8, sizeof(bf16) * learn::NTAP * learn::P1 * learn::P2);         // w2b
+  take(9, sizeof(float) * (learn::P1 + learn::P2 + learn::P3));       // biases
+  take(10, sizeof(float) * learn::NPARAM * (size_t)wgrid);             // weight-gradient partials
+  take(11, sizeof(bf16) * 16 * cells);                                 // x
+  take(12, sizeof(bf16) * 32 * cells);                                 // a1
+  take(13, sizeof(bf16) * 32 * cells);                                 // a2
+  take(14, sizeof(float) * 32 * cells);                                // z1
+  take(15, sizeof(float) * 32 * cells);                                // z2
+  take(16, sizeof(float) * 8 * cells);                                 // y
+  take(17, sizeof(bf16) * 16 * cells);                                 // dy
+  take(18, sizeof(bf16) * 32 * cells);                                 // dz2
+  take(19, sizeof(bf16) * 32 * cells);                                 // dz1
+  take(20, sizeof(double) * 5 * vol);                                  // R (one volume)
+  take(21, sizeof(double) * 5 * vol);                                  // saved state
+  take(22, sizeof(double) * NPART * kAccelParts);                      // partials
+  take(23, sizeof(double) * 8);                                        // stats
+  return o;
+}
+
+extern "C" int gbcfd_accel_required_bytes(int nx, int ny, int nz, int batch, size_t* bytes) {
+  if (nx < 1 || ny < 1 || nz < 1 || batch < 1) return fail(GBCFD_ERR_ARG, "sizes must be >= 1");
+  if (!bytes) return fail(GBCFD_ERR_ARG, "bytes is NULL");
+  int dev = 0, nsm = 0;
+  int rc = device_sms(&dev, &nsm);
+  if (rc) return rc;
+  size_t off[24];
+  *bytes = accel_carve(nx, ny, nz, batch, nsm, off);
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_accel_create(int nx, int ny, int nz, int batch, int zperiodic, void* dev_mem, size_t bytes,
+                                  gbcfd_accel* out) {
+  if (!out) return fail(GBCFD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  size_t need = 0;
+  int rc = gbcfd_accel_required_bytes(nx, ny, nz, batch, &need);
+  if (rc) return rc;
+  if (!dev_mem) return fail(GBCFD_ERR_ARG, "dev_mem is NULL");
+  if (((uintptr_t)dev_mem & 255u) != 0) return fail(GBCFD_ERR_MEMORY, "dev_mem must be 256-byte aligned");
+  if (bytes < need) return fail(GBCFD_ERR_MEMORY, "dev_mem smaller than gbcfd_accel_required_bytes");
+  int dev = 0, nsm = 0;
+  rc = device_sms(&dev, &nsm);
+  if (rc) return rc;
+  size_t off[24];
+  accel_carve(nx, ny, nz, batch, nsm, off);
+  char* base = static_cast<char*>(dev_mem);
+  gbcfd_accel a = new gbcfd_accel_s();
+  a->nx = nx; a->ny = ny; a->nz = nz; a->batch = batch; a->zper = zperiodic ? 1 : 0;
+  a->cells = (long long)nx * ny * nz * batch;
+  learn::Net& n = a->net;
+  n.w = reinterpret_cast<float*>(base + off[0]);
+  n.m = reinterpret_cast<float*>(base + off[1]);
+  n.v = reinterpret_cast<float*>(base + off[2]);
+  n.grad = reinterpret_cast<float*>(base + off[3]);
+  n.w1 = reinterpret_cast<bf16*>(base + off[4]);
+  n.w2 = reinterpret_cast<bf16*>(base + off[5]);
+  n.w3 = reinterpret_cast<bf16*>(base + off[6]);
+  n.w3b = reinterpret_cast<bf16*>(base + off[7]);
+  n.w2b = reinterpret_cast<bf16*>(base + off[8]);
+  n.b1 = reinterpret_cast<float*>(base + off[9]);
+  n.b2 = n.b1 + learn::P1;
+  n.b3 = n.b2 + learn::P2;
+  n.wpart = reinterpret_cast<float*>(base + off[10]);
+  n.wgrid = 2 * nsm;
+  a->x = reinterpret_cast<bf16*>(base + off[11]);
+  a->a1 = reinterpret_cast<bf16*>(base + off[12]);
+  a->a2 = reinterpret_cast<bf16*>(base + off[13]);
+  a->z1 = reinterpret_cast<float*>(base + off[14]);
+  a->z2 = reinterpret_cast<float*>(base + off[15]);
+  a->y = reinterpret_cast<float*>(base + off[16]);
+  a->dy = reinterpret_cast<bf16*>(base + off[17]);
+  a->dz2 = reinterpret_cast<bf16*>(base + off[18]);
+  a->dz1 = reinterpret_cast<bf16*>(base + off[19]);
+  a->R = reinterpret_cast<double*>(base + off[20]);
+  a->qsave = reinterpret_cast<double*>(base + off[21]);
+  a->partial = reinterpret_cast<double*>(base + off[22]);
+  a->stats = reinterpret_cast<double*>(base + off[23]);
+  a->pgrid = (int)std::min<size_t>(kAccelParts, (size_t)4 * nsm);
+  a->step_count = 0;
+  cudaError_t e = cudaMemset(base, 0, off[11]);  // parameters, moments, packed weights: zero
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { delete a; return cuda_fail(e, "initialising the accelerator"); }
+  *out = a;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_accel_destroy(gbcfd_accel a) {
+  if (!a) return fail(GBCFD_ERR_ARG, "accelerator is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  delete a;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_accel_set_params(gbcfd_accel a, const float* params, void* stream) {
+  if (!a || !params) return fail(GBCFD_ERR_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(a->net.w, params, sizeof(float) * learn::NPARAM, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(a->net.m, 0, sizeof(float) * learn::NPARAM, s));
+  CK(cudaMemsetAsync(a->net.v, 0, sizeof(float) * learn::NPARAM, s));
+  CK(learn::launch_pack(a->net, s));
+  CK(cudaStreamSynchronize(s));
+  a->step_count = 0;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_accel_get_params(gbcfd_accel a, float* params, void* stream) {
+  if (!a || !params) return fail(GBCFD_ERR_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(params, a->net.w, sizeof(float) * learn::NPARAM, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return GBCFD_OK;
+}
+
+static learn::ConvArgs conv_args(gbcfd_accel a, const void* in, const bf16* w, const float* bias, void* out,
+                                 float* zsave, const float* zprev) {
+  learn::ConvArgs c;
+  c.in = static_cast<const bf16*>(in);
+  c.w = w;
+  c.bias = bias;
+  c.out = out;
+  c.zsave = zsave;
+  c.zprev = zprev;
+  c.X = a->nx; c.Y = a->ny; c.Z = a->nz; c.B = a->batch; c.zper = a->zper;
+  return c;
+}
+
+// the three forward convolutions; z1, z2 kept when training
+static int accel_forward(gbcfd_accel a, const void* x, float* y, bool keep, cudaStream_t s) {
+  const learn::Net& n = a->net;
+  CK(learn::launch_conv(1, learn::FWD_SILU, conv_args(a, x, n.w1, n.b1, a->a1, keep ? a->z1 : nullptr, nullptr), s));
+  CK(learn::launch_conv(2, learn::FWD_SILU, conv_args(a, a->a1, n.w2, n.b2, a->a2, keep ? a->z2 : nullptr, nullptr), s));
+  CK(learn::launch_conv(3, learn::FWD_LINEAR, conv_args(a, a->a2, n.w3, n.b3, y, nullptr, nullptr), s));
+  return GBCFD_OK;
+}
+
+static int check_dev(const void* p, const char* what) {
+  bool dev = false;
+  int rc = is_device_ptr(p, &dev);
+  if (rc) return rc;
+  if (!dev) return fail(GBCFD_ERR_ARG, std::string(what) + " must be device memory");
+  if (((uintptr_t)p & 15u) != 0) return fail(GBCFD_ERR_ARG, std::string(what) + " must be 16-byte aligned");
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_accel_forward(gbcfd_accel a, const void* x, float* y, void* stream) {
+  if (!a || !x || !y) return fail(GBCFD_ERR_ARG, "NULL argument");
+  int rc = check_dev(x, "x");
+  if (!rc) rc = check_dev(y, "y");
+  if (rc) return rc;
+  return accel_forward(a, x, y, false, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int gbcfd_accel_train_step(gbcfd_accel a, const void* x, const float* t, float lr, int step, double* loss,
+                                      void* stream) {
+  if (!a || !x || !t) return fail(GBCFD_ERR_ARG, "NULL argument");
+  if (step < 1) return fail(GBCFD_ERR_ARG, "step counts from 1");
+  int rc = check_dev(x, "x");
+  if (!rc) rc = check_dev(t, "t");
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const learn::Net& n = a->net;
+  rc = accel_forward(a, x, a->y, true, s);
+  if (rc) return rc;
+  CK(learn::launch_loss(a->y, t, a->dy, a->partial, a->cells, a->pgrid, s));
+  CK(learn::launch_sum(a->partial, a->pgrid, 1, a->stats + 4, s));
+  CK(learn::launch_wgrad(3, a->a2, a->dy, n, a->nx, a->ny, a->nz, a->batch, a->zper, s));
+  CK(learn::launch_conv(3, learn::BWD_DSILU, conv_args(a, a->dy, n.w3b, nullptr, a->dz2, nullptr, a->z2), s));
+  CK(learn::launch_wgrad(2, a->a1, a->dz2, n, a->nx, a->ny, a->nz, a->batch, a->zper, s));
+  CK(learn::launch_conv(2, learn::BWD_DSILU, conv_args(a, a->dz2, n.w2b, nullptr, a->dz1, nullptr, a->z1), s));
+  CK(learn::launch_wgrad(1, static_cast<const bf16*>(x), a->dz1, n, a->nx, a->ny, a->nz, a->batch, a->zper, s));
+  CK(learn::launch_grad_reduce(n, s));
+  CK(learn::launch_adam(n, lr, step, s));
+  CK(learn::launch_pack(n, s));
+  double h = 0.0;
+  CK(cudaMemcpyAsync(&h, a->stats + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (loss) *loss = h / (5.0 * (double)a->cells);
+  return GBCFD_OK;
+}
+
+// the block as the feature kernels see it
+static int accel_view(gbcfd_accel a, gbcfd_block b, learn::BlockView* v) {
+  if (!b) return fail(GBCFD_ERR_ARG, "block is NULL");
+  if (b->nx != a->nx || b->ny != a->ny || b->nz != a->nz) return fail(GBCFD_ERR_ARG, "block size differs from the accelerator's volume");
+  if (!b->has_state) return fail(GBCFD_ERR_STATE, "block has no state");
+  if (b->next_stage != 1) return fail(GBCFD_ERR_STATE, "block is between stages");
+  int far = -1;
+  for (int f = 0; f < 6; ++f)
+    if (b->bc_kind[f] == GBCFD_BC_FARFIELD && !b->nbr[f]) far = f;
+  if (far < 0) return fail(GBCFD_ERR_ARG, "the block has no far-field face (the free stream scales the features)");
+  const double* inf = b->bc_inf;
+  const double gm = b->p.gamma, c = std::sqrt(gm * inf[4] / inf[0]);
+  v->nx = b->nx; v->ny = b->ny; v->nz = b->nz;
+  v->field = b->g.field; v->fieldf = b->g.fieldf;
+  v->px = b->g.px; v->pxf = b->g.pxf;
+  v->q = state_ptr(b);
+  v->sh = b->p.precision == GBCFD_MIXED ? b->sh[b->cur] : nullptr;
+  v->dtl = b->dtl;
+  v->dtl_f32 = b->p.precision == GBCFD_MIXED;
+  v->dt = &b->ctrl->dt;
+  v->qinf[0] = inf[0];
+  v->qinf[1] = inf[0] * inf[1];
+  v->qinf[2] = inf[0] * inf[2];
+  v->qinf[3] = inf[0] * inf[3];
+  v->qinf[4] = inf[4] / (gm - 1.0) + 0.5 * inf[0] * (inf[1] * inf[1] + inf[2] * inf[2] + inf[3] * inf[3]);
+  v->ref[0] = inf[0];
+  v->ref[1] = v->ref[2] = v->ref[3] = inf[0] * c;
+  v->ref[4] = inf[0] * c * c;
+  return GBCFD_OK;
+}
+
+// residual of the block's current state into a->R and its statistics into a->stats[at], [at+1]
+static int accel_residual_stats(gbcfd_accel a, gbcfd_block b, const learn::BlockView& v, int at, cudaStream_t s) {
+  int rc = prepare_metrics(&b, 1, s);
+  if (rc) return rc;
+  rc = exchange(&b, 1, F_STATE, true, s);
+  if (rc) return rc;
+  rc = run_stage(b, 0, a->R, s);
+  if (rc) return rc;
+  CK(learn::launch_feature_stats(v, a->R, a->partial, a->pgrid, s));
+  CK(learn::launch_sum(a->partial, a->pgrid, 2, a->stats + at, s));
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_accel_features(gbcfd_accel a, gbcfd_block b, void* x, void* stream) {
+  if (!a) return fail(GBCFD_ERR_ARG, "accelerator is NULL");
+  if (x) {
+    int rc = check_dev(x, "x");
+    if (rc) return rc;
+  }
+  learn::BlockView v;
+  int rc = accel_view(a, b, &v);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = accel_residual_stats(a, b, v, 0, s);
+  if (rc) return rc;
+  CK(learn::launch_features(v, a->R, a->stats, x ? static_cast<bf16*>(x) : a->x, a->qsave, s));
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_accel_target(gbcfd_accel a, gbcfd_block b, float* t, void* stream) {
+  if (!a || !t) return fail(GBCFD_ERR_ARG, "NULL argument");
+  int rc = check_dev(t, "t");
+  if (rc) return rc;
+  learn::BlockView v;
+  rc = accel_view(a, b, &v);
+  if (rc) return rc;
+  CK(learn::launch_target(v, a->qsave, a->stats, t, static_cast<cudaStream_t>(stream)));
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_accel_try(gbcfd_accel a, gbcfd_block b, void* stream, int* accepted, double norms[2]) {
+  if (!a || !accepted) return fail(GBCFD_ERR_ARG, "NULL argument");
+  learn::BlockView v;
+  int rc = accel_view(a, b, &v);
+  if (rc) return rc;
+  if (a->batch != 1) return fail(GBCFD_ERR_ARG, "an accelerator for one volume is needed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = accel_residual_stats(a, b, v, 0, s);
+  if (rc) return rc;
+  CK(learn::launch_features(v, a->R, a->stats, a->x, a->qsave, s));
+  rc = accel_forward(a, a->x, a->y, false, s);
+  if (rc) return rc;
+  CK(learn::launch_apply(v, a->y, a->qsave, a->stats, 0, s));
+  rc = accel_residual_stats(a, b, v, 2, s);
+  if (rc) return rc;
+  double h[4];
+  CK(cudaMemcpyAsync(h, a->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double n = (double)b->nx * b->ny * b->nz;
+  const double r0 = std::sqrt(h[1] / n), r1 = std::sqrt(h[3] / n);
+  const bool keep = std::isfinite(r1) && r1 < r0;
+  if (!keep) CK(learn::launch_apply(v, a->y, a->qsave, a->stats, 1, s));
+  rc = init_rate(b, s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  *accepted = keep ? 1 : 0;
+  if (norms) { norms[0] = r0; norms[1] = r1; }
   return GBCFD_OK;
 }
 

@@ -76,6 +76,17 @@ SIGNATURES = {
     "gbcfd_group_step": [_VP, ctypes.c_int, _VP],
     "gbcfd_group_tune": [_VP, _VP, ctypes.POINTER(ctypes.c_int)],
     "gbcfd_group_set_timing": [_VP, ctypes.POINTER(_VP), ctypes.c_int],
+    "gbcfd_accel_required_bytes": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+    "gbcfd_accel_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t,
+                           ctypes.POINTER(_VP)],
+    "gbcfd_accel_destroy": [_VP],
+    "gbcfd_accel_set_params": [_VP, ctypes.POINTER(ctypes.c_float), _VP],
+    "gbcfd_accel_get_params": [_VP, ctypes.POINTER(ctypes.c_float), _VP],
+    "gbcfd_accel_forward": [_VP, _VP, _VP, _VP],
+    "gbcfd_accel_train_step": [_VP, _VP, _VP, ctypes.c_float, ctypes.c_int, _D, _VP],
+    "gbcfd_accel_features": [_VP, _VP, _VP, _VP],
+    "gbcfd_accel_target": [_VP, _VP, _VP, _VP],
+    "gbcfd_accel_try": [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_int), _D],
     "gbcfd_last_error": [],
 }
 
@@ -337,3 +348,84 @@ def gather_lattice(lat, blocks, out=None):
     for b, (zs, ys, xs) in zip(blocks, lat.block_slices().values()):
         out[:, zs, ys, xs] = b.get_state()
     return out
+
+
+ACCEL_NPARAM = 40677
+
+
+class Accel:
+    """The learned convergence accelerator over `batch` volumes of nx x ny x nz cells
+    (gbcfd_accel_*).  Features are bf16 [batch cells][16] tensors (torch.bfloat16), outputs and
+    targets float32 [batch cells][8]."""
+
+    def __init__(self, nx, ny, nz, batch=1, zperiodic=True, device=None):
+        self.nx, self.ny, self.nz, self.batch = int(nx), int(ny), int(nz), int(batch)
+        nbytes = ctypes.c_size_t(0)
+        _check(lib().gbcfd_accel_required_bytes(self.nx, self.ny, self.nz, self.batch, ctypes.byref(nbytes)))
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.memory = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=dev)
+        base = self.memory.data_ptr()
+        off = (-base) % 256
+        h = ctypes.c_void_p(0)
+        _check(lib().gbcfd_accel_create(self.nx, self.ny, self.nz, self.batch, int(bool(zperiodic)),
+                                        ctypes.c_void_p(base + off), nbytes.value, ctypes.byref(h)))
+        self.handle = h
+        self.step_count = 0
+
+    @property
+    def cells(self):
+        return self.nx * self.ny * self.nz * self.batch
+
+    def set_params(self, params, stream=None):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == ACCEL_NPARAM
+        _check(lib().gbcfd_accel_set_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                            _stream(stream)))
+        self.step_count = 0
+
+    def get_params(self, stream=None) -> np.ndarray:
+        p = np.zeros(ACCEL_NPARAM, dtype=np.float32)
+        _check(lib().gbcfd_accel_get_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                            _stream(stream)))
+        return p
+
+    def forward(self, x, y=None, stream=None):
+        if y is None:
+            y = torch.empty((x.shape[0], 8), dtype=torch.float32, device=x.device)
+        _check(lib().gbcfd_accel_forward(self.handle, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def train_step(self, x, t, lr, stream=None) -> float:
+        self.step_count += 1
+        loss = ctypes.c_double(0.0)
+        _check(lib().gbcfd_accel_train_step(self.handle, _ptr(x), _ptr(t), float(lr), self.step_count,
+                                            ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def features(self, block, x=None, stream=None):
+        _check(lib().gbcfd_accel_features(self.handle, block.handle, _ptr(x) if x is not None else None,
+                                          _stream(stream)))
+        return x
+
+    def target(self, block, t, stream=None):
+        _check(lib().gbcfd_accel_target(self.handle, block.handle, _ptr(t), _stream(stream)))
+        return t
+
+    def try_update(self, block, stream=None):
+        """one accelerated update of the block; returns (accepted, rms R_rho before, after)"""
+        acc = ctypes.c_int(0)
+        norms = np.zeros(2)
+        _check(lib().gbcfd_accel_try(self.handle, block.handle, _stream(stream), ctypes.byref(acc),
+                                     norms.ctypes.data_as(_D)))
+        return bool(acc.value), float(norms[0]), float(norms[1])
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().gbcfd_accel_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,164 @@
+"""The learned convergence accelerator's kernels against the plain definitions in oracle/learn.py:
+the tensor-core convolutions (forward), one training step (loss and the sign of every weight's
+first Adam move), the block features and training targets, and the accept-or-restore update."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from oracle import learn as L  # noqa: E402
+from paper_1710_09995_gb300 import cases  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_09995_gb300 import gbcfd
+    gbcfd.lib()
+    return gbcfd
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def random_params(seed, scale=0.15):
+    r = rng(seed)
+    p = np.zeros(L.n_params())
+    o = 0
+    for ci, co in zip(L.CH[:-1], L.CH[1:]):
+        n = co * ci * 27
+        p[o:o + n] = r.standard_normal(n) * scale / np.sqrt(ci * 27 / 10)
+        o += n
+        p[o:o + co] = 0.05 * r.standard_normal(co)
+        o += co
+    return p.astype(np.float32).astype(np.float64)
+
+
+def to_gpu_features(x):
+    """x [B][10][Z][Y][X] -> bf16 [B Z Y X][16]"""
+    B, C, Z, Y, X = x.shape
+    t = np.zeros((B, Z, Y, X, 16), dtype=np.float32)
+    t[..., :C] = np.transpose(x, (0, 2, 3, 4, 1))
+    return torch.from_numpy(t.reshape(-1, 16)).to(torch.bfloat16).cuda()
+
+
+def from_gpu(y, B, Z, Y, X, C=5):
+    return np.transpose(y.float().cpu().numpy().reshape(B, Z, Y, X, -1)[..., :C], (0, 4, 1, 2, 3)).astype(np.float64)
+
+
+@pytest.mark.parametrize("zper", [True, False])
+def test_forward_matches_oracle(gb, zper):
+    B, Z, Y, X = 2, 6, 20, 40
+    p = random_params(1)
+    x = rng(2).standard_normal((B, 10, Z, Y, X))
+    xg = to_gpu_features(x)
+    a = gb.Accel(X, Y, Z, B, zperiodic=zper)
+    a.set_params(p)
+    y = from_gpu(a.forward(xg), B, Z, Y, X)
+    xb = from_gpu(xg, B, Z, Y, X, C=10)  # the bf16 features the GPU read
+    for b in range(B):
+        want, _ = L.forward(p, xb[b], zper=zper)
+        err = np.linalg.norm(y[b] - want) / np.linalg.norm(want)
+        assert err <= 2e-3, err
+
+
+def test_train_step_matches_oracle_gradient(gb):
+    """the loss before the step, and the first Adam move lr g / (|g| + eps) of every parameter
+    whose oracle gradient is not negligible has the oracle gradient's sign"""
+    B, Z, Y, X = 2, 4, 12, 36
+    p = random_params(3)
+    x = rng(4).standard_normal((B, 10, Z, Y, X))
+    t = rng(5).standard_normal((B, 5, Z, Y, X))
+    xg = to_gpu_features(x)
+    tg = np.zeros((B, Z, Y, X, 8), dtype=np.float32)
+    tg[..., :5] = np.transpose(t, (0, 2, 3, 4, 1))
+    tg = torch.from_numpy(tg.reshape(-1, 8)).cuda()
+    a = gb.Accel(X, Y, Z, B)
+    a.set_params(p)
+    lr = 1e-3
+    loss = a.train_step(xg, tg, lr)
+    p1 = a.get_params().astype(np.float64)
+    xb = from_gpu(xg, B, Z, Y, X, C=10)
+    want_loss, g = 0.0, np.zeros_like(p)
+    for b in range(B):
+        lb, gb_ = L.loss_and_grad(p, xb[b], t[b])
+        want_loss += lb / B
+        g += gb_ / B
+    assert abs(loss - want_loss) <= 1e-3 * want_loss
+    move = (p - p1) / lr
+    o = 0
+    for ci, co in zip(L.CH[:-1], L.CH[1:]):
+        for n in (co * ci * 27, co):
+            gs, ms = g[o:o + n], move[o:o + n]
+            big = np.abs(gs) > 0.05 * np.abs(gs).max()
+            assert np.all(np.sign(ms[big]) == np.sign(gs[big]))
+            assert np.allclose(np.abs(ms[big]), 1.0, rtol=1e-3)
+            o += n
+
+
+def test_training_reduces_the_loss(gb):
+    B, Z, Y, X = 2, 4, 12, 36
+    a = gb.Accel(X, Y, Z, B)
+    a.set_params(random_params(6))
+    x = to_gpu_features(rng(7).standard_normal((B, 10, Z, Y, X)))
+    t = torch.zeros((B * Z * Y * X, 8), dtype=torch.float32, device="cuda")
+    t[:, :5] = 0.5 * x[:, 5:10].float()   # a learnable target: half the residual channels
+    losses = [a.train_step(x, t, 3e-3) for _ in range(60)]
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+
+
+def channel(seed=3):
+    c = cases.channel_case(40, 24, 6, height=0.1, mach=0.6)
+    c.state = cases.smooth_random(40, 24, 6, seed=seed, amp=0.02, mach=0.6).state
+    return c
+
+
+def test_features_and_target_match_oracle(gb):
+    c = channel()
+    bcs = oracle.bc(c.extra["bc"], c.extra["inf"])
+    M = oracle.metrics_bc(c.nodes, bcs)
+    p = oracle.params(c.gamma, 0.0, 0.72, c.cfl, c.eps, False, 0)
+    Qp = oracle.fill_halo_bc(oracle.pad(c.state), M, bcs)
+    R = oracle.residual(p, Qp, M)
+    dtl = oracle.dt_local(p, Qp, M)
+    want, s = L.features(c.state, R, dtl, c.extra["inf"])
+    blk = gb.block_for_case(c, precision=gb.FP64)
+    a = gb.Accel(c.nx, c.ny, c.nz)
+    x = torch.empty((c.cells, 16), dtype=torch.bfloat16, device="cuda")
+    a.features(blk, x)
+    got = from_gpu(x, 1, c.nz, c.ny, c.nx, C=10)[0]
+    assert np.all(np.abs(got - L.bf16(want)) <= 2 ** -7 * np.abs(want) + 1e-30)
+    Q0 = blk.get_state().cpu().numpy()
+    gb.step([blk], L.K_STEPS)
+    t = torch.empty((c.cells, 8), dtype=torch.float32, device="cuda")
+    a.target(blk, t)
+    tg = from_gpu(t, 1, c.nz, c.ny, c.nx)[0]
+    tw = L.target(Q0, blk.get_state().cpu().numpy(), s, c.extra["inf"])
+    assert np.linalg.norm(tg - tw) <= 1e-6 * np.linalg.norm(tw)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_try_keeps_or_restores(gb, precision):
+    """zero weights predict no change: the residual does not drop and the state is restored bit
+    for bit; random weights are kept only with a lower residual, else restored bit for bit"""
+    c = channel(seed=4)
+    blk = gb.block_for_case(c, precision=precision)
+    gb.step([blk], 3)
+    a = gb.Accel(c.nx, c.ny, c.nz)
+    a.set_params(np.zeros(gb.ACCEL_NPARAM, dtype=np.float32))
+    before = blk.get_state().clone()
+    kept, r0, r1 = a.try_update(blk)
+    assert not kept and r1 == r0
+    assert torch.equal(blk.get_state(), before)
+    a.set_params(random_params(8, scale=0.05))
+    kept, r0, r1 = a.try_update(blk)
+    if kept:
+        assert r1 < r0
+    else:
+        assert torch.equal(blk.get_state(), before)
+    gb.step([blk], 2)  # the block steps on from either state
+    assert np.all(np.isfinite(blk.residual_norm()))
