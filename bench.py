@@ -552,7 +552,8 @@ def run_lattice(args, world, rank, local, device, torch, cases, gbcfd):
 
 def run_channel(args, world, rank, local, device, torch, cases, gbcfd):
     """Wall time to a residual drop on the steady bump channel: the plain FP64 iteration, the
-    mixed path finished in FP64 (hybrid), and the hybrid with the learned accelerator."""
+    mixed path finished on the FP64 path once it stalls (hybrid), and the hybrid with the
+    learned accelerator's predictions tried every 200 steps."""
     from paper_1710_09995_gb300 import learn
     case = cases.channel_case(*learn.FULL_GRID, height=0.1, mach=0.6)
     params, info = (learn.load() if os.path.exists(learn.WEIGHTS) else (None, None))

@@ -66,6 +66,7 @@ struct gbcfd_block_s {
   int curvi;            // metrics from nodes (curvilinear) rather than a uniform spacing
   int metrics_dirty;    // metric halos not exchanged since the metrics were set
   void* dtl;            // local time steps (local_dt), one padded field of the path's flux type
+  unsigned desc_version;  // bumped whenever the device descriptor changes
   int bc_kind[6];       // GBCFD_BC_* per face (faces without a neighbour)
   double bc_inf[5];     // free stream of GBCFD_BC_FARFIELD faces
 };
@@ -237,6 +238,7 @@ static void fill_desc(gbcfd_block_s* b) {
   for (int i = 0; i < 2; ++i) { D.sh[i] = b->sh[i]; D.d[i] = b->d[i]; }
   D.ctrl = b->ctrl;
   D.dtl = b->dtl;
+  b->desc_version++;
   D.ntx = (b->nx + TX - 1) / TX;
   D.nty = (b->ny + TY - 1) / TY;
   D.units = (long long)D.ntx * D.nty * b->nz;
@@ -282,6 +284,7 @@ extern "C" int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* pa
   b->ctrl = reinterpret_cast<DevCtrl*>(base + c.off[6]);
   b->partial = reinterpret_cast<double*>(base + c.off[7]);
   b->dtl = params->local_dt ? static_cast<void*>(base + c.off[11]) : nullptr;
+  b->desc_version = 0;
   for (int f = 0; f < 6; ++f) b->bc_kind[f] = GBCFD_BC_NONE;
   for (int v = 0; v < 5; ++v) b->bc_inf[v] = 0.0;
   if (params->precision == GBCFD_FP64) {
@@ -697,6 +700,7 @@ struct gbcfd_group_s {
   cudaGraphExec_t exec[2];  // one step, for each parity of the mixed path's ping-pong
   cudaEvent_t marks[7];     // caller's timing events (or none)
   bool timed;
+  std::vector<unsigned> versions;  // members' descriptor versions the table was written with
 };
 
 static int max_group_ctas(int nsm) { return 8 * nsm; }
@@ -716,6 +720,14 @@ extern "C" int gbcfd_group_required_bytes(int n, size_t* bytes) {
 // at least one) and write the descriptor table
 static int group_split(gbcfd_group g, int ctas_per_sm, cudaStream_t s) {
   const int nsm = g->blocks[0]->nsm;
+  g->versions.resize(g->blocks.size());
+  for (size_t i = 0; i < g->blocks.size(); ++i) {  // the members' current descriptors
+    const int cta0 = g->table_host[i].cta0, ctas = g->table_host[i].ctas;
+    g->table_host[i] = g->blocks[i]->desc_host;
+    g->table_host[i].cta0 = cta0;
+    g->table_host[i].ctas = ctas;
+    g->versions[i] = g->blocks[i]->desc_version;
+  }
   const long long target = (long long)nsm * ctas_per_sm;
   long long W = 0;
   for (auto& d : g->table_host) W += d.units;
@@ -845,12 +857,32 @@ static int group_check(gbcfd_group g) {
   return GBCFD_OK;
 }
 
+// rewrite the table when a member's descriptor changed (the graphs read it from device memory)
+static int group_refresh(gbcfd_group g, cudaStream_t s) {
+  bool changed = false;
+  for (size_t i = 0; i < g->blocks.size(); ++i) changed = changed || g->versions[i] != g->blocks[i]->desc_version;
+  if (!changed) return GBCFD_OK;
+  for (size_t i = 0; i < g->blocks.size(); ++i) {
+    const int cta0 = g->table_host[i].cta0, ctas = g->table_host[i].ctas;
+    g->table_host[i] = g->blocks[i]->desc_host;
+    g->table_host[i].cta0 = cta0;
+    g->table_host[i].ctas = ctas;
+    g->versions[i] = g->blocks[i]->desc_version;
+  }
+  CK(cudaMemcpyAsync(g->table, g->table_host.data(), sizeof(BlockDesc) * g->table_host.size(),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // the host table is reused
+  return GBCFD_OK;
+}
+
 extern "C" int gbcfd_group_step(gbcfd_group g, int nsteps, void* stream) {
   if (!g) return fail(GBCFD_ERR_ARG, "group is NULL");
   if (nsteps < 0) return fail(GBCFD_ERR_ARG, "nsteps must be >= 0");
   int rc = group_check(g);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = group_refresh(g, s);
+  if (rc) return rc;
   rc = prepare_metrics(g->blocks.data(), (int)g->blocks.size(), s);
   if (rc) return rc;
   const bool mixed = g->blocks[0]->p.precision == GBCFD_MIXED;
@@ -992,7 +1024,7 @@ static size_t accel_carve(int nx, int ny, int nz, int batch, int nsm, size_t* of
   take(3, sizeof(float) * learn::NPARAM);                              // grad
   take(4, sizeof(bf16) * learn::NTAP * learn::P1 * learn::P0);         // w1
   take(5, sizeof(bf16) * learn::NTAP * learn::P2 * learn::P1);         // w2
-  take(6, sizeof(bf16) * learn::NTAP * learn::P3 * learn::P2);         // w3
+  take(6, sizeof(bf16) * learn::NTAP * 16 * learn::P2);               // w3 (16 wide)
   take(7, sizeof(bf16) * learn::NTAP * learn::P2 * 16);                // w3b
   take(8, sizeof(bf16) * learn::NTAP * learn::P1 * learn::P2);         // w2b
   take(9, sizeof(float) * (learn::P1 + learn::P2 + learn::P3));       // biases
@@ -1010,6 +1042,7 @@ static size_t accel_carve(int nx, int ny, int nz, int batch, int nsm, size_t* of
   take(21, sizeof(double) * 5 * vol);                                  // saved state
   take(22, sizeof(double) * NPART * kAccelParts);                      // partials
   take(23, sizeof(double) * 8);                                        // stats
+  take(24, sizeof(int) * 4);                                           // timeout flag
   return o;
 }
 
@@ -1019,7 +1052,7 @@ extern "C" int gbcfd_accel_required_bytes(int nx, int ny, int nz, int batch, siz
   int dev = 0, nsm = 0;
   int rc = device_sms(&dev, &nsm);
   if (rc) return rc;
-  size_t off[24];
+  size_t off[25];
   *bytes = accel_carve(nx, ny, nz, batch, nsm, off);
   return GBCFD_OK;
 }
@@ -1037,7 +1070,7 @@ extern "C" int gbcfd_accel_create(int nx, int ny, int nz, int batch, int zperiod
   int dev = 0, nsm = 0;
   rc = device_sms(&dev, &nsm);
   if (rc) return rc;
-  size_t off[24];
+  size_t off[25];
   accel_carve(nx, ny, nz, batch, nsm, off);
   char* base = static_cast<char*>(dev_mem);
   gbcfd_accel a = new gbcfd_accel_s();
@@ -1071,9 +1104,11 @@ extern "C" int gbcfd_accel_create(int nx, int ny, int nz, int batch, int zperiod
   a->qsave = reinterpret_cast<double*>(base + off[21]);
   a->partial = reinterpret_cast<double*>(base + off[22]);
   a->stats = reinterpret_cast<double*>(base + off[23]);
+  n.flag = reinterpret_cast<int*>(base + off[24]);
   a->pgrid = (int)std::min<size_t>(kAccelParts, (size_t)4 * nsm);
   a->step_count = 0;
   cudaError_t e = cudaMemset(base, 0, off[11]);  // parameters, moments, packed weights: zero
+  if (e == cudaSuccess) e = cudaMemset(n.flag, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) { delete a; return cuda_fail(e, "initialising the accelerator"); }
   *out = a;
@@ -1124,9 +1159,11 @@ static learn::ConvArgs conv_args(gbcfd_accel a, const void* in, const bf16* w, c
 // the three forward convolutions; z1, z2 kept when training
 static int accel_forward(gbcfd_accel a, const void* x, float* y, bool keep, cudaStream_t s) {
   const learn::Net& n = a->net;
-  CK(learn::launch_conv(1, learn::FWD_SILU, conv_args(a, x, n.w1, n.b1, a->a1, keep ? a->z1 : nullptr, nullptr), s));
-  CK(learn::launch_conv(2, learn::FWD_SILU, conv_args(a, a->a1, n.w2, n.b2, a->a2, keep ? a->z2 : nullptr, nullptr), s));
-  CK(learn::launch_conv(3, learn::FWD_LINEAR, conv_args(a, a->a2, n.w3, n.b3, y, nullptr, nullptr), s));
+  CK(learn::launch_conv(1, learn::FWD_SILU, conv_args(a, x, n.w1, n.b1, a->a1, keep ? a->z1 : nullptr, nullptr),
+                        n.flag, s));
+  CK(learn::launch_conv(2, learn::FWD_SILU, conv_args(a, a->a1, n.w2, n.b2, a->a2, keep ? a->z2 : nullptr, nullptr),
+                        n.flag, s));
+  CK(learn::launch_conv(3, learn::FWD_LINEAR, conv_args(a, a->a2, n.w3, n.b3, y, nullptr, nullptr), n.flag, s));
   return GBCFD_OK;
 }
 
@@ -1139,12 +1176,27 @@ static int check_dev(const void* p, const char* what) {
   return GBCFD_OK;
 }
 
+// report (and clear) a timeout flagged by a convolution's bounded wait; synchronises the stream
+static int accel_flag(gbcfd_accel a, cudaStream_t s) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, a->net.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h) {
+    CK(cudaMemsetAsync(a->net.flag, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    return fail(GBCFD_ERR_TIMEOUT, "a tensor-core convolution's bounded wait timed out");
+  }
+  return GBCFD_OK;
+}
+
 extern "C" int gbcfd_accel_forward(gbcfd_accel a, const void* x, float* y, void* stream) {
   if (!a || !x || !y) return fail(GBCFD_ERR_ARG, "NULL argument");
   int rc = check_dev(x, "x");
   if (!rc) rc = check_dev(y, "y");
   if (rc) return rc;
-  return accel_forward(a, x, y, false, static_cast<cudaStream_t>(stream));
+  rc = accel_forward(a, x, y, false, static_cast<cudaStream_t>(stream));
+  if (rc) return rc;
+  return accel_flag(a, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int gbcfd_accel_train_step(gbcfd_accel a, const void* x, const float* t, float lr, int step, double* loss,
@@ -1161,9 +1213,9 @@ extern "C" int gbcfd_accel_train_step(gbcfd_accel a, const void* x, const float*
   CK(learn::launch_loss(a->y, t, a->dy, a->partial, a->cells, a->pgrid, s));
   CK(learn::launch_sum(a->partial, a->pgrid, 1, a->stats + 4, s));
   CK(learn::launch_wgrad(3, a->a2, a->dy, n, a->nx, a->ny, a->nz, a->batch, a->zper, s));
-  CK(learn::launch_conv(3, learn::BWD_DSILU, conv_args(a, a->dy, n.w3b, nullptr, a->dz2, nullptr, a->z2), s));
+  CK(learn::launch_conv(3, learn::BWD_DSILU, conv_args(a, a->dy, n.w3b, nullptr, a->dz2, nullptr, a->z2), n.flag, s));
   CK(learn::launch_wgrad(2, a->a1, a->dz2, n, a->nx, a->ny, a->nz, a->batch, a->zper, s));
-  CK(learn::launch_conv(2, learn::BWD_DSILU, conv_args(a, a->dz2, n.w2b, nullptr, a->dz1, nullptr, a->z1), s));
+  CK(learn::launch_conv(2, learn::BWD_DSILU, conv_args(a, a->dz2, n.w2b, nullptr, a->dz1, nullptr, a->z1), n.flag, s));
   CK(learn::launch_wgrad(1, static_cast<const bf16*>(x), a->dz1, n, a->nx, a->ny, a->nz, a->batch, a->zper, s));
   CK(learn::launch_grad_reduce(n, s));
   CK(learn::launch_adam(n, lr, step, s));
@@ -1172,7 +1224,7 @@ extern "C" int gbcfd_accel_train_step(gbcfd_accel a, const void* x, const float*
   CK(cudaMemcpyAsync(&h, a->stats + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (loss) *loss = h / (5.0 * (double)a->cells);
-  return GBCFD_OK;
+  return accel_flag(a, s);
 }
 
 // the block as the feature kernels see it
@@ -1264,6 +1316,12 @@ extern "C" int gbcfd_accel_try(gbcfd_accel a, gbcfd_block b, void* stream, int* 
   double h[4];
   CK(cudaMemcpyAsync(h, a->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  rc = accel_flag(a, s);
+  if (rc) {  // restore the state before reporting
+    CK(learn::launch_apply(v, a->y, a->qsave, a->stats, 1, s));
+    int rc2 = init_rate(b, s);
+    return rc2 ? rc2 : rc;
+  }
   const double n = (double)b->nx * b->ny * b->nz;
   const double r0 = std::sqrt(h[1] / n), r1 = std::sqrt(h[3] / n);
   const bool keep = std::isfinite(r1) && r1 < r0;

@@ -1,6 +1,6 @@
-// learn.cu -- kernels of the learned convergence accelerator (see learn.cuh): the implicit-GEMM
-// 3D convolution on the tensor cores (mma.sync m16n8k16, bf16 x bf16 -> f32), its weight
-// gradient, Adam, weight packing, the loss, and the kernels that connect the network to a block.
+// learn.cu -- kernels of the learned convergence accelerator (see learn.cuh): the weight gradient
+// of the convolutions, Adam, weight packing, the loss, and the kernels that connect the network
+// to a block.  The convolutions themselves (tcgen05 implicit GEMM) are in learn_tc.cu.
 #include "internal.cuh"
 #include "learn.cuh"
 
@@ -8,14 +8,6 @@ namespace gbcfd {
 namespace learn {
 
 using bf16 = __nv_bfloat16;
-
-__device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, const unsigned* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
 __device__ __forceinline__ float dsilu(float z) {
@@ -47,88 +39,6 @@ __device__ __forceinline__ long long box_source(int x0, int y0, int z, int b, in
   return (((long long)b * Z + gz) * Y + gy) * X + gx;
 }
 
-// ---- implicit-GEMM convolution ---------------------------------------------------------------
-// CTA: 8 warps, 128 output cells (32 along x, 4 along y, one z).  GEMM view: M = cells, N = COP
-// output channels, K = 27 taps x CIP input channels.  The input box (34 x 6 x 3 cells) and all
-// weights are staged in shared memory with a padded cell stride (conflict-free fragment loads);
-// warp w owns the 16 cells of row w / 2, half w % 2, and runs COP / 8 m16n8k16 MMAs per tap and
-// 16-channel slice.
-template <int CIP, int COP, int MODE>
-__global__ void __launch_bounds__(NTHREADS) conv_kernel(const ConvArgs A) {
-  constexpr int CS = CIP + 8;
-  extern __shared__ __align__(16) unsigned char smem[];
-  bf16* in_s = reinterpret_cast<bf16*>(smem);
-  bf16* w_s = in_s + BOX * CS;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int x0, y0, z, b;
-  tile_coords(blockIdx.x, A.X, A.Y, A.Z, x0, y0, z, b);
-
-  for (int i = tid; i < NTAP * COP * (CIP / 8); i += NTHREADS) {
-    const int row = i / (CIP / 8), ch = i % (CIP / 8);
-    *reinterpret_cast<uint4*>(w_s + row * CS + ch * 8) = *reinterpret_cast<const uint4*>(A.w + row * CIP + ch * 8);
-  }
-  for (int i = tid; i < BOX * (CIP / 8); i += NTHREADS) {
-    const int cellb = i / (CIP / 8), ch = i % (CIP / 8);
-    const long long src = box_source(x0, y0, z, b, cellb, A.X, A.Y, A.Z, A.zper);
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (src >= 0) v = *reinterpret_cast<const uint4*>(A.in + src * CIP + ch * 8);
-    *reinterpret_cast<uint4*>(in_s + cellb * CS + ch * 8) = v;
-  }
-  __syncthreads();
-
-  const int yw = warp >> 1, xh = (warp & 1) * 16;
-  const int g = lane >> 2, t4 = lane & 3;
-  float acc[COP / 8][4];
-#pragma unroll
-  for (int n = 0; n < COP / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  for (int t = 0; t < NTAP; ++t) {
-    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-    const int base = (dz * BOX_Y + yw + dy) * BOX_X + xh + dx;  // box cell of the warp's row 0
-    const bf16* ar0 = in_s + (base + g) * CS + 2 * t4;
-    const bf16* ar1 = ar0 + 8 * CS;
-#pragma unroll
-    for (int kc = 0; kc < CIP / 16; ++kc) {
-      unsigned a[4];
-      a[0] = *reinterpret_cast<const unsigned*>(ar0 + kc * 16);
-      a[1] = *reinterpret_cast<const unsigned*>(ar1 + kc * 16);
-      a[2] = *reinterpret_cast<const unsigned*>(ar0 + kc * 16 + 8);
-      a[3] = *reinterpret_cast<const unsigned*>(ar1 + kc * 16 + 8);
-#pragma unroll
-      for (int n = 0; n < COP / 8; ++n) {
-        const bf16* br = w_s + (t * COP + n * 8 + g) * CS + kc * 16 + 2 * t4;
-        const unsigned bb[2] = {*reinterpret_cast<const unsigned*>(br), *reinterpret_cast<const unsigned*>(br + 8)};
-        mma_bf16(acc[n], a, bb);
-      }
-    }
-  }
-
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int gx = x0 + xh + g + 8 * h, gy = y0 + yw;
-    if (gx >= A.X || gy >= A.Y) continue;
-    const long long cell = (((long long)b * A.Z + z) * A.Y + gy) * A.X + gx;
-#pragma unroll
-    for (int n = 0; n < COP / 8; ++n) {
-      const int co = n * 8 + 2 * t4;
-      float v0 = acc[n][2 * h], v1 = acc[n][2 * h + 1];
-      if constexpr (MODE == FWD_SILU) {
-        v0 += A.bias[co];
-        v1 += A.bias[co + 1];
-        if (A.zsave) *reinterpret_cast<float2*>(A.zsave + cell * COP + co) = make_float2(v0, v1);
-        *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(A.out) + cell * COP + co) =
-            __floats2bfloat162_rn(silu(v0), silu(v1));
-      } else if constexpr (MODE == FWD_LINEAR) {
-        *reinterpret_cast<float2*>(static_cast<float*>(A.out) + cell * COP + co) =
-            make_float2(v0 + A.bias[co], v1 + A.bias[co + 1]);
-      } else {
-        const float2 zp = *reinterpret_cast<const float2*>(A.zprev + cell * COP + co);
-        *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(A.out) + cell * COP + co) =
-            __floats2bfloat162_rn(v0 * dsilu(zp.x), v1 * dsilu(zp.y));
-      }
-    }
-  }
-}
-
 // a kernel's dynamic shared-memory limit, set once per device
 template <typename F>
 static cudaError_t smem_attr(F* kernel, size_t bytes, unsigned long long& done) {
@@ -139,27 +49,6 @@ static cudaError_t smem_attr(F* kernel, size_t bytes, unsigned long long& done) 
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
   return e;
-}
-
-template <int CIP, int COP, int MODE>
-static cudaError_t conv_go(const ConvArgs& a, cudaStream_t s) {
-  const size_t bytes = (size_t)(BOX + NTAP * COP) * (CIP + 8) * sizeof(bf16);
-  static unsigned long long done = 0;
-  cudaError_t e = smem_attr(conv_kernel<CIP, COP, MODE>, bytes, done);
-  if (e != cudaSuccess) return e;
-  const long long tiles = (long long)((a.X + TILE_X - 1) / TILE_X) * ((a.Y + TILE_Y - 1) / TILE_Y) * a.Z * a.B;
-  conv_kernel<CIP, COP, MODE><<<(unsigned)tiles, NTHREADS, bytes, s>>>(a);
-  return cudaGetLastError();
-}
-
-// layer 1..3 forward; layers 3 and 2 backward-data (mode BWD_DSILU)
-cudaError_t launch_conv(int layer, int mode, const ConvArgs& a, cudaStream_t s) {
-  if (mode == FWD_SILU && layer == 1) return conv_go<P0, P1, FWD_SILU>(a, s);
-  if (mode == FWD_SILU && layer == 2) return conv_go<P1, P2, FWD_SILU>(a, s);
-  if (mode == FWD_LINEAR && layer == 3) return conv_go<P2, P3, FWD_LINEAR>(a, s);
-  if (mode == BWD_DSILU && layer == 3) return conv_go<16, P2, BWD_DSILU>(a, s);   // dY (16 ch) -> dZ2
-  if (mode == BWD_DSILU && layer == 2) return conv_go<P2, P1, BWD_DSILU>(a, s);   // dZ2 -> dZ1
-  return cudaErrorInvalidValue;
 }
 
 // ---- weight gradient ---------------------------------------------------------------------------
@@ -294,8 +183,8 @@ __global__ void pack_kernel(Net n) {
     const int tb = i / (P1 * P2), cb = (i / P2) % P1, ob = i % P2;  // w2b[tb][cb][ob] = W2[ob][cb][26 - tb]
     n.w2b[i] = __float2bfloat16(w[OFF_W2 + (ob * C1 + cb) * NTAP + (NTAP - 1 - tb)]);
   }
-  if (i < NTAP * P3 * P2) {  // w3 [t][o<8][c<32]
-    const int t = i / (P3 * P2), o = (i / P2) % P3, c = i % P2;
+  if (i < NTAP * 16 * P2) {  // w3 [t][o<16][c<32] (the MMA is 16 wide; 5 used)
+    const int t = i / (16 * P2), o = (i / P2) % 16, c = i % P2;
     n.w3[i] = __float2bfloat16(o < C3 ? w[OFF_W3 + (o * C2 + c) * NTAP + t] : 0.f);
   }
   if (i < NTAP * P2 * 16) {  // w3b [t'][c<32][o<16] = W3[o][c][26 - t']

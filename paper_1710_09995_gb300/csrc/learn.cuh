@@ -23,7 +23,7 @@ constexpr int NW1 = C1 * C0 * NTAP, NW2 = C2 * C1 * NTAP, NW3 = C3 * C2 * NTAP;
 constexpr int OFF_W1 = 0, OFF_B1 = NW1, OFF_W2 = NW1 + C1, OFF_B2 = OFF_W2 + NW2, OFF_W3 = OFF_B2 + C2,
               OFF_B3 = OFF_W3 + NW3, NPARAM = OFF_B3 + C3;  // 40677
 constexpr float STATE_GAIN = 10.0f;
-constexpr int TILE_X = 32, TILE_Y = 4;               // 128 output cells per CTA
+constexpr int TILE_X = 32, TILE_Y = 4;               // 128 cells per weight-gradient tile
 constexpr int BOX_X = TILE_X + 2, BOX_Y = TILE_Y + 2, BOX_Z = 3;
 constexpr int BOX = BOX_X * BOX_Y * BOX_Z;           // input cells a tile reads
 constexpr int NTHREADS = 256;
@@ -33,7 +33,7 @@ enum ConvMode { FWD_SILU = 0, FWD_LINEAR = 1, BWD_DSILU = 2 };
 // one convolution launch over a volume of B batches of X x Y x Z cells (channels-last tensors)
 struct ConvArgs {
   const __nv_bfloat16* in;   // [cell][CIP]
-  const __nv_bfloat16* w;    // [27][COP][CIP]
+  const __nv_bfloat16* w;    // [27][N][CIP] (N = the MMA width: COP, or 16 for the 8-channel output)
   const float* bias;         // [COP] (forward modes)
   void* out;                 // bf16 [cell][COP] (FWD_SILU, BWD_DSILU) or f32 [cell][COP] (FWD_LINEAR)
   float* zsave;              // FWD_SILU: pre-activation f32 [cell][COP] when not null (training)
@@ -44,14 +44,15 @@ struct ConvArgs {
 // the accelerator's device arrays (carved from one caller buffer)
 struct Net {
   float *w, *m, *v, *grad;            // master parameters, Adam moments, gradient (NPARAM each)
-  __nv_bfloat16 *w1, *w2, *w3;        // forward GEMM layouts [27][COP][CIP]
+  __nv_bfloat16 *w1, *w2, *w3;        // forward GEMM layouts [27][N][CIP] (w3: N = 16, 5 used)
   __nv_bfloat16 *w3b, *w2b;           // backward-data layouts (taps mirrored, in/out swapped)
   float *b1, *b2, *b3;                // padded biases
   float* wpart;                       // weight-gradient partials [grid][NPARAM]
   int wgrid;
+  int* flag;                          // FLAG_TIMEOUT when a bounded wait of a convolution gave up
 };
 
-cudaError_t launch_conv(int layer, int mode, const ConvArgs& a, cudaStream_t s);
+cudaError_t launch_conv(int layer, int mode, const ConvArgs& a, int* flag, cudaStream_t s);
 cudaError_t launch_wgrad(int layer, const __nv_bfloat16* a, const __nv_bfloat16* g, const Net& n, int X, int Y,
                          int Z, int B, int zper, cudaStream_t s);
 cudaError_t launch_grad_reduce(const Net& n, cudaStream_t s);

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(TC_THREADS) conv_tc_kernel(const ConvArgs A, c
   bf16* wsm = box + TC_NBOX * CIP;                                // 27 x CIP x N
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(wsm + NTAP * CIP * N);
   unsigned* tslot = reinterpret_cast<unsigned*>(bar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
 
   const int tx = (A.X + TC_M - 1) / TC_M;
   long long tile = blockIdx.x;
@@ -207,6 +207,16 @@ static cudaError_t conv_tc_go(const ConvArgs& a, const bf16* wtc, int* flag, cud
   const long long tiles = (long long)((a.X + TC_M - 1) / TC_M) * a.Y * a.Z * a.B;
   conv_tc_kernel<CIP, N, COP, MODE><<<(unsigned)tiles, TC_THREADS, bytes, s>>>(a, wtc, flag);
   return cudaGetLastError();
+}
+
+// layers 1..3 forward; layers 3 and 2 backward-data (taps mirrored, channels swapped, x SiLU')
+cudaError_t launch_conv(int layer, int mode, const ConvArgs& a, int* flag, cudaStream_t s) {
+  if (mode == FWD_SILU && layer == 1) return conv_tc_go<P0, P1, P1, FWD_SILU>(a, a.w, flag, s);
+  if (mode == FWD_SILU && layer == 2) return conv_tc_go<P1, P2, P2, FWD_SILU>(a, a.w, flag, s);
+  if (mode == FWD_LINEAR && layer == 3) return conv_tc_go<P2, 16, P3, FWD_LINEAR>(a, a.w, flag, s);
+  if (mode == BWD_DSILU && layer == 3) return conv_tc_go<16, P2, P2, BWD_DSILU>(a, a.w, flag, s);  // dY -> dZ2
+  if (mode == BWD_DSILU && layer == 2) return conv_tc_go<P2, P1, P1, BWD_DSILU>(a, a.w, flag, s);  // dZ2 -> dZ1
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace learn
