@@ -37,6 +37,8 @@ WORKLOADS = {
     "vortex256": "isentropic vortex 256^3, Navier-Stokes Re 1e4 Pr 0.72, MUSCL/minmod + Roe, SSP-RK3 CFL 0.5",
     "warped512": ("warped curvilinear block 512x512x384, Navier-Stokes Re 1e5, 5% broadband velocity on Mach 0.3, "
                   "MUSCL/minmod + Roe, SSP-RK3 CFL 0.5"),
+    "accel": ("learned accelerator inference: 3-layer conv3d 10->32->32->5, 3^3 taps, bf16 x bf16 -> f32 on "
+              "tcgen05, over the 192x96x64 bump-channel grid (periodic in z)"),
     "channel": ("bump channel 192x96x64 (curvilinear, 10% bump, stretched 1.1 to the wall), Euler, Mach 0.6, "
                 "far field in/out, slip walls, local pseudo-time steps to a 1e-6 density-residual drop"),
     "lattice96": ("96 uneven Cartesian blocks (4x4x6 lattice, sides 16..160, seed 4: 506x492x550 = 1.37e8 cells), "
@@ -442,6 +444,8 @@ def run_gbcfd(args):
         return run_lattice(args, world, rank, local, device, torch, cases, gbcfd)
     if args.workload == "channel":
         return run_channel(args, world, rank, local, device, torch, cases, gbcfd)
+    if args.workload == "accel":
+        return run_accel(args, world, rank, local, device, torch, gbcfd)
     if args.workload == "warped512":
         case = cases.broadband_warped(512, 512, 384, seed=0, device=device)
         prec = args.precision or "mixed"
@@ -548,6 +552,95 @@ def run_lattice(args, world, rank, local, device, torch, cases, gbcfd):
                   "roofline": fp64_alu_roofline(rp, lat.cells, args.steps, hbm, "lattice96") if p == "fp64" else hbm,
                   "gpu_launches": rp["launches"]}
     print(json.dumps(out))
+
+
+def bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (cuBLAS bf16 burst)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+ACCEL_FLOPS_PER_CELL = 2 * 27 * (10 * 32 + 32 * 32 + 32 * 5)  # useful multiply-adds x 2 per inference
+
+
+def run_accel(args, world, rank, local, device, torch, gbcfd):
+    """The accelerator's forward pass (three tensor-core convolutions) on the full channel grid:
+    cells per second and the tensor roofline (useful flops / time against the bf16 peak)."""
+    from paper_1710_09995_gb300 import learn
+    nx, ny, nz = learn.FULL_GRID
+    cells = nx * ny * nz
+    acc = gbcfd.Accel(nx, ny, nz, 1, device=device)
+    params = learn.load()[0] if os.path.exists(learn.WEIGHTS) else learn.init_params(0)
+    acc.set_params(params)
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn((cells, 16), generator=gen).to(device=device, dtype=torch.bfloat16)
+    y = torch.empty((cells, 8), dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        acc.forward(x, y, stream)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        acc.forward(x, y, stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(start.elapsed_time(stop), world, device)
+    clk = clocks.stop()
+    host_x = x.cpu().pin_memory()
+    host_y = torch.empty((cells, 8), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(min(args.e2e_steps, args.steps)):
+        x.copy_(host_x, non_blocking=True)
+        acc.forward(x, y, stream)
+        host_y.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if rank != 0:
+        return
+    peak, peak_kind = bf16_peak()
+    per = ms / args.steps
+    achieved = ACCEL_FLOPS_PER_CELL * cells / (per / 1e3) / 1e12
+    out = {
+        "metric": "cell inferences/s", "value": world * cells * args.steps / (ms / 1e3), "unit": "cells/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 x bf16 -> f32",
+        "data": "synthetic (random features; trained weights)",
+        "config": {"workload": WORKLOADS["accel"], "cells": cells, "l2": "activations 1.2e6 x 64 B per layer"},
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": None,
+                     "kernel": "conv_tc_kernel (3 launches)", "flops_per_cell": ACCEL_FLOPS_PER_CELL},
+        "e2e": {"value": world * cells * min(args.e2e_steps, args.steps) / e2e_s, "unit": "cells/s",
+                "h2d_bytes_per_step": cells * 16 * 2, "d2h_bytes_per_step": cells * 8 * 4},
+        "gpu_launches": 3 * args.steps, "clocks": clk,
+        "cpu_baseline": None if (world > 1 or args.no_cpu_baseline) else cpu_baseline_accel(params),
+    }
+    print(json.dumps(out))
+
+
+def cpu_baseline_accel(params):
+    """the numpy network of the oracle (FP64, bf16-rounded storage) on a 96 x 48 x 4 sample of
+    the grid, best of 2"""
+    import numpy as np
+    from oracle import learn as L
+    r = np.random.Generator(np.random.PCG64(0))
+    x = r.standard_normal((10, 4, 48, 96))
+    p = np.asarray(params, dtype=np.float64)
+    best = math.inf
+    for _ in range(2):
+        t0 = time.perf_counter()
+        L.forward(p, x)
+        best = min(best, time.perf_counter() - t0)
+    return {"value": x[0].size / best, "unit": "cells/s", "cores": 1, "kind": "oracle",
+            "sample": "numpy forward (oracle/learn.py, einsum per tap, one thread) of a 96x48x4 volume, best of 2"}
 
 
 def run_channel(args, world, rank, local, device, torch, cases, gbcfd):

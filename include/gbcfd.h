@@ -257,9 +257,9 @@ int gbcfd_accel_features(gbcfd_accel accel, gbcfd_block block, void* x, void* st
 int gbcfd_accel_target(gbcfd_accel accel, gbcfd_block block, float* t, void* stream);
 
 /* One accelerated update: residual and features at Q, prediction Q' = Q + 20 s ref y, residual at
- * Q'; Q' is kept when RMS(R_rho(Q')) < RMS(R_rho(Q)), else Q is restored.  *accepted (host) tells
- * which; norms[0], norms[1] (host, may be NULL) get the two RMS values.  The time steps are then
- * re-evaluated from the block's state.  Synchronises the stream. */
+ * Q'; Q' is kept when RMS(R_rho(Q')) < RMS(R_rho(Q)) (the time steps are then re-evaluated from
+ * it), else Q is restored and the block is left bit for bit as it was.  *accepted (host) tells
+ * which; norms[0], norms[1] (host, may be NULL) get the two RMS values.  Synchronises. */
 int gbcfd_accel_try(gbcfd_accel accel, gbcfd_block block, void* stream, int* accepted, double norms[2]);
 
 /* Message of the last error on the calling host thread ("" if none). */

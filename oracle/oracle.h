@@ -20,7 +20,8 @@
  *   a[v][k+2][j+2][i+2], i in [-2, nx+1], dims (nx+4) x (ny+4) x (nz+4), no padding.
  * Metrics: M[10][cells] = S_xi(3), S_eta(3), S_zeta(3), V; S_d of cell c is the area vector of
  * the cell's lower face in direction d (pointing towards +d).
- * Nodes: X[3][nz+1][ny+1][nx+1] (interior block only; halo metrics come from periodic copies).
+ * Nodes: X[3][nz+1][ny+1][nx+1] (interior block only); halo metrics are periodic copies, or on
+ * non-periodic faces (oracle_metrics_bc) come from nodes reflected through the boundary node.
  *
  * Every function returns 0 on success and a negative number on bad arguments or allocation
  * failure.  Nothing is kept between calls.
@@ -78,7 +79,8 @@ void oracle_muscl(int limiter, const double w0[5], const double w1[5], const dou
 void oracle_roe_flux(double gamma, double eps, const double wl[5], const double wr[5],
                      const double S[3], double F[5]);
 
-/* face area vectors and volumes of interior cells from nodes, halo cells by periodic copy */
+/* face area vectors and volumes of interior cells from nodes, halo cells by periodic copy
+ * (oracle_metrics_bc with bc NULL) */
 int oracle_metrics(int nx, int ny, int nz, const double* X, double* M);
 
 /* metrics as oracle_metrics; halo cells of non-periodic directions from reflected nodes

@@ -1325,9 +1325,12 @@ extern "C" int gbcfd_accel_try(gbcfd_accel a, gbcfd_block b, void* stream, int* 
   const double n = (double)b->nx * b->ny * b->nz;
   const double r0 = std::sqrt(h[1] / n), r1 = std::sqrt(h[3] / n);
   const bool keep = std::isfinite(r1) && r1 < r0;
-  if (!keep) CK(learn::launch_apply(v, a->y, a->qsave, a->stats, 1, s));
-  rc = init_rate(b, s);
-  if (rc) return rc;
+  if (keep) {  // the time steps of the new state
+    rc = init_rate(b, s);
+    if (rc) return rc;
+  } else {     // the state back, bit for bit; nothing else of the block was changed
+    CK(learn::launch_apply(v, a->y, a->qsave, a->stats, 1, s));
+  }
   CK(cudaStreamSynchronize(s));
   *accepted = keep ? 1 : 0;
   if (norms) { norms[0] = r0; norms[1] = r1; }

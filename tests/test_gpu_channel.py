@@ -167,3 +167,17 @@ def test_boundary_argument_errors(gb):
         visc.set_boundary("-y", gb.BC_SLIP_WALL)                      # viscous block
     with pytest.raises(gb.GbcfdError):
         gb.Block(8, 8, 4, gb.params(G, 1e-3, 0.72, 0.5, 0.1, True, 0, gb.FP64, True))  # local dt + viscous
+
+
+def test_hybrid_solve_reaches_what_fp64_reaches(gb):
+    """on a coarse bump channel the mixed path alone stalls near its FP32 floor (a few 1e-6),
+    while the hybrid (mixed, then FP64 from the stalled state) reaches a 1e-8 drop like the
+    plain FP64 iteration"""
+    from paper_1710_09995_gb300 import learn
+    c = cases.channel_case(48, 24, 2, height=0.1, mach=0.5)
+    fp64 = learn.solve(c, target=1e-8, precision="fp64", max_seconds=60)
+    mixed = learn.solve(c, target=1e-8, precision="mixed", max_seconds=8)
+    hybrid = learn.solve(c, target=1e-8, precision="hybrid", max_seconds=60, stall_checks=10)
+    assert fp64["reached"] and hybrid["reached"], (fp64["drop"], hybrid["drop"])
+    assert not mixed["reached"] and mixed["drop"] > 1e-7
+    assert "fp64" in {h[3] for h in hybrid["history"]}

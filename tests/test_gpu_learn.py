@@ -66,6 +66,19 @@ def test_forward_matches_oracle(gb, zper):
         assert err <= 2e-3, err
 
 
+def test_forward_many_tiles_per_cta(gb):
+    """a volume with a ragged second x-tile (130 cells) and several tiles per persistent CTA, so
+    both input boxes and both tensor-memory accumulators are reused"""
+    B, Z, Y, X = 1, 8, 40, 130
+    p = random_params(11)
+    xg = to_gpu_features(rng(12).standard_normal((B, 10, Z, Y, X)))
+    a = gb.Accel(X, Y, Z, B)
+    a.set_params(p)
+    y = from_gpu(a.forward(xg), B, Z, Y, X)[0]
+    want, _ = L.forward(p, from_gpu(xg, B, Z, Y, X, C=10)[0])
+    assert np.linalg.norm(y - want) / np.linalg.norm(want) <= 2e-3
+
+
 def test_train_step_matches_oracle_gradient(gb):
     """the loss before the step, and the first Adam move lr g / (|g| + eps) of every parameter
     whose oracle gradient is not negligible has the oracle gradient's sign"""
@@ -154,11 +167,16 @@ def test_try_keeps_or_restores(gb, precision):
     kept, r0, r1 = a.try_update(blk)
     assert not kept and r1 == r0
     assert torch.equal(blk.get_state(), before)
+    twin = gb.block_for_case(c, precision=precision)
+    gb.step([twin], 3)
     a.set_params(random_params(8, scale=0.05))
     kept, r0, r1 = a.try_update(blk)
     if kept:
         assert r1 < r0
-    else:
+    else:  # nothing else of the block changed either: it steps on exactly like its untouched twin
         assert torch.equal(blk.get_state(), before)
-    gb.step([blk], 2)  # the block steps on from either state
+        gb.step([blk], 2)
+        gb.step([twin], 2)
+        assert torch.equal(blk.get_state(), twin.get_state())
+    gb.step([blk], 2)
     assert np.all(np.isfinite(blk.residual_norm()))
