@@ -9,7 +9,12 @@
  *   update (Sec. 3.2.5 (2)) and the residual norm of the convergence check (Sec. 2.3).
  * The scheme where the paper leaves the choice open: cell-centred finite volume, MUSCL
  * reconstruction of primitive variables with the minmod limiter, Roe flux with Harten's entropy
- * fix, second-order central viscous fluxes, SSP-RK3, a 2-cell halo, a global CFL time step.
+ * fix, second-order central viscous fluxes, SSP-RK3, a 2-cell halo, a global CFL time step (or
+ * every cell's own, for pseudo-time marching to a steady state).
+ * Beyond the paper: inviscid boundary conditions of unconnected faces (slip wall,
+ * characteristic far field), groups of blocks advanced by one launch per stage from a CUDA graph,
+ * and a learned convergence accelerator (a conv3d network on the tensor cores whose predictions
+ * are kept only when the residual drops).
  *
  * Conventions
  *  - Every function returns GBCFD_OK (0) or a negative GBCFD_ERR_* code; gbcfd_last_error()
