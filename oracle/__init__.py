@@ -78,6 +78,11 @@ def lib():
         L.oracle_dt_local.argtypes = [P, i, i, i, _D, _D, _D]
         L.oracle_step_ex.argtypes = [P, i, i, i, _D, B, i, ctypes.c_double, _D, i, _D, _D]
         L.oracle_threads.argtypes = []
+        L.oracle_wcns_edge.argtypes = [i, _D]
+        L.oracle_wcns_edge.restype = ctypes.c_double
+        L.oracle_wcns_residual.argtypes = [P, i, i, i, _D, _D, _D]
+        L.oracle_wcns_dt.argtypes = [P, i, i, i, _D, _D, _D]
+        L.oracle_wcns_step.argtypes = [P, i, i, i, _D, _D, i, ctypes.c_double, _D, _D]
         _lib = L
     return _lib
 
@@ -240,4 +245,44 @@ def step_ex(p: Params, Qp: np.ndarray, M: np.ndarray, nsteps: int, bcs: BC = Non
     _check(lib().oracle_step_ex(ctypes.byref(p), nx, ny, nz, _ptr(M), ctypes.byref(bcs) if bcs else None,
                                 int(bool(local_dt)), float(dt_fixed or 0.0), _ptr(Q), nsteps, _ptr(dts),
                                 _ptr(norms_)), "step_ex")
+    return Q, dts[:nsteps], norms_[:nsteps]
+
+
+# ---- the paper's own scheme: WCNS-E-5 (Eq. 2) on periodic uniform Cartesian blocks -----------
+# compact arrays [5][nz][ny][nx]; p.limiter 0 = nonlinear interpolation weights, 1 = linear
+
+def wcns_edge(u, linear=False) -> float:
+    """value at i + 1/2 interpolated from the left, u = (u_{i-2} .. u_{i+2})"""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    assert u.size == 5
+    return float(lib().oracle_wcns_edge(int(bool(linear)), _ptr(u)))
+
+
+def wcns_residual(p: Params, Q: np.ndarray, h) -> np.ndarray:
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    _, nz, ny, nx = Q.shape
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    R = np.zeros_like(Q)
+    _check(lib().oracle_wcns_residual(ctypes.byref(p), nx, ny, nz, _ptr(hh), _ptr(Q), _ptr(R)), "wcns_residual")
+    return R
+
+
+def wcns_dt(p: Params, Q: np.ndarray, h) -> float:
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    _, nz, ny, nx = Q.shape
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    out = ctypes.c_double(0.0)
+    _check(lib().oracle_wcns_dt(ctypes.byref(p), nx, ny, nz, _ptr(hh), _ptr(Q), ctypes.byref(out)), "wcns_dt")
+    return out.value
+
+
+def wcns_step(p: Params, Q: np.ndarray, h, nsteps: int, dt_fixed=None):
+    """nsteps SSP-RK3 steps; returns (Q, dts, stage-1 norms)"""
+    Q = np.array(Q, dtype=np.float64, order="C", copy=True)
+    _, nz, ny, nx = Q.shape
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    dts = np.zeros(max(nsteps, 1))
+    norms_ = np.zeros((max(nsteps, 1), 5))
+    _check(lib().oracle_wcns_step(ctypes.byref(p), nx, ny, nz, _ptr(hh), _ptr(Q), nsteps, float(dt_fixed or 0.0),
+                                  _ptr(dts), _ptr(norms_)), "wcns_step")
     return Q, dts[:nsteps], norms_[:nsteps]

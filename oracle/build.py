@@ -10,7 +10,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
-SRC = [os.path.join(HERE, "oracle.c")]
+SRC = [os.path.join(HERE, "oracle.c"), os.path.join(HERE, "wcns.c")]
 HDR = [os.path.join(HERE, "oracle.h")]
 
 

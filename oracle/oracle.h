@@ -11,10 +11,12 @@
  *   Eqs. 4-6  third-order Runge-Kutta in Shu-Osher form with lambda read as -dt;
  *   Sec. 2.2  cell-edge left/right states combined by a flux function, central viscous fluxes,
  *             multi-block interfaces that preserve a uniform flow (geometric conservation).
- * Where the paper leaves the choice open (its WCNS-E-5 interpolation is not specified beyond
- * Eq. 2) this oracle uses cell-centred finite volume, MUSCL reconstruction of primitive
- * variables with the minmod limiter, the Roe flux with Harten's entropy fix, second-order
- * central viscous fluxes and SSP-RK3.
+ * Two spatial schemes.  oracle.c: cell-centred finite volume with MUSCL reconstruction of
+ * primitive variables and the minmod limiter, the Roe flux with Harten's entropy fix,
+ * second-order central viscous fluxes (the scheme taken where the paper leaves the choice
+ * open).  wcns.c: the paper's own WCNS-E-5 (Eq. 2) with a fifth-order weighted nonlinear
+ * interpolation and fourth-order central viscous derivatives, on periodic Cartesian blocks.
+ * Both advance with SSP-RK3.
  *
  * Layout (the oracle's own): every field is stored with a 2-cell halo on all sides,
  *   a[v][k+2][j+2][i+2], i in [-2, nx+1], dims (nx+4) x (ny+4) x (nz+4), no padding.
@@ -129,6 +131,27 @@ int oracle_step(const oracle_params* p, int nx, int ny, int nz, const double* M,
 /* same as oracle_step with the time step fixed to dt (no CFL evaluation) */
 int oracle_step_fixed_dt(const oracle_params* p, int nx, int ny, int nz, const double* M,
                          double* Q, int nsteps, double dt, double* norms);
+
+/* ---- the paper's own scheme: WCNS-E-5 (Sec. 2.2, Eq. 2), periodic uniform Cartesian blocks ----
+ * (wcns.c).  Arrays are compact q[5][nz][ny][nx]; h[3] the cell sizes.  `limiter` selects the
+ * interpolation weights: 0 the nonlinear ones, 1 the optimal linear ones. */
+
+/* value at i + 1/2 interpolated from the left, u[0..4] = u_{i-2} .. u_{i+2} */
+double oracle_wcns_edge(int linear, const double u[5]);
+
+/* R(Q) of Eq. 3: Eq. 2 in each direction with Roe edge fluxes of the interpolated primitives,
+ * minus the fourth-order central viscous derivatives (viscous != 0) */
+int oracle_wcns_residual(const oracle_params* p, int nx, int ny, int nz, const double h[3], const double* Q,
+                         double* R);
+
+/* global CFL time step of Q */
+int oracle_wcns_dt(const oracle_params* p, int nx, int ny, int nz, const double h[3], const double* Q,
+                   double* dt);
+
+/* nsteps SSP-RK3 steps (Eqs. 4-6, lambda = -dt) in place; fixed_dt > 0 replaces the CFL step.
+ * dts[nsteps] and norms[nsteps][5] (RMS of the stage-1 residual) when not NULL. */
+int oracle_wcns_step(const oracle_params* p, int nx, int ny, int nz, const double h[3], double* Q, int nsteps,
+                     double fixed_dt, double* dts, double* norms);
 
 /* threads the oracle's OpenMP loops use (1 when built without OpenMP) */
 int oracle_threads(void);
