@@ -41,6 +41,8 @@ WORKLOADS = {
               "tcgen05, over the 192x96x64 bump-channel grid (periodic in z)"),
     "channel": ("bump channel 192x96x64 (curvilinear, 10% bump, stretched 1.1 to the wall), Euler, Mach 0.6, "
                 "far field in/out, slip walls, local pseudo-time steps to a 1e-6 density-residual drop"),
+    "wcns256": ("isentropic vortex 256^3, Navier-Stokes Re 1e4 Pr 0.72, the paper's WCNS-E-5 (Eq. 2, weighted "
+                "nonlinear interpolation, Roe edge fluxes) + fourth-order central viscous terms, SSP-RK3 CFL 0.5"),
     "lattice96": ("96 uneven Cartesian blocks (4x4x6 lattice, sides 16..160, seed 4: 506x492x550 = 1.37e8 cells), "
                   "Euler, Mach 0.8 + 1e-2 Fourier perturbation, MUSCL/minmod + Roe, SSP-RK3 CFL 0.5, "
                   "one group: one launch per stage, CUDA graph per step, autotuned grid split"),
@@ -446,6 +448,8 @@ def run_gbcfd(args):
         return run_channel(args, world, rank, local, device, torch, cases, gbcfd)
     if args.workload == "accel":
         return run_accel(args, world, rank, local, device, torch, gbcfd)
+    if args.workload == "wcns256":
+        return run_wcns(args, world, rank, local, device, torch, cases, gbcfd)
     if args.workload == "warped512":
         case = cases.broadband_warped(512, 512, 384, seed=0, device=device)
         prec = args.precision or "mixed"
@@ -685,6 +689,154 @@ def run_channel(args, world, rank, local, device, torch, cases, gbcfd):
         "clocks": clk,
         "runs": runs,
     }
+    print(json.dumps(out))
+
+
+# ---- the paper's own scheme: WCNS-E-5 ----------------------------------------------------------
+WCNS_KERNELS = ("prim_kernel", "visc_kernel", "dir_kernel<x>", "dir_kernel<y>", "dir_kernel<z>")
+
+
+def wcns_kernel_bytes(precision, stage):
+    """algorithmic HBM bytes per interior cell of each WCNS kernel of a stage (T = 4 mixed, 8 FP64):
+    prim reads the f64 stage input and writes 6 primitive fields; visc reads u, v, w, theta and
+    writes 12 viscous-flux fields; the x pass reads 5 primitives and 4 viscous fluxes and writes R;
+    y also reads R; z reads R and the stage input (+ Q^n at stages 2, 3) and writes the f64 output"""
+    t = 4 if precision == "mixed" else 8
+    return {"prim_kernel": 40 + 6 * t, "visc_kernel": 16 * t, "dir_kernel<x>": 14 * t,
+            "dir_kernel<y>": 19 * t, "dir_kernel<z>": 14 * t + 80 + (40 if stage > 1 else 0)}
+
+
+def time_wcns(gbcfd, torch, case, precision, steps, warmup, world, device):
+    blk = gbcfd.wcns_block_for_case(case, precision=gbcfd.MIXED if precision == "mixed" else gbcfd.FP64,
+                                    device=device)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        blk.step(1, stream)
+    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(18)] for _ in range(steps)]
+    for ev in marks:
+        for e in ev:
+            e.record(stream)  # creates the events before the timed region
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(steps):
+        blk.set_timing(marks[k], created=True)
+        blk.step(1, stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(start.elapsed_time(stop), world, device)
+    kern = {n: 0.0 for n in WCNS_KERNELS}
+    per_stage = {n: [0.0, 0.0, 0.0] for n in WCNS_KERNELS}
+    for ev in marks:
+        for st in range(3):
+            for m, n in enumerate(WCNS_KERNELS):
+                t = ev[6 * st + m].elapsed_time(ev[6 * st + m + 1])
+                kern[n] += t
+                per_stage[n][st] += t
+    blk.set_timing(None)
+    norms = blk.residual_norm()
+    blk.close()
+    nlaunch = 3 * (5 if case.viscous else 4) * steps
+    return {"ms": ms, "kernel_ms": kern, "kernel_stage_ms": per_stage, "launches": nlaunch, "norms": norms.tolist()}
+
+
+def wcns_roofline(precision, res, cells, steps, peak, peak_kind):
+    """HBM roofline of the WCNS path's dominant kernel: its algorithmic bytes per launch over its
+    mean launch time (CUDA events around every launch of the timed region)"""
+    name = max(res["kernel_ms"], key=res["kernel_ms"].get)
+    nbytes = sum(wcns_kernel_bytes(precision, st)[name] * cells * steps for st in (1, 2, 3))
+    sec = res["kernel_ms"][name] / 1e3
+    achieved = nbytes / sec / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": None,
+            "algorithmic_bytes_per_launch": nbytes / (3 * steps), "kernel": name,
+            "avg_launch_ms": round(res["kernel_ms"][name] / (3 * steps), 4),
+            "share_of_step": round(res["kernel_ms"][name] / max(res["ms"], 1e-9), 4),
+            "kernels_ms_per_step": {n: round(v / steps, 4) for n, v in res["kernel_ms"].items()}}
+
+
+def e2e_wcns(gbcfd, torch, case, precision, steps, world, device):
+    blk = gbcfd.wcns_block_for_case(case, precision=gbcfd.MIXED if precision == "mixed" else gbcfd.FP64,
+                                    device=device)
+    host_in = torch.from_numpy(case.state).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+
+    def one():
+        blk.set_state(host_in)
+        blk.step(1)
+        blk.get_state(host_out)
+        blk.residual_norm()
+
+    one()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, world, device)
+    blk.close()
+    nbytes = case.state.nbytes
+    return {"value": world * case.cells * steps / dt, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 112}
+
+
+def cpu_baseline_wcns(n):
+    """The WCNS oracle (FP64) on the host cores: one SSP-RK3 step of a 256 x 256 x 8 z-slab of the
+    z-invariant vortex, best of 2."""
+    import oracle
+    from paper_1710_09995_gb300 import cases
+    nz = 8
+    c = cases.isentropic_vortex(n=n, L=10.0, nz=nz, viscous=True)
+    p = oracle.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, 0)
+    best = math.inf
+    for _ in range(2):
+        t0 = time.perf_counter()
+        oracle.wcns_step(p, c.state, c.spacing, 1)
+        best = min(best, time.perf_counter() - t0)
+    return {"value": c.cells / best, "unit": "cell-updates/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"1 SSP-RK3 step (FP64 WCNS-E-5 oracle) of a {n}x{n}x{nz} z-slab of the vortex, best of 2"}
+
+
+def run_wcns(args, world, rank, local, device, torch, cases, gbcfd):
+    case = cases.isentropic_vortex(n=args.side, L=10.0, viscous=True)
+    prec = args.precision or "both"
+    paths = ["mixed", "fp64"] if prec == "both" else [prec]
+    peak, peak_kind = hbm_peak()
+    clocks = ClockSampler(local)
+    clocks.start()
+    steps = {p: (args.steps if p == "mixed" else min(args.steps, 10)) for p in paths}
+    results = {p: time_wcns(gbcfd, torch, case, p, steps[p], args.warmup if p == "mixed" else 1, world, device)
+               for p in paths}
+    clk = clocks.stop()
+    head = paths[0]
+    e2e = e2e_wcns(gbcfd, torch, case, head, min(args.e2e_steps, steps[head]), world, device)
+    cpu = cpu_baseline_wcns(args.side) if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    if rank != 0:
+        return
+    r = results[head]
+    out = {
+        "metric": "cell-updates/s", "value": world * case.cells * steps[head] / (r["ms"] / 1e3),
+        "unit": "cell-updates/s", "n_gpus": world, "steps": steps[head], "warmup": args.warmup,
+        "ms_per_step": r["ms"] / steps[head], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if head == "mixed" else "f64",
+        "data": "synthetic (seeded closed-form vortex; the paper's meshes are not available)",
+        "config": {"workload": WORKLOADS["wcns256"], "cells": case.cells, "precision": head,
+                   "l2": "working set > 1.4 GB >> 129 MB L2, no flush needed",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": wcns_roofline(head, r, case.cells, steps[head], peak, peak_kind),
+        "e2e": e2e, "gpu_launches": r["launches"], "clocks": clk, "cpu_baseline": cpu,
+        "residual_norm": r["norms"],
+    }
+    for p in paths[1:]:
+        rp = results[p]
+        out[p] = {"value": world * case.cells * steps[p] / (rp["ms"] / 1e3), "unit": "cell-updates/s",
+                  "steps": steps[p], "ms_per_step": rp["ms"] / steps[p], "dtype": "f64",
+                  "roofline": wcns_roofline(p, rp, case.cells, steps[p], peak, peak_kind),
+                  "gpu_launches": rp["launches"]}
     print(json.dumps(out))
 
 

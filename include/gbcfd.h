@@ -15,6 +15,8 @@
  * characteristic far field), groups of blocks advanced by one launch per stage from a CUDA graph,
  * and a learned convergence accelerator (a conv3d network on the tensor cores whose predictions
  * are kept only when the residual drops).
+ * The paper's own scheme, WCNS-E-5 (Eq. 2) with fourth-order central viscous terms, is the
+ * gbcfd_wcns_* family, on periodic uniform Cartesian blocks.
  *
  * Conventions
  *  - Every function returns GBCFD_OK (0) or a negative GBCFD_ERR_* code; gbcfd_last_error()
@@ -266,6 +268,64 @@ int gbcfd_accel_target(gbcfd_accel accel, gbcfd_block block, float* t, void* str
  * it), else Q is restored and the block is left bit for bit as it was.  *accepted (host) tells
  * which; norms[0], norms[1] (host, may be NULL) get the two RMS values.  Synchronises. */
 int gbcfd_accel_try(gbcfd_accel accel, gbcfd_block block, void* stream, int* accepted, double norms[2]);
+
+/* ---- the paper's own scheme: WCNS-E-5 on periodic uniform Cartesian blocks -------------------
+ * Sec. 2.2: the inviscid derivative at a cell centre is Eq. 2, the sixth-order combination of the
+ * flux differences at the cell edges i +- 1/2, i +- 3/2, i +- 5/2, each edge flux the Roe flux
+ * (Harten's fix) of left and right cell-edge states from a fifth-order weighted nonlinear
+ * interpolation of the primitive variables; the viscous derivatives are fourth-order central
+ * (gradients of u, v, w, p/rho by (f_{i-2} - 8 f_{i-1} + 8 f_{i+1} - f_{i+2}) / 12h at the cell
+ * centres, the viscous flux vectors of Eq. 1 there, and the same difference of those).  The
+ * interpolation, which the paper does not spell out: per variable, three three-point stencils
+ * with candidates u_i + g_k/2 + s_k/8 (g_k, s_k the stencil's first and second differences),
+ * smoothness g_k^2 + s_k^2, weights C_k / (1e-6 + smoothness)^2 normalised, C = (1/16, 10/16,
+ * 5/16); the right state at i + 1/2 from the mirrored stencil.  Time stepping as gbcfd_step
+ * (Eqs. 4-6, lambda = -dt, the global CFL step of Q^n).  Every direction is periodic (the block
+ * is its own neighbour; its 5-cell halo is filled by index wrap) and the grid uniform.
+ * params: as for blocks; `limiter` 0 takes the nonlinear weights, 1 the optimal linear ones
+ * (linear fifth-order interpolation); `precision` GBCFD_MIXED evaluates the interpolation, the
+ * fluxes and the derivatives in FP32 (state and update in FP64); `local_dt` must be 0. */
+typedef struct gbcfd_wcns_s* gbcfd_wcns;
+
+/* Bytes of caller device memory a WCNS block of nx x ny x nz cells needs (the states Q^n, Q1, Q2,
+ * the padded primitive box, the viscous flux vectors when viscous, the residual, the control
+ * block and reduction partials).  Sizes must be >= 1.  Needs a current CUDA device. */
+int gbcfd_wcns_required_bytes(int nx, int ny, int nz, const gbcfd_params* params, size_t* bytes);
+
+/* Create a WCNS block with cell sizes spacing[0..2] on the current device inside caller memory
+ * dev_mem (256-byte aligned, at least gbcfd_wcns_required_bytes), which must stay valid until
+ * gbcfd_wcns_destroy.  GBCFD_ERR_ARG for bad sizes or params, GBCFD_ERR_MEMORY for short or
+ * misaligned memory. */
+int gbcfd_wcns_create(int nx, int ny, int nz, const gbcfd_params* params, const double spacing[3],
+                      void* dev_mem, size_t bytes, gbcfd_wcns* out);
+
+/* Release the host descriptor (the caller frees the device memory).  Waits for the device. */
+int gbcfd_wcns_destroy(gbcfd_wcns block);
+
+/* Load the conserved state q[5][nz][ny][nx] (host or device pointer). */
+int gbcfd_wcns_set_state(gbcfd_wcns block, const double* q, void* stream);
+
+/* Copy the state out to q[5][nz][ny][nx] (host or device pointer; a host one synchronises). */
+int gbcfd_wcns_get_state(gbcfd_wcns block, double* q, void* stream);
+
+/* R(Q) of Eq. 3 for the current state into r[5][nz][ny][nx] float64 (device pointer). */
+int gbcfd_wcns_compute_residual(gbcfd_wcns block, double* r, void* stream);
+
+/* nsteps SSP-RK3 steps; asynchronous, device errors reported by gbcfd_wcns_residual_norm. */
+int gbcfd_wcns_step(gbcfd_wcns block, int nsteps, void* stream);
+
+/* RMS per component of R(Q^n) of the last step's stage 1, to out[5] on the host (synchronises;
+ * GBCFD_ERR_NONPHYSICAL if rho <= 0 or p <= 0 was met since the last call). */
+int gbcfd_wcns_residual_norm(gbcfd_wcns block, double out[5], void* stream);
+
+/* The time step of the last step (0 before the first), to *dt on the host (synchronises). */
+int gbcfd_wcns_get_dt(gbcfd_wcns block, double* dt, void* stream);
+
+/* Timing marks inside every step: events[0..17] are CUDA events (cudaEvent_t) the caller created
+ * with timing enabled and owns.  Stage s (1..3) records events[6(s-1) + m] before its primitive
+ * kernel (m = 0) and after its primitive, viscous (also when inviscid: no launch), x, y and z
+ * kernels (m = 1..5); the next step overwrites them.  events NULL removes them; n must be 18. */
+int gbcfd_wcns_set_timing(gbcfd_wcns block, void* const* events, int n);
 
 /* Message of the last error on the calling host thread ("" if none). */
 const char* gbcfd_last_error(void);

@@ -87,6 +87,18 @@ SIGNATURES = {
     "gbcfd_accel_features": [_VP, _VP, _VP, _VP],
     "gbcfd_accel_target": [_VP, _VP, _VP, _VP],
     "gbcfd_accel_try": [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_int), _D],
+    "gbcfd_wcns_required_bytes": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params),
+                                  ctypes.POINTER(ctypes.c_size_t)],
+    "gbcfd_wcns_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), _D, _VP, ctypes.c_size_t,
+                          ctypes.POINTER(_VP)],
+    "gbcfd_wcns_destroy": [_VP],
+    "gbcfd_wcns_set_state": [_VP, _VP, _VP],
+    "gbcfd_wcns_get_state": [_VP, _VP, _VP],
+    "gbcfd_wcns_compute_residual": [_VP, _VP, _VP],
+    "gbcfd_wcns_step": [_VP, ctypes.c_int, _VP],
+    "gbcfd_wcns_residual_norm": [_VP, _D, _VP],
+    "gbcfd_wcns_get_dt": [_VP, _D, _VP],
+    "gbcfd_wcns_set_timing": [_VP, ctypes.POINTER(_VP), ctypes.c_int],
     "gbcfd_last_error": [],
 }
 
@@ -429,3 +441,95 @@ class Accel:
             self.close()
         except Exception:
             pass
+
+
+class WcnsBlock:
+    """A periodic uniform Cartesian block advanced with the paper's own WCNS-E-5 scheme (Eq. 2)
+    and fourth-order central viscous terms (gbcfd_wcns_*); prm.limiter 0 = nonlinear weights,
+    1 = linear."""
+
+    def __init__(self, nx, ny, nz, prm: Params, spacing, device=None):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.params = prm
+        nbytes = ctypes.c_size_t(0)
+        _check(lib().gbcfd_wcns_required_bytes(self.nx, self.ny, self.nz, ctypes.byref(prm), ctypes.byref(nbytes)))
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.memory = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=dev)
+        base = self.memory.data_ptr()
+        off = (-base) % 256
+        sp = (ctypes.c_double * 3)(*spacing)
+        h = ctypes.c_void_p(0)
+        _check(lib().gbcfd_wcns_create(self.nx, self.ny, self.nz, ctypes.byref(prm), sp, ctypes.c_void_p(base + off),
+                                       nbytes.value, ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def set_state(self, q, stream=None):
+        if isinstance(q, np.ndarray):
+            q = np.ascontiguousarray(q, dtype=np.float64)
+        else:
+            assert q.dtype == torch.float64 and q.is_contiguous()
+        assert tuple(q.shape) == (5, self.nz, self.ny, self.nx)
+        _check(lib().gbcfd_wcns_set_state(self.handle, _ptr(q), _stream(stream)))
+
+    def get_state(self, out=None, stream=None):
+        if out is None:
+            out = torch.empty((5, self.nz, self.ny, self.nx), dtype=torch.float64, device=self.memory.device)
+        _check(lib().gbcfd_wcns_get_state(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def compute_residual(self, out=None, stream=None):
+        if out is None:
+            out = torch.empty((5, self.nz, self.ny, self.nx), dtype=torch.float64, device=self.memory.device)
+        _check(lib().gbcfd_wcns_compute_residual(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def step(self, nsteps=1, stream=None):
+        _check(lib().gbcfd_wcns_step(self.handle, int(nsteps), _stream(stream)))
+
+    def residual_norm(self, stream=None) -> np.ndarray:
+        out = np.zeros(5)
+        _check(lib().gbcfd_wcns_residual_norm(self.handle, out.ctypes.data_as(_D), _stream(stream)))
+        return out
+
+    def get_dt(self, stream=None) -> float:
+        out = ctypes.c_double(0.0)
+        _check(lib().gbcfd_wcns_get_dt(self.handle, ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def set_timing(self, events, created=False):
+        """events: 18 torch.cuda.Event(enable_timing=True), 6 per stage (or None).  created: the
+        events have been recorded once already (so they exist), which skips a synchronisation."""
+        self._events = events
+        if events is None:
+            _check(lib().gbcfd_wcns_set_timing(self.handle, None, 0))
+            return
+        if not created:
+            for e in events:
+                e.record()  # creates the underlying CUDA event
+            torch.cuda.current_stream().synchronize()
+        arr = (ctypes.c_void_p * 18)(*[e.cuda_event for e in events])
+        _check(lib().gbcfd_wcns_set_timing(self.handle, arr, 18))
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().gbcfd_wcns_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wcns_block_for_case(case, precision=FP64, linear=False, device=None) -> WcnsBlock:
+    """WCNS block configured from a periodic Cartesian cases.Case (physics, spacing, state)"""
+    assert case.nodes is None, "WCNS blocks are uniform Cartesian"
+    prm = params(case.gamma, case.mu, case.Pr, case.cfl, case.eps, case.viscous, int(bool(linear)), precision)
+    b = WcnsBlock(case.nx, case.ny, case.nz, prm, case.spacing, device)
+    b.set_state(torch.from_numpy(np.ascontiguousarray(case.state)).to(b.memory.device))
+    return b

@@ -1,0 +1,157 @@
+"""Parity of the CUDA WCNS-E-5 path (the paper's own scheme, Eq. 2, with fourth-order central
+viscous terms; gbcfd_wcns_* through the C ABI) with the FP64 CPU oracle on the same seeded inputs.
+
+Bars as for the finite-volume path: FP64 relative L2 <= 1e-12 per conserved variable (residual
+and after N steps); mixed (FP32 interpolation, fluxes and derivatives, FP64 state) density
+relative L2 <= 1e-5 after 100 steps.  Sizes span several line segments and 16-line tiles with
+ragged tails in every direction; the full 256^3 vortex is checked through its exact z-invariance
+against the oracle run on one plane of it.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1710_09995_gb300 import cases  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_09995_gb300 import gbcfd
+    gbcfd.lib()
+    return gbcfd
+
+
+def oparams(case, linear=False):
+    return oracle.params(case.gamma, case.mu, case.Pr, case.cfl, case.eps, case.viscous, int(bool(linear)))
+
+
+def per_var(a, b):
+    floor = 1e-3 * np.linalg.norm(b[0].ravel())
+    return [np.linalg.norm((a[m] - b[m]).ravel()) / max(np.linalg.norm(b[m].ravel()), floor) for m in range(5)]
+
+
+def ragged(viscous, seed=3, nx=70, ny=19, nz=21, amp=0.05):
+    c = cases.smooth_random(nx, ny, nz, seed=seed, amp=amp, viscous=viscous, mu=3e-3 if viscous else 0.0)
+    c.spacing = (1.0 / 64, 1.0 / 16, 1.0 / 20)
+    return c
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("linear", [False, True])
+def test_residual_fp64(gb, viscous, linear):
+    c = ragged(viscous)
+    blk = gb.wcns_block_for_case(c, precision=gb.FP64, linear=linear)
+    R = blk.compute_residual().cpu().numpy()
+    ref = oracle.wcns_residual(oparams(c, linear), c.state, c.spacing)
+    assert max(per_var(R, ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 5), (5, 17, 4), (60, 3, 61), (118, 7, 2)])
+def test_residual_fp64_small_and_ragged(gb, shape):
+    """blocks narrower than the 5-cell halo (multiple periodic wraps), one cell, and segment
+    splits of 60, 61 and 118 cells"""
+    nx, ny, nz = shape
+    c = ragged(True, seed=9, nx=nx, ny=ny, nz=nz, amp=0.1)
+    blk = gb.wcns_block_for_case(c, precision=gb.FP64)
+    R = blk.compute_residual().cpu().numpy()
+    ref = oracle.wcns_residual(oparams(c), c.state, c.spacing)
+    # a block of one cell is uniform: R is rounding noise (~1e-32) on both sides
+    assert np.abs(R - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1.0)
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_residual_mixed(gb, viscous):
+    """FP32 edge states and fluxes: the differences of Eq. 2 carry ~1e-7 |F| / h of rounding."""
+    c = ragged(viscous)
+    blk = gb.wcns_block_for_case(c, precision=gb.MIXED)
+    R = blk.compute_residual().cpu().numpy()
+    ref = oracle.wcns_residual(oparams(c), c.state, c.spacing)
+    assert max(per_var(R, ref)) <= 1e-4
+
+
+def test_residual_conserves(gb):
+    c = ragged(True)
+    blk = gb.wcns_block_for_case(c, precision=gb.FP64)
+    R = blk.compute_residual().cpu().numpy()
+    for m in range(5):
+        assert abs(R[m].sum()) < 1e-12 * np.abs(R[m]).sum()
+
+
+def test_uniform_flow_stays_uniform(gb):
+    """Constant data: every edge state is the cell state to rounding (the GPU contracts the
+    interpolation's differences into fused multiply-adds, so not bitwise), and the residual
+    vanishes to rounding."""
+    nx, ny, nz = 40, 18, 9
+    Q = cases.conserved(np.full((nz, ny, nx), 1.1), 0.3, -0.2, 0.1, 0.8)
+    c = cases.Case("uniform", nx, ny, nz, Q, None, (0.1, 0.12, 0.13), viscous=True, mu=1e-2)
+    blk = gb.wcns_block_for_case(c, precision=gb.FP64)
+    R = blk.compute_residual().cpu().numpy()
+    assert np.abs(R).max() < 1e-12
+    blk.step(3)
+    assert np.abs(blk.get_state().cpu().numpy() - Q).max() < 1e-14
+
+
+def test_gaussian_pulse_32_fp64_10_steps(gb):
+    """32^3 Euler Gaussian pulse, CFL 0.5, WCNS-E-5 + Roe, 10 SSP-RK3 steps, FP64."""
+    c = cases.gaussian_pulse(32, seed=0)
+    ref, dts, norms = oracle.wcns_step(oparams(c), c.state, c.spacing, 10)
+    blk = gb.wcns_block_for_case(c, precision=gb.FP64)
+    blk.step(9)
+    got_norm9 = blk.residual_norm()
+    blk.step(1)
+    got = blk.get_state().cpu().numpy()
+    assert max(per_var(got, ref)) <= 1e-12
+    assert abs(blk.get_dt() - dts[-1]) <= 1e-13 * dts[-1]
+    assert np.allclose(blk.residual_norm(), norms[-1], rtol=1e-11, atol=0)
+    assert np.allclose(got_norm9, norms[-2], rtol=1e-11, atol=0)
+
+
+def test_vortex_ns_fp64_steps(gb):
+    c = cases.isentropic_vortex(n=48, nz=6, L=10.0, viscous=True, Re=1e2)
+    ref, _, _ = oracle.wcns_step(oparams(c), c.state, c.spacing, 8)
+    blk = gb.wcns_block_for_case(c, precision=gb.FP64)
+    blk.step(8)
+    assert max(per_var(blk.get_state().cpu().numpy(), ref)) <= 1e-12
+
+
+def test_vortex_ns_mixed_100_steps(gb):
+    """The mixed-precision bar: density relative L2 <= 1e-5 after 100 steps."""
+    c = cases.isentropic_vortex(n=64, nz=4, L=10.0, viscous=True, Re=1e4)
+    ref, _, _ = oracle.wcns_step(oparams(c), c.state, c.spacing, 100)
+    blk = gb.wcns_block_for_case(c, precision=gb.MIXED)
+    blk.step(100)
+    got = blk.get_state().cpu().numpy()
+    err = per_var(got, ref)
+    assert err[0] <= 1e-5, err
+
+
+def test_full_size_vortex_256_fp64(gb):
+    """Config-2 size (256^3, NS Re 1e4, vortex): the state is z-invariant, so after 2 steps every
+    z-plane must equal the oracle run on a single plane (nz = 1; the z derivatives vanish)."""
+    c = cases.isentropic_vortex(n=256, L=10.0, viscous=True, Re=1e4)
+    blk = gb.wcns_block_for_case(c, precision=gb.FP64)
+    blk.step(2)
+    got = blk.get_state()
+    one = cases.isentropic_vortex(n=256, nz=1, L=10.0, viscous=True, Re=1e4)
+    ref, _, _ = oracle.wcns_step(oparams(one), one.state, one.spacing, 2)
+    for k in (0, 77, 255):
+        assert max(per_var(got[:, k:k + 1].cpu().numpy(), ref)) <= 1e-12
+    spread = (got - got[:, :1]).abs().max().item()
+    assert spread == 0.0
+
+
+def test_errors(gb):
+    prm = gb.params(local_dt=True)
+    with pytest.raises(gb.GbcfdError):
+        gb.WcnsBlock(8, 8, 8, prm, (0.1, 0.1, 0.1))
+    with pytest.raises(gb.GbcfdError):
+        gb.WcnsBlock(8, 8, 8, gb.params(), (0.1, -0.1, 0.1))
+    blk = gb.WcnsBlock(8, 8, 8, gb.params(), (0.1, 0.1, 0.1))
+    with pytest.raises(gb.GbcfdError) as e:
+        blk.step(1)
+    assert e.value.code == gb.ERR_STATE
