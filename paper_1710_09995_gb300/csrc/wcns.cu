@@ -3,19 +3,25 @@
 // the third-order Runge-Kutta stages of Eqs. 4-6 (lambda = -dt), and its C ABI (gbcfd_wcns_*).
 //
 // Per Runge-Kutta stage (all launches on the caller's stream):
-//   prim_kernel  the stage input Q (compact, f64) -> primitives W = (rho, u, v, w, p, theta) of
-//                every cell of a box padded by 5 cells (periodic images by index wrap: the halo
-//                exchange of a self-connected block); stage 1 also reduces the CFL rate of Q^n to
-//                the step's time step.
+//   prim_kernel  the stage input -> primitives W = (rho, u, v, w, p, theta) of every cell of a box
+//                padded by 5 cells (periodic images by index wrap: the halo exchange of a
+//                self-connected block); stage 1 also reduces the CFL rate of Q^n to the step's
+//                time step.
 //   visc_kernel  (Navier-Stokes) the viscous flux vectors Fv, Gv, Hv of Eq. 1 at every cell of
 //                the box padded by 2, from fourth-order central gradients (D4) of u, v, w, theta.
-//   dir_kernel<D> for D = x, y, z: a tile of 16 lines x L cells along D; the tile's primitives
-//                (L + 10 cells per line) go to shared memory, every edge flux of the tile
-//                (L + 5 per line) is computed once (weighted interpolation of the left and right
-//                states, Roe flux) into shared memory, and each cell takes Eq. 2 of its six edge
-//                fluxes minus D4 of its viscous flux along D.  x writes R, y adds to it, z adds
-//                and applies the stage update (or writes R out), with the residual norm of
+//   dir_kernel<D> for D = x, y, z: a tile of 16 lines x L cells along D.  The tile's primitives
+//                (L + 10 cells per line) go to shared memory; a lane per cell evaluates both edge
+//                values of its cell (the two share the stencils' smoothness indicators), a shuffle
+//                pairs the left state of cell i with the right state of cell i + 1, and the Roe
+//                flux of every edge of the tile (L + 5 per line) is computed once; the fluxes
+//                replace the primitives in shared memory and each cell takes Eq. 2 of its six
+//                edge fluxes minus D4 of its viscous flux along D.  x writes R, y adds to it, z
+//                adds and applies the stage update (or writes R out), with the residual norm of
 //                stage 1 reduced per CTA and by the last CTA in a fixed order.
+// Precision: FP64 everywhere, or mixed: the stage inputs are the f32 shadow S^n of Q^n plus an
+// f32 increment, D1 = -dt R(S^n), D2 = (D1 - dt R(S^n + D1)) / 4, and only the last stage touches
+// FP64: Q^{n+1} = Q^n + 2/3 (D2 - dt R(S^n + D2)), S^{n+1} = f32(Q^{n+1}) (algebraically Eqs. 4-6);
+// primitives, interpolation, fluxes and derivatives are f32.
 // The interpolation (the paper names it only "weighted nonlinear"): three three-point stencils,
 // candidates u_i + g_k/2 + s_k/8 with g_k, s_k the stencil's first and second differences,
 // smoothness beta_k = g_k^2 + s_k^2, weights C_k / (1e-6 + beta_k)^2 normalised, optimal
@@ -34,9 +40,11 @@ namespace wcns {
 constexpr int H = 5;        // halo of the primitive box: Eq. 2 reaches 5 cells
 constexpr int NL = 16;      // lines per tile
 constexpr int NLP = NL + 1; // padded line stride in shared memory
-constexpr int LMAX = 59;    // cells per line segment: <= 64 edge fluxes, <= 69 staged cells
+constexpr int FCH = 31;     // edges per warp chunk (lane 31 only lends its cell's right state)
+constexpr int LMAX = 57;    // cells per line segment: <= 62 edges (two chunks), <= 67 staged cells
 constexpr int NTW = 256;    // threads per CTA
 constexpr int NPW = 6;      // primitive fields: rho, u, v, w, p, theta
+constexpr int ITEMS = 2 * NL / (NTW / 32);  // (line, chunk) items per warp and tile
 
 struct Box {                // the padded box of W (halo H) and of the viscous fluxes
   int nx, ny, nz, px;       // interior sizes, row pitch (elements)
@@ -45,9 +53,11 @@ struct Box {                // the padded box of W (halo H) and of the viscous f
 __host__ __device__ __forceinline__ long long bidx(const Box& b, int i, int j, int k) {
   return ((long long)(k + H) * (b.ny + 2 * H) + (j + H)) * b.px + (i + H);
 }
+// periodic image of index i in [0, n): i lies within a few block lengths of the block
 __device__ __forceinline__ int wrap(int i, int n) {
-  const int r = i % n;
-  return r < 0 ? r + n : r;
+  while (i < 0) i += n;
+  while (i >= n) i -= n;
+  return i;
 }
 
 struct Args {
@@ -59,9 +69,16 @@ struct Args {
   void* W;                  // NPW padded fields (T)
   void* Fv;                 // 12 padded fields (T): [d][mx, my, mz, energy]
   void* R;                  // compact [5][n] (T): the residual accumulated over the passes
+  // FP64 path
   const double* qn;         // Q^n (compact f64)
   const double* qs;         // the stage input
-  double* qout;             // the stage output (may be qn at stage 3)
+  double* qout;             // the stage output (qn at stage 3)
+  // mixed path
+  double* q;                // Q^n (f64), updated in place at stage 3
+  float* sh;                // S^n = f32(Q^n), rewritten at stage 3
+  const float* din;         // the stage input's increment over S^n (NULL at stage 1)
+  float* d1;                // D1
+  float* d2;                // D2
   double* rout;             // residual mode: compact f64 R
   DevCtrl* ctrl;
   double* partial;          // per-CTA partials, NPART doubles each
@@ -71,46 +88,65 @@ struct Args {
 
 // ---- primitives of the padded box (and the time step of Q^n) -------------------------------
 template <typename T>
+__device__ __forceinline__ void load_conserved(const Args& a, long long c, T* U);
+template <>
+__device__ __forceinline__ void load_conserved<double>(const Args& a, long long c, double* U) {
+#pragma unroll
+  for (int m = 0; m < 5; ++m) U[m] = a.qs[m * a.n + c];
+}
+template <>
+__device__ __forceinline__ void load_conserved<float>(const Args& a, long long c, float* U) {
+#pragma unroll
+  for (int m = 0; m < 5; ++m) U[m] = a.din ? a.sh[m * a.n + c] + a.din[m * a.n + c] : a.sh[m * a.n + c];
+}
+
+template <typename T>
 __global__ void __launch_bounds__(NTW) prim_kernel(Args a, int with_rate) {
   __shared__ double wmax[NTW / 32];
   __shared__ int last;
   const Box& b = a.b;
   const int wx = b.nx + 2 * H, wy = b.ny + 2 * H, wz = b.nz + 2 * H;
-  const long long total = (long long)wx * wy * wz;
   T* W = static_cast<T*>(a.W);
-  const double gm1 = a.gamma - 1.0;
-  const double vf = 4.0 * fmax(4.0 / 3.0, a.gamma / a.Pr) * a.mu;
-  double best = 0.0;
+  const T gm1 = T(a.gamma - 1.0), gam = T(a.gamma), half = T(0.5);
+  const T vf = T(4.0 * fmax(4.0 / 3.0, a.gamma / a.Pr) * a.mu);
+  const T ih0 = T(a.ih[0]), ih1 = T(a.ih[1]), ih2 = T(a.ih[2]);
+  const T ihs = T(a.ih[0] * a.ih[0] + a.ih[1] * a.ih[1] + a.ih[2] * a.ih[2]);
+  T best = T(0);
   bool bad = false;
-  for (long long t = (long long)blockIdx.x * NTW + threadIdx.x; t < total; t += (long long)gridDim.x * NTW) {
-    const int ii = (int)(t % wx);
-    const long long r = t / wx;
-    const int jj = (int)(r % wy), kk = (int)(r / wy);
-    const int i = ii - H, j = jj - H, k = kk - H;
-    const int si = wrap(i, b.nx), sj = wrap(j, b.ny), sk = wrap(k, b.nz);
-    const long long c = ((long long)sk * b.ny + sj) * b.nx + si;
-    const double rho = a.qs[c], ir = 1.0 / rho;
-    const double u = a.qs[a.n + c] * ir, v = a.qs[2 * a.n + c] * ir, w = a.qs[3 * a.n + c] * ir;
-    const double p = gm1 * (a.qs[4 * a.n + c] - 0.5 * rho * (u * u + v * v + w * w));
-    const long long o = (long long)kk * wy * b.px + (long long)jj * b.px + ii;
-    W[o] = T(rho);
-    W[b.field + o] = T(u);
-    W[2 * b.field + o] = T(v);
-    W[3 * b.field + o] = T(w);
-    W[4 * b.field + o] = T(p);
-    W[5 * b.field + o] = T(p * ir);
-    if (with_rate && i == si && j == sj && k == sk) {  // each interior cell once
-      if (!(rho > 0.0 && p > 0.0)) bad = true;
-      const double cs = sqrt(a.gamma * p * ir);
-      double rate = (fabs(u) + cs) * a.ih[0] + (fabs(v) + cs) * a.ih[1] + (fabs(w) + cs) * a.ih[2];
-      if (a.viscous) rate += vf * ir * (a.ih[0] * a.ih[0] + a.ih[1] * a.ih[1] + a.ih[2] * a.ih[2]);
-      best = fmax(best, rate);
+  for (int row = blockIdx.x; row < wy * wz; row += gridDim.x) {  // rows (j, k) of the padded box
+    const int jj = row % wy, kk = row / wy;
+    const int j = jj - H, k = kk - H;
+    const int sj = wrap(j, b.ny), sk = wrap(k, b.nz);
+    const long long src = ((long long)sk * b.ny + sj) * b.nx;
+    T* dst = W + ((long long)kk * wy + jj) * b.px;
+    const bool inner_row = j == sj && k == sk;
+    for (int ii = threadIdx.x; ii < wx; ii += NTW) {
+      const int i = ii - H, si = wrap(i, b.nx);
+      T U[5];
+      load_conserved<T>(a, src + si, U);
+      const T rho = U[0], ir = T(1) / rho;
+      const T u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+      const T p = gm1 * (U[4] - half * rho * (u * u + v * v + w * w));
+      dst[ii] = rho;
+      dst[b.field + ii] = u;
+      dst[2 * b.field + ii] = v;
+      dst[3 * b.field + ii] = w;
+      dst[4 * b.field + ii] = p;
+      dst[5 * b.field + ii] = p * ir;
+      if (with_rate && inner_row && i == si) {  // each interior cell once
+        if (!(rho > T(0) && p > T(0))) bad = true;
+        const T cs = sqrt(gam * p * ir);
+        T rate = (fabs(u) + cs) * ih0 + (fabs(v) + cs) * ih1 + (fabs(w) + cs) * ih2;
+        if (a.viscous) rate += vf * ir * ihs;
+        best = fmax(best, rate);
+      }
     }
   }
   if (!with_rate) return;
   if (bad) atomicOr(&a.ctrl->flag, FLAG_NONPHYSICAL);
-  for (int off = 16; off > 0; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = best;
+  double bd = double(best);
+  for (int off = 16; off > 0; off >>= 1) bd = fmax(bd, __shfl_xor_sync(0xffffffffu, bd, off));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = bd;
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = 0.0;
@@ -129,6 +165,12 @@ __global__ void __launch_bounds__(NTW) prim_kernel(Args a, int with_rate) {
   a.ctrl->counter = 0u;
 }
 
+// S = f32(Q) of a compact state (mixed path, after the state is set)
+__global__ void shadow_kernel(const double* __restrict__ q, float* __restrict__ sh, long long n) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+    sh[c] = f64_to_f32_bits(q[c]);
+}
+
 // ---- viscous flux vectors at the cells of the box padded by 2 ------------------------------
 template <typename T>
 __device__ __forceinline__ T d4(const T* f, long long o, long long st, T ih) {
@@ -140,16 +182,14 @@ template <typename T>
 __global__ void __launch_bounds__(NTW) visc_kernel(Args a) {
   const Box& b = a.b;
   const int wx = b.nx + 4, wy = b.ny + 4, wz = b.nz + 4;
-  const long long total = (long long)wx * wy * wz;
   const T* W = static_cast<const T*>(a.W);
   T* F = static_cast<T*>(a.Fv);
   const T mu = T(a.mu), kappa = T(a.mu * a.gamma / ((a.gamma - 1.0) * a.Pr));
   const T ih[3] = {T(a.ih[0]), T(a.ih[1]), T(a.ih[2])};
   const long long st[3] = {1, b.px, (long long)b.px * (b.ny + 2 * H)};
-  for (long long t = (long long)blockIdx.x * NTW + threadIdx.x; t < total; t += (long long)gridDim.x * NTW) {
-    const int i = (int)(t % wx) - 2;
-    const long long r = t / wx;
-    const int j = (int)(r % wy) - 2, k = (int)(r / wy) - 2;
+  for (int row = blockIdx.x; row < wy * wz; row += gridDim.x)  // rows (j, k) of the box padded by 2
+  for (int i = (int)threadIdx.x - 2; i < wx - 2; i += NTW) {
+    const int j = row % wy - 2, k = row / wy - 2;
     const long long o = bidx(b, i, j, k);
     T g[3][3], gt[3], vel[3];
 #pragma unroll
@@ -174,24 +214,35 @@ __global__ void __launch_bounds__(NTW) visc_kernel(Args a) {
   }
 }
 
-// ---- the weighted interpolation (value at i + 1/2 from u_{i-2} .. u_{i+2}) --------------------
+// ---- the weighted interpolation: both edge values of cell i from u_{i-2} .. u_{i+2} -----------
+// The three stencils A = {i-2, i-1, i}, B = {i-1, i, i+1}, C = {i, i+1, i+2} give, with g and s
+// their first and second differences at i, the candidates u_i +- g/2 + s/8 at i +- 1/2 and the
+// smoothness g^2 + s^2; the optimal weights are (1, 10, 5)/16 on (A, B, C) at i + 1/2 and the
+// mirrored (5, 10, 1)/16 at i - 1/2.  alpha = C_k / d_k with d_k = (1e-6 + smoothness)^2, and the
+// normalised combination takes one reciprocal: sum C_k (prod_{m != k} d_m) c_k / sum C_k (...).
 template <typename V>
-__device__ __forceinline__ V edge(V u0, V u1, V u2, V u3, V u4, bool linear) {
+__device__ __forceinline__ void edges(V u0, V u1, V u2, V u3, V u4, bool linear, V& up, V& um) {
   using O = VM<V>;
   const V half = O::c(0.5), eighth = O::c(0.125);
-  const V g0 = half * (u0 - O::c(4) * u1 + O::c(3) * u2), s0 = u0 - O::c(2) * u1 + u2;
-  const V g1 = half * (u3 - u1), s1 = u1 - O::c(2) * u2 + u3;
-  const V g2 = half * (O::c(-3) * u2 + O::c(4) * u3 - u4), s2 = u2 - O::c(2) * u3 + u4;
-  const V c0 = O::fma(half, g0, eighth * s0), c1 = O::fma(half, g1, eighth * s1), c2 = O::fma(half, g2, eighth * s2);
-  if (linear) return u2 + (O::c(1.0 / 16.0) * c0 + O::c(10.0 / 16.0) * c1 + O::c(5.0 / 16.0) * c2);
-  // alpha_k = C_k / d_k with d_k = (eps + beta_k)^2; the normalised combination takes one
-  // reciprocal: sum_k C_k (prod_{m != k} d_m) c_k / sum_k C_k (prod_{m != k} d_m)
+  const V gA = half * (u0 - O::c(4) * u1 + O::c(3) * u2), sA = u0 - O::c(2) * u1 + u2;
+  const V gB = half * (u3 - u1), sB = u1 - O::c(2) * u2 + u3;
+  const V gC = half * (O::c(-3) * u2 + O::c(4) * u3 - u4), sC = u2 - O::c(2) * u3 + u4;
+  const V eA = eighth * sA, eB = eighth * sB, eC = eighth * sC;
+  const V pA = O::fma(half, gA, eA), pB = O::fma(half, gB, eB), pC = O::fma(half, gC, eC);
+  const V mA = O::fma(-half, gA, eA), mB = O::fma(-half, gB, eB), mC = O::fma(-half, gC, eC);
+  if (linear) {
+    up = u2 + (O::c(1.0 / 16.0) * pA + O::c(10.0 / 16.0) * pB + O::c(5.0 / 16.0) * pC);
+    um = u2 + (O::c(5.0 / 16.0) * mA + O::c(10.0 / 16.0) * mB + O::c(1.0 / 16.0) * mC);
+    return;
+  }
   const V e = O::c(1e-6);
-  V d0 = e + O::fma(g0, g0, s0 * s0), d1 = e + O::fma(g1, g1, s1 * s1), d2 = e + O::fma(g2, g2, s2 * s2);
-  d0 = d0 * d0; d1 = d1 * d1; d2 = d2 * d2;
-  const V n0 = O::c(1.0 / 16.0) * (d1 * d2), n1 = O::c(10.0 / 16.0) * (d0 * d2), n2 = O::c(5.0 / 16.0) * (d0 * d1);
-  const V num = O::fma(n0, c0, O::fma(n1, c1, n2 * c2));
-  return u2 + num * O::rcp(n0 + n1 + n2);
+  V dA = e + O::fma(gA, gA, sA * sA), dB = e + O::fma(gB, gB, sB * sB), dC = e + O::fma(gC, gC, sC * sC);
+  dA = dA * dA; dB = dB * dB; dC = dC * dC;
+  const V bc = dB * dC, ac = dA * dC, ab = dA * dB;
+  const V nA = O::c(1.0 / 16.0) * bc, nB = O::c(10.0 / 16.0) * ac, nC = O::c(5.0 / 16.0) * ab;
+  const V kA = O::c(5.0 / 16.0) * bc, kC = O::c(1.0 / 16.0) * ab;
+  up = u2 + O::fma(nA, pA, O::fma(nB, pB, nC * pC)) * O::rcp(nA + nB + nC);
+  um = u2 + O::fma(kA, mA, O::fma(nB, mB, kC * mC)) * O::rcp(kA + nB + kC);
 }
 
 template <int D> struct Fr;
@@ -201,10 +252,33 @@ template <> struct Fr<2> { static constexpr int N = 3, T1 = 1, T2 = 2; };
 
 template <typename T>
 struct Smem {
-  static constexpr int WS = 5 * (LMAX + 10) * NLP;   // staged primitives [5][L+10][NLP]
-  static constexpr int FS = 5 * (LMAX + 5) * NLP;    // edge fluxes [5][L+5][NLP]
-  static constexpr size_t red = (sizeof(T) * (WS + FS) + 15) / 16 * 16;  // norm partials (double)
+  static constexpr int WS = 5 * (LMAX + 10) * NLP;   // staged primitives [5][L+10][NLP], then
+                                                     // the edge fluxes [5][L+5][NLP] over them;
+                                                     // two buffers (the next tile lands in one)
+  static constexpr size_t red = (2 * sizeof(T) * WS + 15) / 16 * 16;  // norm partials (double)
   static constexpr size_t bytes = red + sizeof(double) * (NTW / 32) * 5;
+};
+
+// asynchronous global -> shared copy of one element (cp.async, completes by group)
+template <typename T>
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Kahan-compensated running sum (the mixed path's per-thread sums of squares)
+struct KSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c, t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
 };
 
 // MODE: 0 x pass (R =), 1 y pass (R +=), 2 z pass (stage update or residual output)
@@ -212,8 +286,7 @@ template <typename T, int D, int MODE>
 __global__ void __launch_bounds__(NTW) dir_kernel(Args a) {
   using O = VM<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Ws = reinterpret_cast<T*>(smem_raw);
-  T* Fs = Ws + Smem<T>::WS;
+  T* const Wbuf = reinterpret_cast<T*>(smem_raw);
   double* red = reinterpret_cast<double*>(smem_raw + Smem<T>::red);
   __shared__ int last;
   const Box& b = a.b;
@@ -231,62 +304,108 @@ __global__ void __launch_bounds__(NTW) dir_kernel(Args a) {
   const T ih = T(a.ih[D]);
   const bool linear = a.linear != 0;
   const double dt = (MODE == 2 && a.stage > 0) ? a.ctrl->dt : 0.0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double sq[5] = {0, 0, 0, 0, 0};
+  KSum ks[5];
   constexpr int idx[5] = {0, Fr<D>::N, Fr<D>::T1, Fr<D>::T2, 4};
-  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+  struct TileInfo { int s0, Ls, a0, ob; };
+  auto decode = [&](long long tile) {
+    TileInfo t;
     const int seg = (int)(tile % nseg);
     const long long r = tile / nseg;
-    const int grp = (int)(r % ngrp), ob = (int)(r / ngrp);
-    const int s0 = seg * L, Ls = min(L, nd - s0), a0 = grp * NL;
-    // cell (line l, position s along D) -> (i, j, k)
-    auto ijk = [&](int l, int s, int& i, int& j, int& k) {
-      if (D == 0) { i = s; j = a0 + l; k = ob; }
-      else if (D == 1) { i = a0 + l; j = s; k = ob; }
-      else { i = a0 + l; j = ob; k = s; }
-    };
-    __syncthreads();  // the previous tile's readers are done with the shared arrays
-    // 1. stage the primitives of cells s0 - 5 .. s0 + Ls + 4 of every line
-    const int nst = Ls + 10, nfc = Ls + 5;
-    for (int e = threadIdx.x; e < 5 * nst * NL; e += NTW) {
-      const int v = e / (nst * NL), rr = e % (nst * NL);
-      int l, s;
-      if (D == 0) { l = rr / nst; s = rr % nst; } else { s = rr / NL; l = rr % NL; }
-      T val;
-      if (a0 + l < na) {
+    t.s0 = seg * L;
+    t.Ls = min(L, nd - t.s0);
+    t.a0 = (int)(r % ngrp) * NL;
+    t.ob = (int)(r / ngrp);
+    return t;
+  };
+  // cell (line l, position s along D) of tile t -> (i, j, k)
+  auto ijk = [&](const TileInfo& t, int l, int s, int& i, int& j, int& k) {
+    if (D == 0) { i = s; j = t.a0 + l; k = t.ob; }
+    else if (D == 1) { i = t.a0 + l; j = s; k = t.ob; }
+    else { i = t.a0 + l; j = t.ob; k = s; }
+  };
+  // 1. stage the primitives of cells s0 - 5 .. s0 + Ls + 4 of every line into buffer Ws
+  //    (staged cell s is cell s0 - 5 + s), asynchronously, as one commit group
+  auto issue_stage = [&](const TileInfo& t, T* Ws) {
+    const int nst = t.Ls + 10;
+    auto stage_one = [&](int v, int l, int s) {
+      T* dst = Ws + (v * (LMAX + 10) + s) * NLP + l;
+      if (t.a0 + l < na) {
         int i, j, k;
-        ijk(l, s0 - H + s, i, j, k);
-        val = W[(long long)v * b.field + bidx(b, i, j, k)];
+        ijk(t, l, t.s0 - H + s, i, j, k);
+        cp_async(dst, W + (long long)v * b.field + bidx(b, i, j, k));
       } else {
-        val = (v == 0 || v == 4) ? T(1) : T(0);  // lines past the block: any physical state
+        *dst = (v == 0 || v == 4) ? T(1) : T(0);  // lines past the block: any physical state
       }
-      Ws[(v * (LMAX + 10) + s) * NLP + l] = val;
+    };
+    if (D == 0) {  // a warp per (variable, line), lanes along x
+      for (int vl = warp; vl < 5 * NL; vl += NTW / 32)
+        for (int s = lane; s < nst; s += 32) stage_one(vl / NL, vl % NL, s);
+    } else {       // 16 lines (x) per row s
+      for (int v = 0; v < 5; ++v)
+        for (int e = threadIdx.x; e < nst * NL; e += NTW) stage_one(v, e % NL, e / NL);
     }
-    __syncthreads();
-    // 2. every edge flux of the tile: face f lies between staged cells f + 2 and f + 3 (staged
-    //    cell s is cell s0 - 5 + s), so cell c (staged c + 5) has faces c .. c + 5 around it
-    for (int e = threadIdx.x; e < nfc * NL; e += NTW) {
-      const int f = e / NL, l = e % NL;
+    cp_async_commit();
+  };
+  int buf = 0;
+  if ((long long)blockIdx.x < tiles) issue_stage(decode(blockIdx.x), Wbuf);
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, buf ^= 1) {
+    const TileInfo t = decode(tile);
+    const int s0 = t.s0, Ls = t.Ls, a0 = t.a0;
+    T* const Ws = Wbuf + buf * Smem<T>::WS;
+    T* const Fs = Ws;  // the edge fluxes replace the primitives once every lane holds its fluxes
+    const int nfc = Ls + 5;
+    cp_async_wait_all();
+    __syncthreads();  // the tile has landed; the previous tile's cells are done with the other buffer
+    if (tile + gridDim.x < tiles) issue_stage(decode(tile + gridDim.x), Wbuf + (buf ^ 1) * Smem<T>::WS);
+    // 2. edge fluxes: edge f lies between staged cells f + 2 and f + 3, so cell c (staged c + 5)
+    //    has edges c .. c + 5 around it.  Item (line, chunk): lane t takes staged cell
+    //    m = 31 chunk + t + 2, evaluates its two edge states, and edge f = m - 2 pairs its
+    //    left state with lane t + 1's right state.
+    T F[ITEMS][5];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const int item = warp * ITEMS + it, l = item >> 1, ch = item & 1;
+      const int f = FCH * ch + lane;
+      if (a0 + l >= na || FCH * ch >= nfc) continue;  // warp-uniform
+      const int m = min(f + 2, nfc + 2);              // centres 2 .. nfc + 2 (stencil <= nst - 1)
       T Lq[5], Rq[5];
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
-        const T* w = Ws + (idx[q] * (LMAX + 10) + f) * NLP + l;
-        const T u0 = w[0], u1 = w[NLP], u2 = w[2 * NLP], u3 = w[3 * NLP], u4 = w[4 * NLP], u5 = w[5 * NLP];
-        Lq[q] = edge<T>(u0, u1, u2, u3, u4, linear);
-        Rq[q] = edge<T>(u5, u4, u3, u2, u1, linear);
+        const T* w = Ws + (idx[q] * (LMAX + 10) + m - 2) * NLP + l;
+        T up, um;
+        edges<T>(w[0], w[NLP], w[2 * NLP], w[3 * NLP], w[4 * NLP], linear, up, um);
+        Lq[q] = up;
+        Rq[q] = __shfl_down_sync(0xffffffffu, um, 1);
       }
-      T F[5];
-      roe_frame<T>(Lq, Rq, K, F);
+      if (lane < FCH && f < nfc) roe_frame<T>(Lq, Rq, K, F[it]);
+    }
+    __syncthreads();  // every lane is done reading the primitives
 #pragma unroll
-      for (int q = 0; q < 5; ++q) Fs[(idx[q] * (LMAX + 5) + f) * NLP + l] = F[q];
+    for (int it = 0; it < ITEMS; ++it) {
+      const int item = warp * ITEMS + it, l = item >> 1, ch = item & 1;
+      const int f = FCH * ch + lane;
+      if (a0 + l >= na || FCH * ch >= nfc || lane >= FCH || f >= nfc) continue;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) Fs[(idx[q] * (LMAX + 5) + f) * NLP + l] = F[it][q];
     }
     __syncthreads();
     // 3. Eq. 2 per cell, minus D4 of the viscous flux along D, then the pass's output
-    for (int e = threadIdx.x; e < Ls * NL; e += NTW) {
+    const int ncell = D == 0 ? NL * 64 : Ls * NL;  // D = 0: a warp per line, lanes along x
+    for (int e = threadIdx.x; e < ncell; e += NTW) {
       int l, c;
-      if (D == 0) { l = e / Ls; c = e % Ls; } else { c = e / NL; l = e % NL; }
+      if (D == 0) {
+        l = e >> 6;
+        c = e & 63;
+        if (c >= Ls) continue;
+      } else {
+        c = e / NL;
+        l = e % NL;
+      }
       if (a0 + l >= na) continue;
       int i, j, k;
-      ijk(l, s0 + c, i, j, k);
+      ijk(t, l, s0 + c, i, j, k);
       const long long cc = ((long long)k * b.ny + j) * b.nx + i;
       T add[5];
 #pragma unroll
@@ -309,7 +428,7 @@ __global__ void __launch_bounds__(NTW) dir_kernel(Args a) {
       } else if (MODE == 1) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) R[q * a.n + cc] = R[q * a.n + cc] + add[q];
-      } else {
+      } else if (sizeof(T) == 8) {  // FP64: Eqs. 4-6 as written
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           const double tot = double(R[q * a.n + cc]) + double(add[q]);
@@ -325,18 +444,40 @@ __global__ void __launch_bounds__(NTW) dir_kernel(Args a) {
           else out = a.qn[q * a.n + cc] / 3.0 + 2.0 / 3.0 * adv;
           a.qout[q * a.n + cc] = out;
         }
+      } else {  // mixed: f32 increments, FP64 only for Q^{n+1} = Q^n + 2/3 (D2 - dt R)
+        const float dtf = float(dt);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const float tot = float(R[q * a.n + cc]) + float(add[q]);
+          const long long o = q * a.n + cc;
+          if (a.stage == 0) {
+            a.rout[o] = f32_to_f64_bits(tot);
+          } else if (a.stage == 1) {
+            ks[q].add(tot * tot);
+            a.d1[o] = -dtf * tot;
+          } else if (a.stage == 2) {
+            a.d2[o] = 0.25f * (a.d1[o] - dtf * tot);
+          } else {
+            const double qn1 = a.q[o] + f32_to_f64_bits((2.0f / 3.0f) * (a.d2[o] - dtf * tot));
+            a.q[o] = qn1;
+            a.sh[o] = f64_to_f32_bits(qn1);
+          }
+        }
       }
     }
   }
   if (MODE != 2 || a.stage != 1) return;
   // residual norm of R(Q^n): per-CTA sums of squares, the last CTA folds them in CTA order
+  if (sizeof(T) == 4)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) sq[q] = double(ks[q].s) - double(ks[q].c);
 #pragma unroll
   for (int q = 0; q < 5; ++q)
     for (int off = 16; off > 0; off >>= 1) sq[q] += __shfl_xor_sync(0xffffffffu, sq[q], off);
   __syncthreads();
-  if ((threadIdx.x & 31) == 0)
+  if (lane == 0)
 #pragma unroll
-    for (int q = 0; q < 5; ++q) red[(threadIdx.x >> 5) * 5 + q] = sq[q];
+    for (int q = 0; q < 5; ++q) red[warp * 5 + q] = sq[q];
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int q = 0; q < 5; ++q) {
@@ -389,7 +530,9 @@ struct gbcfd_wcns_s {
   double h[3];
   int device, nsm, mixed;
   Box box;
-  double* q[3];      // Q^n, Q1, Q2 (compact f64)
+  double* q[3];      // FP64: Q^n, Q1, Q2.  mixed: Q^n only (compact f64)
+  float* sh;         // mixed: S^n = f32(Q^n)
+  float* d[2];       // mixed: D1, D2
   void* W;
   void* Fv;
   void* R;
@@ -412,6 +555,7 @@ struct WLayout {
   int rows;
 };
 
+// FP64: Q^n, Q1, Q2 (f64).  mixed: Q^n (f64) and S^n, D1, D2 (f32) in the same three slots
 bool layout(int nx, int ny, int nz, const gbcfd_params* p, int nsm, WLayout* L) {
   const size_t elem = p->precision == GBCFD_MIXED ? 4 : 8;
   const long long n = (long long)nx * ny * nz;
@@ -423,7 +567,7 @@ bool layout(int nx, int ny, int nz, const gbcfd_params* p, int nsm, WLayout* L) 
   L->box = b;
   L->rows = std::max(nsm * 8, 1024);
   size_t off = 0;
-  L->q = off;       off += 3 * al256((size_t)n * 5 * 8);
+  L->q = off;       off += elem == 8 ? 3 * al256((size_t)n * 5 * 8) : al256((size_t)n * 5 * 8) + 3 * al256((size_t)n * 5 * 4);
   L->w = off;       off += al256((size_t)b.field * NPW * elem);
   L->fv = off;      off += p->viscous ? al256((size_t)b.field * 12 * elem) : 0;
   L->r = off;       off += al256((size_t)n * 5 * elem);
@@ -502,10 +646,17 @@ int run_stage(gbcfd_wcns w, int stage, double* rout, cudaStream_t s) {
   Args a = make_args(w);
   a.stage = stage;
   a.rout = rout;
-  a.qn = w->q[0];
-  if (stage == 0) a.qs = w->q[0];
-  else a.qs = w->q[stage - 1];
-  a.qout = stage == 3 ? w->q[0] : (stage >= 1 ? w->q[stage] : nullptr);
+  if (w->mixed) {
+    a.q = w->q[0];
+    a.sh = w->sh;
+    a.d1 = w->d[0];
+    a.d2 = w->d[1];
+    a.din = stage == 2 ? w->d[0] : (stage == 3 ? w->d[1] : nullptr);
+  } else {
+    a.qn = w->q[0];
+    a.qs = stage <= 1 ? w->q[0] : w->q[stage - 1];
+    a.qout = stage == 3 ? w->q[0] : (stage >= 1 ? w->q[stage] : nullptr);
+  }
   const cudaEvent_t* ev = (w->timing && stage >= 1) ? w->events + 6 * (stage - 1) : nullptr;
   const cudaError_t e = w->mixed ? launch_pass<float>(w, a, stage == 1, ev, s) : launch_pass<double>(w, a, stage == 1, ev, s);
   if (e != cudaSuccess) return cuda_err(e, "WCNS stage launch");
@@ -559,8 +710,18 @@ extern "C" int gbcfd_wcns_create(int nx, int ny, int nz, const gbcfd_params* par
   w->mixed = mixed;
   w->box = L.box;
   char* base = static_cast<char*>(dev_mem);
-  const size_t qbytes = al256((size_t)nx * ny * nz * 5 * 8);
-  for (int s = 0; s < 3; ++s) w->q[s] = reinterpret_cast<double*>(base + L.q + s * qbytes);
+  const size_t qbytes = al256((size_t)nx * ny * nz * 5 * 8), fbytes = al256((size_t)nx * ny * nz * 5 * 4);
+  if (mixed) {
+    w->q[0] = reinterpret_cast<double*>(base + L.q);
+    w->q[1] = w->q[2] = nullptr;
+    w->sh = reinterpret_cast<float*>(base + L.q + qbytes);
+    w->d[0] = reinterpret_cast<float*>(base + L.q + qbytes + fbytes);
+    w->d[1] = reinterpret_cast<float*>(base + L.q + qbytes + 2 * fbytes);
+  } else {
+    for (int s = 0; s < 3; ++s) w->q[s] = reinterpret_cast<double*>(base + L.q + s * qbytes);
+    w->sh = nullptr;
+    w->d[0] = w->d[1] = nullptr;
+  }
   w->W = base + L.w;
   w->Fv = params->viscous ? base + L.fv : nullptr;
   w->R = base + L.r;
@@ -591,6 +752,11 @@ extern "C" int gbcfd_wcns_set_state(gbcfd_wcns w, const double* q, void* stream)
   const size_t n = (size_t)w->nx * w->ny * w->nz;
   cudaError_t e = cudaMemcpyAsync(w->q[0], q, n * 5 * sizeof(double), cudaMemcpyDefault, s);
   if (e != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
+  if (w->mixed) {
+    shadow_kernel<<<w->nsm * 8, 256, 0, s>>>(w->q[0], w->sh, (long long)n * 5);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(e, "shadow kernel launch");
+  }
   e = cudaMemsetAsync(w->ctrl, 0, sizeof(DevCtrl), s);
   if (e != cudaSuccess) return cuda_err(e, "cudaMemsetAsync");
   w->has_state = 1;
