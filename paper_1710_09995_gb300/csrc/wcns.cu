@@ -8,14 +8,15 @@
 //                self-connected block); stage 1 also reduces the CFL rate of Q^n to the step's
 //                time step.
 //   visc_kernel  (Navier-Stokes) the viscous flux vectors Fv, Gv, Hv of Eq. 1 at every cell of
-//                the box padded by 2, from fourth-order central gradients (D4) of u, v, w, theta.
+//                the box padded by 2, from fourth-order central gradients (D4) of u, v, w, theta;
+//   viscdiv_kernel  their derivatives, Rv = -(D4_x Fv + D4_y Gv + D4_z Hv), at the interior cells.
 //   dir_kernel<D> for D = x, y, z: a tile of 16 lines x L cells along D.  The tile's primitives
 //                (L + 10 cells per line) go to shared memory; a lane per cell evaluates both edge
 //                values of its cell (the two share the stencils' smoothness indicators), a shuffle
 //                pairs the left state of cell i with the right state of cell i + 1, and the Roe
 //                flux of every edge of the tile (L + 5 per line) is computed once; the fluxes
 //                replace the primitives in shared memory and each cell takes Eq. 2 of its six
-//                edge fluxes minus D4 of its viscous flux along D.  x writes R, y adds to it, z
+//                edge fluxes (the x pass also adds Rv).  x writes R, y adds to it, z
 //                adds and applies the stage update (or writes R out), with the residual norm of
 //                stage 1 reduced per CTA and by the last CTA in a fixed order.
 // Precision: FP64 everywhere, or mixed: the stage inputs are the f32 shadow S^n of Q^n plus an
@@ -69,6 +70,7 @@ struct Args {
   void* W;                  // NPW padded fields (T)
   void* Fv;                 // 12 padded fields (T): [d][mx, my, mz, energy]
   void* R;                  // compact [5][n] (T): the residual accumulated over the passes
+  void* Rv;                 // compact [4][n] (T): the viscous part, -sum_d D4_d(F_v,d) (momentum, energy)
   // FP64 path
   const double* qn;         // Q^n (compact f64)
   const double* qs;         // the stage input
@@ -172,46 +174,203 @@ __global__ void shadow_kernel(const double* __restrict__ q, float* __restrict__ 
 }
 
 // ---- viscous flux vectors at the cells of the box padded by 2 ------------------------------
+// asynchronous global -> shared copy of one element (cp.async, completes by group)
 template <typename T>
-__device__ __forceinline__ T d4(const T* f, long long o, long long st, T ih) {
-  // (f_{-2} - 8 f_{-1} + 8 f_{+1} - f_{+2}) / (12 h)
-  return ((f[o - 2 * st] - f[o + 2 * st]) + T(8) * (f[o + st] - f[o - st])) * (ih * T(1.0 / 12.0));
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// The viscous kernel works on tiles of VX x VY cells of the box padded by 2, marching in z over
+// chunks of VZ planes; the planes of u, v, w, theta it reads (the tile plus 2 cells around, k-2 ..
+// k+2) sit in a 6-slot shared ring, and plane k+3 lands by cp.async while plane k is computed.
+constexpr int VX = 32, VY = 8, VZ = 32, VBX = VX + 4, VBY = VY + 4, VRING = 6;
+template <typename T>
+struct VSmem {
+  static constexpr int PLANE = 4 * VBY * VBX;  // u, v, w, theta of one plane's box
+  static constexpr size_t bytes = sizeof(T) * VRING * PLANE;
+};
 
 template <typename T>
 __global__ void __launch_bounds__(NTW) visc_kernel(Args a) {
+  extern __shared__ __align__(16) unsigned char vsm[];
+  T* ring = reinterpret_cast<T*>(vsm);
   const Box& b = a.b;
-  const int wx = b.nx + 4, wy = b.ny + 4, wz = b.nz + 4;
   const T* W = static_cast<const T*>(a.W);
   T* F = static_cast<T*>(a.Fv);
   const T mu = T(a.mu), kappa = T(a.mu * a.gamma / ((a.gamma - 1.0) * a.Pr));
-  const T ih[3] = {T(a.ih[0]), T(a.ih[1]), T(a.ih[2])};
-  const long long st[3] = {1, b.px, (long long)b.px * (b.ny + 2 * H)};
-  for (int row = blockIdx.x; row < wy * wz; row += gridDim.x)  // rows (j, k) of the box padded by 2
-  for (int i = (int)threadIdx.x - 2; i < wx - 2; i += NTW) {
-    const int j = row % wy - 2, k = row / wy - 2;
-    const long long o = bidx(b, i, j, k);
-    T g[3][3], gt[3], vel[3];
+  const T ih[3] = {T(a.ih[0] / 12.0), T(a.ih[1] / 12.0), T(a.ih[2] / 12.0)};
+  const int ex = b.nx + 4, ey = b.ny + 4, ez = b.nz + 4;  // the output box: [-2, n + 2) each way
+  const int ntx = (ex + VX - 1) / VX, nty = (ey + VY - 1) / VY, nch = (ez + VZ - 1) / VZ;
+  const int units = ntx * nty * nch;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int ch = u % nch, t = u / nch;
+    const int x0 = (t % ntx) * VX - 2, y0 = (t / ntx) * VY - 2;  // first output cell of the tile
+    const int kb = ch * VZ - 2, ke = min(kb + VZ, b.nz + 2);
+    // plane kp of the box (cells x0-2 .. x0+VX+1, y0-2 .. y0+VY+1) into its ring slot
+    auto load_plane = [&](int kp) {  // rows of 36 cells: 4 fields x 12 rows, a warp per row
+      T* dst = ring + ((kp + 16 * VRING) % VRING) * VSmem<T>::PLANE;
+      for (int r = warp; r < 4 * VBY; r += NTW / 32) {
+        const int f = r / VBY, j = y0 - 2 + (r - f * VBY);
+        T* drow = dst + r * VBX;
+        const T* srow = W + (long long)(f < 3 ? 1 + f : 5) * b.field +  // u, v, w, theta
+                        (((kp + H) * (b.ny + 2 * H) + j + H) * b.px + x0 - 2 + H);
+        for (int cx = lane; cx < VBX; cx += 32) {
+          if (x0 - 2 + cx < b.nx + H && j < b.ny + H) cp_async(drow + cx, srow + cx);  // i, j >= -4
+          else drow[cx] = T(0);
+        }
+      }
+      cp_async_commit();
+    };
+    __syncthreads();  // the previous unit is done with the ring
+    for (int kp = kb - 2; kp <= kb + 2; ++kp) load_plane(kp);
+    for (int k = kb; k < ke; ++k) {
+      load_plane(k + 3);   // one plane ahead (into the slot of plane k - 3, no longer read)
+      cp_async_wait_one(); // everything but that plane has landed
+      __syncthreads();
+      const int i = x0 + lane, j = y0 + warp;
+      if (i < b.nx + 2 && j < b.ny + 2) {
+        const int c = (warp + 2) * VBX + lane + 2;
+        const T* pl[5];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      vel[q] = W[(1 + q) * b.field + o];
+        for (int m = 0; m < 5; ++m) pl[m] = ring + ((k - 2 + m + 16 * VRING) % VRING) * VSmem<T>::PLANE;
+        T g[4][3], vel[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) g[q][d] = d4(W + (1 + q) * b.field, o, st[d], ih[d]);
-    }
+        for (int f = 0; f < 4; ++f) {
+          const T* p0 = pl[2] + f * VBY * VBX;
+          if (f < 3) vel[f] = p0[c];
+          g[f][0] = ((p0[c - 2] - p0[c + 2]) + T(8) * (p0[c + 1] - p0[c - 1])) * ih[0];
+          g[f][1] = ((p0[c - 2 * VBX] - p0[c + 2 * VBX]) + T(8) * (p0[c + VBX] - p0[c - VBX])) * ih[1];
+          const int o = f * VBY * VBX + c;
+          g[f][2] = ((pl[0][o] - pl[4][o]) + T(8) * (pl[3][o] - pl[1][o])) * ih[2];
+        }
+        const T div = g[0][0] + g[1][1] + g[2][2];
+        const long long o = bidx(b, i, j, k);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) gt[d] = d4(W + 5 * b.field, o, st[d], ih[d]);
-    const T div = g[0][0] + g[1][1] + g[2][2];
+        for (int d = 0; d < 3; ++d) {
+          T tau[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T tau[3];
+          for (int q = 0; q < 3; ++q) tau[q] = mu * (g[q][d] + g[d][q]);
+          tau[d] = tau[d] - T(2.0 / 3.0) * mu * div;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) tau[q] = mu * (g[q][d] + g[d][q]);
-      tau[d] = tau[d] - T(2.0 / 3.0) * mu * div;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) F[(4 * d + q) * b.field + o] = tau[q];
-      F[(4 * d + 3) * b.field + o] = vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kappa * gt[d];
+          for (int q = 0; q < 3; ++q) F[(4 * d + q) * b.field + o] = tau[q];
+          F[(4 * d + 3) * b.field + o] = vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kappa * g[3][d];
+        }
+      }
+      __syncthreads();  // plane k-2's slot is refilled next
     }
   }
+  cp_async_wait_all();
+}
+
+// ---- the viscous residual: Rv = -(D4_x Fv + D4_y Gv + D4_z Hv) at the interior cells ----------
+// Tiles of 32 x 8 cells marching in z over each CTA's contiguous share of tile-planes.  Per plane
+// k the x-fluxes of the tile's rows plus 2 cells each side, the y-fluxes of its columns plus 2
+// rows each side (double-buffered) and the z-fluxes of planes k-2 .. k+2 (a 6-slot ring) are in
+// shared memory; the copies for plane k+1 run while plane k is computed.
+constexpr int DX = 32, DY = 8, DRING = 6;
+template <typename T>
+struct DSmem {
+  static constexpr int FX = 4 * DY * (DX + 4);    // Fv of rows y0..y0+7, x0-2 .. x0+33
+  static constexpr int GY = 4 * (DY + 4) * DX;    // Gv of columns x0..x0+31, y0-2 .. y0+9
+  static constexpr int HZ = 4 * DY * DX;          // Hv of the tile, one plane
+  static constexpr int XY = FX + GY;
+  static constexpr size_t bytes = sizeof(T) * (2 * XY + DRING * HZ);
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NTW) viscdiv_kernel(Args a) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* xy = reinterpret_cast<T*>(dsm);            // 2 buffers of [FX | GY]
+  T* hz = xy + 2 * DSmem<T>::XY;                 // DRING planes of HZ
+  const Box& b = a.b;
+  const T* F = static_cast<const T*>(a.Fv);
+  T* Rv = static_cast<T*>(a.Rv);
+  const T ih[3] = {T(a.ih[0] / 12.0), T(a.ih[1] / 12.0), T(a.ih[2] / 12.0)};
+  const int ntx = (b.nx + DX - 1) / DX, nty = (b.ny + DY - 1) / DY;
+  const long long units = (long long)ntx * nty * b.nz;
+  const long long u0 = (long long)blockIdx.x * units / gridDim.x, u1 = (long long)(blockIdx.x + 1) * units / gridDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto hslot = [](int kp) { return (kp + 4 * DRING) % DRING; };
+  for (long long u = u0; u < u1;) {
+    const long long tile = u / b.nz;
+    const int k0 = (int)(u - tile * b.nz);
+    const int k1 = (int)min((long long)b.nz, k0 + (u1 - u));
+    u += k1 - k0;
+    const int x0 = (int)(tile % ntx) * DX, y0 = (int)(tile / ntx) * DY;
+    // rows of the flux boxes, a warp per row; the offsets within a field fit 32 bits
+    auto row_off = [&](int j, int k, int i) { return ((k + H) * (b.ny + 2 * H) + j + H) * b.px + i + H; };
+    auto load_xy = [&](int k, T* dst) {  // x-fluxes (4 comps) of the rows, y-fluxes of the columns
+      for (int r = warp; r < 4 * DY; r += NTW / 32) {
+        const int q = r / DY, j = y0 + (r - q * DY);
+        T* drow = dst + r * (DX + 4);
+        const T* srow = F + (long long)q * b.field + row_off(j, k, x0 - 2);
+        for (int cx = lane; cx < DX + 4; cx += 32) {
+          if (x0 - 2 + cx < b.nx + 2 && j < b.ny) cp_async(drow + cx, srow + cx);
+          else drow[cx] = T(0);
+        }
+      }
+      for (int r = warp; r < 4 * (DY + 4); r += NTW / 32) {
+        const int q = r / (DY + 4), j = y0 - 2 + (r - q * (DY + 4));
+        T* drow = dst + DSmem<T>::FX + r * DX;
+        const T* srow = F + (long long)(4 + q) * b.field + row_off(j, k, x0);
+        if (x0 + lane < b.nx && j < b.ny + 2) cp_async(drow + lane, srow + lane);
+        else drow[lane] = T(0);
+      }
+    };
+    auto load_z = [&](int kp) {  // z-fluxes of the tile at plane kp
+      T* dst = hz + hslot(kp) * DSmem<T>::HZ;
+      for (int r = warp; r < 4 * DY; r += NTW / 32) {
+        const int q = r / DY, j = y0 + (r - q * DY);
+        T* drow = dst + r * DX;
+        const T* srow = F + (long long)(8 + q) * b.field + row_off(j, kp, x0);
+        if (x0 + lane < b.nx && j < b.ny) cp_async(drow + lane, srow + lane);
+        else drow[lane] = T(0);
+      }
+    };
+    __syncthreads();  // the previous segment is done with the buffers
+    for (int kp = k0 - 2; kp <= k0 + 2; ++kp) load_z(kp);
+    load_xy(k0, xy);
+    cp_async_commit();
+    for (int k = k0; k < k1; ++k) {
+      const int cur = (k - k0) & 1;
+      if (k + 1 < k1) {  // plane k+1: its x/y fluxes and the z-fluxes of plane k+3
+        load_xy(k + 1, xy + (cur ^ 1) * DSmem<T>::XY);
+        load_z(k + 3);
+        cp_async_commit();
+        cp_async_wait_one();
+      } else {
+        cp_async_wait_all();
+      }
+      __syncthreads();
+      const int i = x0 + lane, j = y0 + warp;
+      if (i < b.nx && j < b.ny) {
+        const T* fx = xy + cur * DSmem<T>::XY;
+        const T* gy = fx + DSmem<T>::FX;
+        const long long c = ((long long)k * b.ny + j) * b.nx + i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const T* f = fx + (q * DY + warp) * (DX + 4) + lane + 2;
+          const T dx = (f[-2] - f[2]) + T(8) * (f[1] - f[-1]);
+          const T* g = gy + (q * (DY + 4) + warp + 2) * DX + lane;
+          const T dy = (g[-2 * DX] - g[2 * DX]) + T(8) * (g[DX] - g[-DX]);
+          const int o = q * DY * DX + warp * DX + lane;
+          const T dz = (hz[hslot(k - 2) * DSmem<T>::HZ + o] - hz[hslot(k + 2) * DSmem<T>::HZ + o]) +
+                       T(8) * (hz[hslot(k + 1) * DSmem<T>::HZ + o] - hz[hslot(k - 1) * DSmem<T>::HZ + o]);
+          Rv[q * a.n + c] = -(dx * ih[0] + dy * ih[1] + dz * ih[2]);
+        }
+      }
+      __syncthreads();  // the buffers of plane k (and z-plane k-2) are refilled next
+    }
+  }
+  cp_async_wait_all();
 }
 
 // ---- the weighted interpolation: both edge values of cell i from u_{i-2} .. u_{i+2} -----------
@@ -259,17 +418,7 @@ struct Smem {
   static constexpr size_t bytes = red + sizeof(double) * (NTW / 32) * 5;
 };
 
-// asynchronous global -> shared copy of one element (cp.async, completes by group)
-template <typename T>
-__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  if (sizeof(T) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 
 // Kahan-compensated running sum (the mixed path's per-thread sums of squares)
 struct KSum {
@@ -283,7 +432,7 @@ struct KSum {
 
 // MODE: 0 x pass (R =), 1 y pass (R +=), 2 z pass (stage update or residual output)
 template <typename T, int D, int MODE>
-__global__ void __launch_bounds__(NTW) dir_kernel(Args a) {
+__global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a) {
   using O = VM<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* const Wbuf = reinterpret_cast<T*>(smem_raw);
@@ -296,9 +445,7 @@ __global__ void __launch_bounds__(NTW) dir_kernel(Args a) {
   const int L = a.Lseg[D];
   const int nseg = (nd + L - 1) / L, ngrp = (na + NL - 1) / NL;
   const long long tiles = (long long)nseg * ngrp * nb;
-  const long long stD = D == 0 ? 1 : (D == 1 ? b.px : (long long)b.px * (b.ny + 2 * H));
   const T* W = static_cast<const T*>(a.W);
-  const T* Fv = static_cast<const T*>(a.Fv);
   T* R = static_cast<T*>(a.R);
   const Consts<T> K = make_consts<T>(a.gamma, a.eps, a.mu, a.Pr, 0);
   const T ih = T(a.ih[D]);
@@ -320,7 +467,7 @@ __global__ void __launch_bounds__(NTW) dir_kernel(Args a) {
     return t;
   };
   // cell (line l, position s along D) of tile t -> (i, j, k)
-  auto ijk = [&](const TileInfo& t, int l, int s, int& i, int& j, int& k) {
+  auto ijk = [&](const TileInfo& t, int l, int s, int& i, int& j, int& k) {  // (the cell phase)
     if (D == 0) { i = s; j = t.a0 + l; k = t.ob; }
     else if (D == 1) { i = t.a0 + l; j = s; k = t.ob; }
     else { i = t.a0 + l; j = t.ob; k = s; }
@@ -329,22 +476,33 @@ __global__ void __launch_bounds__(NTW) dir_kernel(Args a) {
   //    (staged cell s is cell s0 - 5 + s), asynchronously, as one commit group
   auto issue_stage = [&](const TileInfo& t, T* Ws) {
     const int nst = t.Ls + 10;
-    auto stage_one = [&](int v, int l, int s) {
-      T* dst = Ws + (v * (LMAX + 10) + s) * NLP + l;
-      if (t.a0 + l < na) {
-        int i, j, k;
-        ijk(t, l, t.s0 - H + s, i, j, k);
-        cp_async(dst, W + (long long)v * b.field + bidx(b, i, j, k));
-      } else {
-        *dst = (v == 0 || v == 4) ? T(1) : T(0);  // lines past the block: any physical state
-      }
+    // offset of cell (line l, position s along D) within a field (fits 32 bits)
+    auto off = [&](int l, int s) {
+      if (D == 0) return ((t.ob + H) * (b.ny + 2 * H) + t.a0 + l + H) * b.px + s + H;
+      if (D == 1) return ((t.ob + H) * (b.ny + 2 * H) + s + H) * b.px + t.a0 + l + H;
+      return ((s + H) * (b.ny + 2 * H) + t.ob + H) * b.px + t.a0 + l + H;
     };
     if (D == 0) {  // a warp per (variable, line), lanes along x
-      for (int vl = warp; vl < 5 * NL; vl += NTW / 32)
-        for (int s = lane; s < nst; s += 32) stage_one(vl / NL, vl % NL, s);
+      for (int vl = warp; vl < 5 * NL; vl += NTW / 32) {
+        const int v = vl / NL, l = vl % NL;
+        T* drow = Ws + v * (LMAX + 10) * NLP + l;
+        if (t.a0 + l < na) {
+          const T* srow = W + (long long)v * b.field + off(l, t.s0 - H);
+          for (int s = lane; s < nst; s += 32) cp_async(drow + s * NLP, srow + s);
+        } else {
+          for (int s = lane; s < nst; s += 32) drow[s * NLP] = (v == 0 || v == 4) ? T(1) : T(0);
+        }
+      }
     } else {       // 16 lines (x) per row s
-      for (int v = 0; v < 5; ++v)
-        for (int e = threadIdx.x; e < nst * NL; e += NTW) stage_one(v, e % NL, e / NL);
+      for (int v = 0; v < 5; ++v) {
+        const T* src = W + (long long)v * b.field;
+        T* dv = Ws + v * (LMAX + 10) * NLP;
+        for (int e = threadIdx.x; e < nst * NL; e += NTW) {
+          const int s = e / NL, l = e % NL;
+          if (t.a0 + l < na) cp_async(dv + s * NLP + l, src + off(l, t.s0 - H + s));
+          else dv[s * NLP + l] = (v == 0 || v == 4) ? T(1) : T(0);  // lines past the block
+        }
+      }
     }
     cp_async_commit();
   };
@@ -414,13 +572,10 @@ __global__ void __launch_bounds__(NTW) dir_kernel(Args a) {
         const T f0 = fq[0], f1 = fq[NLP], f2 = fq[2 * NLP], f3 = fq[3 * NLP], f4 = fq[4 * NLP], f5 = fq[5 * NLP];
         add[q] = (O::c(75.0 / 64.0) * (f3 - f2) - O::c(25.0 / 384.0) * (f4 - f1) + O::c(3.0 / 640.0) * (f5 - f0)) * ih;
       }
-      if (a.viscous) {
-        const long long o = bidx(b, i, j, k);
+      if (D == 0 && a.viscous) {  // the viscous residual, once (x pass)
+        const T* rv = static_cast<const T*>(a.Rv);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const T* fv = Fv + (long long)(4 * D + q) * b.field;
-          add[1 + q] = add[1 + q] - d4(fv, o, stD, ih);
-        }
+        for (int q = 0; q < 4; ++q) add[1 + q] = add[1 + q] + rv[q * a.n + cc];
       }
       if (MODE == 0) {
 #pragma unroll
@@ -508,7 +663,25 @@ static cudaError_t set_smem() {
   if (e != cudaSuccess) return e;
   GB_SET(0, 0) GB_SET(1, 1) GB_SET(2, 2)
 #undef GB_SET
+  e = cudaFuncSetAttribute(visc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)VSmem<T>::bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(viscdiv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DSmem<T>::bytes);
+  if (e != cudaSuccess) return e;
   return cudaSuccess;
+}
+
+template <typename T>
+static int visc_occupancy() {
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, visc_kernel<T>, NTW, VSmem<T>::bytes);
+  return std::max(1, occ);
+}
+
+template <typename T>
+static int viscdiv_occupancy() {
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, viscdiv_kernel<T>, NTW, DSmem<T>::bytes);
+  return std::max(1, occ);
 }
 
 template <typename T>
@@ -535,12 +708,13 @@ struct gbcfd_wcns_s {
   float* d[2];       // mixed: D1, D2
   void* W;
   void* Fv;
+  void* Rv;
   void* R;
   DevCtrl* ctrl;
   double* partial;
   int rows;          // partial rows (CTAs of the widest launch)
   int has_state;
-  int dir_grid, occ;
+  int dir_grid, occ, vocc, docc;
   cudaEvent_t events[18];  // timing marks (gbcfd_wcns_set_timing), 6 per stage
   int timing;
 };
@@ -550,7 +724,7 @@ namespace {
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WLayout {
-  size_t q, w, fv, r, ctrl, partial, total;
+  size_t q, w, fv, rv, r, ctrl, partial, total;
   Box box;
   int rows;
 };
@@ -570,6 +744,7 @@ bool layout(int nx, int ny, int nz, const gbcfd_params* p, int nsm, WLayout* L) 
   L->q = off;       off += elem == 8 ? 3 * al256((size_t)n * 5 * 8) : al256((size_t)n * 5 * 8) + 3 * al256((size_t)n * 5 * 4);
   L->w = off;       off += al256((size_t)b.field * NPW * elem);
   L->fv = off;      off += p->viscous ? al256((size_t)b.field * 12 * elem) : 0;
+  L->rv = off;      off += p->viscous ? al256((size_t)n * 4 * elem) : 0;
   L->r = off;       off += al256((size_t)n * 5 * elem);
   L->ctrl = off;    off += al256(sizeof(DevCtrl));
   L->partial = off; off += al256((size_t)L->rows * NPART * sizeof(double));
@@ -608,6 +783,7 @@ Args make_args(gbcfd_wcns w) {
   a.linear = w->p.limiter;
   a.W = w->W;
   a.Fv = w->Fv;
+  a.Rv = w->Rv;
   a.R = w->R;
   a.ctrl = w->ctrl;
   a.partial = w->partial;
@@ -628,7 +804,10 @@ cudaError_t launch_pass(gbcfd_wcns w, Args a, int with_rate, const cudaEvent_t* 
   mark(0);
   prim_kernel<T><<<pgrid, NTW, 0, s>>>(a, with_rate);
   mark(1);
-  if (a.viscous) visc_kernel<T><<<w->nsm * 8, NTW, 0, s>>>(a);
+  if (a.viscous) {
+    visc_kernel<T><<<w->nsm * w->vocc, NTW, VSmem<T>::bytes, s>>>(a);
+    viscdiv_kernel<T><<<w->nsm * w->docc, NTW, DSmem<T>::bytes, s>>>(a);
+  }
   mark(2);
   const size_t sm = Smem<T>::bytes;
   const int g = w->dir_grid;
@@ -698,6 +877,8 @@ extern "C" int gbcfd_wcns_create(int nx, int ny, int nz, const gbcfd_params* par
   layout(nx, ny, nz, params, nsm, &L);
   if (bytes < L.total)
     return set_error(GBCFD_ERR_MEMORY, "caller memory too small: need " + std::to_string(L.total) + " bytes");
+  if (L.box.field >= (1LL << 31))
+    return set_error(GBCFD_ERR_ARG, "WCNS block too large: the padded box must hold fewer than 2^31 cells");
   const bool mixed = params->precision == GBCFD_MIXED;
   e = mixed ? set_smem<float>() : set_smem<double>();
   if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute");
@@ -724,11 +905,14 @@ extern "C" int gbcfd_wcns_create(int nx, int ny, int nz, const gbcfd_params* par
   }
   w->W = base + L.w;
   w->Fv = params->viscous ? base + L.fv : nullptr;
+  w->Rv = params->viscous ? base + L.rv : nullptr;
   w->R = base + L.r;
   w->ctrl = reinterpret_cast<DevCtrl*>(base + L.ctrl);
   w->partial = reinterpret_cast<double*>(base + L.partial);
   w->rows = L.rows;
   w->occ = mixed ? dir_occupancy<float>() : dir_occupancy<double>();
+  w->vocc = mixed ? visc_occupancy<float>() : visc_occupancy<double>();
+  w->docc = mixed ? viscdiv_occupancy<float>() : viscdiv_occupancy<double>();
   w->dir_grid = std::min(w->rows, nsm * w->occ);
   e = cudaMemset(w->ctrl, 0, sizeof(DevCtrl));
   if (e != cudaSuccess) {
