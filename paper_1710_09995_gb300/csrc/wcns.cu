@@ -31,9 +31,13 @@
 #include <cstring>
 #include <string>
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "gbcfd.h"
 #include "launch.h"
-#include "physics.cuh"
+#include "stage.cuh"  // mbarrier / TMA helpers (and the shared physics)
 
 namespace gbcfd {
 namespace wcns {
@@ -61,7 +65,22 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i;
 }
 
+// the physical and grid coefficients every kernel needs, computed once on the host in the path's
+// precision (no FP64 arithmetic in an FP32 kernel: it is slow on this part)
+template <typename T>
+struct Coef {
+  T gm1, gam, half, vf;      // gamma - 1, gamma, 1/2, 4 max(4/3, gamma/Pr) mu (viscous rate)
+  T mu, kappa;               // viscosity, heat conductivity mu gamma / ((gamma - 1) Pr)
+  T ih[3], ih12[3], ihs;     // inverse cell sizes, the same / 12, sum of their squares
+  Consts<T> K;               // the Roe / viscous flux constants
+};
+
 struct Args {
+  Coef<float> cf;
+  Coef<double> cd;
+  CUtensorMap mw;           // W: 6 padded fields, box 40 x 12 x 1 x 1 (one field's plane box)
+  CUtensorMap mf8;          // Fv: 12 padded fields, box 40 x 8 x 1 x 4 (x- or z-fluxes of a tile)
+  CUtensorMap mf12;         // Fv: box 40 x 12 x 1 x 4 (y-fluxes of a tile and 2 rows each side)
   Box b;
   long long n;              // interior cells
   double gamma, mu, Pr, cfl, eps;
@@ -88,6 +107,10 @@ struct Args {
   int Lseg[3];              // cells per line segment along x, y, z
 };
 
+template <typename T> __device__ __forceinline__ const Coef<T>& coef(const Args& a);
+template <> __device__ __forceinline__ const Coef<float>& coef<float>(const Args& a) { return a.cf; }
+template <> __device__ __forceinline__ const Coef<double>& coef<double>(const Args& a) { return a.cd; }
+
 // ---- primitives of the padded box (and the time step of Q^n) -------------------------------
 template <typename T>
 __device__ __forceinline__ void load_conserved(const Args& a, long long c, T* U);
@@ -109,10 +132,10 @@ __global__ void __launch_bounds__(NTW) prim_kernel(Args a, int with_rate) {
   const Box& b = a.b;
   const int wx = b.nx + 2 * H, wy = b.ny + 2 * H, wz = b.nz + 2 * H;
   T* W = static_cast<T*>(a.W);
-  const T gm1 = T(a.gamma - 1.0), gam = T(a.gamma), half = T(0.5);
-  const T vf = T(4.0 * fmax(4.0 / 3.0, a.gamma / a.Pr) * a.mu);
-  const T ih0 = T(a.ih[0]), ih1 = T(a.ih[1]), ih2 = T(a.ih[2]);
-  const T ihs = T(a.ih[0] * a.ih[0] + a.ih[1] * a.ih[1] + a.ih[2] * a.ih[2]);
+  using O = VM<T>;
+  const Coef<T>& C = coef<T>(a);
+  const T gm1 = C.gm1, gam = C.gam, half = C.half, vf = C.vf;
+  const T ih0 = C.ih[0], ih1 = C.ih[1], ih2 = C.ih[2], ihs = C.ihs;
   T best = T(0);
   bool bad = false;
   for (int row = blockIdx.x; row < wy * wz; row += gridDim.x) {  // rows (j, k) of the padded box
@@ -137,18 +160,21 @@ __global__ void __launch_bounds__(NTW) prim_kernel(Args a, int with_rate) {
       dst[5 * b.field + ii] = p * ir;
       if (with_rate && inner_row && i == si) {  // each interior cell once
         if (!(rho > T(0) && p > T(0))) bad = true;
-        const T cs = sqrt(gam * p * ir);
-        T rate = (fabs(u) + cs) * ih0 + (fabs(v) + cs) * ih1 + (fabs(w) + cs) * ih2;
+        const T c2 = gam * p * ir;
+        const T cs = c2 * O::rsqrt(c2);
+        T rate = (O::ab(u) + cs) * ih0 + (O::ab(v) + cs) * ih1 + (O::ab(w) + cs) * ih2;
         if (a.viscous) rate += vf * ir * ihs;
-        best = fmax(best, rate);
+        best = best > rate ? best : rate;
       }
     }
   }
   if (!with_rate) return;
   if (bad) atomicOr(&a.ctrl->flag, FLAG_NONPHYSICAL);
-  double bd = double(best);
-  for (int off = 16; off > 0; off >>= 1) bd = fmax(bd, __shfl_xor_sync(0xffffffffu, bd, off));
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = bd;
+  for (int off = 16; off > 0; off >>= 1) {
+    const T o = __shfl_xor_sync(0xffffffffu, best, off);
+    best = best > o ? best : o;
+  }
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = double(best);
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = 0.0;
@@ -187,68 +213,96 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// The viscous kernel works on tiles of VX x VY cells of the box padded by 2, marching in z over
-// chunks of VZ planes; the planes of u, v, w, theta it reads (the tile plus 2 cells around, k-2 ..
-// k+2) sit in a 6-slot shared ring, and plane k+3 lands by cp.async while plane k is computed.
-constexpr int VX = 32, VY = 8, VZ = 32, VBX = VX + 4, VBY = VY + 4, VRING = 6;
+// The viscous kernel works on tiles of VX x VY output cells of the box padded by 2, marching in z
+// over chunks of VZ planes.  The planes it reads (u, v, w, theta of the tile plus 2 cells around,
+// k-2 .. k+2) sit in a 6-slot shared ring; one thread loads each plane as four TMA boxes of 40 x 12
+// cells (starting at a 16-byte aligned column) while the other planes are computed.
+constexpr int VX = 32, VY = 8, VZ = 32, VBX = 40, VBY = 12, VRING = 6;
 template <typename T>
 struct VSmem {
-  static constexpr int PLANE = 4 * VBY * VBX;  // u, v, w, theta of one plane's box
-  static constexpr size_t bytes = sizeof(T) * VRING * PLANE;
+  static constexpr int FIELD = VBY * VBX;             // one field's box
+  static constexpr int PLANE = 4 * FIELD;             // u, v, w, theta
+  static constexpr size_t bar = sizeof(T) * VRING * PLANE;
+  static constexpr size_t bytes = bar + 8 * VRING + 16;
 };
 
+// drain the copies of a CTA that stops early (bounded), flag the timeout
+__device__ __forceinline__ void tma_abort(uint64_t* bar, unsigned pending, unsigned parity, int nslot, DevCtrl* ctrl) {
+  for (int q = 0; q < nslot; ++q)
+    if (pending & (1u << q)) mbar_wait_bounded(&bar[q], (parity >> q) & 1u);
+  atomicOr(&ctrl->flag, FLAG_TIMEOUT);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(NTW) visc_kernel(Args a) {
-  extern __shared__ __align__(16) unsigned char vsm[];
+__global__ void __launch_bounds__(NTW) visc_kernel(const __grid_constant__ Args a) {
+  extern __shared__ __align__(128) unsigned char vsm[];
   T* ring = reinterpret_cast<T*>(vsm);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(vsm + VSmem<T>::bar);
+  int* sabort = reinterpret_cast<int*>(bar + VRING);
   const Box& b = a.b;
-  const T* W = static_cast<const T*>(a.W);
   T* F = static_cast<T*>(a.Fv);
-  const T mu = T(a.mu), kappa = T(a.mu * a.gamma / ((a.gamma - 1.0) * a.Pr));
-  const T ih[3] = {T(a.ih[0] / 12.0), T(a.ih[1] / 12.0), T(a.ih[2] / 12.0)};
+  const Coef<T>& C = coef<T>(a);
+  const T mu = C.mu, kappa = C.kappa;
+  const T* ih = C.ih12;
   const int ex = b.nx + 4, ey = b.ny + 4, ez = b.nz + 4;  // the output box: [-2, n + 2) each way
   const int ntx = (ex + VX - 1) / VX, nty = (ey + VY - 1) / VY, nch = (ez + VZ - 1) / VZ;
   const int units = ntx * nty * nch;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < VRING; ++q) mbar_init(&bar[q], 1);
+    fence_barrier_init();
+    *sabort = 0;
+  }
+  __syncthreads();
+  unsigned parity = 0, pending = 0;  // per slot (parity uniform across threads; pending in thread 0)
+  auto slot = [](int kp) { return (kp + 16 * VRING) % VRING; };
+  for (int u = blockIdx.x; u < units && !*sabort; u += gridDim.x) {
     const int ch = u % nch, t = u / nch;
-    const int x0 = (t % ntx) * VX - 2, y0 = (t / ntx) * VY - 2;  // first output cell of the tile
+    const int tx = t % ntx, ty = t / ntx;
+    const int x0 = tx * VX - 2, y0 = ty * VY - 2;  // first output cell of the tile
     const int kb = ch * VZ - 2, ke = min(kb + VZ, b.nz + 2);
-    // plane kp of the box (cells x0-2 .. x0+VX+1, y0-2 .. y0+VY+1) into its ring slot
-    auto load_plane = [&](int kp) {  // rows of 36 cells: 4 fields x 12 rows, a warp per row
-      T* dst = ring + ((kp + 16 * VRING) % VRING) * VSmem<T>::PLANE;
-      for (int r = warp; r < 4 * VBY; r += NTW / 32) {
-        const int f = r / VBY, j = y0 - 2 + (r - f * VBY);
-        T* drow = dst + r * VBX;
-        const T* srow = W + (long long)(f < 3 ? 1 + f : 5) * b.field +  // u, v, w, theta
-                        (((kp + H) * (b.ny + 2 * H) + j + H) * b.px + x0 - 2 + H);
-        for (int cx = lane; cx < VBX; cx += 32) {
-          if (x0 - 2 + cx < b.nx + H && j < b.ny + H) cp_async(drow + cx, srow + cx);  // i, j >= -4
-          else drow[cx] = T(0);
-        }
-      }
-      cp_async_commit();
+    // the box of plane kp: storage columns 32 tx .. 32 tx + 39 (cells x0 - 3 .. x0 + 36), rows
+    // y0 - 2 .. y0 + 9 (storage y0 + 3): u, v, w, theta (fields 1, 2, 3, 5)
+    auto issue = [&](int kp) {  // thread 0
+      const int q = slot(kp);
+      T* dst = ring + q * VSmem<T>::PLANE;
+      fence_proxy_async();
+      mbar_expect_tx(&bar[q], (unsigned)(sizeof(T) * VSmem<T>::PLANE));
+      const int fld[4] = {1, 2, 3, 5};
+      for (int f = 0; f < 4; ++f)
+        tma_load_4d(dst + f * VSmem<T>::FIELD, &a.mw, &bar[q], tx * VX, y0 + 3, kp + H, fld[f]);
+      pending |= 1u << q;
+    };
+    auto wait = [&](int kp) {  // all threads; a copy that never landed stays pending
+      const int q = slot(kp);
+      const bool ok = mbar_wait_bounded(&bar[q], (parity >> q) & 1u);
+      if (!ok) atomicOr(sabort, 1);
+      if (ok) parity ^= 1u << q;  // a failed wait leaves the phase for the drain below
+      if (threadIdx.x == 0 && ok) pending &= ~(1u << q);
     };
     __syncthreads();  // the previous unit is done with the ring
-    for (int kp = kb - 2; kp <= kb + 2; ++kp) load_plane(kp);
+    if (threadIdx.x == 0)
+      for (int kp = kb - 2; kp <= min(kb + 2, ke + 1); ++kp) issue(kp);
+    for (int kp = kb - 2; kp <= min(kb + 1, ke + 1); ++kp) wait(kp);
     for (int k = kb; k < ke; ++k) {
-      load_plane(k + 3);   // one plane ahead (into the slot of plane k - 3, no longer read)
-      cp_async_wait_one(); // everything but that plane has landed
+      if (threadIdx.x == 0 && k + 3 <= ke + 1 && !*sabort) issue(k + 3);  // into the slot of plane k - 3
+      wait(k + 2);
       __syncthreads();
+      if (*sabort) break;
       const int i = x0 + lane, j = y0 + warp;
       if (i < b.nx + 2 && j < b.ny + 2) {
-        const int c = (warp + 2) * VBX + lane + 2;
+        const int c = (warp + 2) * VBX + lane + 3;  // the cell in the box
         const T* pl[5];
 #pragma unroll
-        for (int m = 0; m < 5; ++m) pl[m] = ring + ((k - 2 + m + 16 * VRING) % VRING) * VSmem<T>::PLANE;
+        for (int m = 0; m < 5; ++m) pl[m] = ring + slot(k - 2 + m) * VSmem<T>::PLANE;
         T g[4][3], vel[3];
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-          const T* p0 = pl[2] + f * VBY * VBX;
+          const T* p0 = pl[2] + f * VSmem<T>::FIELD;
           if (f < 3) vel[f] = p0[c];
           g[f][0] = ((p0[c - 2] - p0[c + 2]) + T(8) * (p0[c + 1] - p0[c - 1])) * ih[0];
           g[f][1] = ((p0[c - 2 * VBX] - p0[c + 2 * VBX]) + T(8) * (p0[c + VBX] - p0[c - VBX])) * ih[1];
-          const int o = f * VBY * VBX + c;
+          const int o = f * VSmem<T>::FIELD + c;
           g[f][2] = ((pl[0][o] - pl[4][o]) + T(8) * (pl[3][o] - pl[1][o])) * ih[2];
         }
         const T div = g[0][0] + g[1][1] + g[2][2];
@@ -267,89 +321,79 @@ __global__ void __launch_bounds__(NTW) visc_kernel(Args a) {
       __syncthreads();  // plane k-2's slot is refilled next
     }
   }
-  cp_async_wait_all();
+  if (*sabort && threadIdx.x == 0) tma_abort(bar, pending, parity, VRING, a.ctrl);
 }
 
 // ---- the viscous residual: Rv = -(D4_x Fv + D4_y Gv + D4_z Hv) at the interior cells ----------
 // Tiles of 32 x 8 cells marching in z over each CTA's contiguous share of tile-planes.  Per plane
-// k the x-fluxes of the tile's rows plus 2 cells each side, the y-fluxes of its columns plus 2
-// rows each side (double-buffered) and the z-fluxes of planes k-2 .. k+2 (a 6-slot ring) are in
-// shared memory; the copies for plane k+1 run while plane k is computed.
-constexpr int DX = 32, DY = 8, DRING = 6;
+// k the x-fluxes of the tile's rows (columns 32 t - 5 .. 32 t + 34), the y-fluxes of its columns
+// and 2 rows each side (double-buffered) and the z-fluxes of planes k-2 .. k+2 (a 6-slot ring) are
+// in shared memory; one thread loads them as TMA boxes, those of plane k+1 while k is computed.
+constexpr int DX = 32, DY = 8, DBX = 40, DRING = 6;
 template <typename T>
 struct DSmem {
-  static constexpr int FX = 4 * DY * (DX + 4);    // Fv of rows y0..y0+7, x0-2 .. x0+33
-  static constexpr int GY = 4 * (DY + 4) * DX;    // Gv of columns x0..x0+31, y0-2 .. y0+9
-  static constexpr int HZ = 4 * DY * DX;          // Hv of the tile, one plane
+  static constexpr int FX = 4 * DY * DBX;          // x-fluxes, 4 components x 8 rows x 40
+  static constexpr int GY = 4 * (DY + 4) * DBX;    // y-fluxes, 4 components x 12 rows x 40
+  static constexpr int HZ = 4 * DY * DBX;          // z-fluxes of one plane
   static constexpr int XY = FX + GY;
-  static constexpr size_t bytes = sizeof(T) * (2 * XY + DRING * HZ);
+  static constexpr size_t bar = sizeof(T) * (2 * XY + DRING * HZ);
+  static constexpr size_t bytes = bar + 8 * 2 + 16;
 };
 
 template <typename T>
-__global__ void __launch_bounds__(NTW) viscdiv_kernel(Args a) {
-  extern __shared__ __align__(16) unsigned char dsm[];
+__global__ void __launch_bounds__(NTW) viscdiv_kernel(const __grid_constant__ Args a) {
+  extern __shared__ __align__(128) unsigned char dsm[];
   T* xy = reinterpret_cast<T*>(dsm);            // 2 buffers of [FX | GY]
   T* hz = xy + 2 * DSmem<T>::XY;                 // DRING planes of HZ
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + DSmem<T>::bar);
+  int* sabort = reinterpret_cast<int*>(bar + 2);
   const Box& b = a.b;
-  const T* F = static_cast<const T*>(a.Fv);
   T* Rv = static_cast<T*>(a.Rv);
-  const T ih[3] = {T(a.ih[0] / 12.0), T(a.ih[1] / 12.0), T(a.ih[2] / 12.0)};
+  const T* ih = coef<T>(a).ih12;
   const int ntx = (b.nx + DX - 1) / DX, nty = (b.ny + DY - 1) / DY;
   const long long units = (long long)ntx * nty * b.nz;
   const long long u0 = (long long)blockIdx.x * units / gridDim.x, u1 = (long long)(blockIdx.x + 1) * units / gridDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+    *sabort = 0;
+  }
+  __syncthreads();
+  unsigned parity = 0, pending = 0;
   auto hslot = [](int kp) { return (kp + 4 * DRING) % DRING; };
-  for (long long u = u0; u < u1;) {
+  for (long long u = u0; u < u1 && !*sabort;) {
     const long long tile = u / b.nz;
     const int k0 = (int)(u - tile * b.nz);
     const int k1 = (int)min((long long)b.nz, k0 + (u1 - u));
     u += k1 - k0;
-    const int x0 = (int)(tile % ntx) * DX, y0 = (int)(tile / ntx) * DY;
-    // rows of the flux boxes, a warp per row; the offsets within a field fit 32 bits
-    auto row_off = [&](int j, int k, int i) { return ((k + H) * (b.ny + 2 * H) + j + H) * b.px + i + H; };
-    auto load_xy = [&](int k, T* dst) {  // x-fluxes (4 comps) of the rows, y-fluxes of the columns
-      for (int r = warp; r < 4 * DY; r += NTW / 32) {
-        const int q = r / DY, j = y0 + (r - q * DY);
-        T* drow = dst + r * (DX + 4);
-        const T* srow = F + (long long)q * b.field + row_off(j, k, x0 - 2);
-        for (int cx = lane; cx < DX + 4; cx += 32) {
-          if (x0 - 2 + cx < b.nx + 2 && j < b.ny) cp_async(drow + cx, srow + cx);
-          else drow[cx] = T(0);
-        }
-      }
-      for (int r = warp; r < 4 * (DY + 4); r += NTW / 32) {
-        const int q = r / (DY + 4), j = y0 - 2 + (r - q * (DY + 4));
-        T* drow = dst + DSmem<T>::FX + r * DX;
-        const T* srow = F + (long long)(4 + q) * b.field + row_off(j, k, x0);
-        if (x0 + lane < b.nx && j < b.ny + 2) cp_async(drow + lane, srow + lane);
-        else drow[lane] = T(0);
-      }
-    };
-    auto load_z = [&](int kp) {  // z-fluxes of the tile at plane kp
-      T* dst = hz + hslot(kp) * DSmem<T>::HZ;
-      for (int r = warp; r < 4 * DY; r += NTW / 32) {
-        const int q = r / DY, j = y0 + (r - q * DY);
-        T* drow = dst + r * DX;
-        const T* srow = F + (long long)(8 + q) * b.field + row_off(j, kp, x0);
-        if (x0 + lane < b.nx && j < b.ny) cp_async(drow + lane, srow + lane);
-        else drow[lane] = T(0);
-      }
+    const int tx = (int)(tile % ntx), x0 = tx * DX, y0 = (int)(tile / ntx) * DY;
+    constexpr unsigned XYB = sizeof(T) * DSmem<T>::XY, HZB = sizeof(T) * DSmem<T>::HZ;
+    // the loads plane k waits for: its x- and y-fluxes into buffer k & 1 and the z-fluxes of
+    // plane k + 2 (with, for the first plane, those of planes k - 2 .. k + 1), on barrier k & 1
+    auto issue = [&](int k, bool first) {  // thread 0
+      const int q = k & 1;
+      T* d = xy + q * DSmem<T>::XY;
+      fence_proxy_async();
+      mbar_expect_tx(&bar[q], XYB + (first ? 5 : 1) * HZB);
+      tma_load_4d(d, &a.mf8, &bar[q], tx * DX, y0 + H, k + H, 0);                     // Fv, rows y0..y0+7
+      tma_load_4d(d + DSmem<T>::FX, &a.mf12, &bar[q], tx * DX, y0 - 2 + H, k + H, 4);  // Gv, rows y0-2..y0+9
+      for (int kp = first ? k - 2 : k + 2; kp <= k + 2; ++kp)
+        tma_load_4d(hz + hslot(kp) * DSmem<T>::HZ, &a.mf8, &bar[q], tx * DX, y0 + H, kp + H, 8);  // Hv
+      pending |= 1u << q;
     };
     __syncthreads();  // the previous segment is done with the buffers
-    for (int kp = k0 - 2; kp <= k0 + 2; ++kp) load_z(kp);
-    load_xy(k0, xy);
-    cp_async_commit();
+    if (threadIdx.x == 0) issue(k0, true);
     for (int k = k0; k < k1; ++k) {
-      const int cur = (k - k0) & 1;
-      if (k + 1 < k1) {  // plane k+1: its x/y fluxes and the z-fluxes of plane k+3
-        load_xy(k + 1, xy + (cur ^ 1) * DSmem<T>::XY);
-        load_z(k + 3);
-        cp_async_commit();
-        cp_async_wait_one();
-      } else {
-        cp_async_wait_all();
-      }
+      const int cur = k & 1;
+      const bool ok = mbar_wait_bounded(&bar[cur], (parity >> cur) & 1u);
+      if (!ok) atomicOr(sabort, 1);
+      if (ok) parity ^= 1u << cur;  // a failed wait leaves the phase for the drain below
+      if (threadIdx.x == 0 && ok) pending &= ~(1u << cur);
+      if (threadIdx.x == 0 && k + 1 < k1 && !*sabort) issue(k + 1, false);  // buffers of plane k-1: free
       __syncthreads();
+      if (*sabort) break;
       const int i = x0 + lane, j = y0 + warp;
       if (i < b.nx && j < b.ny) {
         const T* fx = xy + cur * DSmem<T>::XY;
@@ -357,11 +401,11 @@ __global__ void __launch_bounds__(NTW) viscdiv_kernel(Args a) {
         const long long c = ((long long)k * b.ny + j) * b.nx + i;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const T* f = fx + (q * DY + warp) * (DX + 4) + lane + 2;
+          const T* f = fx + (q * DY + warp) * DBX + lane + H;        // column of cell i: i - x0 + 5
           const T dx = (f[-2] - f[2]) + T(8) * (f[1] - f[-1]);
-          const T* g = gy + (q * (DY + 4) + warp + 2) * DX + lane;
-          const T dy = (g[-2 * DX] - g[2 * DX]) + T(8) * (g[DX] - g[-DX]);
-          const int o = q * DY * DX + warp * DX + lane;
+          const T* g = gy + (q * (DY + 4) + warp + 2) * DBX + lane + H;
+          const T dy = (g[-2 * DBX] - g[2 * DBX]) + T(8) * (g[DBX] - g[-DBX]);
+          const int o = (q * DY + warp) * DBX + lane + H;
           const T dz = (hz[hslot(k - 2) * DSmem<T>::HZ + o] - hz[hslot(k + 2) * DSmem<T>::HZ + o]) +
                        T(8) * (hz[hslot(k + 1) * DSmem<T>::HZ + o] - hz[hslot(k - 1) * DSmem<T>::HZ + o]);
           Rv[q * a.n + c] = -(dx * ih[0] + dy * ih[1] + dz * ih[2]);
@@ -370,7 +414,7 @@ __global__ void __launch_bounds__(NTW) viscdiv_kernel(Args a) {
       __syncthreads();  // the buffers of plane k (and z-plane k-2) are refilled next
     }
   }
-  cp_async_wait_all();
+  if (*sabort && threadIdx.x == 0) tma_abort(bar, pending, parity, 2, a.ctrl);
 }
 
 // ---- the weighted interpolation: both edge values of cell i from u_{i-2} .. u_{i+2} -----------
@@ -447,8 +491,8 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
   const long long tiles = (long long)nseg * ngrp * nb;
   const T* W = static_cast<const T*>(a.W);
   T* R = static_cast<T*>(a.R);
-  const Consts<T> K = make_consts<T>(a.gamma, a.eps, a.mu, a.Pr, 0);
-  const T ih = T(a.ih[D]);
+  const Consts<T> K = coef<T>(a).K;
+  const T ih = coef<T>(a).ih[D];
   const bool linear = a.linear != 0;
   const double dt = (MODE == 2 && a.stage > 0) ? a.ctrl->dt : 0.0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -698,6 +742,7 @@ using namespace gbcfd;
 using namespace gbcfd::wcns;
 
 struct gbcfd_wcns_s {
+  CUtensorMap mw, mf8, mf12;  // TMA maps of the primitive box and of the viscous fluxes
   int nx, ny, nz;
   gbcfd_params p;
   double h[3];
@@ -768,9 +813,65 @@ int cuda_err(cudaError_t e, const char* what) {
   return set_error(GBCFD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// 4D map (x, y, z, field) over nfield padded fields of the box; boxes of bx x by x 1 x bf.  The x
+// extent is the padded width nx + 10, so columns past it read zero.
+int encode_box_map(CUtensorMap* m, void* base, const Box& b, int elem, int nfield, int bx, int by, int bf) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return set_error(GBCFD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[4] = {(cuuint64_t)(b.nx + 2 * H), (cuuint64_t)(b.ny + 2 * H), (cuuint64_t)(b.nz + 2 * H),
+                        (cuuint64_t)nfield};
+  cuuint64_t strides[3] = {(cuuint64_t)b.px * elem, (cuuint64_t)b.px * elem * (b.ny + 2 * H),
+                           (cuuint64_t)b.field * elem};
+  cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, (cuuint32_t)bf};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims,
+                   strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(GBCFD_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return GBCFD_OK;
+}
+
+template <typename T>
+void fill_coef(const Args& a, Coef<T>& c) {
+  const double kappa = a.Pr > 0.0 ? a.mu * a.gamma / ((a.gamma - 1.0) * a.Pr) : 0.0;
+  c.gm1 = T(a.gamma - 1.0);
+  c.gam = T(a.gamma);
+  c.half = T(0.5);
+  c.vf = T(4.0 * std::max(4.0 / 3.0, a.gamma / a.Pr) * a.mu);
+  c.mu = T(a.mu);
+  c.kappa = T(kappa);
+  for (int d = 0; d < 3; ++d) {
+    c.ih[d] = T(a.ih[d]);
+    c.ih12[d] = T(a.ih[d] / 12.0);
+  }
+  c.ihs = T(a.ih[0] * a.ih[0] + a.ih[1] * a.ih[1] + a.ih[2] * a.ih[2]);
+  c.K.gm1 = T(a.gamma - 1.0);
+  c.K.ggm1 = T(a.gamma / (a.gamma - 1.0));
+  c.K.eps = T(a.eps);
+  c.K.mu = T(a.mu);
+  c.K.kappa = T(kappa);
+  c.K.lim = 0;
+}
+
 Args make_args(gbcfd_wcns w) {
   Args a;
   std::memset(&a, 0, sizeof(a));
+  a.mw = w->mw;
+  a.mf8 = w->mf8;
+  a.mf12 = w->mf12;
   a.b = w->box;
   a.n = (long long)w->nx * w->ny * w->nz;
   a.gamma = w->p.gamma;
@@ -781,6 +882,8 @@ Args make_args(gbcfd_wcns w) {
   for (int d = 0; d < 3; ++d) a.ih[d] = 1.0 / w->h[d];
   a.viscous = w->p.viscous;
   a.linear = w->p.limiter;
+  fill_coef(a, a.cf);
+  fill_coef(a, a.cd);
   a.W = w->W;
   a.Fv = w->Fv;
   a.Rv = w->Rv;
@@ -910,6 +1013,16 @@ extern "C" int gbcfd_wcns_create(int nx, int ny, int nz, const gbcfd_params* par
   w->ctrl = reinterpret_cast<DevCtrl*>(base + L.ctrl);
   w->partial = reinterpret_cast<double*>(base + L.partial);
   w->rows = L.rows;
+  {
+    const int elem = mixed ? 4 : 8;
+    int rc = encode_box_map(&w->mw, w->W, w->box, elem, NPW, VBX, VBY, 1);
+    if (rc == GBCFD_OK && params->viscous) rc = encode_box_map(&w->mf8, w->Fv, w->box, elem, 12, DBX, DY, 4);
+    if (rc == GBCFD_OK && params->viscous) rc = encode_box_map(&w->mf12, w->Fv, w->box, elem, 12, DBX, DY + 4, 4);
+    if (rc != GBCFD_OK) {
+      delete w;
+      return rc;
+    }
+  }
   w->occ = mixed ? dir_occupancy<float>() : dir_occupancy<double>();
   w->vocc = mixed ? visc_occupancy<float>() : visc_occupancy<double>();
   w->docc = mixed ? viscdiv_occupancy<float>() : viscdiv_occupancy<double>();
