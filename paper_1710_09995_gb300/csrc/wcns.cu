@@ -215,9 +215,9 @@ __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wai
 
 // The viscous kernel works on tiles of VX x VY output cells of the box padded by 2, marching in z
 // over chunks of VZ planes.  The planes it reads (u, v, w, theta of the tile plus 2 cells around,
-// k-2 .. k+2) sit in a 6-slot shared ring; one thread loads each plane as four TMA boxes of 40 x 12
-// cells (starting at a 16-byte aligned column) while the other planes are computed.
-constexpr int VX = 32, VY = 8, VZ = 32, VBX = 40, VBY = 12, VRING = 6;
+// k-2 .. k+2) sit in a shared ring with VAHEAD more planes in flight; one thread loads each plane as
+// four TMA boxes of 40 x 12 cells (starting at a 16-byte aligned column).
+constexpr int VX = 32, VY = 8, VZ = 32, VBX = 40, VBY = 12, VAHEAD = 1, VRING = 5 + VAHEAD;
 template <typename T>
 struct VSmem {
   static constexpr int FIELD = VBY * VBX;             // one field's box
@@ -282,10 +282,11 @@ __global__ void __launch_bounds__(NTW) visc_kernel(const __grid_constant__ Args 
     };
     __syncthreads();  // the previous unit is done with the ring
     if (threadIdx.x == 0)
-      for (int kp = kb - 2; kp <= min(kb + 2, ke + 1); ++kp) issue(kp);
+      for (int kp = kb - 2; kp <= min(kb + 1 + VAHEAD, ke + 1); ++kp) issue(kp);
     for (int kp = kb - 2; kp <= min(kb + 1, ke + 1); ++kp) wait(kp);
     for (int k = kb; k < ke; ++k) {
-      if (threadIdx.x == 0 && k + 3 <= ke + 1 && !*sabort) issue(k + 3);  // into the slot of plane k - 3
+      // plane k + 2 + VAHEAD goes into the slot of plane k - 3, no longer read
+      if (threadIdx.x == 0 && k + 2 + VAHEAD <= ke + 1 && !*sabort) issue(k + 2 + VAHEAD);
       wait(k + 2);
       __syncthreads();
       if (*sabort) break;
@@ -458,7 +459,10 @@ struct Smem {
   static constexpr int WS = 5 * (LMAX + 10) * NLP;   // staged primitives [5][L+10][NLP], then
                                                      // the edge fluxes [5][L+5][NLP] over them;
                                                      // two buffers (the next tile lands in one)
-  static constexpr size_t red = (2 * sizeof(T) * WS + 15) / 16 * 16;  // norm partials (double)
+  static constexpr int RS = sizeof(T) == 4 ? 5 * LMAX * NLP : 0;  // the running residual of the tile's
+                                                                   // cells (mixed path only)
+  static constexpr size_t rs = (2 * sizeof(T) * WS + 15) / 16 * 16;
+  static constexpr size_t red = (rs + sizeof(T) * RS + 15) / 16 * 16;  // norm partials (double)
   static constexpr size_t bytes = red + sizeof(double) * (NTW / 32) * 5;
 };
 
@@ -550,6 +554,20 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
     }
     cp_async_commit();
   };
+  // the y and z passes add to the residual R of the earlier passes: the tile's R lands in shared
+  // memory (as its own commit group) while the edge fluxes are computed
+  T* const Rs = reinterpret_cast<T*>(smem_raw + Smem<T>::rs);
+  auto issue_r = [&](const TileInfo& t) {
+    for (int q = 0; q < 5; ++q)
+      for (int e = threadIdx.x; e < t.Ls * NL; e += NTW) {
+        const int c = e / NL, l = e % NL;
+        if (t.a0 + l >= na) continue;
+        int i, j, k;
+        ijk(t, l, t.s0 + c, i, j, k);
+        cp_async(Rs + (q * LMAX + c) * NLP + l, R + q * a.n + ((long long)k * b.ny + j) * b.nx + i);
+      }
+    cp_async_commit();
+  };
   int buf = 0;
   if ((long long)blockIdx.x < tiles) issue_stage(decode(blockIdx.x), Wbuf);
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, buf ^= 1) {
@@ -560,7 +578,10 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
     const int nfc = Ls + 5;
     cp_async_wait_all();
     __syncthreads();  // the tile has landed; the previous tile's cells are done with the other buffer
-    if (tile + gridDim.x < tiles) issue_stage(decode(tile + gridDim.x), Wbuf + (buf ^ 1) * Smem<T>::WS);
+    constexpr bool RSTAGE = MODE != 0 && sizeof(T) == 4;  // FP64: shared memory is kept for occupancy
+    if (RSTAGE) issue_r(t);
+    const bool more = tile + gridDim.x < tiles;
+    if (more) issue_stage(decode(tile + gridDim.x), Wbuf + (buf ^ 1) * Smem<T>::WS);
     // 2. edge fluxes: edge f lies between staged cells f + 2 and f + 3, so cell c (staged c + 5)
     //    has edges c .. c + 5 around it.  Item (line, chunk): lane t takes staged cell
     //    m = 31 chunk + t + 2, evaluates its two edge states, and edge f = m - 2 pairs its
@@ -591,6 +612,10 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
       if (a0 + l >= na || FCH * ch >= nfc || lane >= FCH || f >= nfc) continue;
 #pragma unroll
       for (int q = 0; q < 5; ++q) Fs[(idx[q] * (LMAX + 5) + f) * NLP + l] = F[it][q];
+    }
+    if (RSTAGE) {  // the tile's R (the newest group, the next tile's primitives, may fly on)
+      if (more) cp_async_wait_one();
+      else cp_async_wait_all();
     }
     __syncthreads();
     // 3. Eq. 2 per cell, minus D4 of the viscous flux along D, then the pass's output
@@ -626,7 +651,7 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
         for (int q = 0; q < 5; ++q) R[q * a.n + cc] = add[q];
       } else if (MODE == 1) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) R[q * a.n + cc] = R[q * a.n + cc] + add[q];
+        for (int q = 0; q < 5; ++q) R[q * a.n + cc] = (RSTAGE ? Rs[(q * LMAX + c) * NLP + l] : R[q * a.n + cc]) + add[q];
       } else if (sizeof(T) == 8) {  // FP64: Eqs. 4-6 as written
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
@@ -647,7 +672,7 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
         const float dtf = float(dt);
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-          const float tot = float(R[q * a.n + cc]) + float(add[q]);
+          const float tot = float(Rs[(q * LMAX + c) * NLP + l]) + float(add[q]);
           const long long o = q * a.n + cc;
           if (a.stage == 0) {
             a.rout[o] = f32_to_f64_bits(tot);
