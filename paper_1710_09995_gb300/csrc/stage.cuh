@@ -214,25 +214,20 @@ template <typename T> __device__ __forceinline__ Tri<T> ihx3(T x, T y, T z) { re
 template <typename T> __device__ __forceinline__ Tri<T> ihy3(T x, T y, T z) { return {{y, z, x}}; }
 template <typename T> __device__ __forceinline__ Tri<T> ihz3(T x, T y, T z) { return {{z, x, y}}; }
 
-// the rate constants of a run, formed once per thread (the FP64 pipe is slow on this part, so
-// the per-cell code must not redo them): gamma and 4 max(4/3, gamma/Pr) mu in the path's type
-template <typename T>
-__device__ __forceinline__ RateK<T> rate_consts(const Physics& ph) {
-  return {T(ph.gamma), T(4.0 * fmax(4.0 / 3.0, ph.gamma / ph.Pr) * ph.mu)};
-}
-
 // spectral-radius rate of one cell: sum over directions of the convective radius (plus 4x the
-// viscous one) divided by the volume, i.e. the inverse of the cell's stable step / CFL;
-// s2 = ihx^2 + ihy^2 + ihz^2
+// viscous one) divided by the volume, i.e. the inverse of the cell's stable step / CFL
 template <typename T>
-__device__ __forceinline__ T cell_rate(T r, T u, T v, T w, T p, const RateK<T>& RK, bool viscous, T ihx, T ihy,
-                                       T ihz, T s2) {
+__device__ __forceinline__ T cell_rate(T r, T u, T v, T w, T p, const Physics& ph, T ihx, T ihy, T ihz) {
   using O = VM<T>;
   const T ir = O::rcp(r);
-  const T c2 = RK.gam * p * ir;
+  const T c2 = T(ph.gamma) * p * ir;
   const T c = c2 * O::rsqrt(c2);
   T rate = (O::ab(u) + c) * ihx + (O::ab(v) + c) * ihy + (O::ab(w) + c) * ihz;
-  if (viscous) rate += RK.vf * ir * s2;
+  if (ph.viscous) {
+    const T f = T(fmax(4.0 / 3.0, ph.gamma / ph.Pr));
+    const T s2 = ihx * ihx + ihy * ihy + ihz * ihz;
+    rate += T(4.0 * ph.mu) * f * ir * s2;
+  }
   return rate;
 }
 
@@ -267,8 +262,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
   const Physics& ph = P.ph;
   const Consts<T> K = make_consts<T>(ph.gamma, ph.eps, VISC ? ph.mu : 0.0, ph.Pr, ph.limiter);
   const T gm1 = T(ph.gamma - 1.0);
-  const RateK<T> RK = rate_consts<T>(ph);
-  const T cflT = T(ph.cfl);
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE + NMS; ++s) mbar_init(&bar[s], 1);
@@ -378,7 +371,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
       if (STAGE == 3) { dprev = D->d[1]; qout = D->q[1 - c]; sout = D->sh[1 - c]; tmd = &D->td[1]; }
     }
     const T hx = T(D->ihx), hy = T(D->ihy), hz = T(D->ihz);  // inverse cell sizes
-    const T hs2 = hx * hx + hy * hy + hz * hz;
 
     auto request = [&](int kp) {  // thread 0 only
       const int s = (kp + 2) & (NSTAGE - 1);
@@ -585,10 +577,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
             if constexpr (CURVI) {
               T sb[9];
               cell_face_means(mring, mk, mk1, ocy, ocx, sb);
-              rate = cell_rate_curvi<double>(out[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], RK,
-                                             ph.viscous);
+              rate = cell_rate_curvi<double>(out[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], ph);
             } else {
-              rate = cell_rate<double>(out[0], uu, vv, ww, pp, RK, ph.viscous, hx, hy, hz, hs2);
+              rate = cell_rate<double>(out[0], uu, vv, ww, pp, ph, hx, hy, hz);
             }
             rate_max = fmax(rate_max, T(rate));
             if constexpr (!VISC)
@@ -616,20 +607,19 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
             }
             const float ir = VM<float>::rcp(qf[0]);
             const float uu = qf[1] * ir, vv = qf[2] * ir, ww = qf[3] * ir;
-            const float pp = gm1 * (qf[4] - 0.5f * qf[0] * (uu * uu + vv * vv + ww * ww));
+            const float pp = float(ph.gamma - 1.0) * (qf[4] - 0.5f * qf[0] * (uu * uu + vv * vv + ww * ww));
             if (!(qf[0] > 0.0f && pp > 0.0f)) bad = true;
             float rate;
             if constexpr (CURVI) {
               T sb[9];
               cell_face_means(mring, mk, mk1, ocy, ocx, sb);
-              rate = cell_rate_curvi<float>(qf[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], RK,
-                                            ph.viscous);
+              rate = cell_rate_curvi<float>(qf[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], ph);
             } else {
-              rate = cell_rate<float>(qf[0], uu, vv, ww, pp, RK, ph.viscous, hx, hy, hz, hs2);
+              rate = cell_rate<float>(qf[0], uu, vv, ww, pp, ph, hx, hy, hz);
             }
             rate_max = fmax(rate_max, T(rate));
             if constexpr (!VISC)
-              if (ph.local_dt) static_cast<float*>(D->dtl)[of] = cflT / rate;
+              if (ph.local_dt) static_cast<float*>(D->dtl)[of] = float(ph.cfl) / rate;
           }
         }
         if constexpr (STAGE == 1) {
