@@ -763,7 +763,8 @@ def wcns_roofline(precision, res, cells, steps, peak, peak_kind):
             "algorithmic_bytes_per_launch": nbytes / (3 * steps), "kernel": name,
             "avg_launch_ms": round(res["kernel_ms"][name] / (3 * steps), 4),
             "share_of_step": round(res["kernel_ms"][name] / max(res["ms"], 1e-9), 4),
-            "kernels_ms_per_step": {n: round(v / steps, 4) for n, v in res["kernel_ms"].items()}}
+            "kernels_ms_per_step": {n: round(v / steps, 4) for n, v in res["kernel_ms"].items()},
+            "dominant_ms_per_stage": [round(v / steps, 4) for v in res["kernel_stage_ms"][name]]}
 
 
 def e2e_wcns(gbcfd, torch, case, precision, steps, world, device):

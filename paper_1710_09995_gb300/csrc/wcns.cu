@@ -184,13 +184,17 @@ __global__ void __launch_bounds__(NTW) prim_kernel(Args a, int with_rate) {
     last = (atomicAdd(&a.ctrl->counter, 1u) == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last || threadIdx.x >= 32) return;
   __threadfence();
+  // the last CTA's first warp folds the per-CTA maxima: lane-strided, then a fixed shuffle tree
   double m = 0.0;
-  for (unsigned q = 0; q < gridDim.x; ++q) m = fmax(m, __ldcg(a.partial + (size_t)q * NPART + 5));
-  a.ctrl->rate = m;
-  a.ctrl->dt = a.cfl / m;
-  a.ctrl->counter = 0u;
+  for (unsigned q = threadIdx.x; q < gridDim.x; q += 32) m = fmax(m, __ldcg(a.partial + (size_t)q * NPART + 5));
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if (threadIdx.x == 0) {
+    a.ctrl->rate = m;
+    a.ctrl->dt = a.cfl / m;
+    a.ctrl->counter = 0u;
+  }
 }
 
 // S = f32(Q) of a compact state (mixed path, after the state is set)
@@ -449,6 +453,46 @@ __device__ __forceinline__ void edges(V u0, V u1, V u2, V u3, V u4, bool linear,
   um = u2 + O::fma(kA, mA, O::fma(nB, mB, kC * mC)) * O::rcp(kA + nB + kC);
 }
 
+// The same for two variables at once in packed f32x2 arithmetic (one instruction per pair of
+// lanes' values: FFMA2 / FMUL2 / FADD2 of sm_100+); the reciprocals stay scalar.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ void edges2(float2 u0, float2 u1, float2 u2, float2 u3, float2 u4, bool linear,
+                                       float2& up, float2& um) {
+  const float2 half = f2(0.5f), eighth = f2(0.125f), mhalf = f2(-0.5f);
+  const float2 gA = mul2(half, fma2(f2(3.f), u2, fma2(f2(-4.f), u1, u0)));
+  const float2 sA = add2(fma2(f2(-2.f), u1, u0), u2);
+  const float2 gB = fma2(half, u3, mul2(mhalf, u1));
+  const float2 sB = add2(fma2(f2(-2.f), u2, u1), u3);
+  const float2 gC = mul2(half, fma2(f2(-1.f), u4, fma2(f2(4.f), u3, mul2(f2(-3.f), u2))));
+  const float2 sC = add2(fma2(f2(-2.f), u3, u2), u4);
+  const float2 eA = mul2(eighth, sA), eB = mul2(eighth, sB), eC = mul2(eighth, sC);
+  const float2 pA = fma2(half, gA, eA), pB = fma2(half, gB, eB), pC = fma2(half, gC, eC);
+  const float2 mA = fma2(mhalf, gA, eA), mB = fma2(mhalf, gB, eB), mC = fma2(mhalf, gC, eC);
+  if (linear) {
+    up = add2(u2, fma2(f2(1.f / 16.f), pA, fma2(f2(10.f / 16.f), pB, mul2(f2(5.f / 16.f), pC))));
+    um = add2(u2, fma2(f2(5.f / 16.f), mA, fma2(f2(10.f / 16.f), mB, mul2(f2(1.f / 16.f), mC))));
+    return;
+  }
+  const float2 e = f2(1e-6f);
+  float2 dA = add2(e, fma2(gA, gA, mul2(sA, sA)));
+  float2 dB = add2(e, fma2(gB, gB, mul2(sB, sB)));
+  float2 dC = add2(e, fma2(gC, gC, mul2(sC, sC)));
+  dA = mul2(dA, dA); dB = mul2(dB, dB); dC = mul2(dC, dC);
+  const float2 bc = mul2(dB, dC), ac = mul2(dA, dC), ab = mul2(dA, dB);
+  const float2 nA = mul2(f2(1.f / 16.f), bc), nB = mul2(f2(10.f / 16.f), ac), nC = mul2(f2(5.f / 16.f), ab);
+  const float2 kA = mul2(f2(5.f / 16.f), bc), kC = mul2(f2(1.f / 16.f), ab);
+  const float2 np = fma2(nA, pA, fma2(nB, pB, mul2(nC, pC)));
+  const float2 nm = fma2(kA, mA, fma2(nB, mB, mul2(kC, mC)));
+  const float2 dp = add2(add2(nA, nB), nC), dm = add2(add2(kA, nB), kC);
+  const float2 rp = make_float2(__fdividef(1.f, dp.x), __fdividef(1.f, dp.y));
+  const float2 rm = make_float2(__fdividef(1.f, dm.x), __fdividef(1.f, dm.y));
+  up = fma2(np, rp, u2);
+  um = fma2(nm, rm, u2);
+}
+
 template <int D> struct Fr;
 template <> struct Fr<0> { static constexpr int N = 1, T1 = 2, T2 = 3; };
 template <> struct Fr<1> { static constexpr int N = 2, T1 = 3, T2 = 1; };
@@ -594,13 +638,33 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
       if (a0 + l >= na || FCH * ch >= nfc) continue;  // warp-uniform
       const int m = min(f + 2, nfc + 2);              // centres 2 .. nfc + 2 (stencil <= nst - 1)
       T Lq[5], Rq[5];
+      if constexpr (sizeof(T) == 4) {  // mixed: frame variables (0, 1) and (2, 3) as packed pairs
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        const T* w = Ws + (idx[q] * (LMAX + 10) + m - 2) * NLP + l;
+        for (int q = 0; q < 4; q += 2) {
+          const T* w0 = Ws + (idx[q] * (LMAX + 10) + m - 2) * NLP + l;
+          const T* w1 = Ws + (idx[q + 1] * (LMAX + 10) + m - 2) * NLP + l;
+          float2 up, um;
+          edges2(make_float2(w0[0], w1[0]), make_float2(w0[NLP], w1[NLP]), make_float2(w0[2 * NLP], w1[2 * NLP]),
+                 make_float2(w0[3 * NLP], w1[3 * NLP]), make_float2(w0[4 * NLP], w1[4 * NLP]), linear, up, um);
+          Lq[q] = up.x;
+          Lq[q + 1] = up.y;
+          Rq[q] = __shfl_down_sync(0xffffffffu, um.x, 1);
+          Rq[q + 1] = __shfl_down_sync(0xffffffffu, um.y, 1);
+        }
+        const T* w = Ws + (idx[4] * (LMAX + 10) + m - 2) * NLP + l;
         T up, um;
         edges<T>(w[0], w[NLP], w[2 * NLP], w[3 * NLP], w[4 * NLP], linear, up, um);
-        Lq[q] = up;
-        Rq[q] = __shfl_down_sync(0xffffffffu, um, 1);
+        Lq[4] = up;
+        Rq[4] = __shfl_down_sync(0xffffffffu, um, 1);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const T* w = Ws + (idx[q] * (LMAX + 10) + m - 2) * NLP + l;
+          T up, um;
+          edges<T>(w[0], w[NLP], w[2 * NLP], w[3 * NLP], w[4 * NLP], linear, up, um);
+          Lq[q] = up;
+          Rq[q] = __shfl_down_sync(0xffffffffu, um, 1);
+        }
       }
       if (lane < FCH && f < nfc) roe_frame<T>(Lq, Rq, K, F[it]);
     }
@@ -713,14 +777,21 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
     last = (atomicAdd(&a.ctrl->counter, 1u) == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last || threadIdx.x >= 32) return;
   __threadfence();
-  for (int q = 0; q < 5; ++q) {
-    double s = 0.0;
-    for (unsigned c = 0; c < gridDim.x; ++c) s += __ldcg(a.partial + (size_t)c * NPART + q);
-    a.ctrl->norms[q] = sqrt(s / (double)a.n);
+  // the last CTA's first warp folds the per-CTA sums: lane-strided in CTA order, then a fixed
+  // shuffle tree (the same order every run: deterministic)
+  double tot[5] = {0, 0, 0, 0, 0};
+  for (unsigned c = threadIdx.x; c < gridDim.x; c += 32)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) tot[q] += __ldcg(a.partial + (size_t)c * NPART + q);
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+    for (int off = 16; off > 0; off >>= 1) tot[q] += __shfl_xor_sync(0xffffffffu, tot[q], off);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 5; ++q) a.ctrl->norms[q] = sqrt(tot[q] / (double)a.n);
+    a.ctrl->counter = 0u;
   }
-  a.ctrl->counter = 0u;
 }
 
 template <typename T>
