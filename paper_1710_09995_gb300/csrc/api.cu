@@ -223,6 +223,28 @@ static Physics physics_of(const gbcfd_block_s* b) {
   return ph;
 }
 
+// the stage kernel's constants in both precisions (formed here, once)
+template <typename T>
+static PathK<T> path_k_of(const Physics& ph) {
+  PathK<T> k;
+  const double kappa = ph.Pr > 0.0 ? ph.mu * ph.gamma / ((ph.gamma - 1.0) * ph.Pr) : 0.0;
+  k.gm1 = T(ph.gamma - 1.0);
+  k.ggm1 = T(ph.gamma / (ph.gamma - 1.0));
+  k.eps = T(ph.eps);
+  k.mu = T(ph.mu);
+  k.kappa = T(kappa);
+  k.gam = T(ph.gamma);
+  k.vf = T(4.0 * std::max(4.0 / 3.0, ph.gamma / ph.Pr) * ph.mu);
+  k.cfl = T(ph.cfl);
+  return k;
+}
+static PathConsts path_consts(const Physics& ph) {
+  PathConsts c;
+  c.f = path_k_of<float>(ph);
+  c.d = path_k_of<double>(ph);
+  return c;
+}
+
 // the block as the stage kernel sees it
 static void fill_desc(gbcfd_block_s* b) {
   BlockDesc& D = b->desc_host;
@@ -234,6 +256,9 @@ static void fill_desc(gbcfd_block_s* b) {
   D.ihx = 1.0 / b->spacing[0];
   D.ihy = 1.0 / b->spacing[1];
   D.ihz = 1.0 / b->spacing[2];
+  D.ihxf = (float)D.ihx;
+  D.ihyf = (float)D.ihy;
+  D.ihzf = (float)D.ihz;
   for (int i = 0; i < 3; ++i) D.q[i] = b->q[i];
   for (int i = 0; i < 2; ++i) { D.sh[i] = b->sh[i]; D.d[i] = b->d[i]; }
   D.ctrl = b->ctrl;
@@ -617,6 +642,7 @@ static int run_stage(gbcfd_block b, int stage, double* rout, cudaStream_t s) {
   P.nblocks = 1;
   P.cur = b->cur;
   P.ph = physics_of(b);
+  P.pk = path_consts(P.ph);
   P.gctrl = b->ctrl;
   P.partial = b->partial;
   P.rout = rout;
@@ -819,6 +845,7 @@ static GroupParams group_params(gbcfd_group g) {
   P.nblocks = (int)g->blocks.size();
   P.cur = g->blocks[0]->cur;
   P.ph = physics_of(g->blocks[0]);
+  P.pk = path_consts(P.ph);
   P.gctrl = g->gctrl;
   P.partial = g->partial;
   return P;

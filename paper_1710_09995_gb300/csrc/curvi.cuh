@@ -165,19 +165,19 @@ __device__ __forceinline__ MetIdx zface_met(int mk, int mk1, int cy, int cx) {
 // |u.Sb| + c |Sb| (+ 4 max(4/3, gamma/Pr) mu/rho |Sb|^2 / V), divided by V
 template <typename T>
 __device__ __forceinline__ T cell_rate_curvi(T r, T u, T v, T w, T p, const T* sb /*[9]*/, T vol,
-                                             const Physics& ph) {
+                                             const RateK<T>& RK, bool viscous) {
   using O = VM<T>;
   const T ir = O::rcp(r), iv = O::rcp(vol);
-  const T c2 = T(ph.gamma) * p * ir;
+  const T c2 = RK.gam * p * ir;
   const T c = c2 * O::rsqrt(c2);
-  const T fv = T(4.0 * fmax(4.0 / 3.0, ph.gamma / ph.Pr) * ph.mu) * ir * iv;
+  const T fv = RK.vf * ir * iv;
   T rate = T(0);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const T* s = sb + 3 * d;
     const T s2 = O::fma(s[0], s[0], O::fma(s[1], s[1], s[2] * s[2]));
     T lam = O::ab(O::fma(u, s[0], O::fma(v, s[1], w * s[2]))) + c * (s2 * O::rsqrt(s2));
-    if (ph.viscous) lam = O::fma(fv, s2, lam);
+    if (viscous) lam = O::fma(fv, s2, lam);
     rate = rate + lam;
   }
   return rate * iv;

@@ -70,6 +70,18 @@ struct Physics {
   int local_dt;          // 1: every cell advances with its own CFL step (BlockDesc::dtl)
 };
 
+// the constants the stage kernel uses, formed on the host in both precisions: the FP64 pipe is
+// slow on this part, so an FP32 kernel must not convert or divide doubles when it re-forms a
+// constant it could not keep in a register
+template <typename T> struct PathK {
+  T gm1, ggm1, eps, mu, kappa;  // gamma - 1, gamma/(gamma - 1), entropy fix, viscosity, mu gamma/((gamma-1) Pr)
+  T gam, vf, cfl;               // gamma, 4 max(4/3, gamma/Pr) mu (viscous rate), CFL number
+};
+struct PathConsts {
+  PathK<float> f;
+  PathK<double> d;
+};
+
 // ---- one block as the stage kernel sees it (device-resident descriptor table) --------------
 // The TMA descriptors live in global memory (written by the host before any launch that reads
 // them); the kernel selects the arrays of a stage from `stage` and the mixed path's parity `cur`.
@@ -79,6 +91,7 @@ struct BlockDesc {
   CUtensorMap tm;      // metric planes (curvilinear)
   Geometry g;
   double ihx, ihy, ihz;      // 1 / cell size (Cartesian)
+  float ihxf, ihyf, ihzf;    // the same in FP32 (mixed path)
   double* q[3];              // FP64: Qn, Q1, Q2.  mixed: QA, QB
   float* sh[2];              // mixed: shadows
   float* d[2];               // mixed: increments
@@ -98,6 +111,7 @@ struct GroupParams {
   int nblocks;
   int cur;                   // mixed path: which of QA/QB, SA/SB holds Q^n
   Physics ph;                // shared physics (gamma, mu, Pr, cfl, eps, viscous, limiter)
+  PathConsts pk;             // its constants in both precisions
   DevCtrl* gctrl;            // group control: counter, time step (read at stage start)
   double* partial;           // [gridDim.x * NPART]
   double* rout;              // residual mode (one block): compact R[5][nz][ny][nx]

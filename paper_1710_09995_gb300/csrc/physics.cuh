@@ -18,6 +18,9 @@ template <typename V> struct Consts {
   int lim;   // 0 minmod, 1 central slope
 };
 
+// constants of the spectral-radius rate (time step): gamma and 4 max(4/3, gamma/Pr) mu
+template <typename V> struct RateK { V gam, vf; };
+
 template <typename V>
 __device__ __forceinline__ Consts<V> make_consts(double gamma, double eps, double mu, double Pr, int lim) {
   using O = VM<V>;

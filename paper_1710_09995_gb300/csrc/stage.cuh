@@ -215,21 +215,24 @@ template <typename T> __device__ __forceinline__ Tri<T> ihy3(T x, T y, T z) { re
 template <typename T> __device__ __forceinline__ Tri<T> ihz3(T x, T y, T z) { return {{z, x, y}}; }
 
 // spectral-radius rate of one cell: sum over directions of the convective radius (plus 4x the
-// viscous one) divided by the volume, i.e. the inverse of the cell's stable step / CFL
+// viscous one) divided by the volume, i.e. the inverse of the cell's stable step / CFL;
+// s2 = ihx^2 + ihy^2 + ihz^2
 template <typename T>
-__device__ __forceinline__ T cell_rate(T r, T u, T v, T w, T p, const Physics& ph, T ihx, T ihy, T ihz) {
+__device__ __forceinline__ T cell_rate(T r, T u, T v, T w, T p, const RateK<T>& RK, bool viscous, T ihx, T ihy,
+                                       T ihz, T s2) {
   using O = VM<T>;
   const T ir = O::rcp(r);
-  const T c2 = T(ph.gamma) * p * ir;
+  const T c2 = RK.gam * p * ir;
   const T c = c2 * O::rsqrt(c2);
   T rate = (O::ab(u) + c) * ihx + (O::ab(v) + c) * ihy + (O::ab(w) + c) * ihz;
-  if (ph.viscous) {
-    const T f = T(fmax(4.0 / 3.0, ph.gamma / ph.Pr));
-    const T s2 = ihx * ihx + ihy * ihy + ihz * ihz;
-    rate += T(4.0 * ph.mu) * f * ir * s2;
-  }
+  if (viscous) rate += RK.vf * ir * s2;
   return rate;
 }
+
+// the path's constants from the launch parameters (formed on the host)
+template <typename T> __device__ __forceinline__ const PathK<T>& path_k(const GroupParams& P);
+template <> __device__ __forceinline__ const PathK<float>& path_k<float>(const GroupParams& P) { return P.pk.f; }
+template <> __device__ __forceinline__ const PathK<double>& path_k<double>(const GroupParams& P) { return P.pk.d; }
 
 // ---- the kernel ------------------------------------------------------------------------------
 // One launch advances one Runge-Kutta stage of a group of blocks (a single block is a group of
@@ -260,8 +263,17 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Physics& ph = P.ph;
-  const Consts<T> K = make_consts<T>(ph.gamma, ph.eps, VISC ? ph.mu : 0.0, ph.Pr, ph.limiter);
-  const T gm1 = T(ph.gamma - 1.0);
+  const PathK<T>& PK = path_k<T>(P);
+  Consts<T> K;
+  K.gm1 = PK.gm1;
+  K.ggm1 = PK.ggm1;
+  K.eps = PK.eps;
+  K.mu = VISC ? PK.mu : T(0);
+  K.kappa = VISC ? PK.kappa : T(0);
+  K.lim = ph.limiter;
+  const T gm1 = PK.gm1;
+  const RateK<T> RK = {PK.gam, PK.vf};
+  const T cflT = PK.cfl;
 
   if (tid == 0) {
     for (int s = 0; s < NSTAGE + NMS; ++s) mbar_init(&bar[s], 1);
@@ -370,7 +382,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
       if (STAGE == 2) { dprev = D->d[0]; dout = D->d[1]; tmd = &D->td[0]; }
       if (STAGE == 3) { dprev = D->d[1]; qout = D->q[1 - c]; sout = D->sh[1 - c]; tmd = &D->td[1]; }
     }
-    const T hx = T(D->ihx), hy = T(D->ihy), hz = T(D->ihz);  // inverse cell sizes
+    const T hx = MIXED ? T(D->ihxf) : T(D->ihx), hy = MIXED ? T(D->ihyf) : T(D->ihy),
+            hz = MIXED ? T(D->ihzf) : T(D->ihz);  // inverse cell sizes
+    const T hs2 = hx * hx + hy * hy + hz * hz;
 
     auto request = [&](int kp) {  // thread 0 only
       const int s = (kp + 2) & (NSTAGE - 1);
@@ -571,15 +585,16 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
           if constexpr (STAGE == 3) {
             const double ir = 1.0 / out[0];
             const double uu = out[1] * ir, vv = out[2] * ir, ww = out[3] * ir;
-            const double pp = (ph.gamma - 1.0) * (out[4] - 0.5 * out[0] * (uu * uu + vv * vv + ww * ww));
+            const double pp = double(gm1) * (out[4] - 0.5 * out[0] * (uu * uu + vv * vv + ww * ww));
             if (!(out[0] > 0.0 && pp > 0.0)) bad = true;
             double rate;
             if constexpr (CURVI) {
               T sb[9];
               cell_face_means(mring, mk, mk1, ocy, ocx, sb);
-              rate = cell_rate_curvi<double>(out[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], ph);
+              rate = cell_rate_curvi<double>(out[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], RK,
+                                             ph.viscous);
             } else {
-              rate = cell_rate<double>(out[0], uu, vv, ww, pp, ph, hx, hy, hz);
+              rate = cell_rate<double>(out[0], uu, vv, ww, pp, RK, ph.viscous, hx, hy, hz, hs2);
             }
             rate_max = fmax(rate_max, T(rate));
             if constexpr (!VISC)
@@ -607,19 +622,20 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
             }
             const float ir = VM<float>::rcp(qf[0]);
             const float uu = qf[1] * ir, vv = qf[2] * ir, ww = qf[3] * ir;
-            const float pp = float(ph.gamma - 1.0) * (qf[4] - 0.5f * qf[0] * (uu * uu + vv * vv + ww * ww));
+            const float pp = gm1 * (qf[4] - 0.5f * qf[0] * (uu * uu + vv * vv + ww * ww));
             if (!(qf[0] > 0.0f && pp > 0.0f)) bad = true;
             float rate;
             if constexpr (CURVI) {
               T sb[9];
               cell_face_means(mring, mk, mk1, ocy, ocx, sb);
-              rate = cell_rate_curvi<float>(qf[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], ph);
+              rate = cell_rate_curvi<float>(qf[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], RK,
+                                            ph.viscous);
             } else {
-              rate = cell_rate<float>(qf[0], uu, vv, ww, pp, ph, hx, hy, hz);
+              rate = cell_rate<float>(qf[0], uu, vv, ww, pp, RK, ph.viscous, hx, hy, hz, hs2);
             }
             rate_max = fmax(rate_max, T(rate));
             if constexpr (!VISC)
-              if (ph.local_dt) static_cast<float*>(D->dtl)[of] = float(ph.cfl) / rate;
+              if (ph.local_dt) static_cast<float*>(D->dtl)[of] = cflT / rate;
           }
         }
         if constexpr (STAGE == 1) {
