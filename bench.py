@@ -377,9 +377,29 @@ def issue_estimate(precision, res, cells, steps, sm_mhz, workload="vortex256"):
             "frac": round(rate / peak, 4), "instructions_per_cell": inst}
 
 
+def cpu_model():
+    """the host CPU's model name (lscpu or /proc/cpuinfo), for the CPU baseline's record"""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for key in ("Model name:", "Vendor ID:"):
+            for line in out.splitlines():
+                if line.strip().startswith(key):
+                    return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_baseline_sample(n):
     """The FP64 oracle on the host cores: one SSP-RK3 step of a 256 x 256 x 64 z-slab of the
-    (z-invariant) vortex -- exactly a sub-problem of the workload -- best of 2."""
+    (z-invariant) vortex -- exactly a sub-problem of the workload -- best of 2 on all cores, and
+    one step of a 256 x 256 x 8 slab on one core."""
     import oracle
     from paper_1710_09995_gb300 import cases
     nz = 64
@@ -392,8 +412,18 @@ def cpu_baseline_sample(n):
         t0 = time.perf_counter()
         oracle.step(p, Q, M, 1)
         best = min(best, time.perf_counter() - t0)
-    return {"value": c.cells / best, "unit": "cell-updates/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"1 SSP-RK3 step (FP64) of a {n}x{n}x{nz} z-slab of the z-invariant vortex, best of 2"}
+    cores = oracle.threads()
+    c1 = cases.isentropic_vortex(n=n, L=10.0, nz=8, viscous=True)
+    M1, Q1 = oracle.metrics(c1.grid_nodes()), oracle.pad(c1.state)
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    oracle.step(p, Q1, M1, 1)
+    one = c1.cells / (time.perf_counter() - t0)
+    oracle.set_threads(cores)
+    return {"value": c.cells / best, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 SSP-RK3 step (FP64) of a {n}x{n}x{nz} z-slab of the z-invariant vortex, best of 2",
+            "value_1core": one, "sample_1core": f"1 SSP-RK3 step of a {n}x{n}x8 z-slab on one thread",
+            "cpu": cpu_model()}
 
 
 def cpu_baseline_warped():

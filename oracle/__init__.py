@@ -78,6 +78,7 @@ def lib():
         L.oracle_dt_local.argtypes = [P, i, i, i, _D, _D, _D]
         L.oracle_step_ex.argtypes = [P, i, i, i, _D, B, i, ctypes.c_double, _D, i, _D, _D]
         L.oracle_threads.argtypes = []
+        L.oracle_set_threads.argtypes = [i]
         L.oracle_wcns_edge.argtypes = [i, _D]
         L.oracle_wcns_edge.restype = ctypes.c_double
         L.oracle_wcns_residual.argtypes = [P, i, i, i, _D, _D, _D]
@@ -99,6 +100,11 @@ def _check(rc: int, what: str):
 
 def threads() -> int:
     return int(lib().oracle_threads())
+
+
+def set_threads(n: int) -> int:
+    """use n OpenMP threads from now on; returns the number in force"""
+    return int(lib().oracle_set_threads(int(n)))
 
 
 # ---- layout helpers -------------------------------------------------------------------------

@@ -58,6 +58,16 @@ int oracle_threads(void) {
 #endif
 }
 
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Eq. 1 state definitions                                                                     */
 

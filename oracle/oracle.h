@@ -156,6 +156,9 @@ int oracle_wcns_step(const oracle_params* p, int nx, int ny, int nz, const doubl
 /* threads the oracle's OpenMP loops use (1 when built without OpenMP) */
 int oracle_threads(void);
 
+/* set that number (n >= 1) and return the one now in force */
+int oracle_set_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif
