@@ -449,8 +449,18 @@ __device__ __forceinline__ void edges(V u0, V u1, V u2, V u3, V u4, bool linear,
   const V bc = dB * dC, ac = dA * dC, ab = dA * dB;
   const V nA = O::c(1.0 / 16.0) * bc, nB = O::c(10.0 / 16.0) * ac, nC = O::c(5.0 / 16.0) * ab;
   const V kA = O::c(5.0 / 16.0) * bc, kC = O::c(1.0 / 16.0) * ab;
-  up = u2 + O::fma(nA, pA, O::fma(nB, pB, nC * pC)) * O::rcp(nA + nB + nC);
-  um = u2 + O::fma(kA, mA, O::fma(nB, mB, kC * mC)) * O::rcp(kA + nB + kC);
+  const V dp = nA + nB + nC, dm = kA + nB + kC;
+  V rp, rm;
+  if constexpr (sizeof(V) == 8) {  // one FP64 division for both (dp, dm >= ~1e-25: no underflow)
+    const V r = O::rcp(dp * dm);
+    rp = dm * r;
+    rm = dp * r;
+  } else {
+    rp = O::rcp(dp);
+    rm = O::rcp(dm);
+  }
+  up = u2 + O::fma(nA, pA, O::fma(nB, pB, nC * pC)) * rp;
+  um = u2 + O::fma(kA, mA, O::fma(nB, mB, kC * mC)) * rm;
 }
 
 // The same for two variables at once in packed f32x2 arithmetic (one instruction per pair of

@@ -155,3 +155,34 @@ def test_errors(gb):
     with pytest.raises(gb.GbcfdError) as e:
         blk.step(1)
     assert e.value.code == gb.ERR_STATE
+
+
+def test_error_codes(gb):
+    import ctypes
+    L = gb.lib()
+    n = ctypes.c_size_t(0)
+    prm = gb.params()
+    assert L.gbcfd_wcns_required_bytes(0, 4, 4, ctypes.byref(prm), ctypes.byref(n)) == gb.ERR_ARG
+    assert L.gbcfd_wcns_required_bytes(4, 4, 4, ctypes.byref(prm), ctypes.byref(n)) == gb.OK
+    mem = torch.empty(n.value + 512, dtype=torch.uint8, device="cuda")
+    base = mem.data_ptr() + (-mem.data_ptr()) % 256
+    h = ctypes.c_void_p(0)
+    sp = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
+    assert L.gbcfd_wcns_create(4, 4, 4, ctypes.byref(prm), sp, ctypes.c_void_p(base + 8), n.value,
+                               ctypes.byref(h)) == gb.ERR_MEMORY
+    assert L.gbcfd_wcns_create(4, 4, 4, ctypes.byref(prm), sp, ctypes.c_void_p(base), n.value - 256,
+                               ctypes.byref(h)) == gb.ERR_MEMORY
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+def test_nonphysical_state_is_reported(gb, precision):
+    c = ragged(False, nx=20, ny=12, nz=8)
+    q = c.state.copy()
+    q[0, 3, 4, 5] = -0.5  # negative density in one cell
+    blk = gb.wcns_block_for_case(c, precision=getattr(gb, precision))
+    blk.set_state(torch.from_numpy(q).cuda())
+    blk.step(1)
+    with pytest.raises(gb.GbcfdError) as e:
+        blk.residual_norm()
+    assert e.value.code == gb.ERR_NONPHYSICAL
+    blk.residual_norm()  # the flag was cleared by the first report
