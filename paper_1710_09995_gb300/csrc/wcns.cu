@@ -9,16 +9,20 @@
 //                time step.
 //   visc_kernel  (Navier-Stokes) the viscous flux vectors Fv, Gv, Hv of Eq. 1 at every cell of
 //                the box padded by 2, from fourth-order central gradients (D4) of u, v, w, theta;
-//   viscdiv_kernel  their derivatives, Rv = -(D4_x Fv + D4_y Gv + D4_z Hv), at the interior cells.
+//                tiles marching in z over a shared ring of planes loaded by TMA.
+//   viscdiv_kernel  their derivatives, Rv = -(D4_x Fv + D4_y Gv + D4_z Hv), at the interior
+//                cells, from TMA boxes of the three flux families.
 //   dir_kernel<D> for D = x, y, z: a tile of 16 lines x L cells along D.  The tile's primitives
-//                (L + 10 cells per line) go to shared memory; a lane per cell evaluates both edge
-//                values of its cell (the two share the stencils' smoothness indicators), a shuffle
-//                pairs the left state of cell i with the right state of cell i + 1, and the Roe
-//                flux of every edge of the tile (L + 5 per line) is computed once; the fluxes
-//                replace the primitives in shared memory and each cell takes Eq. 2 of its six
-//                edge fluxes (the x pass also adds Rv).  x writes R, y adds to it, z
-//                adds and applies the stage update (or writes R out), with the residual norm of
-//                stage 1 reduced per CTA and by the last CTA in a fixed order.
+//                (L + 10 cells per line) land in shared memory by cp.async one tile ahead; a lane
+//                per cell evaluates both edge values of its cell (the two share the stencils'
+//                smoothness indicators; on the mixed path two variables per packed f32x2
+//                instruction), a shuffle pairs the left state of cell i with the right state of
+//                cell i + 1, and the Roe flux of every edge of the tile (L + 5 per line) is
+//                computed once; the fluxes replace the primitives in shared memory and each cell
+//                takes Eq. 2 of its six edge fluxes (the x pass also adds Rv).  x writes R, y adds
+//                to it, z adds and applies the stage update (or writes R out), with the residual
+//                norm of stage 1 reduced per CTA and folded by a warp of the last CTA in a fixed
+//                order.
 // Precision: FP64 everywhere, or mixed: the stage inputs are the f32 shadow S^n of Q^n plus an
 // f32 increment, D1 = -dt R(S^n), D2 = (D1 - dt R(S^n + D1)) / 4, and only the last stage touches
 // FP64: Q^{n+1} = Q^n + 2/3 (D2 - dt R(S^n + D2)), S^{n+1} = f32(Q^{n+1}) (algebraically Eqs. 4-6);
@@ -27,13 +31,12 @@
 // candidates u_i + g_k/2 + s_k/8 with g_k, s_k the stencil's first and second differences,
 // smoothness beta_k = g_k^2 + s_k^2, weights C_k / (1e-6 + beta_k)^2 normalised, optimal
 // C = (1/16, 10/16, 5/16); `limiter` = 1 takes C itself (linear fifth order).
-#include <algorithm>
-#include <cstring>
-#include <string>
-
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cstring>
 #include <mutex>
+#include <string>
 
 #include "gbcfd.h"
 #include "launch.h"
