@@ -881,6 +881,9 @@ def run_wcns(args, world, rank, local, device, torch, cases, gbcfd):
 
 # ---- the reference arm: the FP64 CPU oracle ----------------------------------------------------
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores, on a bounded z-slab
+    of the workload's vortex per step (the finite-volume oracle, or the WCNS-E-5 one for
+    --workload wcns256); rank 0 alone runs and prints."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -888,22 +891,30 @@ def run_reference(args):
     from paper_1710_09995_gb300 import cases
     nz = 8
     c = cases.isentropic_vortex(n=args.side, L=10.0, nz=nz, viscous=True)
-    M = oracle.metrics(c.grid_nodes())
     p = oracle.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, c.limiter)
-    Q = oracle.pad(c.state)
+    wcns = args.workload == "wcns256"
+    if wcns:
+        Q = c.state
+        step = lambda Q: oracle.wcns_step(p, Q, c.spacing, 1)[0]
+    else:
+        M = oracle.metrics(c.grid_nodes())
+        Q = oracle.pad(c.state)
+        step = lambda Q: oracle.step(p, Q, M, 1)[0]
     for _ in range(args.warmup):
-        Q, _, _ = oracle.step(p, Q, M, 1)
+        Q = step(Q)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        Q, _, _ = oracle.step(p, Q, M, 1)
+        Q = step(Q)
     sec = time.perf_counter() - t0
     value = c.cells * args.steps / sec
-    sample = (f"each step: 1 SSP-RK3 step (FP64 oracle) of a {args.side}x{args.side}x{nz} z-slab of the "
+    scheme = "WCNS-E-5 oracle" if wcns else "FP64 oracle"
+    sample = (f"each step: 1 SSP-RK3 step ({scheme}) of a {args.side}x{args.side}x{nz} z-slab of the "
               f"z-invariant {args.side}^3 vortex")
+    workload = "wcns256" if wcns else "vortex256"
     out = {"impl": "reference", "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOADS["vortex256"], "cells": c.cells, "precision": "fp64"},
+           "data": "synthetic", "config": {"workload": WORKLOADS[workload], "cells": c.cells, "precision": "fp64"},
            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": oracle.threads(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

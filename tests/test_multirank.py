@@ -48,3 +48,13 @@ def test_reference_arm_prints_one_line_from_rank0():
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_wcns_workload():
+    r = torchrun(["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--side", "32",
+                  "--workload", "wcns256"], 29613)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    assert "WCNS" in out["cpu_baseline"]["sample"] and out["value"] > 0
