@@ -723,14 +723,14 @@ def run_channel(args, world, rank, local, device, torch, cases, gbcfd):
 
 
 # ---- the paper's own scheme: WCNS-E-5 ----------------------------------------------------------
-WCNS_KERNELS = ("prim_kernel", "visc_kernel+viscdiv_kernel", "dir_kernel<x>", "dir_kernel<y>", "dir_kernel<z>")
+WCNS_KERNELS = ("prim_kernel", "viscres_kernel", "dir_kernel<x>", "dir_kernel<y>", "dir_kernel<z>")
 
 
 def wcns_kernel_bytes(precision, stage):
     """algorithmic HBM bytes per interior cell of each WCNS kernel of a stage (T = 4 mixed, 8 FP64):
     prim reads the stage input (f64 on the FP64 path; the f32 shadow and increment on the mixed
-    path) and writes 6 primitive fields; visc reads u, v, w, theta and writes 12 viscous-flux
-    fields, viscdiv reads them back and writes the 4-field viscous residual; the x pass reads 5
+    path) and writes 6 primitive fields; viscres reads u, v, w, theta and writes the 4-field
+    viscous residual; the x pass reads 5
     primitives and the viscous residual and writes R; y also reads R; z reads R and writes the
     stage output (mixed: D1 / D2, or Q^{n+1} and its shadow; FP64: Q1, Q2, Q^{n+1})"""
     t = 4 if precision == "mixed" else 8
@@ -740,7 +740,7 @@ def wcns_kernel_bytes(precision, stage):
     else:
         prim_in = 40
         z_io = {1: 80, 2: 120, 3: 120}[stage]
-    return {"prim_kernel": prim_in + 6 * t, "visc_kernel+viscdiv_kernel": 32 * t, "dir_kernel<x>": 14 * t,
+    return {"prim_kernel": prim_in + 6 * t, "viscres_kernel": 8 * t, "dir_kernel<x>": 14 * t,
             "dir_kernel<y>": 15 * t, "dir_kernel<z>": 10 * t + z_io}
 
 
@@ -777,7 +777,7 @@ def time_wcns(gbcfd, torch, case, precision, steps, warmup, world, device):
     blk.set_timing(None)
     norms = blk.residual_norm()
     blk.close()
-    nlaunch = 3 * (6 if case.viscous else 4) * steps
+    nlaunch = 3 * (5 if case.viscous else 4) * steps
     return {"ms": ms, "kernel_ms": kern, "kernel_stage_ms": per_stage, "launches": nlaunch, "norms": norms.tolist()}
 
 

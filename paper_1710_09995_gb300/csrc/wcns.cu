@@ -7,11 +7,11 @@
 //                padded by 5 cells (periodic images by index wrap: the halo exchange of a
 //                self-connected block); stage 1 also reduces the CFL rate of Q^n to the step's
 //                time step.
-//   visc_kernel  (Navier-Stokes) the viscous flux vectors Fv, Gv, Hv of Eq. 1 at every cell of
-//                the box padded by 2, from fourth-order central gradients (D4) of u, v, w, theta;
-//                tiles marching in z over a shared ring of planes loaded by TMA.
-//   viscdiv_kernel  their derivatives, Rv = -(D4_x Fv + D4_y Gv + D4_z Hv), at the interior
-//                cells, from TMA boxes of the three flux families.
+//   viscres_kernel  (Navier-Stokes) the viscous residual Rv = -(D4_x Fv + D4_y Gv + D4_z Hv) at the
+//                interior cells in one pass: tiles marching in z form the gradient tensor (D4 of
+//                u, v, w, theta) once per cell of the tile's union box from a TMA-fed ring of
+//                planes, keep the three viscous-flux families of Eq. 1 in shared rings and write
+//                only Rv.
 //   dir_kernel<D> for D = x, y, z: a tile of 16 lines x L cells along D.  The tile's primitives
 //                (L + 10 cells per line) land in shared memory by cp.async one tile ahead; a lane
 //                per cell evaluates both edge values of its cell (the two share the stencils'
@@ -81,16 +81,13 @@ struct Coef {
 struct Args {
   Coef<float> cf;
   Coef<double> cd;
-  CUtensorMap mw;           // W: 6 padded fields, box 40 x 12 x 1 x 1 (one field's plane box)
-  CUtensorMap mf8;          // Fv: 12 padded fields, box 40 x 8 x 1 x 4 (x- or z-fluxes of a tile)
-  CUtensorMap mf12;         // Fv: box 40 x 12 x 1 x 4 (y-fluxes of a tile and 2 rows each side)
+  CUtensorMap mwv;          // W: 6 padded fields, box 44 x 16 x 1 x 1 (one field's plane box)
   Box b;
   long long n;              // interior cells
   double gamma, mu, Pr, cfl, eps;
   double ih[3];             // inverse cell sizes
   int viscous, linear;
   void* W;                  // NPW padded fields (T)
-  void* Fv;                 // 12 padded fields (T): [d][mx, my, mz, energy]
   void* R;                  // compact [5][n] (T): the residual accumulated over the passes
   void* Rv;                 // compact [4][n] (T): the viscous part, -sum_d D4_d(F_v,d) (momentum, energy)
   // FP64 path
@@ -220,17 +217,33 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// The viscous kernel works on tiles of VX x VY output cells of the box padded by 2, marching in z
-// over chunks of VZ planes.  The planes it reads (u, v, w, theta of the tile plus 2 cells around,
-// k-2 .. k+2) sit in a shared ring with VAHEAD more planes in flight; one thread loads each plane as
-// four TMA boxes of 40 x 12 cells (starting at a 16-byte aligned column).
-constexpr int VX = 32, VY = 8, VZ = 32, VBX = 40, VBY = 12, VAHEAD = 1, VRING = 5 + VAHEAD;
+// ---- the viscous residual Rv = -(D4_x Fv + D4_y Gv + D4_z Hv), in one pass ----------------------
+// Tiles of 32 x 8 interior cells march in z over each CTA's contiguous share of tile-planes, with a
+// lead plane p two planes ahead of the output plane k = p - 2.  Per lead plane the gradient
+// tensor (D4 of u, v, w, theta along x, y, z) is formed once at every cell of the tile's union
+// box (x0 - 2 .. x0 + 33, y0 - 2 .. y0 + 9), from a ring of u, v, w, theta planes p - 2 .. p + 2
+// (each a TMA box of 44 x 16 cells starting at a 16-byte aligned column; plane p + 3 lands
+// meanwhile); from it the x-fluxes of the tile's rows (+2 columns each side) and the y-fluxes of
+// its columns (+2 rows each side) give the x- and y-parts of Rv at once (kept by each cell's
+// thread for two planes), and the z-fluxes of the tile go to a 5-plane ring for the z-part.
+// Only the 4-field residual reaches global memory.
+constexpr int RX = 32, RY = 8;                 // tile
+constexpr int GX = RX + 4, GY = RY + 4;        // union box of gradient cells (36 x 12)
+constexpr int WX = 44, WY = RY + 8;            // primitive box (44 x 16): cells x0-5 .., y0-4 ..
+constexpr int WRING = 6, ZRING = 5;            // 5 planes in use + 1 landing; z-fluxes k-2 .. k+2
 template <typename T>
-struct VSmem {
-  static constexpr int FIELD = VBY * VBX;             // one field's box
-  static constexpr int PLANE = 4 * FIELD;             // u, v, w, theta
-  static constexpr size_t bar = sizeof(T) * VRING * PLANE;
-  static constexpr size_t bytes = bar + 8 * VRING + 16;
+struct RSmem {
+  static constexpr int WF = WY * WX;                 // one field's plane box
+  static constexpr int WP = 4 * WF;                  // u, v, w, theta
+  static constexpr int FXP = 4 * RY * GX;            // x-fluxes of the lead plane: 4 x 8 rows x 36
+  static constexpr int GYP = 4 * GY * RX;            // y-fluxes: 4 x 12 rows x 32
+  static constexpr int HZP = 4 * RY * RX;            // z-fluxes: 4 x 8 x 32
+  static constexpr size_t w = 0;
+  static constexpr size_t fx = w + sizeof(T) * WRING * WP;
+  static constexpr size_t gy = fx + sizeof(T) * FXP;
+  static constexpr size_t hz = gy + sizeof(T) * GYP;
+  static constexpr size_t bar = (hz + sizeof(T) * ZRING * HZP + 15) / 16 * 16;
+  static constexpr size_t bytes = bar + 8 * WRING + 16;
 };
 
 // drain the copies of a CTA that stops early (bounded), flag the timeout
@@ -241,188 +254,154 @@ __device__ __forceinline__ void tma_abort(uint64_t* bar, unsigned pending, unsig
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NTW) visc_kernel(const __grid_constant__ Args a) {
-  extern __shared__ __align__(128) unsigned char vsm[];
-  T* ring = reinterpret_cast<T*>(vsm);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(vsm + VSmem<T>::bar);
-  int* sabort = reinterpret_cast<int*>(bar + VRING);
-  const Box& b = a.b;
-  T* F = static_cast<T*>(a.Fv);
-  const Coef<T>& C = coef<T>(a);
-  const T mu = C.mu, kappa = C.kappa;
-  const T* ih = C.ih12;
-  const int ex = b.nx + 4, ey = b.ny + 4, ez = b.nz + 4;  // the output box: [-2, n + 2) each way
-  const int ntx = (ex + VX - 1) / VX, nty = (ey + VY - 1) / VY, nch = (ez + VZ - 1) / VZ;
-  const int units = ntx * nty * nch;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < VRING; ++q) mbar_init(&bar[q], 1);
-    fence_barrier_init();
-    *sabort = 0;
-  }
-  __syncthreads();
-  unsigned parity = 0, pending = 0;  // per slot (parity uniform across threads; pending in thread 0)
-  auto slot = [](int kp) { return (kp + 16 * VRING) % VRING; };
-  for (int u = blockIdx.x; u < units && !*sabort; u += gridDim.x) {
-    const int ch = u % nch, t = u / nch;
-    const int tx = t % ntx, ty = t / ntx;
-    const int x0 = tx * VX - 2, y0 = ty * VY - 2;  // first output cell of the tile
-    const int kb = ch * VZ - 2, ke = min(kb + VZ, b.nz + 2);
-    // the box of plane kp: storage columns 32 tx .. 32 tx + 39 (cells x0 - 3 .. x0 + 36), rows
-    // y0 - 2 .. y0 + 9 (storage y0 + 3): u, v, w, theta (fields 1, 2, 3, 5)
-    auto issue = [&](int kp) {  // thread 0
-      const int q = slot(kp);
-      T* dst = ring + q * VSmem<T>::PLANE;
-      fence_proxy_async();
-      mbar_expect_tx(&bar[q], (unsigned)(sizeof(T) * VSmem<T>::PLANE));
-      const int fld[4] = {1, 2, 3, 5};
-      for (int f = 0; f < 4; ++f)
-        tma_load_4d(dst + f * VSmem<T>::FIELD, &a.mw, &bar[q], tx * VX, y0 + 3, kp + H, fld[f]);
-      pending |= 1u << q;
-    };
-    auto wait = [&](int kp) {  // all threads; a copy that never landed stays pending
-      const int q = slot(kp);
-      const bool ok = mbar_wait_bounded(&bar[q], (parity >> q) & 1u);
-      if (!ok) atomicOr(sabort, 1);
-      if (ok) parity ^= 1u << q;  // a failed wait leaves the phase for the drain below
-      if (threadIdx.x == 0 && ok) pending &= ~(1u << q);
-    };
-    __syncthreads();  // the previous unit is done with the ring
-    if (threadIdx.x == 0)
-      for (int kp = kb - 2; kp <= min(kb + 1 + VAHEAD, ke + 1); ++kp) issue(kp);
-    for (int kp = kb - 2; kp <= min(kb + 1, ke + 1); ++kp) wait(kp);
-    for (int k = kb; k < ke; ++k) {
-      // plane k + 2 + VAHEAD goes into the slot of plane k - 3, no longer read
-      if (threadIdx.x == 0 && k + 2 + VAHEAD <= ke + 1 && !*sabort) issue(k + 2 + VAHEAD);
-      wait(k + 2);
-      __syncthreads();
-      if (*sabort) break;
-      const int i = x0 + lane, j = y0 + warp;
-      if (i < b.nx + 2 && j < b.ny + 2) {
-        const int c = (warp + 2) * VBX + lane + 3;  // the cell in the box
-        const T* pl[5];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) pl[m] = ring + slot(k - 2 + m) * VSmem<T>::PLANE;
-        T g[4][3], vel[3];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const T* p0 = pl[2] + f * VSmem<T>::FIELD;
-          if (f < 3) vel[f] = p0[c];
-          g[f][0] = ((p0[c - 2] - p0[c + 2]) + T(8) * (p0[c + 1] - p0[c - 1])) * ih[0];
-          g[f][1] = ((p0[c - 2 * VBX] - p0[c + 2 * VBX]) + T(8) * (p0[c + VBX] - p0[c - VBX])) * ih[1];
-          const int o = f * VSmem<T>::FIELD + c;
-          g[f][2] = ((pl[0][o] - pl[4][o]) + T(8) * (pl[3][o] - pl[1][o])) * ih[2];
-        }
-        const T div = g[0][0] + g[1][1] + g[2][2];
-        const long long o = bidx(b, i, j, k);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          T tau[3];
-#pragma unroll
-          for (int q = 0; q < 3; ++q) tau[q] = mu * (g[q][d] + g[d][q]);
-          tau[d] = tau[d] - T(2.0 / 3.0) * mu * div;
-#pragma unroll
-          for (int q = 0; q < 3; ++q) F[(4 * d + q) * b.field + o] = tau[q];
-          F[(4 * d + 3) * b.field + o] = vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kappa * g[3][d];
-        }
-      }
-      __syncthreads();  // plane k-2's slot is refilled next
-    }
-  }
-  if (*sabort && threadIdx.x == 0) tma_abort(bar, pending, parity, VRING, a.ctrl);
-}
-
-// ---- the viscous residual: Rv = -(D4_x Fv + D4_y Gv + D4_z Hv) at the interior cells ----------
-// Tiles of 32 x 8 cells marching in z over each CTA's contiguous share of tile-planes.  Per plane
-// k the x-fluxes of the tile's rows (columns 32 t - 5 .. 32 t + 34), the y-fluxes of its columns
-// and 2 rows each side (double-buffered) and the z-fluxes of planes k-2 .. k+2 (a 6-slot ring) are
-// in shared memory; one thread loads them as TMA boxes, those of plane k+1 while k is computed.
-constexpr int DX = 32, DY = 8, DBX = 40, DRING = 6;
-template <typename T>
-struct DSmem {
-  static constexpr int FX = 4 * DY * DBX;          // x-fluxes, 4 components x 8 rows x 40
-  static constexpr int GY = 4 * (DY + 4) * DBX;    // y-fluxes, 4 components x 12 rows x 40
-  static constexpr int HZ = 4 * DY * DBX;          // z-fluxes of one plane
-  static constexpr int XY = FX + GY;
-  static constexpr size_t bar = sizeof(T) * (2 * XY + DRING * HZ);
-  static constexpr size_t bytes = bar + 8 * 2 + 16;
-};
-
-template <typename T>
-__global__ void __launch_bounds__(NTW) viscdiv_kernel(const __grid_constant__ Args a) {
-  extern __shared__ __align__(128) unsigned char dsm[];
-  T* xy = reinterpret_cast<T*>(dsm);            // 2 buffers of [FX | GY]
-  T* hz = xy + 2 * DSmem<T>::XY;                 // DRING planes of HZ
-  uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + DSmem<T>::bar);
-  int* sabort = reinterpret_cast<int*>(bar + 2);
+__global__ void __launch_bounds__(NTW) viscres_kernel(const __grid_constant__ Args a) {
+  extern __shared__ __align__(128) unsigned char rsm[];
+  T* wr = reinterpret_cast<T*>(rsm + RSmem<T>::w);
+  T* fxr = reinterpret_cast<T*>(rsm + RSmem<T>::fx);
+  T* gyr = reinterpret_cast<T*>(rsm + RSmem<T>::gy);
+  T* hzr = reinterpret_cast<T*>(rsm + RSmem<T>::hz);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(rsm + RSmem<T>::bar);
+  int* sabort = reinterpret_cast<int*>(bar + WRING);
   const Box& b = a.b;
   T* Rv = static_cast<T*>(a.Rv);
-  const T* ih = coef<T>(a).ih12;
-  const int ntx = (b.nx + DX - 1) / DX, nty = (b.ny + DY - 1) / DY;
+  const Coef<T>& C = coef<T>(a);
+  const T mu = C.mu, kappa = C.kappa, twothird = T(2.0 / 3.0);
+  const T ih0 = C.ih12[0], ih1 = C.ih12[1], ih2 = C.ih12[2];
+  const int ntx = (b.nx + RX - 1) / RX, nty = (b.ny + RY - 1) / RY;
   const long long units = (long long)ntx * nty * b.nz;
   const long long u0 = (long long)blockIdx.x * units / gridDim.x, u1 = (long long)(blockIdx.x + 1) * units / gridDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int q = 0; q < WRING; ++q) mbar_init(&bar[q], 1);
     fence_barrier_init();
     *sabort = 0;
   }
   __syncthreads();
-  unsigned parity = 0, pending = 0;
-  auto hslot = [](int kp) { return (kp + 4 * DRING) % DRING; };
+  unsigned parity = 0, pending = 0;  // per W slot (parity uniform; pending in thread 0)
+  auto ws = [](int kp) { return (kp + 4 * WRING) % WRING; };
+  auto zs = [](int kp) { return (kp + 4 * ZRING) % ZRING; };
+  T* fxp = fxr;
+  T* gyp = gyr;
   for (long long u = u0; u < u1 && !*sabort;) {
     const long long tile = u / b.nz;
     const int k0 = (int)(u - tile * b.nz);
     const int k1 = (int)min((long long)b.nz, k0 + (u1 - u));
     u += k1 - k0;
-    const int tx = (int)(tile % ntx), x0 = tx * DX, y0 = (int)(tile / ntx) * DY;
-    constexpr unsigned XYB = sizeof(T) * DSmem<T>::XY, HZB = sizeof(T) * DSmem<T>::HZ;
-    // the loads plane k waits for: its x- and y-fluxes into buffer k & 1 and the z-fluxes of
-    // plane k + 2 (with, for the first plane, those of planes k - 2 .. k + 1), on barrier k & 1
-    auto issue = [&](int k, bool first) {  // thread 0
-      const int q = k & 1;
-      T* d = xy + q * DSmem<T>::XY;
+    const int tx = (int)(tile % ntx), x0 = tx * RX, y0 = (int)(tile / ntx) * RY;
+    auto issue = [&](int kp) {  // thread 0: u, v, w, theta of plane kp (fields 1, 2, 3, 5)
+      const int q = ws(kp);
+      T* dst = wr + q * RSmem<T>::WP;
       fence_proxy_async();
-      mbar_expect_tx(&bar[q], XYB + (first ? 5 : 1) * HZB);
-      tma_load_4d(d, &a.mf8, &bar[q], tx * DX, y0 + H, k + H, 0);                     // Fv, rows y0..y0+7
-      tma_load_4d(d + DSmem<T>::FX, &a.mf12, &bar[q], tx * DX, y0 - 2 + H, k + H, 4);  // Gv, rows y0-2..y0+9
-      for (int kp = first ? k - 2 : k + 2; kp <= k + 2; ++kp)
-        tma_load_4d(hz + hslot(kp) * DSmem<T>::HZ, &a.mf8, &bar[q], tx * DX, y0 + H, kp + H, 8);  // Hv
+      mbar_expect_tx(&bar[q], (unsigned)(sizeof(T) * RSmem<T>::WP));
+      const int fld[4] = {1, 2, 3, 5};
+      for (int f = 0; f < 4; ++f)  // storage column x0 is cell x0 - 5; storage row y0 + 1 is cell y0 - 4
+        tma_load_4d(dst + f * RSmem<T>::WF, &a.mwv, &bar[q], x0, y0 + 1, kp + H, fld[f]);
       pending |= 1u << q;
     };
-    __syncthreads();  // the previous segment is done with the buffers
-    if (threadIdx.x == 0) issue(k0, true);
-    for (int k = k0; k < k1; ++k) {
-      const int cur = k & 1;
-      const bool ok = mbar_wait_bounded(&bar[cur], (parity >> cur) & 1u);
+    auto wait = [&](int kp) {  // all threads; a copy that never landed stays pending
+      const int q = ws(kp);
+      const bool ok = mbar_wait_bounded(&bar[q], (parity >> q) & 1u);
       if (!ok) atomicOr(sabort, 1);
-      if (ok) parity ^= 1u << cur;  // a failed wait leaves the phase for the drain below
-      if (threadIdx.x == 0 && ok) pending &= ~(1u << cur);
-      if (threadIdx.x == 0 && k + 1 < k1 && !*sabort) issue(k + 1, false);  // buffers of plane k-1: free
+      if (ok) parity ^= 1u << q;
+      if (threadIdx.x == 0 && ok) pending &= ~(1u << q);
+    };
+    // each thread owns tile cell (lane, warp): its x- and y-parts of Rv for planes p-2, p-1, p stay
+    // in registers until the z-part of plane p-2 is known
+    T rv2[4] = {0, 0, 0, 0}, rv1[4] = {0, 0, 0, 0};
+    __syncthreads();  // the previous segment is done with the rings
+    if (threadIdx.x == 0)
+      for (int kp = k0 - 4; kp <= k0; ++kp) issue(kp);
+    for (int kp = k0 - 4; kp <= k0 - 1; ++kp) wait(kp);
+    for (int p = k0 - 2; p <= k1 + 1; ++p) {  // lead plane p, output plane p - 2
+      if (threadIdx.x == 0 && p <= k1 && !*sabort) issue(p + 3);  // into the slot of plane p - 3
+      wait(p + 2);
       __syncthreads();
       if (*sabort) break;
-      const int i = x0 + lane, j = y0 + warp;
-      if (i < b.nx && j < b.ny) {
-        const T* fx = xy + cur * DSmem<T>::XY;
-        const T* gy = fx + DSmem<T>::FX;
-        const long long c = ((long long)k * b.ny + j) * b.nx + i;
+      const T* pl[5];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const T* f = fx + (q * DY + warp) * DBX + lane + H;        // column of cell i: i - x0 + 5
-          const T dx = (f[-2] - f[2]) + T(8) * (f[1] - f[-1]);
-          const T* g = gy + (q * (DY + 4) + warp + 2) * DBX + lane + H;
-          const T dy = (g[-2 * DBX] - g[2 * DBX]) + T(8) * (g[DBX] - g[-DBX]);
-          const int o = (q * DY + warp) * DBX + lane + H;
-          const T dz = (hz[hslot(k - 2) * DSmem<T>::HZ + o] - hz[hslot(k + 2) * DSmem<T>::HZ + o]) +
-                       T(8) * (hz[hslot(k + 1) * DSmem<T>::HZ + o] - hz[hslot(k - 1) * DSmem<T>::HZ + o]);
-          Rv[q * a.n + c] = -(dx * ih[0] + dy * ih[1] + dz * ih[2]);
+      for (int m = 0; m < 5; ++m) pl[m] = wr + ws(p - 2 + m) * RSmem<T>::WP;
+      T* hzp = hzr + zs(p) * RSmem<T>::HZP;
+      // the union box: a warp per 32-cell row (rows 0..7, then 8..11), and warps 4, 5 of the second
+      // pass take the 4 extra columns of all 12 rows (a row stride of 44 spreads them over distinct
+      // banks); walking the 36-wide box row-major would split warps over two rows and conflict
+      for (int pass = 0; pass < 2; ++pass) {
+        int gx, gy;
+        if (pass == 0) {
+          gy = warp;
+          gx = lane;
+        } else if (warp < GY - RY) {
+          gy = RY + warp;
+          gx = lane;
+        } else {
+          const int sidx = (warp - (GY - RY)) * 32 + lane;  // 0 .. 63; 48 side cells
+          if (sidx >= GY * (GX - RX)) continue;
+          gy = sidx / (GX - RX);
+          gx = RX + sidx % (GX - RX);
+        }
+        const int c = (gy + 2) * WX + gx + 3;  // the cell in the primitive box
+        T gr[4][3], vel[3];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const T* p0 = pl[2] + f * RSmem<T>::WF;
+          if (f < 3) vel[f] = p0[c];
+          gr[f][0] = ((p0[c - 2] - p0[c + 2]) + T(8) * (p0[c + 1] - p0[c - 1])) * ih0;
+          gr[f][1] = ((p0[c - 2 * WX] - p0[c + 2 * WX]) + T(8) * (p0[c + WX] - p0[c - WX])) * ih1;
+          const int o = f * RSmem<T>::WF + c;
+          gr[f][2] = ((pl[0][o] - pl[4][o]) + T(8) * (pl[3][o] - pl[1][o])) * ih2;
+        }
+        const T div = gr[0][0] + gr[1][1] + gr[2][2];
+        const bool rows = gy >= 2 && gy < RY + 2, cols = gx >= 2 && gx < RX + 2;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if ((d == 0 && !rows) || (d == 1 && !cols) || (d == 2 && !(rows && cols))) continue;
+          T tau[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) tau[q] = mu * (gr[q][d] + gr[d][q]);
+          tau[d] = tau[d] - twothird * mu * div;
+          const T e = vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kappa * gr[3][d];
+          T* dst;
+          int stride;
+          if (d == 0) { dst = fxp + (gy - 2) * GX + gx; stride = RY * GX; }
+          else if (d == 1) { dst = gyp + gy * RX + gx - 2; stride = GY * RX; }
+          else { dst = hzp + (gy - 2) * RX + gx - 2; stride = RY * RX; }
+          dst[0] = tau[0];
+          dst[stride] = tau[1];
+          dst[2 * stride] = tau[2];
+          dst[3 * stride] = e;
         }
       }
-      __syncthreads();  // the buffers of plane k (and z-plane k-2) are refilled next
+      __syncthreads();
+      // the x- and y-parts of the lead plane, then the output plane p - 2 with its z-part
+      T rv0[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T* f = fxp + (q * RY + warp) * GX + lane + 2;
+        const T dx = (f[-2] - f[2]) + T(8) * (f[1] - f[-1]);
+        const T* g = gyp + (q * GY + warp + 2) * RX + lane;
+        const T dy = (g[-2 * RX] - g[2 * RX]) + T(8) * (g[RX] - g[-RX]);
+        rv0[q] = dx * ih0 + dy * ih1;
+      }
+      const int k = p - 2;
+      const int i = x0 + lane, j = y0 + warp;
+      if (k >= k0 && i < b.nx && j < b.ny) {
+        const long long cc = ((long long)k * b.ny + j) * b.nx + i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int o = (q * RY + warp) * RX + lane;
+          const T dz = (hzr[zs(k - 2) * RSmem<T>::HZP + o] - hzr[zs(k + 2) * RSmem<T>::HZP + o]) +
+                       T(8) * (hzr[zs(k + 1) * RSmem<T>::HZP + o] - hzr[zs(k - 1) * RSmem<T>::HZP + o]);
+          Rv[q * a.n + cc] = -(rv2[q] + dz * ih2);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        rv2[q] = rv1[q];
+        rv1[q] = rv0[q];
+      }
+      __syncthreads();  // the x-, y-flux buffers, the z-slot of plane p - 2 and W slots are reused
     }
   }
-  if (*sabort && threadIdx.x == 0) tma_abort(bar, pending, parity, 2, a.ctrl);
+  if (*sabort && threadIdx.x == 0) tma_abort(bar, pending, parity, WRING, a.ctrl);
 }
 
 // ---- the weighted interpolation: both edge values of cell i from u_{i-2} .. u_{i+2} -----------
@@ -816,24 +795,15 @@ static cudaError_t set_smem() {
   if (e != cudaSuccess) return e;
   GB_SET(0, 0) GB_SET(1, 1) GB_SET(2, 2)
 #undef GB_SET
-  e = cudaFuncSetAttribute(visc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)VSmem<T>::bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(viscdiv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DSmem<T>::bytes);
+  e = cudaFuncSetAttribute(viscres_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RSmem<T>::bytes);
   if (e != cudaSuccess) return e;
   return cudaSuccess;
 }
 
 template <typename T>
-static int visc_occupancy() {
+static int viscres_occupancy() {
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, visc_kernel<T>, NTW, VSmem<T>::bytes);
-  return std::max(1, occ);
-}
-
-template <typename T>
-static int viscdiv_occupancy() {
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, viscdiv_kernel<T>, NTW, DSmem<T>::bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, viscres_kernel<T>, NTW, RSmem<T>::bytes);
   return std::max(1, occ);
 }
 
@@ -851,7 +821,7 @@ using namespace gbcfd;
 using namespace gbcfd::wcns;
 
 struct gbcfd_wcns_s {
-  CUtensorMap mw, mf8, mf12;  // TMA maps of the primitive box and of the viscous fluxes
+  CUtensorMap mwv;            // TMA map of the primitive box
   int nx, ny, nz;
   gbcfd_params p;
   double h[3];
@@ -861,14 +831,13 @@ struct gbcfd_wcns_s {
   float* sh;         // mixed: S^n = f32(Q^n)
   float* d[2];       // mixed: D1, D2
   void* W;
-  void* Fv;
   void* Rv;
   void* R;
   DevCtrl* ctrl;
   double* partial;
   int rows;          // partial rows (CTAs of the widest launch)
   int has_state;
-  int dir_grid, occ, vocc, docc;
+  int dir_grid, occ, rocc;
   cudaEvent_t events[18];  // timing marks (gbcfd_wcns_set_timing), 6 per stage
   int timing;
 };
@@ -878,7 +847,7 @@ namespace {
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WLayout {
-  size_t q, w, fv, rv, r, ctrl, partial, total;
+  size_t q, w, rv, r, ctrl, partial, total;
   Box box;
   int rows;
 };
@@ -897,7 +866,6 @@ bool layout(int nx, int ny, int nz, const gbcfd_params* p, int nsm, WLayout* L) 
   size_t off = 0;
   L->q = off;       off += elem == 8 ? 3 * al256((size_t)n * 5 * 8) : al256((size_t)n * 5 * 8) + 3 * al256((size_t)n * 5 * 4);
   L->w = off;       off += al256((size_t)b.field * NPW * elem);
-  L->fv = off;      off += p->viscous ? al256((size_t)b.field * 12 * elem) : 0;
   L->rv = off;      off += p->viscous ? al256((size_t)n * 4 * elem) : 0;
   L->r = off;       off += al256((size_t)n * 5 * elem);
   L->ctrl = off;    off += al256(sizeof(DevCtrl));
@@ -978,9 +946,7 @@ void fill_coef(const Args& a, Coef<T>& c) {
 Args make_args(gbcfd_wcns w) {
   Args a;
   std::memset(&a, 0, sizeof(a));
-  a.mw = w->mw;
-  a.mf8 = w->mf8;
-  a.mf12 = w->mf12;
+  a.mwv = w->mwv;
   a.b = w->box;
   a.n = (long long)w->nx * w->ny * w->nz;
   a.gamma = w->p.gamma;
@@ -994,7 +960,6 @@ Args make_args(gbcfd_wcns w) {
   fill_coef(a, a.cf);
   fill_coef(a, a.cd);
   a.W = w->W;
-  a.Fv = w->Fv;
   a.Rv = w->Rv;
   a.R = w->R;
   a.ctrl = w->ctrl;
@@ -1016,10 +981,7 @@ cudaError_t launch_pass(gbcfd_wcns w, Args a, int with_rate, const cudaEvent_t* 
   mark(0);
   prim_kernel<T><<<pgrid, NTW, 0, s>>>(a, with_rate);
   mark(1);
-  if (a.viscous) {
-    visc_kernel<T><<<w->nsm * w->vocc, NTW, VSmem<T>::bytes, s>>>(a);
-    viscdiv_kernel<T><<<w->nsm * w->docc, NTW, DSmem<T>::bytes, s>>>(a);
-  }
+  if (a.viscous) viscres_kernel<T><<<w->nsm * w->rocc, NTW, RSmem<T>::bytes, s>>>(a);
   mark(2);
   const size_t sm = Smem<T>::bytes;
   const int g = w->dir_grid;
@@ -1116,7 +1078,6 @@ extern "C" int gbcfd_wcns_create(int nx, int ny, int nz, const gbcfd_params* par
     w->d[0] = w->d[1] = nullptr;
   }
   w->W = base + L.w;
-  w->Fv = params->viscous ? base + L.fv : nullptr;
   w->Rv = params->viscous ? base + L.rv : nullptr;
   w->R = base + L.r;
   w->ctrl = reinterpret_cast<DevCtrl*>(base + L.ctrl);
@@ -1124,17 +1085,14 @@ extern "C" int gbcfd_wcns_create(int nx, int ny, int nz, const gbcfd_params* par
   w->rows = L.rows;
   {
     const int elem = mixed ? 4 : 8;
-    int rc = encode_box_map(&w->mw, w->W, w->box, elem, NPW, VBX, VBY, 1);
-    if (rc == GBCFD_OK && params->viscous) rc = encode_box_map(&w->mf8, w->Fv, w->box, elem, 12, DBX, DY, 4);
-    if (rc == GBCFD_OK && params->viscous) rc = encode_box_map(&w->mf12, w->Fv, w->box, elem, 12, DBX, DY + 4, 4);
+    const int rc = encode_box_map(&w->mwv, w->W, w->box, elem, NPW, WX, WY, 1);
     if (rc != GBCFD_OK) {
       delete w;
       return rc;
     }
   }
   w->occ = mixed ? dir_occupancy<float>() : dir_occupancy<double>();
-  w->vocc = mixed ? visc_occupancy<float>() : visc_occupancy<double>();
-  w->docc = mixed ? viscdiv_occupancy<float>() : viscdiv_occupancy<double>();
+  w->rocc = mixed ? viscres_occupancy<float>() : viscres_occupancy<double>();
   w->dir_grid = std::min(w->rows, nsm * w->occ);
   e = cudaMemset(w->ctrl, 0, sizeof(DevCtrl));
   if (e != cudaSuccess) {
