@@ -54,7 +54,7 @@ constexpr int NTW = 256;    // threads per CTA
 constexpr int NPW = 6;      // primitive fields: rho, u, v, w, p, theta
 constexpr int ITEMS = 2 * NL / (NTW / 32);  // (line, chunk) items per warp and tile
 
-struct Box {                // the padded box of W (halo H) and of the viscous fluxes
+struct Box {                // the padded box of the primitives W (halo H)
   int nx, ny, nz, px;       // interior sizes, row pitch (elements)
   long long field;          // elements per field
 };
@@ -203,8 +203,7 @@ __global__ void shadow_kernel(const double* __restrict__ q, float* __restrict__ 
     sh[c] = f64_to_f32_bits(q[c]);
 }
 
-// ---- viscous flux vectors at the cells of the box padded by 2 ------------------------------
-// asynchronous global -> shared copy of one element (cp.async, completes by group)
+// ---- asynchronous global -> shared copies of single elements (cp.async, completed by group) ----
 template <typename T>
 __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -674,7 +673,7 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
       else cp_async_wait_all();
     }
     __syncthreads();
-    // 3. Eq. 2 per cell, minus D4 of the viscous flux along D, then the pass's output
+    // 3. Eq. 2 per cell (plus the viscous residual in the x pass), then the pass's output
     const int ncell = D == 0 ? NL * 64 : Ls * NL;  // D = 0: a warp per line, lanes along x
     for (int e = threadIdx.x; e < ncell; e += NTW) {
       int l, c;
