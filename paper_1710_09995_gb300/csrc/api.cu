@@ -424,12 +424,20 @@ extern "C" int gbcfd_set_metrics(gbcfd_block b, const double* nodes, const doubl
 }
 
 // ---- state in / out ------------------------------------------------------------------------
-static int is_device_ptr(const void* p, bool* dev) {
+// where a caller's array lives: *dev for device (or managed) memory; otherwise *mapped is the
+// device address of pinned host memory (the GPU reads and writes it over the host link with the
+// same pointer under unified addressing), or NULL for pageable memory (copied through staging)
+static int locate_ptr(const void* p, bool* dev, void** mapped) {
   cudaPointerAttributes a;
   cudaError_t e = cudaPointerGetAttributes(&a, p);
   if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes");
   *dev = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  *mapped = (!*dev && a.type == cudaMemoryTypeHost) ? a.devicePointer : nullptr;
   return GBCFD_OK;
+}
+static int is_device_ptr(const void* p, bool* dev) {
+  void* mapped = nullptr;
+  return locate_ptr(p, dev, &mapped);
 }
 
 static double* state_ptr(gbcfd_block b) {
@@ -441,10 +449,13 @@ extern "C" int gbcfd_set_state(gbcfd_block b, const double* q, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t n = (size_t)b->nx * b->ny * b->nz;
   bool dev = false;
-  int rc = is_device_ptr(q, &dev);
+  void* mapped = nullptr;
+  int rc = locate_ptr(q, &dev, &mapped);
   if (rc) return rc;
   const double* src = q;
-  if (!dev) {
+  if (!dev && mapped) {
+    src = static_cast<const double*>(mapped);  // pinned host memory: the scatter reads it directly
+  } else if (!dev) {
     if (b->staging_bytes < 5 * n * sizeof(double)) return fail(GBCFD_ERR_MEMORY, "staging too small");
     CK(cudaMemcpyAsync(b->staging, q, 5 * n * sizeof(double), cudaMemcpyHostToDevice, s));
     src = reinterpret_cast<const double*>(b->staging);
@@ -463,10 +474,16 @@ extern "C" int gbcfd_get_state(gbcfd_block b, double* q, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t n = (size_t)b->nx * b->ny * b->nz;
   bool dev = false;
-  int rc = is_device_ptr(q, &dev);
+  void* mapped = nullptr;
+  int rc = locate_ptr(q, &dev, &mapped);
   if (rc) return rc;
   if (dev) {
     CK(launch_gather(b->g, state_ptr(b), q, s));
+    return GBCFD_OK;
+  }
+  if (mapped) {  // pinned host memory: the gather writes it directly
+    CK(launch_gather(b->g, state_ptr(b), static_cast<double*>(mapped), s));
+    CK(cudaStreamSynchronize(s));
     return GBCFD_OK;
   }
   double* tmp = reinterpret_cast<double*>(b->staging);

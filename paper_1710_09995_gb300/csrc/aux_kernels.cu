@@ -1,5 +1,8 @@
 // aux_kernels.cu -- halo exchange, state scatter/gather and time-step kernels.
+#include <algorithm>
+
 #include "launch.h"
+#include "vmath.cuh"
 
 namespace gbcfd {
 
@@ -87,31 +90,32 @@ cudaError_t launch_halo(const HaloGroup& G, cudaStream_t s) {
 
 // ---- compact <-> padded state --------------------------------------------------------------
 // shadow (may be null): the f32 rounding of the state, written alongside
+// A CTA per row (v, k, j) of nx values: src is compact [5][nz][ny][nx] (device memory, or pinned
+// host memory read over the host link), dst the padded f64 field; the mixed path's f32 shadow is
+// rounded on the integer pipe (bitwise the hardware rounding, see vmath.cuh).
 __global__ void scatter_kernel(Geometry g, const double* __restrict__ src, double* __restrict__ dst,
                                float* __restrict__ shadow) {
-  const long long n = (long long)g.nx * g.ny * g.nz;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 5 * n; t += stride) {
-    const int v = (int)(t / n);
-    const long long c = t - v * n;
-    const int i = (int)(c % g.nx);
-    const long long r = c / g.nx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    const double x = src[t];
-    dst[v * g.field + gidx(g, i, j, k)] = x;
-    if (shadow) shadow[v * g.fieldf + gidxf(g, i, j, k)] = float(x);
+  const int rows = 5 * g.ny * g.nz;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % g.ny, r = row / g.ny, k = r % g.nz, v = r / g.nz;
+    const double* s = src + (long long)row * g.nx;
+    double* d = dst + v * g.field + gidx(g, 0, j, k);
+    float* sh = shadow ? shadow + v * g.fieldf + gidxf(g, 0, j, k) : nullptr;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const double x = s[i];
+      d[i] = x;
+      if (sh) sh[i] = f64_to_f32_bits(x);
+    }
   }
 }
+// the reverse: padded f64 field -> compact [5][nz][ny][nx] (device memory or pinned host memory)
 __global__ void gather_kernel(Geometry g, const double* __restrict__ src, double* __restrict__ dst) {
-  const long long n = (long long)g.nx * g.ny * g.nz;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 5 * n; t += stride) {
-    const int v = (int)(t / n);
-    const long long c = t - v * n;
-    const int i = (int)(c % g.nx);
-    const long long r = c / g.nx;
-    const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-    dst[t] = src[v * g.field + gidx(g, i, j, k)];
+  const int rows = 5 * g.ny * g.nz;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % g.ny, r = row / g.ny, k = r % g.nz, v = r / g.nz;
+    const double* s = src + v * g.field + gidx(g, 0, j, k);
+    double* d = dst + (long long)row * g.nx;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) d[i] = s[i];
   }
 }
 static unsigned grid_for(long long work, int threads) {
@@ -120,14 +124,17 @@ static unsigned grid_for(long long work, int threads) {
   if (b < 1) b = 1;
   return (unsigned)b;
 }
+static unsigned row_grid(const Geometry& g) {
+  const long long rows = 5LL * g.ny * g.nz;
+  return (unsigned)std::min(rows, 65535LL * 16);
+}
+static int row_threads(const Geometry& g) { return g.nx >= 256 ? 256 : (g.nx >= 128 ? 128 : 64); }
 cudaError_t launch_scatter(const Geometry& g, const double* src, double* dst, float* shadow, cudaStream_t s) {
-  const long long n = 5LL * g.nx * g.ny * g.nz;
-  scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(g, src, dst, shadow);
+  scatter_kernel<<<row_grid(g), row_threads(g), 0, s>>>(g, src, dst, shadow);
   return cudaGetLastError();
 }
 cudaError_t launch_gather(const Geometry& g, const double* src, double* dst, cudaStream_t s) {
-  const long long n = 5LL * g.nx * g.ny * g.nz;
-  gather_kernel<<<grid_for(n, 256), 256, 0, s>>>(g, src, dst);
+  gather_kernel<<<row_grid(g), row_threads(g), 0, s>>>(g, src, dst);
   return cudaGetLastError();
 }
 

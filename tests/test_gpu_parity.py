@@ -246,6 +246,30 @@ def test_host_state_roundtrip(gb):
         assert np.array_equal(out, c.state)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pinned_host_state_paths(gb, precision):
+    """State in and out through pinned host buffers (read and written by the scatter / gather
+    kernels directly) equals the pageable and device paths: bitwise, and one step from either
+    start gives the same state."""
+    c = cases.smooth_random(37, 11, 7, seed=13, viscous=True, mu=2e-3)
+    pinned_in = torch.from_numpy(c.state).pin_memory()
+    pinned_out = torch.zeros_like(pinned_in).pin_memory()
+    prm = gb.params(mu=2e-3, viscous=True, precision=precision)
+    a = gb.Block(37, 11, 7, prm).periodic()
+    a.set_metrics(spacing=(0.05, 0.06, 0.1))
+    a.set_state(pinned_in)
+    a.get_state(pinned_out)
+    assert torch.equal(pinned_out, pinned_in)
+    b = gb.Block(37, 11, 7, prm).periodic()
+    b.set_metrics(spacing=(0.05, 0.06, 0.1))
+    b.set_state(c.state)  # pageable: through the staging copy
+    gb.step([a], 2)
+    gb.step([b], 2)
+    assert torch.equal(a.get_state(), b.get_state())
+    a.get_state(pinned_out)
+    assert torch.equal(pinned_out, b.get_state().cpu())
+
+
 def test_nonphysical_state_is_reported(gb):
     c = cases.smooth_random(16, 8, 4, seed=13)
     bad = c.state.copy()
