@@ -163,6 +163,39 @@ int gbcfd_residual_norm(gbcfd_block block, double out[5], void* stream);
 /* The time step the next stage 1 will use, copied to *dt on the host (synchronises). */
 int gbcfd_get_dt(gbcfd_block block, double* dt, void* stream);
 
+/* ---- host-to-host pipeline ------------------------------------------------------------------
+ * Advances many states that live in host memory (independent problems: an ensemble, the
+ * trajectories a learned model is trained on, states streamed in by a service) through a set
+ * of identical blocks, so that the host-link transfers overlap the computation.  Not in the
+ * paper.  Item i runs on member i mod n: its state q_in[5][nz][ny][nx] (float64, host) is
+ * uploaded by a copy engine into the member's staging area, set as by gbcfd_set_state (time step
+ * included), advanced nsteps SSP-RK3 steps as by gbcfd_step, and copied back to q_out[5][nz][ny][nx]
+ * on the host; results are bitwise those of gbcfd_set_state / gbcfd_step / gbcfd_get_state on
+ * one block.  Uploads, device work and downloads run on three streams of the pipeline, so with
+ * 3 members item i+1's upload and item i-1's download (the two directions of the link) run while
+ * item i steps. */
+typedef struct gbcfd_pipe_s* gbcfd_pipe;
+
+/* Create a pipeline over n (1..8) blocks of equal sizes, parameters, grid and boundary
+ * conditions, none connected to another block (periodic self-connections and boundary faces
+ * only).  The blocks must outlive the pipeline and are used by nothing else while items are in
+ * flight.  Waits for the device (the members' earlier work) before returning.  GBCFD_ERR_ARG for
+ * a mismatch, GBCFD_ERR_MEMORY if a member's staging area cannot hold a state. */
+int gbcfd_pipe_create(const gbcfd_block* blocks, int n, gbcfd_pipe* out);
+
+/* Wait for the pipeline's work and release its streams and events (not the blocks). */
+int gbcfd_pipe_destroy(gbcfd_pipe pipe);
+
+/* Enqueue one item and return.  q_in, q_out and norms (5 doubles: the RMS residual of the item's
+ * last step, as gbcfd_residual_norm reports it; NULL for none; not written when nsteps is 0) must
+ * be page-locked host memory (cudaHostAlloc, or a pinned torch tensor), else GBCFD_ERR_ARG;
+ * q_in must not change and q_out / norms must not be read until gbcfd_pipe_sync returns. */
+int gbcfd_pipe_submit(gbcfd_pipe pipe, const double* q_in, double* q_out, int nsteps, double* norms);
+
+/* Wait until every submitted item is in host memory.  Reports GBCFD_ERR_NONPHYSICAL /
+ * GBCFD_ERR_TIMEOUT if a kernel of any item flagged one (the flags are then cleared). */
+int gbcfd_pipe_sync(gbcfd_pipe pipe);
+
 /* The CFL time step of a state, with no device memory allocated by anyone: for callers that
  * cannot call cudaMalloc -- code running where the device allocator is off limits (inside a
  * pre-sized memory pool or a fixed-footprint service) or that holds no block.  The paper has no

@@ -465,7 +465,6 @@ extern "C" int gbcfd_set_state(gbcfd_block b, const double* q, void* stream) {
   b->next_stage = 1;
   if (b->metrics_dirty) return prepare_metrics(&b, 1, s);  // also evaluates the time step
   return init_rate(b, s);
-  return GBCFD_OK;
 }
 
 extern "C" int gbcfd_get_state(gbcfd_block b, double* q, void* stream) {
@@ -1039,6 +1038,146 @@ extern "C" int gbcfd_get_dt(gbcfd_block b, double* dt, void* stream) {
   int rc = read_ctrl(b, &h, static_cast<cudaStream_t>(stream));
   if (rc) return rc;
   *dt = h.dt;
+  return GBCFD_OK;
+}
+
+// ---- host-to-host pipeline ----------------------------------------------------------------
+// Items (a host state, nsteps steps, the host result) rotate over the member blocks.  Three
+// streams carry the uploads (copy engine, host -> the block's staging area), the device work
+// (scatter into the padded state, time step, the steps, gather into staging) and the downloads
+// (copy engine, staging -> host).  Item i+1's upload and item i-1's download use the two
+// directions of the host link while item i steps; a block takes its next item only after the
+// download of its previous one (events).
+struct gbcfd_pipe_s {
+  std::vector<gbcfd_block> blocks;
+  cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
+  std::vector<cudaEvent_t> up_done, comp_done, down_done;  // per member, of its latest item
+  long long items = 0;
+  size_t bytes = 0;  // one compact state, 5 nx ny nz doubles
+};
+
+static void pipe_release(gbcfd_pipe p) {
+  if (p->up) cudaStreamSynchronize(p->up);
+  if (p->comp) cudaStreamSynchronize(p->comp);
+  if (p->down) cudaStreamSynchronize(p->down);
+  for (auto* v : {&p->up_done, &p->comp_done, &p->down_done})
+    for (cudaEvent_t e : *v)
+      if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : {p->up, p->comp, p->down})
+    if (s) cudaStreamDestroy(s);
+  delete p;
+}
+
+static bool page_locked(const void* ptr) {
+  bool dev = false;
+  void* mapped = nullptr;
+  if (locate_ptr(ptr, &dev, &mapped) != GBCFD_OK) return false;
+  return !dev && mapped != nullptr;
+}
+
+extern "C" int gbcfd_pipe_create(const gbcfd_block* blocks, int n, gbcfd_pipe* out) {
+  if (!blocks || !out) return fail(GBCFD_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (n < 1 || n > 8) return fail(GBCFD_ERR_ARG, "a pipeline takes 1 to 8 blocks");
+  const gbcfd_block a = blocks[0];
+  if (!a) return fail(GBCFD_ERR_ARG, "NULL block");
+  const size_t bytes = sizeof(double) * 5 * (size_t)a->nx * a->ny * a->nz;
+  for (int i = 0; i < n; ++i) {
+    const gbcfd_block b = blocks[i];
+    if (!b) return fail(GBCFD_ERR_ARG, "NULL block");
+    for (int k = 0; k < i; ++k)
+      if (blocks[k] == b) return fail(GBCFD_ERR_ARG, "a block is listed twice");
+    if (b->nx != a->nx || b->ny != a->ny || b->nz != a->nz) return fail(GBCFD_ERR_ARG, "members differ in size");
+    if (memcmp(&b->p, &a->p, sizeof(gbcfd_params)) != 0) return fail(GBCFD_ERR_ARG, "members differ in parameters");
+    if (b->curvi != a->curvi || memcmp(b->spacing, a->spacing, sizeof(a->spacing)) != 0)
+      return fail(GBCFD_ERR_ARG, "members differ in grid");
+    for (int f = 0; f < 6; ++f) {
+      if (b->nbr[f] && b->nbr[f] != b) return fail(GBCFD_ERR_ARG, "members must not connect to other blocks");
+      if (!b->nbr[f] != !a->nbr[f] || (!b->nbr[f] && b->bc_kind[f] != a->bc_kind[f]))
+        return fail(GBCFD_ERR_ARG, "members differ in boundary conditions");
+    }
+    if (b->staging_bytes < bytes) return fail(GBCFD_ERR_MEMORY, "member staging area too small");
+  }
+  CK(cudaDeviceSynchronize());  // the members' earlier work (any stream) is done
+  gbcfd_pipe p = new gbcfd_pipe_s;
+  p->blocks.assign(blocks, blocks + n);
+  p->bytes = bytes;
+  p->up_done.assign(n, nullptr);
+  p->comp_done.assign(n, nullptr);
+  p->down_done.assign(n, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (cudaStream_t* s : {&p->up, &p->comp, &p->down})
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+  for (auto* v : {&p->up_done, &p->comp_done, &p->down_done})
+    for (cudaEvent_t& ev : *v)
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    pipe_release(p);
+    return cuda_fail(e, "pipeline streams and events");
+  }
+  *out = p;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_pipe_destroy(gbcfd_pipe p) {
+  if (!p) return fail(GBCFD_ERR_ARG, "NULL pipeline");
+  pipe_release(p);
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_pipe_submit(gbcfd_pipe p, const double* q_in, double* q_out, int nsteps, double* norms) {
+  if (!p || !q_in || !q_out) return fail(GBCFD_ERR_ARG, "NULL argument");
+  if (nsteps < 0) return fail(GBCFD_ERR_ARG, "nsteps must be >= 0");
+  if (!page_locked(q_in) || !page_locked(q_out) || (norms && !page_locked(norms)))
+    return fail(GBCFD_ERR_ARG, "pipeline buffers must be page-locked host memory");
+  const int nb = (int)p->blocks.size();
+  const int j = (int)(p->items % nb);
+  gbcfd_block b = p->blocks[j];
+  if (b->next_stage != 1) return fail(GBCFD_ERR_STATE, "a member block was left between stages");
+  // upload: the block's staging area is free once its previous item is downloaded
+  if (p->items >= nb) CK(cudaStreamWaitEvent(p->up, p->down_done[j], 0));
+  CK(cudaMemcpyAsync(b->staging, q_in, p->bytes, cudaMemcpyHostToDevice, p->up));
+  CK(cudaEventRecord(p->up_done[j], p->up));
+  // device work: the state as gbcfd_set_state sets it, the steps, the result into staging
+  CK(cudaStreamWaitEvent(p->comp, p->up_done[j], 0));
+  CK(launch_scatter(b->g, reinterpret_cast<const double*>(b->staging), state_ptr(b),
+                    b->p.precision == GBCFD_MIXED ? b->sh[b->cur] : nullptr, p->comp));
+  b->has_state = 1;
+  b->next_stage = 1;
+  int rc = b->metrics_dirty ? prepare_metrics(&b, 1, p->comp) : init_rate(b, p->comp);
+  if (rc) return rc;
+  rc = gbcfd_step(&b, 1, nsteps, p->comp);
+  if (rc) return rc;
+  CK(launch_gather(b->g, state_ptr(b), reinterpret_cast<double*>(b->staging), p->comp));
+  CK(cudaEventRecord(p->comp_done[j], p->comp));
+  // download: the result and the last step's stage-1 norms
+  CK(cudaStreamWaitEvent(p->down, p->comp_done[j], 0));
+  CK(cudaMemcpyAsync(q_out, b->staging, p->bytes, cudaMemcpyDeviceToHost, p->down));
+  if (norms && nsteps > 0)
+    CK(cudaMemcpyAsync(norms, b->ctrl->norms, 5 * sizeof(double), cudaMemcpyDeviceToHost, p->down));
+  CK(cudaEventRecord(p->down_done[j], p->down));
+  p->items++;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_pipe_sync(gbcfd_pipe p) {
+  if (!p) return fail(GBCFD_ERR_ARG, "NULL pipeline");
+  CK(cudaStreamSynchronize(p->up));
+  CK(cudaStreamSynchronize(p->comp));
+  CK(cudaStreamSynchronize(p->down));
+  int flags = 0;
+  for (gbcfd_block b : p->blocks) {
+    DevCtrl h;
+    const int rc = read_ctrl(b, &h, p->comp);
+    if (rc) return rc;
+    if (h.flag) {
+      flags |= h.flag;
+      CK(cudaMemsetAsync(&b->ctrl->flag, 0, sizeof(int), p->comp));
+    }
+  }
+  CK(cudaStreamSynchronize(p->comp));
+  if (flags & FLAG_TIMEOUT) return fail(GBCFD_ERR_TIMEOUT, "a bounded device wait timed out");
+  if (flags) return fail(GBCFD_ERR_NONPHYSICAL, "non-positive density or pressure, or a non-finite value");
   return GBCFD_OK;
 }
 

@@ -70,6 +70,10 @@ SIGNATURES = {
     "gbcfd_time_step_noalloc": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), _D, _VP,
                                 _VP],
     "gbcfd_set_boundary": [_VP, ctypes.c_int, ctypes.c_int, _D],
+    "gbcfd_pipe_create": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)],
+    "gbcfd_pipe_destroy": [_VP],
+    "gbcfd_pipe_submit": [_VP, _VP, _VP, ctypes.c_int, _VP],
+    "gbcfd_pipe_sync": [_VP],
     "gbcfd_group_required_bytes": [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
     "gbcfd_group_create": [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.c_size_t, ctypes.POINTER(_VP)],
     "gbcfd_group_destroy": [_VP],
@@ -279,6 +283,48 @@ def time_step_noalloc(q, prm: Params, spacing, out=None, stream=None):
     sp = (ctypes.c_double * 3)(*spacing)
     _check(lib().gbcfd_time_step_noalloc(_ptr(q), nx, ny, nz, ctypes.byref(prm), sp, _ptr(out), _stream(stream)))
     return out
+
+
+class Pipe:
+    """States in host memory advanced through identical blocks with the host-link copies
+    overlapping the steps (gbcfd_pipe_*).  submit() enqueues one item; sync() waits for all.
+    Buffers must be pinned (page-locked) float64 tensors of shape (5, nz, ny, nx); the pipeline
+    holds references to them until sync()."""
+
+    def __init__(self, blocks):
+        self.blocks = list(blocks)
+        h = ctypes.c_void_p(0)
+        _check(lib().gbcfd_pipe_create(_handles(self.blocks), len(self.blocks), ctypes.byref(h)))
+        self.handle = h
+        self._inflight = []
+
+    def submit(self, q_in, q_out, nsteps=1, norms=None):
+        b = self.blocks[0]
+        for t in (q_in, q_out):
+            assert t.dtype == torch.float64 and t.is_contiguous() and tuple(t.shape) == (5, b.nz, b.ny, b.nx)
+        if norms is not None:
+            assert norms.dtype == torch.float64 and norms.is_contiguous() and norms.numel() == 5
+        self._inflight.append((q_in, q_out, norms))
+        _check(lib().gbcfd_pipe_submit(self.handle, _ptr(q_in), _ptr(q_out), int(nsteps),
+                                       _ptr(norms) if norms is not None else None))
+
+    def sync(self):
+        try:
+            _check(lib().gbcfd_pipe_sync(self.handle))
+        finally:
+            self._inflight = []
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(lib().gbcfd_pipe_destroy(self.handle))
+        self.handle = None
+        self._inflight = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Group:
