@@ -835,10 +835,12 @@ def wcns_roofline(precision, res, cells, steps, peak, peak_kind):
 
 
 def e2e_wcns(gbcfd, torch, case, precision, steps, world, device):
-    blk = gbcfd.wcns_block_for_case(case, precision=gbcfd.MIXED if precision == "mixed" else gbcfd.FP64,
-                                    device=device)
+    """As e2e_path, on WCNS-E-5 blocks: the headline through a 3-block pipeline
+    (gbcfd_wcns_pipe_create + gbcfd_pipe_submit / _sync), `serial_value` through the block calls."""
+    prec = gbcfd.MIXED if precision == "mixed" else gbcfd.FP64
     host_in = torch.from_numpy(case.state).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
+    blk = gbcfd.wcns_block_for_case(case, precision=prec, device=device)
 
     def one():
         blk.set_state(host_in)
@@ -853,11 +855,32 @@ def e2e_wcns(gbcfd, torch, case, precision, steps, world, device):
     for _ in range(steps):
         one()
     torch.cuda.synchronize()
-    dt = max_over_ranks(time.perf_counter() - t0, world, device)
+    serial = max_over_ranks(time.perf_counter() - t0, world, device)
     blk.close()
+    members = [gbcfd.wcns_block_for_case(case, precision=prec, device=device) for _ in range(3)]
+    pipe = gbcfd.Pipe(members)
+    outs = [torch.empty_like(host_in).pin_memory() for _ in range(3)]
+    norms = torch.zeros((max(steps, 3), 5), dtype=torch.float64).pin_memory()
+    for i in range(3):
+        pipe.submit(host_in, outs[i], 1, norms[i])
+    pipe.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        pipe.submit(host_in, outs[i % 3], 1, norms[i])
+    pipe.sync()
+    dt = max_over_ranks(time.perf_counter() - t0, world, device)
+    pipe.close()
+    for b in members:
+        b.close()
     nbytes = case.state.nbytes
     return {"value": world * case.cells * steps / dt, "unit": "cell-updates/s",
-            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 112}
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 40,
+            "api": "gbcfd_pipe_submit x steps + gbcfd_pipe_sync (3 WCNS member blocks)",
+            "serial_value": world * case.cells * steps / serial,
+            "serial_api": "gbcfd_wcns_set_state + _step + _get_state + _residual_norm per step",
+            "serial_d2h_bytes_per_step": nbytes + 112, "steps": steps}
 
 
 def cpu_baseline_wcns(n):
@@ -889,7 +912,7 @@ def run_wcns(args, world, rank, local, device, torch, cases, gbcfd):
                for p in paths}
     clk = clocks.stop()
     head = paths[0]
-    e2e = e2e_wcns(gbcfd, torch, case, head, min(args.e2e_steps, steps[head]), world, device)
+    e2e = e2e_wcns(gbcfd, torch, case, head, args.e2e_steps, world, device)
     cpu = cpu_baseline_wcns(args.side) if rank == 0 and world == 1 and not args.no_cpu_baseline else None
     if rank != 0:
         return

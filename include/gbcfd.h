@@ -360,6 +360,12 @@ int gbcfd_wcns_get_dt(gbcfd_wcns block, double* dt, void* stream);
  * kernels (m = 1..5); the next step overwrites them.  events NULL removes them; n must be 18. */
 int gbcfd_wcns_set_timing(gbcfd_wcns block, void* const* events, int n);
 
+/* A host-to-host pipeline (gbcfd_pipe_submit / _sync / _destroy) over n (1..8) WCNS blocks of
+ * equal sizes, parameters and cell sizes: each item's state is uploaded into a member's Q^n,
+ * set as by gbcfd_wcns_set_state, advanced nsteps steps as by gbcfd_wcns_step and copied back;
+ * bitwise the results of those calls on one block.  Waits for the device before returning. */
+int gbcfd_wcns_pipe_create(const gbcfd_wcns* blocks, int n, gbcfd_pipe* out);
+
 /* Message of the last error on the calling host thread ("" if none). */
 const char* gbcfd_last_error(void);
 

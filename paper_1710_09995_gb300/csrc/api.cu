@@ -1042,18 +1042,17 @@ extern "C" int gbcfd_get_dt(gbcfd_block b, double* dt, void* stream) {
 }
 
 // ---- host-to-host pipeline ----------------------------------------------------------------
-// Items (a host state, nsteps steps, the host result) rotate over the member blocks.  Three
-// streams carry the uploads (copy engine, host -> the block's staging area), the device work
-// (scatter into the padded state, time step, the steps, gather into staging) and the downloads
-// (copy engine, staging -> host).  Item i+1's upload and item i-1's download use the two
-// directions of the host link while item i steps; a block takes its next item only after the
-// download of its previous one (events).
+// Items (a host state, nsteps steps, the host result) rotate over the members.  Three streams
+// carry the uploads (copy engine, host -> the member's landing area), the device work (state
+// from the landing area, the steps, the result back into it) and the downloads (copy engine,
+// landing area -> host).  Item i+1's upload and item i-1's download use the two directions of
+// the host link while item i steps; a member takes its next item only after the download of its
+// previous one (events).
 struct gbcfd_pipe_s {
-  std::vector<gbcfd_block> blocks;
+  std::vector<PipeMember> members;
   cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
   std::vector<cudaEvent_t> up_done, comp_done, down_done;  // per member, of its latest item
   long long items = 0;
-  size_t bytes = 0;  // one compact state, 5 nx ny nz doubles
 };
 
 static void pipe_release(gbcfd_pipe p) {
@@ -1075,33 +1074,10 @@ static bool page_locked(const void* ptr) {
   return !dev && mapped != nullptr;
 }
 
-extern "C" int gbcfd_pipe_create(const gbcfd_block* blocks, int n, gbcfd_pipe* out) {
-  if (!blocks || !out) return fail(GBCFD_ERR_ARG, "NULL argument");
-  *out = nullptr;
-  if (n < 1 || n > 8) return fail(GBCFD_ERR_ARG, "a pipeline takes 1 to 8 blocks");
-  const gbcfd_block a = blocks[0];
-  if (!a) return fail(GBCFD_ERR_ARG, "NULL block");
-  const size_t bytes = sizeof(double) * 5 * (size_t)a->nx * a->ny * a->nz;
-  for (int i = 0; i < n; ++i) {
-    const gbcfd_block b = blocks[i];
-    if (!b) return fail(GBCFD_ERR_ARG, "NULL block");
-    for (int k = 0; k < i; ++k)
-      if (blocks[k] == b) return fail(GBCFD_ERR_ARG, "a block is listed twice");
-    if (b->nx != a->nx || b->ny != a->ny || b->nz != a->nz) return fail(GBCFD_ERR_ARG, "members differ in size");
-    if (memcmp(&b->p, &a->p, sizeof(gbcfd_params)) != 0) return fail(GBCFD_ERR_ARG, "members differ in parameters");
-    if (b->curvi != a->curvi || memcmp(b->spacing, a->spacing, sizeof(a->spacing)) != 0)
-      return fail(GBCFD_ERR_ARG, "members differ in grid");
-    for (int f = 0; f < 6; ++f) {
-      if (b->nbr[f] && b->nbr[f] != b) return fail(GBCFD_ERR_ARG, "members must not connect to other blocks");
-      if (!b->nbr[f] != !a->nbr[f] || (!b->nbr[f] && b->bc_kind[f] != a->bc_kind[f]))
-        return fail(GBCFD_ERR_ARG, "members differ in boundary conditions");
-    }
-    if (b->staging_bytes < bytes) return fail(GBCFD_ERR_MEMORY, "member staging area too small");
-  }
+int gbcfd::pipe_create(const PipeMember* members, int n, gbcfd_pipe* out) {
   CK(cudaDeviceSynchronize());  // the members' earlier work (any stream) is done
   gbcfd_pipe p = new gbcfd_pipe_s;
-  p->blocks.assign(blocks, blocks + n);
-  p->bytes = bytes;
+  p->members.assign(members, members + n);
   p->up_done.assign(n, nullptr);
   p->comp_done.assign(n, nullptr);
   p->down_done.assign(n, nullptr);
@@ -1119,6 +1095,76 @@ extern "C" int gbcfd_pipe_create(const gbcfd_block* blocks, int n, gbcfd_pipe* o
   return GBCFD_OK;
 }
 
+// finite-volume members: the landing area is the block's staging area
+static int fv_upload(void* self, const double* q_in, cudaStream_t s) {
+  gbcfd_block b = static_cast<gbcfd_block>(self);
+  CK(cudaMemcpyAsync(b->staging, q_in, sizeof(double) * 5 * (size_t)b->nx * b->ny * b->nz,
+                     cudaMemcpyHostToDevice, s));
+  return GBCFD_OK;
+}
+static int fv_run(void* self, int nsteps, cudaStream_t s) {
+  gbcfd_block b = static_cast<gbcfd_block>(self);
+  if (b->next_stage != 1) return fail(GBCFD_ERR_STATE, "a member block was left between stages");
+  // the state as gbcfd_set_state sets it from device memory
+  CK(launch_scatter(b->g, reinterpret_cast<const double*>(b->staging), state_ptr(b),
+                    b->p.precision == GBCFD_MIXED ? b->sh[b->cur] : nullptr, s));
+  b->has_state = 1;
+  b->next_stage = 1;
+  int rc = b->metrics_dirty ? prepare_metrics(&b, 1, s) : init_rate(b, s);
+  if (rc) return rc;
+  rc = gbcfd_step(&b, 1, nsteps, s);
+  if (rc) return rc;
+  CK(launch_gather(b->g, state_ptr(b), reinterpret_cast<double*>(b->staging), s));
+  return GBCFD_OK;
+}
+static int fv_download(void* self, double* q_out, double* norms, int nsteps, cudaStream_t s) {
+  gbcfd_block b = static_cast<gbcfd_block>(self);
+  CK(cudaMemcpyAsync(q_out, b->staging, sizeof(double) * 5 * (size_t)b->nx * b->ny * b->nz,
+                     cudaMemcpyDeviceToHost, s));
+  if (norms && nsteps > 0) CK(cudaMemcpyAsync(norms, b->ctrl->norms, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return GBCFD_OK;
+}
+static int fv_flags(void* self, cudaStream_t s, int* flags) {
+  gbcfd_block b = static_cast<gbcfd_block>(self);
+  DevCtrl h;
+  const int rc = read_ctrl(b, &h, s);
+  if (rc) return rc;
+  *flags = h.flag;
+  if (h.flag) {
+    CK(cudaMemsetAsync(&b->ctrl->flag, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_pipe_create(const gbcfd_block* blocks, int n, gbcfd_pipe* out) {
+  if (!blocks || !out) return fail(GBCFD_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (n < 1 || n > 8) return fail(GBCFD_ERR_ARG, "a pipeline takes 1 to 8 blocks");
+  const gbcfd_block a = blocks[0];
+  if (!a) return fail(GBCFD_ERR_ARG, "NULL block");
+  const size_t bytes = sizeof(double) * 5 * (size_t)a->nx * a->ny * a->nz;
+  std::vector<PipeMember> m(n);
+  for (int i = 0; i < n; ++i) {
+    const gbcfd_block b = blocks[i];
+    if (!b) return fail(GBCFD_ERR_ARG, "NULL block");
+    for (int k = 0; k < i; ++k)
+      if (blocks[k] == b) return fail(GBCFD_ERR_ARG, "a block is listed twice");
+    if (b->nx != a->nx || b->ny != a->ny || b->nz != a->nz) return fail(GBCFD_ERR_ARG, "members differ in size");
+    if (memcmp(&b->p, &a->p, sizeof(gbcfd_params)) != 0) return fail(GBCFD_ERR_ARG, "members differ in parameters");
+    if (b->curvi != a->curvi || memcmp(b->spacing, a->spacing, sizeof(a->spacing)) != 0)
+      return fail(GBCFD_ERR_ARG, "members differ in grid");
+    for (int f = 0; f < 6; ++f) {
+      if (b->nbr[f] && b->nbr[f] != b) return fail(GBCFD_ERR_ARG, "members must not connect to other blocks");
+      if (!b->nbr[f] != !a->nbr[f] || (!b->nbr[f] && b->bc_kind[f] != a->bc_kind[f]))
+        return fail(GBCFD_ERR_ARG, "members differ in boundary conditions");
+    }
+    if (b->staging_bytes < bytes) return fail(GBCFD_ERR_MEMORY, "member staging area too small");
+    m[i] = PipeMember{b, bytes, fv_upload, fv_run, fv_download, fv_flags};
+  }
+  return pipe_create(m.data(), n, out);
+}
+
 extern "C" int gbcfd_pipe_destroy(gbcfd_pipe p) {
   if (!p) return fail(GBCFD_ERR_ARG, "NULL pipeline");
   pipe_release(p);
@@ -1130,31 +1176,21 @@ extern "C" int gbcfd_pipe_submit(gbcfd_pipe p, const double* q_in, double* q_out
   if (nsteps < 0) return fail(GBCFD_ERR_ARG, "nsteps must be >= 0");
   if (!page_locked(q_in) || !page_locked(q_out) || (norms && !page_locked(norms)))
     return fail(GBCFD_ERR_ARG, "pipeline buffers must be page-locked host memory");
-  const int nb = (int)p->blocks.size();
+  const int nb = (int)p->members.size();
   const int j = (int)(p->items % nb);
-  gbcfd_block b = p->blocks[j];
-  if (b->next_stage != 1) return fail(GBCFD_ERR_STATE, "a member block was left between stages");
-  // upload: the block's staging area is free once its previous item is downloaded
+  const PipeMember& m = p->members[j];
+  // upload: the member's landing area is free once its previous item is downloaded
   if (p->items >= nb) CK(cudaStreamWaitEvent(p->up, p->down_done[j], 0));
-  CK(cudaMemcpyAsync(b->staging, q_in, p->bytes, cudaMemcpyHostToDevice, p->up));
+  int rc = m.upload(m.self, q_in, p->up);
+  if (rc) return rc;
   CK(cudaEventRecord(p->up_done[j], p->up));
-  // device work: the state as gbcfd_set_state sets it, the steps, the result into staging
   CK(cudaStreamWaitEvent(p->comp, p->up_done[j], 0));
-  CK(launch_scatter(b->g, reinterpret_cast<const double*>(b->staging), state_ptr(b),
-                    b->p.precision == GBCFD_MIXED ? b->sh[b->cur] : nullptr, p->comp));
-  b->has_state = 1;
-  b->next_stage = 1;
-  int rc = b->metrics_dirty ? prepare_metrics(&b, 1, p->comp) : init_rate(b, p->comp);
+  rc = m.run(m.self, nsteps, p->comp);
   if (rc) return rc;
-  rc = gbcfd_step(&b, 1, nsteps, p->comp);
-  if (rc) return rc;
-  CK(launch_gather(b->g, state_ptr(b), reinterpret_cast<double*>(b->staging), p->comp));
   CK(cudaEventRecord(p->comp_done[j], p->comp));
-  // download: the result and the last step's stage-1 norms
   CK(cudaStreamWaitEvent(p->down, p->comp_done[j], 0));
-  CK(cudaMemcpyAsync(q_out, b->staging, p->bytes, cudaMemcpyDeviceToHost, p->down));
-  if (norms && nsteps > 0)
-    CK(cudaMemcpyAsync(norms, b->ctrl->norms, 5 * sizeof(double), cudaMemcpyDeviceToHost, p->down));
+  rc = m.download(m.self, q_out, norms, nsteps, p->down);
+  if (rc) return rc;
   CK(cudaEventRecord(p->down_done[j], p->down));
   p->items++;
   return GBCFD_OK;
@@ -1166,16 +1202,12 @@ extern "C" int gbcfd_pipe_sync(gbcfd_pipe p) {
   CK(cudaStreamSynchronize(p->comp));
   CK(cudaStreamSynchronize(p->down));
   int flags = 0;
-  for (gbcfd_block b : p->blocks) {
-    DevCtrl h;
-    const int rc = read_ctrl(b, &h, p->comp);
+  for (const PipeMember& m : p->members) {
+    int f = 0;
+    const int rc = m.flags(m.self, p->comp, &f);
     if (rc) return rc;
-    if (h.flag) {
-      flags |= h.flag;
-      CK(cudaMemsetAsync(&b->ctrl->flag, 0, sizeof(int), p->comp));
-    }
+    flags |= f;
   }
-  CK(cudaStreamSynchronize(p->comp));
   if (flags & FLAG_TIMEOUT) return fail(GBCFD_ERR_TIMEOUT, "a bounded device wait timed out");
   if (flags) return fail(GBCFD_ERR_NONPHYSICAL, "non-positive density or pressure, or a non-finite value");
   return GBCFD_OK;

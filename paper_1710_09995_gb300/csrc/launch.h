@@ -2,6 +2,7 @@
 #pragma once
 #include <string>
 
+#include "gbcfd.h"
 #include "internal.cuh"
 
 namespace gbcfd {
@@ -43,5 +44,18 @@ cudaError_t launch_init_rate_curvi(const Geometry& g, const Physics& ph, const d
                                    cudaStream_t s);
 // global time step of a group: dt = cfl / max rate, written to every block
 cudaError_t launch_group_dt(DevCtrl* const* ctrls, int n, double cfl, cudaStream_t s, DevCtrl* extra = nullptr);
+
+// one member of a host-to-host pipeline (gbcfd_pipe_*): its phases, each enqueued on the stream
+// it is given; every one returns GBCFD_OK or an error code set by set_error
+struct PipeMember {
+  void* self;
+  size_t bytes;  // one compact state, 5 nx ny nz doubles
+  int (*upload)(void* self, const double* q_in, cudaStream_t s);    // host -> landing area (copy engine)
+  int (*run)(void* self, int nsteps, cudaStream_t s);               // landing area -> state, steps, result -> landing area
+  int (*download)(void* self, double* q_out, double* norms, int nsteps, cudaStream_t s);  // landing area -> host
+  int (*flags)(void* self, cudaStream_t s, int* flags);             // read and clear the device flags (synchronises s)
+};
+// a pipeline over n members (streams and events created here); waits for the device first
+int pipe_create(const PipeMember* members, int n, gbcfd_pipe* out);
 
 }  // namespace gbcfd

@@ -37,6 +37,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "gbcfd.h"
 #include "launch.h"
@@ -1206,4 +1207,71 @@ extern "C" int gbcfd_wcns_set_timing(gbcfd_wcns w, void* const* events, int n) {
   }
   w->timing = 1;
   return GBCFD_OK;
+}
+
+// ---- host-to-host pipeline members: the landing area is the compact state Q^n itself ----------
+namespace {
+int wp_upload(void* self, const double* q_in, cudaStream_t s) {
+  gbcfd_wcns w = static_cast<gbcfd_wcns>(self);
+  cudaError_t e = cudaMemcpyAsync(w->q[0], q_in, (size_t)w->nx * w->ny * w->nz * 5 * sizeof(double),
+                                  cudaMemcpyHostToDevice, s);
+  return e == cudaSuccess ? GBCFD_OK : cuda_err(e, "cudaMemcpyAsync");
+}
+int wp_run(void* self, int nsteps, cudaStream_t s) {
+  gbcfd_wcns w = static_cast<gbcfd_wcns>(self);
+  if (w->mixed) {  // as gbcfd_wcns_set_state; the control block keeps its flags until read
+    shadow_kernel<<<w->nsm * 8, 256, 0, s>>>(w->q[0], w->sh, (long long)w->nx * w->ny * w->nz * 5);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(e, "shadow kernel launch");
+  }
+  w->has_state = 1;
+  for (int n = 0; n < nsteps; ++n)
+    for (int st = 1; st <= 3; ++st) {
+      const int rc = run_stage(w, st, nullptr, s);
+      if (rc != GBCFD_OK) return rc;
+    }
+  return GBCFD_OK;
+}
+int wp_download(void* self, double* q_out, double* norms, int nsteps, cudaStream_t s) {
+  gbcfd_wcns w = static_cast<gbcfd_wcns>(self);
+  cudaError_t e = cudaMemcpyAsync(q_out, w->q[0], (size_t)w->nx * w->ny * w->nz * 5 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && norms && nsteps > 0)
+    e = cudaMemcpyAsync(norms, w->ctrl->norms, 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  return e == cudaSuccess ? GBCFD_OK : cuda_err(e, "cudaMemcpyAsync");
+}
+int wp_flags(void* self, cudaStream_t s, int* flags) {
+  gbcfd_wcns w = static_cast<gbcfd_wcns>(self);
+  DevCtrl h;
+  int rc = read_ctrl(w, &h, s);
+  if (rc != GBCFD_OK) return rc;
+  *flags = h.flag;
+  if (h.flag) {
+    cudaError_t e = cudaMemsetAsync(&w->ctrl->flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(e, "clearing the device flag");
+  }
+  return GBCFD_OK;
+}
+}  // namespace
+
+extern "C" int gbcfd_wcns_pipe_create(const gbcfd_wcns* blocks, int n, gbcfd_pipe* out) {
+  if (!blocks || !out) return set_error(GBCFD_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (n < 1 || n > 8) return set_error(GBCFD_ERR_ARG, "a pipeline takes 1 to 8 blocks");
+  const gbcfd_wcns a = blocks[0];
+  if (!a) return set_error(GBCFD_ERR_ARG, "NULL block");
+  const size_t bytes = (size_t)a->nx * a->ny * a->nz * 5 * sizeof(double);
+  std::vector<PipeMember> m(n);
+  for (int i = 0; i < n; ++i) {
+    const gbcfd_wcns w = blocks[i];
+    if (!w) return set_error(GBCFD_ERR_ARG, "NULL block");
+    for (int k = 0; k < i; ++k)
+      if (blocks[k] == w) return set_error(GBCFD_ERR_ARG, "a block is listed twice");
+    if (w->nx != a->nx || w->ny != a->ny || w->nz != a->nz) return set_error(GBCFD_ERR_ARG, "members differ in size");
+    if (memcmp(&w->p, &a->p, sizeof(gbcfd_params)) != 0 || memcmp(w->h, a->h, sizeof(a->h)) != 0)
+      return set_error(GBCFD_ERR_ARG, "members differ in parameters or cell sizes");
+    m[i] = PipeMember{w, bytes, wp_upload, wp_run, wp_download, wp_flags};
+  }
+  return pipe_create(m.data(), n, out);
 }

@@ -74,6 +74,7 @@ SIGNATURES = {
     "gbcfd_pipe_destroy": [_VP],
     "gbcfd_pipe_submit": [_VP, _VP, _VP, ctypes.c_int, _VP],
     "gbcfd_pipe_sync": [_VP],
+    "gbcfd_wcns_pipe_create": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)],
     "gbcfd_group_required_bytes": [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
     "gbcfd_group_create": [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.c_size_t, ctypes.POINTER(_VP)],
     "gbcfd_group_destroy": [_VP],
@@ -292,9 +293,12 @@ class Pipe:
     holds references to them until sync()."""
 
     def __init__(self, blocks):
+        """blocks: finite-volume Blocks, or WcnsBlocks (the paper's scheme)"""
         self.blocks = list(blocks)
+        assert self.blocks and all(type(b) is type(self.blocks[0]) for b in self.blocks)
         h = ctypes.c_void_p(0)
-        _check(lib().gbcfd_pipe_create(_handles(self.blocks), len(self.blocks), ctypes.byref(h)))
+        create = lib().gbcfd_wcns_pipe_create if isinstance(self.blocks[0], WcnsBlock) else lib().gbcfd_pipe_create
+        _check(create(_handles(self.blocks), len(self.blocks), ctypes.byref(h)))
         self.handle = h
         self._inflight = []
 

@@ -1,8 +1,8 @@
-"""The host-to-host pipeline (gbcfd_pipe_*): states in pinned host memory advanced through a set
-of identical blocks, with the host-link copies overlapping the steps.  Its results must equal,
-bit for bit, gbcfd_set_state / gbcfd_step / gbcfd_get_state on one block (same kernels, launch
-shapes and reduction order), and the FP64 results the oracle's to the FP64 bar (1e-12 relative
-L2 per conserved variable)."""
+"""The host-to-host pipeline (gbcfd_pipe_*, gbcfd_wcns_pipe_create): states in pinned host
+memory advanced through a set of identical blocks, with the host-link copies overlapping the
+steps.  Its results must equal, bit for bit, the set-state / step / get-state calls on one block
+(same kernels, launch shapes and reduction order), and the FP64 results the oracle's to the FP64
+bar (1e-12 relative L2 per conserved variable)."""
 import numpy as np
 import pytest
 
@@ -131,4 +131,71 @@ def test_pipe_nonphysical_item_is_reported(gb, precision):
     assert e.value.code == gb.ERR_NONPHYSICAL
     pipe.submit(ins[0], outs[0], nsteps=1)
     pipe.sync()  # the flag was cleared by the first report
+    pipe.close()
+
+
+# ---- the paper's WCNS-E-5 blocks -------------------------------------------------------------
+
+def wcns_member(gb, precision, shape=SHAPE):
+    nx, ny, nz = shape
+    return gb.WcnsBlock(nx, ny, nz, gb.params(mu=2e-3, viscous=True, precision=precision), SPACING)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_wcns_pipe_equals_block_calls_bitwise(gb, precision):
+    qs = states(5)
+    pipe = gb.Pipe([wcns_member(gb, precision) for _ in range(3)])
+    ins = [pinned(q) for q in qs]
+    outs = [torch.empty_like(t).pin_memory() for t in ins]
+    norms = [torch.zeros(5, dtype=torch.float64).pin_memory() for _ in ins]
+    for q, o, r in zip(ins, outs, norms):
+        pipe.submit(q, o, nsteps=2, norms=r)
+    pipe.sync()
+    ref = wcns_member(gb, precision)
+    for q, o, r in zip(qs, outs, norms):
+        ref.set_state(torch.from_numpy(q).cuda())
+        ref.step(2)
+        assert torch.equal(o, ref.get_state().cpu())
+        assert np.array_equal(r.numpy(), ref.residual_norm())
+    pipe.close()
+
+
+def test_wcns_pipe_fp64_matches_oracle(gb):
+    c = cases.smooth_random(*SHAPE, seed=42, amp=0.05, viscous=True, mu=2e-3)
+    pipe = gb.Pipe([wcns_member(gb, 0) for _ in range(2)])
+    qin = pinned(c.state)
+    out = torch.empty_like(qin).pin_memory()
+    pipe.submit(qin, out, nsteps=2)
+    pipe.sync()
+    prm = oracle.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, 0)
+    ref, _, _ = oracle.wcns_step(prm, c.state, SPACING, 2)
+    got = out.numpy()
+    floor = 1e-3 * np.linalg.norm(ref[0].ravel())
+    err = [np.linalg.norm((got[m] - ref[m]).ravel()) / max(np.linalg.norm(ref[m].ravel()), floor) for m in range(5)]
+    assert max(err) <= 1e-12, err
+
+
+def test_wcns_pipe_arguments_checked(gb):
+    a = wcns_member(gb, 0)
+    for bad in ([a, wcns_member(gb, 0, shape=(20, 19, 10))], [a, wcns_member(gb, 1)], [a, a]):
+        with pytest.raises(gb.GbcfdError) as e:
+            gb.Pipe(bad)
+        assert e.value.code == gb.ERR_ARG
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_wcns_pipe_nonphysical_item_is_reported(gb, precision):
+    q = states(2)
+    bad = q[1].copy()
+    bad[0, 4, 5, 6] = -0.5
+    pipe = gb.Pipe([wcns_member(gb, precision) for _ in range(2)])
+    ins = [pinned(q[0]), pinned(bad)]
+    outs = [torch.empty_like(t).pin_memory() for t in ins]
+    for i, o in zip(ins, outs):
+        pipe.submit(i, o, nsteps=1)
+    with pytest.raises(gb.GbcfdError) as e:
+        pipe.sync()
+    assert e.value.code == gb.ERR_NONPHYSICAL
+    pipe.submit(ins[0], outs[0], nsteps=1)
+    pipe.sync()
     pipe.close()
