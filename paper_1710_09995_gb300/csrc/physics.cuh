@@ -57,8 +57,9 @@ __device__ __forceinline__ void muscl(V w0, V w1, V w2, V w3, int lim, V& L, V& 
 }
 
 // Roe flux per unit area in the face frame.  L, R: (rho, u_n, u_t1, u_t2, p).
-// F: (mass, normal momentum, t1 momentum, t2 momentum, energy).
-template <typename V>
+// F: (mass, normal momentum, t1 momentum, t2 momentum, energy); TWICE: 2F, the factor 1/2 left
+// to the caller (exact: a product by a power of two only moves the exponent).
+template <typename V, bool TWICE = false>
 __device__ __forceinline__ void roe_frame(const V* L, const V* R, const Consts<V>& K, V* F) {
   using O = VM<V>;
   const V half = O::c(0.5);
@@ -104,30 +105,39 @@ __device__ __forceinline__ void roe_frame(const V* L, const V* R, const Consts<V
   const V cu = c * ut;
   const V sh = O::fma(a2 * half, q2, O::fma(vt, s1, wt * s2));
   const V de = O::fma(w1, ht - cu, O::fma(l2, sh, w5 * (ht + cu)));
-  F[0] = half * ((ml + mr) - ws);
-  F[1] = half * ((O::fma(ml, ul, pl) + O::fma(mr, ur, pr)) - dn);
-  F[2] = half * (O::fma(ml, vl, mr * vr) - dv);
-  F[3] = half * (O::fma(ml, wl, mr * wr) - dw);
-  F[4] = half * (O::fma(ml, hl, mr * hr) - de);
+  F[0] = (ml + mr) - ws;
+  F[1] = (O::fma(ml, ul, pl) + O::fma(mr, ur, pr)) - dn;
+  F[2] = O::fma(ml, vl, mr * vr) - dv;
+  F[3] = O::fma(ml, wl, mr * wr) - dw;
+  F[4] = O::fma(ml, hl, mr * hr) - de;
+  if constexpr (!TWICE) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = half * F[q];
+  }
 }
 
-// Viscous flux per unit area in the face frame from index-space differences:
+// Viscous flux of Eq. 1 (Fv, Gv, Hv) per unit area in the face frame from index-space
+// differences, subtracted from a doubled Roe flux F2 = 2F in place:
 //   gn[q]  = d(phi_q)/dn at the face,  q = u_n, u_t1, u_t2, theta
 //   dnt1   = d(u_n)/dt1,  dnt2 = d(u_n)/dt2,  dt1t1 = d(u_t1)/dt1,  dt2t2 = d(u_t2)/dt2
-//   ub     = face-average (u_n, u_t1, u_t2)
+//   us     = u_L + u_R of (u_n, u_t1, u_t2) (twice the face average)
+// tau_nn = mu (2 du_n/dn - 2/3 div u), tau_nt = mu (du_t/dn + du_n/dt), energy flux
+// u_face . tau + kappa dtheta/dn.  The caller passes K.mu = 2 mu and K.kappa = 4 kappa, so the
+// result is F2 - 2 Fv, bit for bit twice F - Fv (products by powers of two are exact), with the
+// face average and the final halving folded into one fused multiply-add.
 template <typename V>
-__device__ __forceinline__ void viscous_frame(const V* gn, V dnt1, V dnt2, V dt1t1, V dt2t2, const V* ub,
-                                              const Consts<V>& K, V* Fv) {
+__device__ __forceinline__ void viscous_sub_twice(const V* gn, V dnt1, V dnt2, V dt1t1, V dt2t2, const V* us,
+                                                  const Consts<V>& K, V* F2) {
   using O = VM<V>;
   const V div = gn[0] + dt1t1 + dt2t2;
   const V tnn = K.mu * O::fma(O::c(-2.0 / 3.0), div, gn[0] + gn[0]);
   const V tt1 = K.mu * (gn[1] + dnt1);
   const V tt2 = K.mu * (gn[2] + dnt2);
-  Fv[0] = O::c(0);
-  Fv[1] = tnn;
-  Fv[2] = tt1;
-  Fv[3] = tt2;
-  Fv[4] = O::fma(ub[0], tnn, O::fma(ub[1], tt1, O::fma(ub[2], tt2, K.kappa * gn[3])));
+  F2[1] = F2[1] - tnn;
+  F2[2] = F2[2] - tt1;
+  F2[3] = F2[3] - tt2;
+  // 4 (u_face . tau + kappa dtheta/dn) accumulated, then halved inside the subtraction
+  F2[4] = O::fma(O::c(-0.5), O::fma(us[0], tnn, O::fma(us[1], tt1, O::fma(us[2], tt2, K.kappa * gn[3]))), F2[4]);
 }
 
 }  // namespace gbcfd

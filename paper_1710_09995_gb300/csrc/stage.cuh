@@ -137,26 +137,25 @@ __device__ __forceinline__ FaceIdx zface_idx(int s0, int s1, int s2, int s3, int
           b1 + BX, b1 - BX, b2 + BX, b2 - BX};
 }
 
-// the per-face arithmetic once the stencil is in registers: w[cell][frame variable]
+// the per-face arithmetic once the stencil is in registers: w[cell][frame variable].  Returns
+// twice the face flux F - Fv (the assembly multiplies the differences by half the inverse cell
+// sizes, which gives the same bits); K.mu = 2 mu and K.kappa = 4 kappa on this path, us = the
+// sum of the two cells' velocities.
 template <typename V, bool VISC>
 __device__ __forceinline__ void flux_core(const V (&w)[4][5], const V* gn, V dnt1, V dnt2, V d11, V d22,
-                                          const V* ub, const Consts<V>& K, V* Fr) {
+                                          const V* us, const Consts<V>& K, V* Fr) {
   V L[5], R[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) muscl(w[0][q], w[1][q], w[2][q], w[3][q], K.lim, L[q], R[q]);
-  roe_frame(L, R, K, Fr);
-  if constexpr (VISC) {
-    V Fv[5];
-    viscous_frame(gn, dnt1, dnt2, d11, d22, ub, K, Fv);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) Fr[q] = Fr[q] - Fv[q];
-  }
+  roe_frame<V, true>(L, R, K, Fr);
+  if constexpr (VISC) viscous_sub_twice(gn, dnt1, dnt2, d11, d22, us, K, Fr);
 }
 
-// stencil gather of one face, then flux_core.  ih = inverse spacings along (normal, tangent 1,
-// tangent 2).
+// stencil gather of one face, then flux_core (twice the flux).  ih = inverse spacings along
+// (normal, tangent 1, tangent 2), qih = a quarter of them (the tangential differences average
+// two central differences of two cells: 1/4 x the sum of four differences).
 template <typename T, bool VISC, int D>
-__device__ __forceinline__ void face_flux(const T* __restrict__ ring, const FaceIdx& f, const T* ih,
+__device__ __forceinline__ void face_flux(const T* __restrict__ ring, const FaceIdx& f, const T* ih, const T* qih,
                                           const Consts<T>& K, T* F) {
   constexpr int MS = BY * BX;
   using Fr_ = Frame<D>;
@@ -166,24 +165,23 @@ __device__ __forceinline__ void face_flux(const T* __restrict__ ring, const Face
   for (int c = 0; c < 4; ++c)
 #pragma unroll
     for (int q = 0; q < 5; ++q) w[c][q] = ring[f.b[c] + idx[q] * MS];
-  T gn[4], ub[3], dnt1 = T(0), dnt2 = T(0), d11 = T(0), d22 = T(0);
+  T gn[4], us[3], dnt1 = T(0), dnt2 = T(0), d11 = T(0), d22 = T(0);
   if constexpr (VISC) {
     const int L = f.b[1], R = f.b[2];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       gn[q] = (w[2][q + 1] - w[1][q + 1]) * ih[0];
-      ub[q] = T(0.5) * (w[1][q + 1] + w[2][q + 1]);
+      us[q] = w[1][q + 1] + w[2][q + 1];
     }
     constexpr int TH = 5 * MS, mn = Fr_::N * MS, m1 = Fr_::T1 * MS, m2 = Fr_::T2 * MS;
     gn[3] = (ring[R + TH] - ring[L + TH]) * ih[0];
-    const T q4 = T(0.25);
-    dnt1 = q4 * ((ring[f.lp1 + mn] - ring[f.lm1 + mn]) + (ring[f.rp1 + mn] - ring[f.rm1 + mn])) * ih[1];
-    dnt2 = q4 * ((ring[f.lp2 + mn] - ring[f.lm2 + mn]) + (ring[f.rp2 + mn] - ring[f.rm2 + mn])) * ih[2];
-    d11 = q4 * ((ring[f.lp1 + m1] - ring[f.lm1 + m1]) + (ring[f.rp1 + m1] - ring[f.rm1 + m1])) * ih[1];
-    d22 = q4 * ((ring[f.lp2 + m2] - ring[f.lm2 + m2]) + (ring[f.rp2 + m2] - ring[f.rm2 + m2])) * ih[2];
+    dnt1 = ((ring[f.lp1 + mn] - ring[f.lm1 + mn]) + (ring[f.rp1 + mn] - ring[f.rm1 + mn])) * qih[1];
+    dnt2 = ((ring[f.lp2 + mn] - ring[f.lm2 + mn]) + (ring[f.rp2 + mn] - ring[f.rm2 + mn])) * qih[2];
+    d11 = ((ring[f.lp1 + m1] - ring[f.lm1 + m1]) + (ring[f.rp1 + m1] - ring[f.rm1 + m1])) * qih[1];
+    d22 = ((ring[f.lp2 + m2] - ring[f.lm2 + m2]) + (ring[f.rp2 + m2] - ring[f.rm2 + m2])) * qih[2];
   }
   T Fr[5];
-  flux_core<T, VISC>(w, gn, dnt1, dnt2, d11, d22, ub, K, Fr);
+  flux_core<T, VISC>(w, gn, dnt1, dnt2, d11, d22, us, K, Fr);
   F[0] = Fr[0];
   F[Fr_::N] = Fr[1];
   F[Fr_::T1] = Fr[2];
@@ -268,8 +266,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
   K.gm1 = PK.gm1;
   K.ggm1 = PK.ggm1;
   K.eps = PK.eps;
-  K.mu = VISC ? PK.mu : T(0);
-  K.kappa = VISC ? PK.kappa : T(0);
+  // the Cartesian face path returns twice the flux (flux_core): 2 mu, 4 kappa there
+  K.mu = VISC ? (CURVI ? PK.mu : PK.mu + PK.mu) : T(0);
+  K.kappa = VISC ? (CURVI ? PK.kappa : T(4) * PK.kappa) : T(0);
   K.lim = ph.limiter;
   const T gm1 = PK.gm1;
   const RateK<T> RK = {PK.gam, PK.vf};
@@ -385,6 +384,10 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
     const T hx = MIXED ? T(D->ihxf) : T(D->ihx), hy = MIXED ? T(D->ihyf) : T(D->ihy),
             hz = MIXED ? T(D->ihzf) : T(D->ihz);  // inverse cell sizes
     const T hs2 = hx * hx + hy * hy + hz * hz;
+    // a quarter of the inverse cell sizes (tangential face derivatives) and half of them (the
+    // assembly of the doubled Cartesian face fluxes); products by powers of two are exact
+    const T qhx = T(0.25) * hx, qhy = T(0.25) * hy, qhz = T(0.25) * hz;
+    const T hx2 = T(0.5) * hx, hy2 = T(0.5) * hy, hz2 = T(0.5) * hz;
 
     auto request = [&](int kp) {  // thread 0 only
       const int s = (kp + 2) & (NSTAGE - 1);
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
         face_flux_curvi<T, VISC>(ring, mring, NV * MS, iz.b, tg_of(iz), zface_met(mslot(k0 - 1), mslot(k0), ocy, ocx),
                                  K, fzl);
       else
-        face_flux<T, VISC, 2>(ring, iz, ihz3(hx, hy, hz).v, K, fzl);
+        face_flux<T, VISC, 2>(ring, iz, ihz3(hx, hy, hz).v, ihz3(qhx, qhy, qhz).v, K, fzl);
     }
     __syncthreads();  // the first consume below overwrites plane k0-2, read by the z-face above
 
@@ -515,8 +518,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
           face_flux_curvi<T, VISC>(ring, mring, NV * MS, ix.b, tg_of(ix), xface_met(mk, mk1, ocy, ocx), K, Fa);
           face_flux_curvi<T, VISC>(ring, mring, NV * MS, iy.b, tg_of(iy), yface_met(mk, mk1, ocy, ocx), K, Fb);
         } else {
-          face_flux<T, VISC, 0>(ring, ix, ihx3(hx, hy, hz).v, K, Fa);
-          face_flux<T, VISC, 1>(ring, iy, ihy3(hx, hy, hz).v, K, Fb);
+          face_flux<T, VISC, 0>(ring, ix, ihx3(hx, hy, hz).v, ihx3(qhx, qhy, qhz).v, K, Fa);
+          face_flux<T, VISC, 1>(ring, iy, ihy3(hx, hy, hz).v, ihy3(qhx, qhy, qhz).v, K, Fb);
         }
 #pragma unroll
         for (int m = 0; m < 5; ++m) fx[(m * TY + warp) * (TX + 1) + lane] = Fa[m];
@@ -526,7 +529,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
         if constexpr (CURVI)
           face_flux_curvi<T, VISC>(ring, mring, NV * MS, iz.b, tg_of(iz), zface_met(mk, mk1, ocy, ocx), K, fzu);
         else
-          face_flux<T, VISC, 2>(ring, iz, ihz3(hx, hy, hz).v, K, fzu);
+          face_flux<T, VISC, 2>(ring, iz, ihz3(hx, hy, hz).v, ihz3(qhx, qhy, qhz).v, K, fzu);
       } else {
         // the tile's upper y-faces (all lanes) and upper x-faces (lanes < TY)
         T Fa[5], Fb[5];
@@ -539,8 +542,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
             face_flux_curvi<T, VISC>(ring, mring, NV * MS, ix.b, tg_of(ix),
                                      xface_met(mk, mk1, lane + HALO, TX + HALO), K, Fb);
         } else {
-          face_flux<T, VISC, 1>(ring, iy, ihy3(hx, hy, hz).v, K, Fa);
-          if (lane < TY) face_flux<T, VISC, 0>(ring, ix, ihx3(hx, hy, hz).v, K, Fb);
+          face_flux<T, VISC, 1>(ring, iy, ihy3(hx, hy, hz).v, ihy3(qhx, qhy, qhz).v, K, Fa);
+          if (lane < TY) face_flux<T, VISC, 0>(ring, ix, ihx3(hx, hy, hz).v, ihx3(qhx, qhy, qhz).v, K, Fb);
         }
 #pragma unroll
         for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + TY) * TX + lane] = Fa[m];
@@ -559,7 +562,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
           if constexpr (CURVI)
             R[m] = (ddx + ddy) + (fzu[m] - fzl[m]);  // face fluxes carry |S|; divided by V below
           else
-            R[m] = (ddx * hx + ddy * hy) + (fzu[m] - fzl[m]) * hz;
+            R[m] = (ddx * hx2 + ddy * hy2) + (fzu[m] - fzl[m]) * hz2;  // doubled fluxes
         }
         if constexpr (CURVI) {
           const T iv = Fm::rcp(mring[mb(mk, ocy, ocx) + 9 * MS]);
