@@ -189,7 +189,8 @@ int gbcfd_pipe_destroy(gbcfd_pipe pipe);
 /* Enqueue one item and return.  q_in, q_out and norms (5 doubles: the RMS residual of the item's
  * last step, as gbcfd_residual_norm reports it; NULL for none; not written when nsteps is 0) must
  * be page-locked host memory (cudaHostAlloc, or a pinned torch tensor), else GBCFD_ERR_ARG;
- * q_in must not change and q_out / norms must not be read until gbcfd_pipe_sync returns. */
+ * q_in must not change and q_out / norms must not be read until gbcfd_pipe_sync returns.  After
+ * an item fails (error code returned), further submits return GBCFD_ERR_STATE until a sync. */
 int gbcfd_pipe_submit(gbcfd_pipe pipe, const double* q_in, double* q_out, int nsteps, double* norms);
 
 /* Wait until every submitted item is in host memory.  Reports GBCFD_ERR_NONPHYSICAL /

@@ -1053,6 +1053,7 @@ struct gbcfd_pipe_s {
   cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
   std::vector<cudaEvent_t> up_done, comp_done, down_done;  // per member, of its latest item
   long long items = 0;
+  int broken = 0;  // an item failed after its upload was enqueued: no new items until a sync
 };
 
 static void pipe_release(gbcfd_pipe p) {
@@ -1176,6 +1177,7 @@ extern "C" int gbcfd_pipe_submit(gbcfd_pipe p, const double* q_in, double* q_out
   if (nsteps < 0) return fail(GBCFD_ERR_ARG, "nsteps must be >= 0");
   if (!page_locked(q_in) || !page_locked(q_out) || (norms && !page_locked(norms)))
     return fail(GBCFD_ERR_ARG, "pipeline buffers must be page-locked host memory");
+  if (p->broken) return fail(GBCFD_ERR_STATE, "a pipeline item failed; call gbcfd_pipe_sync first");
   const int nb = (int)p->members.size();
   const int j = (int)(p->items % nb);
   const PipeMember& m = p->members[j];
@@ -1183,6 +1185,8 @@ extern "C" int gbcfd_pipe_submit(gbcfd_pipe p, const double* q_in, double* q_out
   if (p->items >= nb) CK(cudaStreamWaitEvent(p->up, p->down_done[j], 0));
   int rc = m.upload(m.self, q_in, p->up);
   if (rc) return rc;
+  // from here on a failure leaves work of this item in flight: refuse new items until a sync
+  p->broken = 1;
   CK(cudaEventRecord(p->up_done[j], p->up));
   CK(cudaStreamWaitEvent(p->comp, p->up_done[j], 0));
   rc = m.run(m.self, nsteps, p->comp);
@@ -1192,6 +1196,7 @@ extern "C" int gbcfd_pipe_submit(gbcfd_pipe p, const double* q_in, double* q_out
   rc = m.download(m.self, q_out, norms, nsteps, p->down);
   if (rc) return rc;
   CK(cudaEventRecord(p->down_done[j], p->down));
+  p->broken = 0;
   p->items++;
   return GBCFD_OK;
 }
@@ -1201,6 +1206,7 @@ extern "C" int gbcfd_pipe_sync(gbcfd_pipe p) {
   CK(cudaStreamSynchronize(p->up));
   CK(cudaStreamSynchronize(p->comp));
   CK(cudaStreamSynchronize(p->down));
+  p->broken = 0;  // nothing of a failed item is in flight any more
   int flags = 0;
   for (const PipeMember& m : p->members) {
     int f = 0;
