@@ -251,6 +251,15 @@ int gbcfd_group_tune(gbcfd_group group, void* stream, int* ctas_per_sm);
  * them.  Drops the captured graphs; the events of one step are overwritten by the next. */
 int gbcfd_group_set_timing(gbcfd_group group, void* const* events, int n);
 
+/* A host-to-host pipeline (gbcfd_pipe_submit / _sync / _destroy) over n (1..8) groups built
+ * alike: the same number of blocks, block k of every group with the same sizes, parameters,
+ * grid, boundary conditions and connections (to the same member indices).  An item's state is
+ * the concatenation, in the group's block order, of the blocks' compact states
+ * q[5][nz][ny][nx] (float64); norms, when not NULL, receives 5 doubles per block in that order.
+ * Each item is set block by block as by gbcfd_set_state and advanced as by gbcfd_group_step;
+ * the results are bitwise those calls'.  No block may belong to two member groups. */
+int gbcfd_group_pipe_create(const gbcfd_group* groups, int n, gbcfd_pipe* out);
+
 /* ---- learned convergence accelerator (not in the paper: the project's addition) --------------
  * A 3-layer 3D convolutional network (channels 10 -> 32 -> 32 -> 5, 3x3x3 taps, SiLU, zero
  * padding in x and y, periodic in z) predicts the change of a block's state over K = 20

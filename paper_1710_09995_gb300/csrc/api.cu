@@ -1065,6 +1065,8 @@ static void pipe_release(gbcfd_pipe p) {
       if (e) cudaEventDestroy(e);
   for (cudaStream_t s : {p->up, p->comp, p->down})
     if (s) cudaStreamDestroy(s);
+  for (const PipeMember& m : p->members)
+    if (m.release) m.release(m.self);
   delete p;
 }
 
@@ -1075,14 +1077,14 @@ static bool page_locked(const void* ptr) {
   return !dev && mapped != nullptr;
 }
 
+// takes ownership of the members (released with the pipeline, or here when creation fails)
 int gbcfd::pipe_create(const PipeMember* members, int n, gbcfd_pipe* out) {
-  CK(cudaDeviceSynchronize());  // the members' earlier work (any stream) is done
   gbcfd_pipe p = new gbcfd_pipe_s;
   p->members.assign(members, members + n);
   p->up_done.assign(n, nullptr);
   p->comp_done.assign(n, nullptr);
   p->down_done.assign(n, nullptr);
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = cudaDeviceSynchronize();  // the members' earlier work (any stream) is done
   for (cudaStream_t* s : {&p->up, &p->comp, &p->down})
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
   for (auto* v : {&p->up_done, &p->comp_done, &p->down_done})
@@ -1161,7 +1163,112 @@ extern "C" int gbcfd_pipe_create(const gbcfd_block* blocks, int n, gbcfd_pipe* o
         return fail(GBCFD_ERR_ARG, "members differ in boundary conditions");
     }
     if (b->staging_bytes < bytes) return fail(GBCFD_ERR_MEMORY, "member staging area too small");
-    m[i] = PipeMember{b, bytes, fv_upload, fv_run, fv_download, fv_flags};
+    m[i] = PipeMember{b, bytes, fv_upload, fv_run, fv_download, fv_flags, nullptr};
+  }
+  return pipe_create(m.data(), n, out);
+}
+
+// group members: an item is the concatenation of the member blocks' compact states, in the
+// group's block order; each block lands in its own staging area
+struct GroupMember {
+  gbcfd_group g;
+  std::vector<size_t> off;  // byte offset of each block's state in the item
+  size_t bytes;
+};
+static size_t compact_bytes(gbcfd_block b) { return sizeof(double) * 5 * (size_t)b->nx * b->ny * b->nz; }
+static int gp_upload(void* self, const double* q_in, cudaStream_t s) {
+  const GroupMember* G = static_cast<const GroupMember*>(self);
+  const char* src = reinterpret_cast<const char*>(q_in);
+  for (size_t i = 0; i < G->g->blocks.size(); ++i) {
+    gbcfd_block b = G->g->blocks[i];
+    CK(cudaMemcpyAsync(b->staging, src + G->off[i], compact_bytes(b), cudaMemcpyHostToDevice, s));
+  }
+  return GBCFD_OK;
+}
+static int gp_run(void* self, int nsteps, cudaStream_t s) {
+  const GroupMember* G = static_cast<const GroupMember*>(self);
+  for (gbcfd_block b : G->g->blocks) {
+    if (b->next_stage != 1) return fail(GBCFD_ERR_STATE, "a member block was left between stages");
+    CK(launch_scatter(b->g, reinterpret_cast<const double*>(b->staging), state_ptr(b),
+                      b->p.precision == GBCFD_MIXED ? b->sh[b->cur] : nullptr, s));
+    b->has_state = 1;
+    b->next_stage = 1;
+    const int rc = b->metrics_dirty ? prepare_metrics(&b, 1, s) : init_rate(b, s);
+    if (rc) return rc;
+  }
+  const int rc = gbcfd_group_step(G->g, nsteps, s);
+  if (rc) return rc;
+  for (gbcfd_block b : G->g->blocks)
+    CK(launch_gather(b->g, state_ptr(b), reinterpret_cast<double*>(b->staging), s));
+  return GBCFD_OK;
+}
+static int gp_download(void* self, double* q_out, double* norms, int nsteps, cudaStream_t s) {
+  const GroupMember* G = static_cast<const GroupMember*>(self);
+  char* dst = reinterpret_cast<char*>(q_out);
+  for (size_t i = 0; i < G->g->blocks.size(); ++i) {
+    gbcfd_block b = G->g->blocks[i];
+    CK(cudaMemcpyAsync(dst + G->off[i], b->staging, compact_bytes(b), cudaMemcpyDeviceToHost, s));
+    if (norms && nsteps > 0)
+      CK(cudaMemcpyAsync(norms + 5 * i, b->ctrl->norms, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  return GBCFD_OK;
+}
+static int gp_flags(void* self, cudaStream_t s, int* flags) {
+  const GroupMember* G = static_cast<const GroupMember*>(self);
+  *flags = 0;
+  for (gbcfd_block b : G->g->blocks) {
+    int f = 0;
+    const int rc = fv_flags(b, s, &f);
+    if (rc) return rc;
+    *flags |= f;
+  }
+  return GBCFD_OK;
+}
+static void gp_release(void* self) { delete static_cast<GroupMember*>(self); }
+
+extern "C" int gbcfd_group_pipe_create(const gbcfd_group* groups, int n, gbcfd_pipe* out) {
+  if (!groups || !out) return fail(GBCFD_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (n < 1 || n > 8) return fail(GBCFD_ERR_ARG, "a pipeline takes 1 to 8 groups");
+  const gbcfd_group a = groups[0];
+  if (!a) return fail(GBCFD_ERR_ARG, "NULL group");
+  const size_t nb = a->blocks.size();
+  std::vector<gbcfd_block> seen;
+  for (int i = 0; i < n; ++i) {
+    const gbcfd_group g = groups[i];
+    if (!g) return fail(GBCFD_ERR_ARG, "NULL group");
+    if (g->blocks.size() != nb) return fail(GBCFD_ERR_ARG, "member groups differ in their blocks");
+    for (size_t k = 0; k < nb; ++k) {
+      const gbcfd_block b = g->blocks[k], r = a->blocks[k];
+      if (std::find(seen.begin(), seen.end(), b) != seen.end())
+        return fail(GBCFD_ERR_ARG, "a block belongs to two member groups (or a group is listed twice)");
+      seen.push_back(b);
+      if (b->nx != r->nx || b->ny != r->ny || b->nz != r->nz || memcmp(&b->p, &r->p, sizeof(gbcfd_params)) != 0 ||
+          b->curvi != r->curvi || memcmp(b->spacing, r->spacing, sizeof(r->spacing)) != 0)
+        return fail(GBCFD_ERR_ARG, "member groups differ in their blocks");
+      for (int f = 0; f < 6; ++f) {
+        // the same connection pattern: neighbour k' of block k in every group
+        const auto idx = [](gbcfd_group G, gbcfd_block x) -> long {
+          if (!x) return -1;
+          return (long)(std::find(G->blocks.begin(), G->blocks.end(), x) - G->blocks.begin());
+        };
+        if (idx(g, b->nbr[f]) != idx(a, r->nbr[f]) || (!b->nbr[f] && b->bc_kind[f] != r->bc_kind[f]))
+          return fail(GBCFD_ERR_ARG, "member groups differ in connections or boundary conditions");
+      }
+      if (b->staging_bytes < compact_bytes(b)) return fail(GBCFD_ERR_MEMORY, "member staging area too small");
+    }
+  }
+  std::vector<PipeMember> m(n);
+  for (int i = 0; i < n; ++i) {
+    GroupMember* G = new GroupMember;
+    G->g = groups[i];
+    size_t off = 0;
+    for (gbcfd_block b : G->g->blocks) {
+      G->off.push_back(off);
+      off += compact_bytes(b);
+    }
+    G->bytes = off;
+    m[i] = PipeMember{G, off, gp_upload, gp_run, gp_download, gp_flags, gp_release};
   }
   return pipe_create(m.data(), n, out);
 }

@@ -54,8 +54,10 @@ struct PipeMember {
   int (*run)(void* self, int nsteps, cudaStream_t s);               // landing area -> state, steps, result -> landing area
   int (*download)(void* self, double* q_out, double* norms, int nsteps, cudaStream_t s);  // landing area -> host
   int (*flags)(void* self, cudaStream_t s, int* flags);             // read and clear the device flags (synchronises s)
+  void (*release)(void* self);                                      // frees `self` with the pipeline (or null)
 };
-// a pipeline over n members (streams and events created here); waits for the device first
+// a pipeline over n members (streams and events created here); waits for the device first and
+// takes ownership of the members (their release functions run with the pipeline, or on failure)
 int pipe_create(const PipeMember* members, int n, gbcfd_pipe* out);
 
 }  // namespace gbcfd

@@ -1271,7 +1271,7 @@ extern "C" int gbcfd_wcns_pipe_create(const gbcfd_wcns* blocks, int n, gbcfd_pip
     if (w->nx != a->nx || w->ny != a->ny || w->nz != a->nz) return set_error(GBCFD_ERR_ARG, "members differ in size");
     if (memcmp(&w->p, &a->p, sizeof(gbcfd_params)) != 0 || memcmp(w->h, a->h, sizeof(a->h)) != 0)
       return set_error(GBCFD_ERR_ARG, "members differ in parameters or cell sizes");
-    m[i] = PipeMember{w, bytes, wp_upload, wp_run, wp_download, wp_flags};
+    m[i] = PipeMember{w, bytes, wp_upload, wp_run, wp_download, wp_flags, nullptr};
   }
   return pipe_create(m.data(), n, out);
 }

@@ -75,6 +75,7 @@ SIGNATURES = {
     "gbcfd_pipe_submit": [_VP, _VP, _VP, ctypes.c_int, _VP],
     "gbcfd_pipe_sync": [_VP],
     "gbcfd_wcns_pipe_create": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)],
+    "gbcfd_group_pipe_create": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)],
     "gbcfd_group_required_bytes": [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
     "gbcfd_group_create": [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.c_size_t, ctypes.POINTER(_VP)],
     "gbcfd_group_destroy": [_VP],
@@ -293,21 +294,29 @@ class Pipe:
     holds references to them until sync()."""
 
     def __init__(self, blocks):
-        """blocks: finite-volume Blocks, or WcnsBlocks (the paper's scheme)"""
+        """blocks: finite-volume Blocks, WcnsBlocks (the paper's scheme) or Groups built alike
+        (an item is then the concatenation of the blocks' states, see item_numel)"""
         self.blocks = list(blocks)
         assert self.blocks and all(type(b) is type(self.blocks[0]) for b in self.blocks)
         h = ctypes.c_void_p(0)
-        create = lib().gbcfd_wcns_pipe_create if isinstance(self.blocks[0], WcnsBlock) else lib().gbcfd_pipe_create
+        first = self.blocks[0]
+        if isinstance(first, Group):
+            create = lib().gbcfd_group_pipe_create
+            self.item_numel = sum(5 * b.cells for b in first.blocks)
+            self.norms_numel = 5 * len(first.blocks)
+        else:
+            create = lib().gbcfd_wcns_pipe_create if isinstance(first, WcnsBlock) else lib().gbcfd_pipe_create
+            self.item_numel = 5 * first.cells
+            self.norms_numel = 5
         _check(create(_handles(self.blocks), len(self.blocks), ctypes.byref(h)))
         self.handle = h
         self._inflight = []
 
     def submit(self, q_in, q_out, nsteps=1, norms=None):
-        b = self.blocks[0]
         for t in (q_in, q_out):
-            assert t.dtype == torch.float64 and t.is_contiguous() and tuple(t.shape) == (5, b.nz, b.ny, b.nx)
+            assert t.dtype == torch.float64 and t.is_contiguous() and t.numel() == self.item_numel
         if norms is not None:
-            assert norms.dtype == torch.float64 and norms.is_contiguous() and norms.numel() == 5
+            assert norms.dtype == torch.float64 and norms.is_contiguous() and norms.numel() == self.norms_numel
         self._inflight.append((q_in, q_out, norms))
         _check(lib().gbcfd_pipe_submit(self.handle, _ptr(q_in), _ptr(q_out), int(nsteps),
                                        _ptr(norms) if norms is not None else None))

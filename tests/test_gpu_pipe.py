@@ -199,3 +199,48 @@ def test_wcns_pipe_nonphysical_item_is_reported(gb, precision):
     pipe.submit(ins[0], outs[0], nsteps=1)
     pipe.sync()
     pipe.close()
+
+
+# ---- groups of uneven blocks ------------------------------------------------------------------
+
+SMALL = ([21, 40, 16], [17, 33], [9, 25, 14, 20])   # 3 x 2 x 4 = 24 blocks, 77 x 50 x 68 cells
+
+
+def lattice_item(lat):
+    """an item of a group pipeline: the blocks' compact states, concatenated in block order"""
+    parts = [lat.state[:, zs, ys, xs].contiguous().reshape(-1) for zs, ys, xs in lat.block_slices().values()]
+    return torch.cat(parts).pin_memory()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_group_pipe_equals_group_calls_bitwise(gb, precision):
+    lats = [cases.lattice_case(sizes=SMALL, seed=s) for s in (2, 3, 4, 5)]
+    groups = [gb.Group(gb.blocks_for_lattice(lats[0], precision)) for _ in range(3)]
+    pipe = gb.Pipe(groups)
+    nb = len(groups[0].blocks)
+    ins = [lattice_item(lat) for lat in lats]
+    outs = [torch.empty_like(t).pin_memory() for t in ins]
+    norms = [torch.zeros(5 * nb, dtype=torch.float64).pin_memory() for _ in ins]
+    for q, o, r in zip(ins, outs, norms):
+        pipe.submit(q, o, nsteps=2, norms=r)
+    pipe.sync()
+    ref_blocks = gb.blocks_for_lattice(lats[0], precision)
+    ref = gb.Group(ref_blocks)
+    for lat, o, r in zip(lats, outs, norms):
+        for b, (zs, ys, xs) in zip(ref_blocks, lat.block_slices().values()):
+            b.set_state(lat.state[:, zs, ys, xs].contiguous().cuda())
+        ref.step(2)
+        got = torch.cat([b.get_state().reshape(-1) for b in ref_blocks]).cpu()
+        assert torch.equal(o, got)
+        assert np.array_equal(r.numpy(), np.concatenate([b.residual_norm() for b in ref_blocks]))
+    pipe.close()
+
+
+def test_group_pipe_arguments_checked(gb):
+    lat = cases.lattice_case(sizes=SMALL, seed=2)
+    other = cases.lattice_case(sizes=([21, 40, 16], [17, 33], [9, 25, 14, 21]), seed=2)
+    a = gb.Group(gb.blocks_for_lattice(lat, 1))
+    for bad in ([a, gb.Group(gb.blocks_for_lattice(other, 1))], [a, gb.Group(gb.blocks_for_lattice(lat, 0))], [a, a]):
+        with pytest.raises(gb.GbcfdError) as e:
+            gb.Pipe(bad)
+        assert e.value.code == gb.ERR_ARG
