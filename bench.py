@@ -269,7 +269,7 @@ def e2e_group_path(gbcfd, torch, lat, precision, steps, world, device):
     and per-block get_state / residual_norm calls."""
     import gc
     prec = gbcfd.MIXED if precision == "mixed" else gbcfd.FP64
-    parts = [lat.state[:, zs, ys, xs].contiguous() for zs, ys, xs in lat.block_slices().values()]
+    parts = [lat.state[:, zs, ys, xs].contiguous().cpu() for zs, ys, xs in lat.block_slices().values()]
     nbytes = sum(h.numel() * 8 for h in parts)
     # serial calls
     blocks = gbcfd.blocks_for_lattice(lat, prec, device)
