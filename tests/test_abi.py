@@ -46,3 +46,24 @@ def test_binding_wraps_exactly_the_declared_symbols():
 def test_library_is_built_for_sm_103a_only(libpath):
     from paper_1710_09995_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_pipeline_argument_checks_need_no_device(libpath):
+    """the pipeline entry points refuse null handles and bad counts on the host, before any CUDA
+    call (so these run without a GPU)"""
+    from paper_1710_09995_gb300 import gbcfd
+    lib = gbcfd.lib()
+    out = ctypes.c_void_p(0)
+    one = (ctypes.c_void_p * 1)(None)
+    assert lib.gbcfd_pipe_create(None, 1, ctypes.byref(out)) == gbcfd.ERR_ARG
+    assert lib.gbcfd_pipe_create(one, 0, ctypes.byref(out)) == gbcfd.ERR_ARG
+    assert lib.gbcfd_pipe_create(one, 9, ctypes.byref(out)) == gbcfd.ERR_ARG
+    assert lib.gbcfd_pipe_create(one, 1, ctypes.byref(out)) == gbcfd.ERR_ARG  # a NULL block
+    assert b"NULL block" in lib.gbcfd_last_error()
+    assert lib.gbcfd_wcns_pipe_create(one, 1, ctypes.byref(out)) == gbcfd.ERR_ARG
+    assert lib.gbcfd_group_pipe_create(one, 1, ctypes.byref(out)) == gbcfd.ERR_ARG
+    assert lib.gbcfd_group_pipe_create(one, 0, ctypes.byref(out)) == gbcfd.ERR_ARG
+    assert out.value is None
+    assert lib.gbcfd_pipe_submit(None, None, None, 1, None) == gbcfd.ERR_ARG
+    assert lib.gbcfd_pipe_sync(None) == gbcfd.ERR_ARG
+    assert lib.gbcfd_pipe_destroy(None) == gbcfd.ERR_ARG

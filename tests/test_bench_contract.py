@@ -1,0 +1,27 @@
+"""Host logic of bench.py's roofline: the HBM roofline counts the method's FP64-state minimum
+of 320 bytes per cell-step (stage 1 reads Q^n and writes Q^1; stages 2 and 3 read the stage
+input and Q^n and write the stage output) on both paths, and reports the mixed path's own
+layout (f32 shadow and f32 stage increments, 240 bytes per cell-step) beside it."""
+import bench
+
+
+def test_algorithmic_bytes_per_cell_step():
+    assert sum(bench.ALGO_BYTES) == 320
+    assert bench.ALGO_BYTES == (80, 120, 120)
+    assert sum(bench.DESIGN_BYTES["mixed"]) == 240
+    assert bench.DESIGN_BYTES["fp64"] == bench.ALGO_BYTES
+
+
+def test_roofline_arithmetic():
+    cells, steps, ms = 1000, 2, 0.5
+    res = {"stage_ms": {1: ms * steps, 2: ms * steps, 3: ms * steps}}  # 0.5 ms per launch
+    r = bench.roofline("mixed", res, cells, steps, 1000.0, "measured")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["algorithmic_bytes_per_launch"] - cells * 320 / 3) < 1e-6
+    assert abs(r["design_bytes_per_launch"] - cells * 240 / 3) < 1e-6
+    assert abs(r["achieved"] - round(cells * 320 / 3 / 0.5e-3 / 1e9, 1)) < 1e-9
+    assert abs(r["frac"] - round(cells * 320 / 3 / 0.5e-3 / 1e9 / 1000.0, 4)) < 1e-12
+    assert r["avg_launch_ms"] == ms
+    # curvilinear blocks add their metrics (f32 on the mixed path) to every stage
+    w = bench.roofline("mixed", res, cells, steps, 1000.0, "measured", workload="warped512")
+    assert abs(w["algorithmic_bytes_per_launch"] - cells * (320 + 3 * 40) / 3) < 1e-6
