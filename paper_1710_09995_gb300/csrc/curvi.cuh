@@ -61,35 +61,38 @@ __device__ __forceinline__ void face_flux_curvi(const T* __restrict__ ring, cons
   Rf[2] = O::fma(R[1], t1[0], O::fma(R[2], t1[1], R[3] * t1[2]));
   Rf[3] = O::fma(R[1], t2[0], O::fma(R[2], t2[1], R[3] * t2[2]));
   T Fr[5];
-  roe_frame(Lf, Rf, K, Fr);
-  F[0] = area * Fr[0];
+  roe_frame<T, true>(Lf, Rf, K, Fr);  // twice the flux: the 1/2 rides on the area (exact)
+  const T ha = T(0.5) * area;
+  F[0] = ha * Fr[0];
 #pragma unroll
-  for (int x = 0; x < 3; ++x) F[1 + x] = area * O::fma(Fr[1], n[x], O::fma(Fr[2], t1[x], Fr[3] * t2[x]));
-  F[4] = area * Fr[4];
+  for (int x = 0; x < 3; ++x) F[1 + x] = ha * O::fma(Fr[1], n[x], O::fma(Fr[2], t1[x], Fr[3] * t2[x]));
+  F[4] = ha * Fr[4];
 
   if constexpr (VISC) {
     constexpr int TH = 5 * MS;
     const int lp1 = tg[0], lm1 = tg[1], rp1 = tg[2], rm1 = tg[3];
     const int lp2 = tg[4], lm2 = tg[5], rp2 = tg[6], rm2 = tg[7];
+    // the tangential means (1/4 of four face vectors, 1/4 of two central differences) are kept
+    // as sums: their product carries 1/16, folded into 16 x the normal difference and 1/16 x the
+    // inverse volume (products by powers of two are exact: the same gradients bit for bit)
     T sb1[3], sb2[3];
-    const T q4 = T(0.25);
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
       const int m = x * MS;
-      sb1[x] = q4 * ((mring[mi.t1[0] + m] + mring[mi.t1[1] + m]) + (mring[mi.t1[2] + m] + mring[mi.t1[3] + m]));
-      sb2[x] = q4 * ((mring[mi.t2[0] + m] + mring[mi.t2[1] + m]) + (mring[mi.t2[2] + m] + mring[mi.t2[3] + m]));
+      sb1[x] = (mring[mi.t1[0] + m] + mring[mi.t1[1] + m]) + (mring[mi.t1[2] + m] + mring[mi.t1[3] + m]);
+      sb2[x] = (mring[mi.t2[0] + m] + mring[mi.t2[1] + m]) + (mring[mi.t2[2] + m] + mring[mi.t2[3] + m]);
     }
-    const T iv = O::rcp(T(0.5) * (mring[mi.vl] + mring[mi.vr]));
+    const T iv16 = T(0.0625) * O::rcp(T(0.5) * (mring[mi.vl] + mring[mi.vr]));
     // gradients of u, v, w (primitives 1..3) and theta (slot 5)
     T g[4][3];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const int m = (f < 3 ? f + 1 : 5) * MS;
-      const T dn = ring[b[2] + m] - ring[b[1] + m];
-      const T d1 = q4 * ((ring[lp1 + m] - ring[lm1 + m]) + (ring[rp1 + m] - ring[rm1 + m]));
-      const T d2 = q4 * ((ring[lp2 + m] - ring[lm2 + m]) + (ring[rp2 + m] - ring[rm2 + m]));
+      const T dn16 = T(16) * (ring[b[2] + m] - ring[b[1] + m]);
+      const T d1 = (ring[lp1 + m] - ring[lm1 + m]) + (ring[rp1 + m] - ring[rm1 + m]);
+      const T d2 = (ring[lp2 + m] - ring[lm2 + m]) + (ring[rp2 + m] - ring[rm2 + m]);
 #pragma unroll
-      for (int x = 0; x < 3; ++x) g[f][x] = O::fma(dn, S[x], O::fma(d1, sb1[x], d2 * sb2[x])) * iv;
+      for (int x = 0; x < 3; ++x) g[f][x] = O::fma(dn16, S[x], O::fma(d1, sb1[x], d2 * sb2[x])) * iv16;
     }
     (void)TH;
     const T div = g[0][0] + g[1][1] + g[2][2];
