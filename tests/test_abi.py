@@ -67,3 +67,15 @@ def test_pipeline_argument_checks_need_no_device(libpath):
     assert lib.gbcfd_pipe_submit(None, None, None, 1, None) == gbcfd.ERR_ARG
     assert lib.gbcfd_pipe_sync(None) == gbcfd.ERR_ARG
     assert lib.gbcfd_pipe_destroy(None) == gbcfd.ERR_ARG
+
+
+def test_header_is_plain_c():
+    """include/gbcfd.h compiles as C99 (no C++ or torch types cross the boundary)"""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    r = subprocess.run([cc, "-fsyntax-only", "-std=c99", "-Wall", "-Werror", "-x", "c",
+                        os.path.join(ROOT, "include", "gbcfd.h")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
