@@ -983,44 +983,80 @@ def run_wcns(args, world, rank, local, device, torch, cases, gbcfd):
 
 
 # ---- the reference arm: the FP64 CPU oracle ----------------------------------------------------
+def reference_sample(args):
+    """The oracle's bounded sample of the workload: (cells, one-step function, initial state,
+    sample text, metric, unit).  Every sample has the workload's recipe and physics on fewer cells."""
+    import oracle
+    from paper_1710_09995_gb300 import cases
+    w = args.workload
+    cu = ("cell-updates/s", "cell-updates/s")
+    if w in ("vortex256", "wcns256"):
+        nz = 8
+        c = cases.isentropic_vortex(n=args.side, L=10.0, nz=nz, viscous=True)
+        p = oracle.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, c.limiter)
+        scheme = "WCNS-E-5 oracle" if w == "wcns256" else "FP64 oracle"
+        text = (f"each step: 1 SSP-RK3 step ({scheme}) of a {args.side}x{args.side}x{nz} z-slab of the "
+                f"z-invariant {args.side}^3 vortex")
+        if w == "wcns256":
+            return c.cells, (lambda Q: oracle.wcns_step(p, Q, c.spacing, 1)[0]), c.state, text, *cu
+        M = oracle.metrics(c.grid_nodes())
+        return c.cells, (lambda Q: oracle.step(p, Q, M, 1)[0]), oracle.pad(c.state), text, *cu
+    if w == "warped512":
+        c = cases.broadband_warped(128, 128, 96, seed=0)
+        p = oracle.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, c.limiter)
+        M = oracle.metrics(c.nodes)
+        text = "each step: 1 SSP-RK3 step (FP64 oracle) of a periodic 128x128x96 warped block, same recipe"
+        return c.cells, (lambda Q: oracle.step(p, Q, M, 1)[0]), oracle.pad(c.state), text, *cu
+    if w == "lattice96":
+        lat = cases.lattice_case(sizes=([128], [128], [96]), seed=4)
+        p = oracle.params(lat.gamma, 0.0, 0.72, lat.cfl, lat.eps, False, 0)
+        M = oracle.metrics(cases.cartesian_nodes(128, 128, 96, *lat.spacing))
+        text = "each step: 1 SSP-RK3 step (FP64 oracle, Euler) of a periodic 128x128x96 block, same recipe"
+        return lat.cells, (lambda Q: oracle.step(p, Q, M, 1)[0]), oracle.pad(lat.state.numpy()), text, *cu
+    if w == "channel":
+        # z-invariant flow: a z-slab of the grid is the same problem; the plain FP64 iteration's
+        # rate (its seconds to the drop are ~80,000 such steps of the full grid: no bounded run)
+        c = cases.channel_case(nz=8)
+        p = oracle.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, c.limiter)
+        bcs = oracle.bc(c.extra["bc"], c.extra["inf"])
+        M = oracle.metrics_bc(c.nodes, bcs)
+        text = ("each step: 1 SSP-RK3 step (FP64 oracle, local time steps, wall and far-field ghost cells) "
+                "of a 192x96x8 z-slab of the bump channel; the GPU arm's metric for this workload is "
+                "seconds to the 1e-6 drop, which the oracle cannot reach in a bounded run")
+        return c.cells, (lambda Q: oracle.step_ex(p, Q, M, 1, bcs, local_dt=True)[0]), oracle.pad(c.state), text, *cu
+    if w == "accel":
+        import numpy as np
+        from oracle import learn as L
+        r = np.random.Generator(np.random.PCG64(0))
+        x = r.standard_normal((10, 4, 48, 96))
+        params = r.standard_normal(L.n_params()) * 0.05
+        text = "each step: numpy forward of the network (oracle/learn.py, FP64) on a 96x48x4 volume"
+        return 96 * 48 * 4, (lambda X: (L.forward(params, X), X)[1]), x, text, "cell inferences/s", "cells/s"
+    raise ValueError(f"no oracle sample for workload {w}")
+
+
 def run_reference(args):
-    """The reference arm: the FP64 CPU oracle as it stands, on the host cores, on a bounded z-slab
-    of the workload's vortex per step (the finite-volume oracle, or the WCNS-E-5 one for
-    --workload wcns256); rank 0 alone runs and prints."""
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores, on a bounded sample
+    of the workload per step; rank 0 alone runs and prints."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
-    from paper_1710_09995_gb300 import cases
-    nz = 8
-    c = cases.isentropic_vortex(n=args.side, L=10.0, nz=nz, viscous=True)
-    p = oracle.params(c.gamma, c.mu, c.Pr, c.cfl, c.eps, c.viscous, c.limiter)
-    wcns = args.workload == "wcns256"
-    if wcns:
-        Q = c.state
-        step = lambda Q: oracle.wcns_step(p, Q, c.spacing, 1)[0]
-    else:
-        M = oracle.metrics(c.grid_nodes())
-        Q = oracle.pad(c.state)
-        step = lambda Q: oracle.step(p, Q, M, 1)[0]
+    cells, step, Q, sample, metric, unit = reference_sample(args)
     for _ in range(args.warmup):
         Q = step(Q)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         Q = step(Q)
     sec = time.perf_counter() - t0
-    value = c.cells * args.steps / sec
-    scheme = "WCNS-E-5 oracle" if wcns else "FP64 oracle"
-    sample = (f"each step: 1 SSP-RK3 step ({scheme}) of a {args.side}x{args.side}x{nz} z-slab of the "
-              f"z-invariant {args.side}^3 vortex")
-    workload = "wcns256" if wcns else "vortex256"
-    out = {"impl": "reference", "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+    value = cells * args.steps / sec
+    out = {"impl": "reference", "metric": metric, "value": value, "unit": unit,
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOADS[workload], "cells": c.cells, "precision": "fp64"},
-           "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": oracle.threads(), "kind": "oracle",
+           "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "cells": cells, "precision": "fp64"},
+           "cpu_baseline": {"value": value, "unit": unit, "cores": oracle.threads(), "kind": "oracle",
                             "sample": sample},
-           "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
