@@ -25,3 +25,14 @@ def test_roofline_arithmetic():
     # curvilinear blocks add their metrics (f32 on the mixed path) to every stage
     w = bench.roofline("mixed", res, cells, steps, 1000.0, "measured", workload="warped512")
     assert abs(w["algorithmic_bytes_per_launch"] - cells * (320 + 3 * 40) / 3) < 1e-6
+
+
+def test_reference_arm_has_a_sample_for_every_workload():
+    """--impl reference times the oracle on a bounded sample of each workload (one step here)"""
+    import argparse
+    for w in bench.WORKLOADS:
+        args = argparse.Namespace(workload=w, side=64)
+        cells, step, state, text, metric, unit = bench.reference_sample(args)
+        assert cells > 0 and text and unit in ("cell-updates/s", "cells/s")
+        out = step(state)
+        assert out.shape == state.shape
