@@ -1,6 +1,8 @@
 // learn.cu -- kernels of the learned convergence accelerator (see learn.cuh): the weight gradient
 // of the convolutions, Adam, weight packing, the loss, and the kernels that connect the network
 // to a block.  The convolutions themselves (tcgen05 implicit GEMM) are in learn_tc.cu.
+#include <atomic>
+
 #include "internal.cuh"
 #include "learn.cuh"
 
@@ -41,13 +43,13 @@ __device__ __forceinline__ long long box_source(int x0, int y0, int z, int b, in
 
 // a kernel's dynamic shared-memory limit, set once per device
 template <typename F>
-static cudaError_t smem_attr(F* kernel, size_t bytes, unsigned long long& done) {
+static cudaError_t smem_attr(F* kernel, size_t bytes, std::atomic<unsigned long long>& done) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 64 && ((done >> dev) & 1ull)) return cudaSuccess;
+  if (dev < 64 && ((done.load(std::memory_order_acquire) >> dev) & 1ull)) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+  if (e == cudaSuccess && dev < 64) done.fetch_or(1ull << dev, std::memory_order_acq_rel);
   return e;
 }
 
@@ -120,7 +122,7 @@ template <int CIP, int CI, int COPG, int CO>
 static cudaError_t wgrad_go(const bf16* a, const bf16* g, const Net& n, int off_w, int off_b, int X, int Y, int Z,
                             int B, int zper, cudaStream_t s) {
   const size_t bytes = (size_t)(BOX * CI + TILE_X * TILE_Y * CO) * sizeof(float);
-  static unsigned long long done = 0;
+  static std::atomic<unsigned long long> done{0};
   cudaError_t e = smem_attr(wgrad_kernel<CIP, CI, COPG, CO>, bytes, done);
   if (e != cudaSuccess) return e;
   constexpr int NO = CO * CI * NTAP + CO;

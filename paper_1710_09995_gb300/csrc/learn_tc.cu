@@ -12,6 +12,8 @@
 // so for tap t the A matrix of the tile starts at box cell (dz 3 + dy) 136 + dx (rows = cells,
 // 8 consecutive rows one 128-byte core matrix, SBO 128 B, LBO = NBOX x 16 B along K) and the B
 // matrix at weight group t CIP/8 (SBO 128 B, LBO = N x 16 B).  The boxes are filled by TMA.
+#include <atomic>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -315,15 +317,15 @@ static cudaError_t tc_map(CUtensorMap* m, const void* base, int CIP, const ConvA
 template <int CIP, int N, int COP, int MODE>
 static cudaError_t conv_tc_go(const ConvArgs& a, const bf16* wtc, int* flag, cudaStream_t s) {
   const size_t bytes = (size_t)(2 * TC_NBOX * CIP + NTAP * CIP * N) * sizeof(bf16) + 64;
-  static unsigned long long done = 0;
+  static std::atomic<unsigned long long> done{0};  // per-device bit; host threads may race here
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (!(dev < 64 && ((done >> dev) & 1ull))) {
+  if (!(dev < 64 && ((done.load(std::memory_order_acquire) >> dev) & 1ull))) {
     e = cudaFuncSetAttribute(conv_tc_kernel<CIP, N, COP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes);
     if (e != cudaSuccess) return e;
-    if (dev < 64) done |= 1ull << dev;
+    if (dev < 64) done.fetch_or(1ull << dev, std::memory_order_acq_rel);
   }
   if (((uintptr_t)a.in & 15u) != 0) return cudaErrorMisalignedAddress;
   CUtensorMap map;

@@ -115,6 +115,15 @@ extern "C" int gbcfd_time_step_noalloc(const double* q, int nx, int ny, int nz, 
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {  // once per device, with that device current
+      // the lookup may load the module, which a stream capture in progress would not survive:
+      // refuse the first call on a device while its stream is being captured
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      e = cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs);
+      if (e != cudaSuccess)
+        return set_error(GBCFD_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+      if (cs != cudaStreamCaptureStatusNone)
+        return set_error(GBCFD_ERR_STATE, "the first gbcfd_time_step_noalloc call on a device must come before "
+                                          "any stream capture (it looks up the scratch array's address)");
       void* addr = nullptr;
       e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
       if (e != cudaSuccess)

@@ -1,21 +1,25 @@
 // stage_inst.cuh -- launch helpers shared by the stage-kernel instantiation units
 #pragma once
+#include <atomic>
+
 #include "launch.h"
 #include "stage.cuh"
 
 namespace gbcfd {
 
 // the kernel's dynamic shared-memory limit, set once per device (before any graph capture)
+// (a per-device bit set atomically: host threads may set up blocks concurrently, and setting the
+// attribute twice is harmless)
 template <typename T, bool VISC, int STAGE, bool CURVI>
 cudaError_t stage_attr() {
-  static unsigned long long done = 0;
+  static std::atomic<unsigned long long> done{0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 64 && ((done >> dev) & 1ull)) return cudaSuccess;
+  if (dev < 64 && ((done.load(std::memory_order_acquire) >> dev) & 1ull)) return cudaSuccess;
   e = cudaFuncSetAttribute(stage_kernel<T, VISC, STAGE, CURVI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)Plan<T, VISC, CURVI>::bytes);
-  if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+  if (e == cudaSuccess && dev < 64) done.fetch_or(1ull << dev, std::memory_order_acq_rel);
   return e;
 }
 

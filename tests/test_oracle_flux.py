@@ -211,3 +211,107 @@ def test_norms_bruteforce():
     for m in range(5):
         s = sum(float(v) ** 2 for v in R[m].ravel())
         assert abs(out[m] - math.sqrt(s / R[m].size)) <= 1e-15 * out[m]
+
+
+# ---- Harten's entropy fix where it is active ---------------------------------------------------
+def _jacobian_fn():
+    """d F_n / d U of Eq. 1's inviscid flux through a unit normal, differentiated symbolically
+    (sympy) from the conserved variables: independent of every formula of the oracle's flux"""
+    sp = pytest.importorskip("sympy")
+    U = sp.symbols("U0:5")
+    n = sp.symbols("n0:3")
+    g = sp.Symbol("gamma")
+    rho, mx, my, mz, E = U
+    u, v, w = mx / rho, my / rho, mz / rho
+    p = (g - 1) * (E - (mx * mx + my * my + mz * mz) / (2 * rho))
+    un = u * n[0] + v * n[1] + w * n[2]
+    F = [rho * un, mx * un + p * n[0], my * un + p * n[1], mz * un + p * n[2], (E + p) * un]
+    J = sp.Matrix(F).jacobian(sp.Matrix(U))
+    return sp.lambdify((U, n, g), J, "numpy")
+
+
+def _conserved(w, gamma=G):
+    rho, u, v, x, p = w
+    return np.array([rho, rho * u, rho * v, rho * x, p / (gamma - 1) + 0.5 * rho * (u * u + v * v + x * x)])
+
+
+def _roe_harten_by_eig(jac, wl, wr, S, eps, gamma=G):
+    """(F_L + F_R)/2 - |A|_H (U_R - U_L)/2 with A the flux Jacobian at Roe's average (sqrt(rho)-weighted
+    velocity and total enthalpy) and |A|_H = sum_k h(l_k) P_k over its three distinct eigenvalues
+    (numpy's eigvals), P_k the spectral projectors prod_{j != k} (A - l_j) / (l_k - l_j) (Sylvester's
+    formula; A is diagonalisable with minimal polynomial (A - l_1)(A - l_2)(A - l_5)), and Harten's
+    modulus h(l) = (l^2 + d^2) / (2 d) below d = eps (|u.n| + c) of that average, |l| above"""
+    area = np.linalg.norm(S)
+    n = np.asarray(S) / area
+    sl, sr = math.sqrt(wl[0]), math.sqrt(wr[0])
+    H = lambda w: gamma / (gamma - 1) * w[4] / w[0] + 0.5 * (w[1] ** 2 + w[2] ** 2 + w[3] ** 2)
+    vel = (sl * np.asarray(wl[1:4]) + sr * np.asarray(wr[1:4])) / (sl + sr)
+    Ht = (sl * H(wl) + sr * H(wr)) / (sl + sr)
+    rho_t = sl * sr
+    c2 = (gamma - 1) * (Ht - 0.5 * vel @ vel)
+    p_t = rho_t * c2 / gamma
+    Ut = _conserved(np.array([rho_t, *vel, p_t]), gamma)
+    A = np.array(jac(tuple(Ut), tuple(n), gamma), dtype=np.float64)
+    # the Roe property A dU = dF holds for this average (pins the average itself)
+    dU = _conserved(wr, gamma) - _conserved(wl, gamma)
+    dF = euler_flux(wr, n, gamma) - euler_flux(wl, n, gamma)
+    assert np.max(np.abs(A @ dU - dF)) <= 1e-13 * max(1.0, np.max(np.abs(dF)))
+    ev = np.sort(np.linalg.eigvals(A).real)
+    assert np.ptp(ev[1:4]) < 1e-10 * (1 + np.max(np.abs(ev)))  # the triple eigenvalue
+    lam = np.array([ev[0], np.mean(ev[1:4]), ev[4]])
+    delta = eps * (abs(vel @ n) + math.sqrt(c2))
+    mod = np.where(np.abs(lam) < delta, (lam * lam + delta * delta) / (2 * delta), np.abs(lam))
+    I5 = np.eye(5)
+    absA = np.zeros((5, 5))
+    for k in range(3):
+        P = I5.copy()
+        for j in range(3):
+            if j != k:
+                P = P @ (A - lam[j] * I5) / (lam[k] - lam[j])
+        absA += mod[k] * P
+    return area * (0.5 * (euler_flux(wl, n, gamma) + euler_flux(wr, n, gamma)) - 0.5 * absA @ dU), lam, delta
+
+
+@pytest.mark.parametrize("kind", ["contact", "transonic_left", "transonic_right", "random"])
+def test_roe_harten_active_matches_eigendecomposition(kind):
+    """States whose Roe average puts one or more eigenvalues inside Harten's band (|l| < d): a
+    near-stationary contact (u.n ~ 0: the entropy and shear waves), a sonic point of the u - c or
+    the u + c wave (transonic rarefaction), and random low-Mach pairs with a wide band.  The
+    oracle must equal the flux assembled from a numerical eigen-decomposition."""
+    jac = _jacobian_fn()
+    rng = np.random.default_rng(11)
+    eps = {"contact": 0.1, "transonic_left": 0.1, "transonic_right": 0.1, "random": 0.6}[kind]
+    active = 0
+    for _ in range(40):
+        S = rng.standard_normal(3)
+        n = S / np.linalg.norm(S)
+        wl, wr = random_state(rng, 0.05), random_state(rng, 0.05)
+        if kind == "contact":      # small normal velocity, pressure nearly continuous
+            wr[4] = wl[4] * (1 + 0.02 * rng.standard_normal())
+        elif kind.startswith("transonic"):  # u.n close to -c / +c on the two sides
+            sgn = -1.0 if kind == "transonic_left" else 1.0
+            for w, f in ((wl, 0.97), (wr, 1.03)):
+                c = math.sqrt(G * w[4] / w[0])
+                w[1:4] += sgn * f * c * n
+        F = oracle.roe_flux(wl, wr, S, eps=eps)
+        ref, lam, delta = _roe_harten_by_eig(jac, wl, wr, S, eps)
+        active += int(np.any(np.abs(lam) < delta))
+        assert rel(F, ref) < 1e-12, (kind, F, ref)
+    assert active >= 30, active  # the fix really is exercised
+
+
+def test_roe_harten_stationary_contact_closed_form():
+    """A contact at rest (u = 0 on both sides, equal p, density jump) has only the entropy wave,
+    with Roe speed 0 < d = eps c~, so Harten's modulus is d / 2.  With c~^2 = gamma p / sqrt(rho_L rho_R)
+    (Roe's enthalpy average at equal p) the flux is exactly
+        F = |S| (-(eps c~ / 4) (rho_R - rho_L), p n, 0):
+    the fix adds mass diffusion eps c~ / 4 and nothing else."""
+    S = np.array([0.3, -0.2, 0.7])
+    area = np.linalg.norm(S)
+    for rl, rr, p, eps in ((1.0, 0.25, 0.7, 0.1), (0.8, 1.9, 1.3, 0.3), (2.0, 0.5, 0.2, 0.05)):
+        wl = np.array([rl, 0.0, 0.0, 0.0, p])
+        wr = np.array([rr, 0.0, 0.0, 0.0, p])
+        ct = math.sqrt(G * p / math.sqrt(rl * rr))
+        F = oracle.roe_flux(wl, wr, S, eps=eps)
+        want = np.array([-area * eps * ct / 4.0 * (rr - rl), p * S[0], p * S[1], p * S[2], 0.0])
+        assert np.allclose(F, want, rtol=1e-13, atol=1e-15), (F, want)

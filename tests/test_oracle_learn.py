@@ -107,3 +107,42 @@ def test_target_and_prediction_are_inverse():
     Q1 = Q0 + 1e-4 * r.standard_normal(Q0.shape)
     y = L.target(Q0, Q1, 3e-3, inf)
     assert np.allclose(L.apply_prediction(Q0, y, 3e-3, inf), Q1, rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("b1,b2", [(0.9, 0.999), (0.5, 0.9)])
+def test_adam_constant_gradient_closed_form(b1, b2):
+    """From zero moments under a constant gradient g, m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2
+    (geometric sums), so both bias corrections give back g and g^2 exactly and every step moves
+    by lr g / (|g| + eps): after T steps w_T = w_0 - T lr g / (|g| + eps).  A missing or wrong
+    correction (t-independent, or b1 and b2 swapped) breaks this from t = 2 on."""
+    r = rng(6)
+    w0 = r.standard_normal(40)
+    g = r.standard_normal(40)
+    lr, eps = 2e-3, 1e-8
+    w, m, v = w0.copy(), np.zeros(40), np.zeros(40)
+    for t in range(1, 8):
+        w, m, v = L.adam(w, g, m, v, t, lr, b1=b1, b2=b2, eps=eps)
+        assert np.allclose(m, (1 - b1 ** t) * g, rtol=1e-14, atol=0)
+        assert np.allclose(v, (1 - b2 ** t) * g * g, rtol=1e-13, atol=0)
+        assert np.allclose(w, w0 - t * lr * g / (np.abs(g) + eps), rtol=1e-13, atol=1e-15)
+
+
+def test_adam_alternating_gradient_closed_form():
+    """Gradients g, -g, g, ... from zero moments: m_t = (1 - b1) g (-1)^(t+1) (1 - (-b1)^t) / (1 + b1)
+    and v_t = (1 - b2^t) g^2, so step t moves by
+        -lr (1 - b1) (-1)^(t+1) (1 - (-b1)^t) / ((1 + b1)(1 - b1^t)) g / (|g| + eps).
+    This fixes the first-moment bias correction independently of the second."""
+    b1, b2, lr, eps = 0.9, 0.999, 1e-3, 1e-8
+    r = rng(7)
+    g = r.standard_normal(30)
+    w = r.standard_normal(30)
+    m, v = np.zeros(30), np.zeros(30)
+    for t in range(1, 10):
+        gt = g if t % 2 else -g
+        w1, m, v = L.adam(w, gt, m, v, t, lr, b1=b1, b2=b2, eps=eps)
+        sgn = 1.0 if t % 2 else -1.0
+        coef = (1 - b1) * sgn * (1 - (-b1) ** t) / (1 + b1)
+        assert np.allclose(m, coef * g, rtol=1e-13, atol=0)
+        step = -lr * coef / (1 - b1 ** t) * g / (np.abs(g) + eps)
+        assert np.allclose(w1 - w, step, rtol=1e-10, atol=1e-18)
+        w = w1
