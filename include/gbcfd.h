@@ -297,6 +297,14 @@ int gbcfd_accel_forward(gbcfd_accel accel, const void* x, float* y, void* stream
 int gbcfd_accel_train_step(gbcfd_accel accel, const void* x, const float* t, float lr, int step, double* loss,
                            void* stream);
 
+/* The training state after the last gbcfd_accel_train_step, copied to host arrays of
+ * GBCFD_ACCEL_NPARAM floats (any pointer may be NULL to skip it), in the parameter layout of
+ * gbcfd_accel_set_params: grad = the gradient of that step's mean squared error at the
+ * parameters it started from (before the Adam move), m and v = Adam's first and second moments
+ * after the move (Kingma & Ba's m_t, v_t, not bias-corrected).  Zeros before any step.
+ * Synchronises the stream. */
+int gbcfd_accel_get_train_state(gbcfd_accel accel, float* grad, float* m, float* v, void* stream);
+
 /* Features of a block (its size must be the accelerator's volume) into x (device bf16
  * [cells][16], NULL: the accelerator's own buffer); remembers the state and s for
  * gbcfd_accel_target.  The block must hold a state, be between steps and have a far-field face. */

@@ -1457,6 +1457,7 @@ extern "C" int gbcfd_accel_set_params(gbcfd_accel a, const float* params, void* 
   CK(cudaMemcpyAsync(a->net.w, params, sizeof(float) * learn::NPARAM, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(a->net.m, 0, sizeof(float) * learn::NPARAM, s));
   CK(cudaMemsetAsync(a->net.v, 0, sizeof(float) * learn::NPARAM, s));
+  CK(cudaMemsetAsync(a->net.grad, 0, sizeof(float) * learn::NPARAM, s));
   CK(learn::launch_pack(a->net, s));
   CK(cudaStreamSynchronize(s));
   a->step_count = 0;
@@ -1467,6 +1468,17 @@ extern "C" int gbcfd_accel_get_params(gbcfd_accel a, float* params, void* stream
   if (!a || !params) return fail(GBCFD_ERR_ARG, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CK(cudaMemcpyAsync(params, a->net.w, sizeof(float) * learn::NPARAM, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_accel_get_train_state(gbcfd_accel a, float* grad, float* m, float* v, void* stream) {
+  if (!a) return fail(GBCFD_ERR_ARG, "accelerator is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = sizeof(float) * learn::NPARAM;
+  if (grad) CK(cudaMemcpyAsync(grad, a->net.grad, bytes, cudaMemcpyDeviceToHost, s));
+  if (m) CK(cudaMemcpyAsync(m, a->net.m, bytes, cudaMemcpyDeviceToHost, s));
+  if (v) CK(cudaMemcpyAsync(v, a->net.v, bytes, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return GBCFD_OK;
 }

@@ -38,7 +38,9 @@ __device__ __forceinline__ Consts<V> make_consts(double gamma, double eps, doubl
 // MUSCL states at the face between w1 and w2 of the stencil w0..w3 (one variable).  minmod
 // without compares: (copysign(1/4, a) + copysign(1/4, b)) * min(|a|, |b|) is exactly half the
 // minmod slope (0.5 min(a,b) when both are positive, 0.5 max(a,b) when both are negative, 0
-// otherwise: the sum is 0 or +-1/2 and a product by a power of two is exact).
+// otherwise: the sum is 0 or +-1/2 and a product by a power of two is exact).  In FP64 the same
+// halved slope comes from integer operations on the bit patterns (half_minmod_f64), so the
+// states are the same bits without any FP64-pipe comparison.
 template <typename V>
 __device__ __forceinline__ void muscl(V w0, V w1, V w2, V w3, int lim, V& L, V& R) {
   using O = VM<V>;
@@ -47,6 +49,9 @@ __device__ __forceinline__ void muscl(V w0, V w1, V w2, V w3, int lim, V& L, V& 
     const V q = O::c(0.25);
     L = O::fma(q, d01 + d12, w1);
     R = w2 - q * (d12 + d23);
+  } else if constexpr (sizeof(V) == 8) {  // FP64: the halved slopes on the integer pipe (same bits)
+    L = w1 + half_minmod_f64(d01, d12);
+    R = w2 - half_minmod_f64(d12, d23);
   } else {
     const V q = O::c(0.25);
     const V sl = O::csign(q, d01) + O::csign(q, d12);

@@ -683,10 +683,12 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
       *slast = (prev == gridDim.x - 1);
     }
     __syncthreads();
-    if (!*slast || warp != 0) return;
+    if (!*slast) return;
     __threadfence();
-    double gmax = 0.0;
-    for (int b = 0; b < P.nblocks; ++b) {
+    // every warp of the last CTA folds blocks warp, warp + NWARP, ... (a group may hold many
+    // blocks: one warp walking all of them serially left the SMs idle behind it)
+    double wmax = 0.0;
+    for (int b = warp; b < P.nblocks; b += NWARP) {
       const BlockDesc* Db = P.table + b;
       double s[6] = {0, 0, 0, 0, 0, 0};
       for (int c = lane; c < Db->ctas; c += 32) {
@@ -700,7 +702,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
         for (int m = 0; m < 5; ++m) s[m] += __shfl_xor_sync(0xffffffffu, s[m], off);
         s[5] = fmax(s[5], __shfl_xor_sync(0xffffffffu, s[5], off));
       }
-      gmax = fmax(gmax, s[5]);
+      wmax = fmax(wmax, s[5]);
       if (lane == 0) {
         const double n = (double)Db->g.nx * Db->g.ny * Db->g.nz;
         if (STAGE == 1)
@@ -708,12 +710,19 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
         if (STAGE == 3) Db->ctrl->rate = s[5];
       }
     }
-    if (lane == 0) {
-      if (STAGE == 3) {
+    if constexpr (STAGE == 3) {
+      if (lane == 0) red[warp] = wmax;
+      __syncthreads();
+      double gmax = 0.0;
+      for (int w = 0; w < NWARP; ++w) gmax = fmax(gmax, red[w]);
+      const double dtn = ph.cfl / gmax;
+      for (int b = tid; b < P.nblocks; b += NT) P.table[b].ctrl->dt = dtn;
+      if (tid == 0) {
         P.gctrl->rate = gmax;
-        P.gctrl->dt = ph.cfl / gmax;
-        for (int b = 0; b < P.nblocks; ++b) P.table[b].ctrl->dt = ph.cfl / gmax;
+        P.gctrl->dt = dtn;
       }
+    }
+    if (tid == 0) {
       P.gctrl->counter = 0u;
     }
   }

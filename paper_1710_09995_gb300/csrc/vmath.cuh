@@ -9,19 +9,52 @@ namespace gbcfd {
 // the operations the generic code uses, per value type
 template <typename V> struct VM;
 
+// The FP64 path is bound by the FP64 pipe (this part issues one FP64 operation per 64 FP32
+// ones), while its integer pipe idles: comparisons whose operands are known to be non-negative
+// run there on the bit patterns (for non-negative IEEE doubles the order of the values is the
+// order of their bit patterns as unsigned integers), and the reciprocal is the hardware's
+// estimate refined by Newton's method instead of an IEEE division.
 template <> struct VM<double> {
   using S = double;
   static __device__ __forceinline__ double c(double s) { return s; }
   static __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
   static __device__ __forceinline__ double rsqrt(double a) { return ::rsqrt(a); }
-  static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+  // 1/a for positive finite a: the estimate r of rcp.approx.ftz.f64 (relative error e0 about
+  // 2^-22) and one third-order Newton step r (1 + e + e^2), e = 1 - a r, whose relative error is
+  // e0^3: three FMAs.  Within an ulp or two of the correctly rounded quotient, not always equal to
+  // it.  a = 0 gives NaN (callers select such values away).
+  static __device__ __forceinline__ double rcp(double a) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
+    const double e = ::fma(-a, r, 1.0);
+    return ::fma(r, ::fma(e, e, e), r);
+  }
   static __device__ __forceinline__ double ab(double a) { return fabs(a); }
   static __device__ __forceinline__ double mn(double a, double b) { return fmin(a, b); }
   static __device__ __forceinline__ double csign(double q, double x) { return copysign(q, x); }
-  // a < b ? x : y
-  static __device__ __forceinline__ double lt(double a, double b, double x, double y) { return a < b ? x : y; }
-  static __device__ __forceinline__ double pos(double a, double x, double y) { return a > 0.0 ? x : y; }
+  // a < b ? x : y, for non-negative a and b: compared as bit patterns on the integer pipe
+  static __device__ __forceinline__ double lt(double a, double b, double x, double y) {
+    return (unsigned long long)__double_as_longlong(a) < (unsigned long long)__double_as_longlong(b) ? x : y;
+  }
+  // a > 0 ? x : y, for non-negative a (its bit pattern is non-zero)
+  static __device__ __forceinline__ double pos(double a, double x, double y) {
+    return __double_as_longlong(a) != 0ll ? x : y;
+  }
 };
+
+// Half the minmod slope of the differences a and b in doubles, on the integer pipe: zero when
+// their signs differ or either is zero, else the smaller magnitude (compared as bit patterns)
+// halved by lowering its exponent by one, with the common sign.  Exact for every magnitude of
+// at least 2^-1021; smaller ones (subnormal halves) give zero.
+__device__ __forceinline__ double half_minmod_f64(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const unsigned long long ma = (unsigned long long)ia & 0x7fffffffffffffffull;
+  const unsigned long long mb = (unsigned long long)ib & 0x7fffffffffffffffull;
+  const unsigned long long m = ma < mb ? ma : mb;
+  const unsigned long long h = m >= (2ull << 52) ? m - (1ull << 52) : 0ull;
+  const unsigned long long sgn = (unsigned long long)ia & 0x8000000000000000ull;
+  return __longlong_as_double((ia ^ ib) >= 0 ? (long long)(h | sgn) : 0ll);
+}
 
 template <> struct VM<float> {
   using S = float;

@@ -90,6 +90,8 @@ SIGNATURES = {
     "gbcfd_accel_get_params": [_VP, ctypes.POINTER(ctypes.c_float), _VP],
     "gbcfd_accel_forward": [_VP, _VP, _VP, _VP],
     "gbcfd_accel_train_step": [_VP, _VP, _VP, ctypes.c_float, ctypes.c_int, _D, _VP],
+    "gbcfd_accel_get_train_state": [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                    ctypes.POINTER(ctypes.c_float), _VP],
     "gbcfd_accel_features": [_VP, _VP, _VP, _VP],
     "gbcfd_accel_target": [_VP, _VP, _VP, _VP],
     "gbcfd_accel_try": [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_int), _D],
@@ -472,6 +474,14 @@ class Accel:
         _check(lib().gbcfd_accel_train_step(self.handle, _ptr(x), _ptr(t), float(lr), self.step_count,
                                             ctypes.byref(loss), _stream(stream)))
         return loss.value
+
+    def train_state(self, stream=None):
+        """(grad, m, v) after the last train_step: the gradient of its loss at the parameters it
+        started from, and Adam's moments after its move (float32 arrays, parameter layout)"""
+        out = [np.zeros(ACCEL_NPARAM, dtype=np.float32) for _ in range(3)]
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(lib().gbcfd_accel_get_train_state(self.handle, *(a.ctypes.data_as(fp) for a in out), _stream(stream)))
+        return tuple(out)
 
     def features(self, block, x=None, stream=None):
         _check(lib().gbcfd_accel_features(self.handle, block.handle, _ptr(x) if x is not None else None,

@@ -1,6 +1,7 @@
 """The learned convergence accelerator's kernels against the plain definitions in oracle/learn.py:
-the tensor-core convolutions (forward), one training step (loss and the sign of every weight's
-first Adam move), the block features and training targets, and the accept-or-restore update."""
+the tensor-core convolutions (forward), the training step (loss, the gradient of every weight and
+bias tensor element by element, Adam's moments and moves over several steps), the block features
+and training targets, and the accept-or-restore update."""
 import numpy as np
 import pytest
 
@@ -111,6 +112,89 @@ def test_train_step_matches_oracle_gradient(gb):
             assert np.all(np.sign(ms[big]) == np.sign(gs[big]))
             assert np.allclose(np.abs(ms[big]), 1.0, rtol=1e-3)
             o += n
+
+
+TENSORS = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def tensor_slices():
+    """(name, slice) of every weight and bias tensor in the flat parameter layout"""
+    out, o = [], 0
+    names = iter(TENSORS)
+    for ci, co in zip(L.CH[:-1], L.CH[1:]):
+        for n in (co * ci * 27, co):
+            out.append((next(names), slice(o, o + n)))
+            o += n
+    return out
+
+
+def batch_loss_and_grad(p, xb, t, zper=True):
+    B = xb.shape[0]
+    loss, g = 0.0, np.zeros_like(p)
+    for b in range(B):
+        lb, gb_ = L.loss_and_grad(p, xb[b], t[b], zper=zper)
+        loss += lb / B
+        g += gb_ / B
+    return loss, g
+
+
+def train_problem(gb, B, Z, Y, X, zper, seed):
+    p = random_params(seed)
+    x = rng(seed + 1).standard_normal((B, 10, Z, Y, X))
+    t = rng(seed + 2).standard_normal((B, 5, Z, Y, X))
+    xg = to_gpu_features(x)
+    tg = np.zeros((B, Z, Y, X, 8), dtype=np.float32)
+    tg[..., :5] = np.transpose(t, (0, 2, 3, 4, 1))
+    tg = torch.from_numpy(tg.reshape(-1, 8)).cuda()
+    a = gb.Accel(X, Y, Z, B, zperiodic=zper)
+    a.set_params(p)
+    return a, p, xg, tg, from_gpu(xg, B, Z, Y, X, C=10), t
+
+
+@pytest.mark.parametrize("shape,zper", [((2, 4, 12, 36), True), ((1, 3, 10, 130), False)])
+def test_train_gradient_matches_oracle_elementwise(gb, shape, zper):
+    """the raw gradient of one training step (weight-gradient kernel, tensor-core backward-data
+    convolutions through SiLU', loss kernel) against the oracle's backward pass on the same bf16
+    features, per tensor: relative L2 <= 1e-2 and every element within 1e-2 of the tensor's
+    largest.  (bf16 storage of dY and dZ between the layers bounds the agreement.)  The second
+    shape has a ragged second x tile (130 cells) and no z wrap."""
+    B, Z, Y, X = shape
+    a, p, xg, tg, xb, t = train_problem(gb, B, Z, Y, X, zper, 31)
+    loss = a.train_step(xg, tg, 1e-3)
+    g_gpu, _, _ = a.train_state()
+    want_loss, g = batch_loss_and_grad(p, xb, t, zper)
+    assert abs(loss - want_loss) <= 1e-3 * want_loss
+    for name, sl in tensor_slices():
+        got, want = g_gpu[sl].astype(np.float64), g[sl]
+        err = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert err <= 1e-2, (name, err)
+        assert np.max(np.abs(got - want)) <= 1e-2 * np.max(np.abs(want)), name
+
+
+def test_adam_state_over_three_steps_matches_oracle(gb):
+    """three training steps on one batch: the gradients, Adam's moments m_t and v_t, and the
+    parameters' moves against the oracle's trajectory (its gradients at its own iterates, its
+    FP64 Adam with bias corrections 1 - b^t); moves compared where the gradient is not negligible
+    (elsewhere Adam's normalised step follows the sign of rounding noise)"""
+    B, Z, Y, X = 2, 4, 12, 36
+    a, p, xg, tg, xb, t = train_problem(gb, B, Z, Y, X, True, 41)
+    lr = 2e-3
+    w, m, v = p.copy(), np.zeros_like(p), np.zeros_like(p)
+    for step in range(1, 4):
+        loss = a.train_step(xg, tg, lr)
+        g_gpu, m_gpu, v_gpu = a.train_state()
+        want_loss, g = batch_loss_and_grad(w, xb, t)
+        w_next, m, v = L.adam(w, g, m, v, step, lr)
+        assert abs(loss - want_loss) <= 1e-3 * want_loss, step
+        w_gpu = a.get_params().astype(np.float64)
+        for name, sl in tensor_slices():
+            for got, want, tol, what in ((g_gpu, g, 1e-2, "grad"), (m_gpu, m, 1e-2, "m"), (v_gpu, v, 2e-2, "v")):
+                err = np.linalg.norm(got[sl] - want[sl]) / np.linalg.norm(want[sl])
+                assert err <= tol, (step, name, what, err)
+            big = np.abs(m[sl]) > 0.1 * np.abs(m[sl]).max()
+            mv_gpu, mv = (w_gpu - p)[sl][big], (w_next - p)[sl][big]
+            assert np.linalg.norm(mv_gpu - mv) <= 2e-2 * np.linalg.norm(mv), (step, name)
+        w = w_next
 
 
 def test_training_reduces_the_loss(gb):

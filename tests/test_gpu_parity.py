@@ -318,16 +318,28 @@ def test_argument_errors(gb):
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
 def test_full_size_vortex_256(gb, precision, tol):
-    """The 256^3 Navier-Stokes vortex, in the launch configuration the benchmark times: the flow
-    is z-invariant, so every plane of the GPU result must equal plane 0 bitwise, and plane 0
-    must match the oracle run on a single-plane periodic slab of the same case."""
+    """The 256^3 Navier-Stokes vortex for the full 100 steps, in the launch configuration the
+    benchmark times: the flow is z-invariant, so every plane of the GPU result must equal plane 0
+    bitwise, and plane 0 must match the oracle run on a single-plane periodic slab of the same case
+    (per conserved variable: <= 1e-12 FP64, <= 1e-5 mixed).  The error against the isentropic
+    vortex's closed form (the Euler solution translated by u_inf t; the Navier-Stokes run departs
+    from it by O(t / Re) besides the discretisation error) is bounded too, and equal on both paths
+    to the oracle's to within the parity bar."""
     full = cases.isentropic_vortex(n=256, L=10.0, viscous=True)
     blk = gb.block_for_case(full, precision=precision)
-    gb.step([blk], 2)
+    nsteps = 100
+    gb.step([blk], nsteps)
     got = blk.get_state()
     assert bool(torch.all(got == got[:, :1]).item())
     plane = got[:, 0].cpu().numpy()
     slab = cases.isentropic_vortex(n=256, L=10.0, nz=1, viscous=True)
-    ref, _, norms = run_oracle(slab, 2)
-    assert max(per_var(plane[:, None], ref)) <= tol
+    ref, dts, norms = run_oracle(slab, nsteps)
+    err = per_var(plane[:, None], ref)
+    assert max(err) <= tol, err
     assert np.allclose(blk.residual_norm(), norms[-1], rtol=1e-10 if precision == 0 else 1e-4, atol=0)
+    t_end = float(np.sum(dts))
+    exact = cases.isentropic_vortex(n=256, L=10.0, nz=1, viscous=True, t=t_end).state
+    e_gpu = np.linalg.norm(plane[0] - exact[0, 0]) / np.linalg.norm(exact[0, 0])
+    e_orc = np.linalg.norm(ref[0, 0] - exact[0, 0]) / np.linalg.norm(exact[0, 0])
+    assert e_orc < 2e-4, e_orc  # observed 6.8e-5 at h = 10/256 after t = 0.378
+    assert abs(e_gpu - e_orc) <= tol * 10 + 1e-15, (e_gpu, e_orc)
