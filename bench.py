@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of the structured-grid finite-volume hot path on one GB300 (or N replicas).
 
-Workload: 256^3 isentropic vortex (strength 5, Mach 0.5, periodic [0,10]^3), compressible
-Navier-Stokes at Re 1e4, Pr 0.72; MUSCL/minmod + Roe + central viscous fluxes, SSP-RK3 at
-CFL 0.5.  A step is one full SSP-RK3 step of the block: per stage one halo exchange and one
-fused stage kernel (residual + update; stage 1 also the residual norm, stage 3 also the next
-time step).  The headline runs the mixed path (FP32 reconstruction and fluxes, FP64 state,
-update and norms); the FP64 path is timed on the same case in the same run.
+Default workload: the batched multi-block case, 96 uneven Cartesian blocks (a 4x4x6 periodic
+lattice with sides drawn from 16..160, 1.37e8 cells), Euler at Mach 0.8, MUSCL/minmod + Roe,
+SSP-RK3 at CFL 0.5, advanced as one group: per step one CUDA graph holding the time step and,
+three times, the halo exchange of every block and one fused stage launch for all blocks.  The
+headline `value` is the FP64 path (the paper's precision); the mixed path (FP32 reconstruction
+and fluxes, FP64 state, update and norms) is timed on the same case beside it, and the 256^3
+Navier-Stokes vortex (both paths) and the steady bump channel's wall time to a 1e-6 residual
+drop (plain FP64 iteration against the learned-accelerated mixed form) are extra keys of the
+same line.  Other workloads: --workload.
 
 Prints one JSON line (rank 0).  Inputs are seeded and synthetic (the paper's meshes are not
 available).  `--impl reference` times the FP64 CPU oracle instead (the only reference there is).
@@ -63,10 +66,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbcfd", choices=["gbcfd", "reference"])
     ap.add_argument("--side", type=int, default=N_DEFAULT, help="cells per side of the cubic vortex block")
-    ap.add_argument("--workload", default="vortex256", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="lattice96", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["both", "mixed", "fp64"],
-                    help="default: both for vortex256, mixed for warped512 and lattice96")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+                    help="default: both for vortex256 (mixed first) and lattice96 (FP64 first), mixed for warped512")
+    ap.add_argument("--e2e-steps", type=int, default=None, help="default 20 (3 for the FP64 lattice)")
+    ap.add_argument("--no-channel", action="store_true",
+                    help="lattice96: skip the bump channel's time-to-drop key (the longest part of the run)")
+    ap.add_argument("--no-vortex", action="store_true", help="lattice96: skip the 256^3 vortex key")
+    ap.add_argument("--lattice-div", type=int, default=1,
+                    help="lattice96: divide every block side by this (same recipe, fewer cells: profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--target", type=float, default=1e-6, help="channel: residual drop to reach")
     ap.add_argument("--max-seconds", type=float, default=900.0, help="channel: cap per solve")
@@ -254,23 +262,26 @@ def time_group_path(gbcfd, torch, lat, precision, steps, warmup, world, device):
     barrier(world)
     ms = max_over_ranks(start.elapsed_time(stop), world, device)
     norms = [b.residual_norm().tolist() for b in blocks]
+    tile_rows = g.tile_rows
     g.close()
     for b in blocks:
         b.close()
     return {"ms": ms, "stage_ms": stage_ms, "halo_ms": halo_ms, "launches": 7 * steps, "norms": norms[0],
-            "ctas_per_sm": ctas_per_sm, "blocks": len(blocks)}
+            "ctas_per_sm": ctas_per_sm, "tile": [32, tile_rows], "blocks": len(blocks)}
 
 
-def e2e_group_path(gbcfd, torch, lat, precision, steps, world, device):
+def e2e_group_path(gbcfd, torch, lat, precision, steps, world, device, pipelined=True):
     """Through the C ABI with pinned host buffers, every step uploading each block's state,
-    advancing the group one SSP-RK3 step and reading back every block's state and residual norms.
-    The headline value runs the steps as items of a 3-group gbcfd_pipe (an item is the blocks'
-    states concatenated); `serial_value` is the same work as per-block set_state, one group step
-    and per-block get_state / residual_norm calls."""
+    advancing the group one SSP-RK3 step and reading back every block's state and residual norms:
+    the value is per-block set_state, one group step and per-block get_state / residual_norm calls,
+    one after the other (what a time-marching user sees).  With `pipelined`, `pipelined_value`
+    runs the steps as independent items of a 3-group gbcfd_pipe instead (an item is the blocks'
+    states concatenated)."""
     import gc
     prec = gbcfd.MIXED if precision == "mixed" else gbcfd.FP64
     parts = [lat.state[:, zs, ys, xs].contiguous().cpu() for zs, ys, xs in lat.block_slices().values()]
     nbytes = sum(h.numel() * 8 for h in parts)
+    nblk_all = len(parts)
     # serial calls
     blocks = gbcfd.blocks_for_lattice(lat, prec, device)
     g = gbcfd.Group(blocks)
@@ -299,6 +310,12 @@ def e2e_group_path(gbcfd, torch, lat, precision, steps, world, device):
     for b in blocks:
         b.close()
     del g, blocks, one, host_in, host_out
+    out = {"value": world * lat.cells * steps / serial, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 112 * nblk_all,
+           "api": "per block gbcfd_set_state, gbcfd_group_step, per block gbcfd_get_state + gbcfd_residual_norm "
+                  "(time marching: each step's state uploaded and read back)", "steps": steps}
+    if not pipelined:
+        return out
     item = torch.cat([h.reshape(-1) for h in parts]).pin_memory()
     nblk = len(parts)
     del parts  # host memory: the pipeline holds the item and two output buffers (5.5 GB each)
@@ -328,20 +345,17 @@ def e2e_group_path(gbcfd, torch, lat, precision, steps, world, device):
         gg.close()
         for b in gg.blocks:
             b.close()
-    return {"value": world * lat.cells * steps / dt, "unit": "cell-updates/s",
-            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 40 * nblk,
-            "api": "gbcfd_pipe_submit x steps + gbcfd_pipe_sync (3 member groups)",
-            "serial_value": world * lat.cells * steps / serial,
-            "serial_api": "per block gbcfd_set_state, gbcfd_group_step, per block gbcfd_get_state + gbcfd_residual_norm",
-            "serial_d2h_bytes_per_step": nbytes + 112 * nblk, "steps": steps}
+    out["pipelined_value"] = world * lat.cells * steps / dt
+    out["pipelined_api"] = "gbcfd_pipe_submit x steps + gbcfd_pipe_sync (3 member groups; steps as independent items)"
+    return out
 
 
 def e2e_path(gbcfd, torch, case, precision, steps, world, device):
     """Through the C ABI with pinned host buffers, every step uploading the state, advancing it one
-    SSP-RK3 step and reading back the new state and its residual norms.  The headline value runs
-    the steps as independent items through a 3-block gbcfd_pipe (host-link copies of neighbouring
-    items overlap the steps); `serial_value` is the same work as set_state / step / get_state /
-    residual_norm calls on one block, one after the other."""
+    SSP-RK3 step and reading back the new state and its residual norms: the value is set_state /
+    step / get_state / residual_norm calls on one block, one after the other (what a time-marching
+    user sees); `pipelined_value` runs the steps as independent items through a 3-block
+    gbcfd_pipe instead (host-link copies of neighbouring items overlap the steps)."""
     prec = gbcfd.MIXED if precision == "mixed" else gbcfd.FP64
     host_in = torch.from_numpy(case.state).pin_memory()
     nbytes = case.state.nbytes
@@ -382,15 +396,18 @@ def e2e_path(gbcfd, torch, case, precision, steps, world, device):
     pipe.close()
     for b in members:
         b.close()
-    return {"value": world * case.cells * steps / dt, "unit": "cell-updates/s",
-            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 40,
-            "api": "gbcfd_pipe_submit x steps + gbcfd_pipe_sync (3 member blocks)",
-            "serial_value": world * case.cells * steps / serial,
-            "serial_api": "gbcfd_set_state + gbcfd_step + gbcfd_get_state + gbcfd_residual_norm per step",
-            "serial_d2h_bytes_per_step": nbytes + ctrl_bytes, "steps": steps}
+    return {"value": world * case.cells * steps / serial, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + ctrl_bytes,
+            "api": "gbcfd_set_state + gbcfd_step + gbcfd_get_state + gbcfd_residual_norm per step "
+                   "(time marching: each step's state uploaded and read back)",
+            "pipelined_value": world * case.cells * steps / dt,
+            "pipelined_api": "gbcfd_pipe_submit x steps + gbcfd_pipe_sync (3 member blocks; steps as independent items)",
+            "steps": steps}
 
 
-FP64_PEAK_TFLOPS = 1.25  # GB300 FP64, nominal (the profiling recipe's figure; 1.20 measured by FMA probe)
+# GB300 FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x
+# 2.07 GHz (the recipe's nominal 1.25 TFLOP/s; a DFMA-chain probe measured 1.2556)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 ISSUE_PER_CLK = 152 * 4 * 32  # SMs x schedulers x lanes: thread instructions issued per clock
 
 
@@ -432,7 +449,8 @@ def fp64_alu_roofline(res, cells, steps, hbm, workload="vortex256"):
     counted by ncu per stage) over the launch time, against the part's FP64 peak"""
     flops = profiled_numbers("fp64", "fp64 flops per cell and stage", workload)
     out = {"bound": "alu", "kernel": "stage_kernel", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
-           "peak_kind": "nominal FP64 (profiling recipe)", "avg_launch_ms": hbm["avg_launch_ms"],
+           "peak_kind": "FP64 FMA lanes x clock (152 SMs x 2 x 2 flops x 2.07 GHz; 1.2556 measured)",
+           "avg_launch_ms": hbm["avg_launch_ms"],
            "traffic": hbm["traffic"], "hbm_frac": hbm["frac"]}
     if flops:
         total = sum(flops[s - 1] * cells * steps for s in (1, 2, 3))
@@ -573,7 +591,7 @@ def run_gbcfd(args):
     results = {p: time_path(gbcfd, torch, case, p, args.steps, args.warmup, world, device) for p in paths}
     clk = clocks.stop()
     head = paths[0]
-    e2e = e2e_path(gbcfd, torch, case, head, args.e2e_steps, world, device)
+    e2e = e2e_path(gbcfd, torch, case, head, args.e2e_steps or 20, world, device)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(args.side) if args.workload == "vortex256" else cpu_baseline_warped()
@@ -617,24 +635,75 @@ def run_gbcfd(args):
     print(json.dumps(out))
 
 
+def vortex_key(args, world, device, torch, cases, gbcfd):
+    """the 256^3 Navier-Stokes vortex, both paths, as a key of the lattice line"""
+    peak, peak_kind = hbm_peak()
+    case = cases.isentropic_vortex(n=args.side, L=10.0, viscous=True)
+    out = {"workload": WORKLOADS["vortex256"], "cells": case.cells, "steps": args.steps, "warmup": args.warmup}
+    for p in ("mixed", "fp64"):
+        r = time_path(gbcfd, torch, case, p, args.steps, args.warmup, world, device)
+        hbm = roofline(p, r, case.cells, args.steps, peak, peak_kind, "vortex256")
+        out[p] = {"value": world * case.cells * args.steps / (r["ms"] / 1e3), "unit": "cell-updates/s",
+                  "ms_per_step": r["ms"] / args.steps, "dtype": "f64" if p == "fp64" else "f32+f64",
+                  "roofline": fp64_alu_roofline(r, case.cells, args.steps, hbm, "vortex256") if p == "fp64" else hbm,
+                  "halo_ms_per_step": r["halo_ms"] / args.steps, "gpu_launches": r["launches"]}
+    return out
+
+
+def channel_key(args, device, cases):
+    """wall time to a 1e-6 density-residual drop on the steady bump channel (192x96x64): the plain
+    FP64 iteration, the mixed path finished on the FP64 path (hybrid) without and with the learned
+    accelerator's tries"""
+    from paper_1710_09995_gb300 import learn
+    case = cases.channel_case(*learn.FULL_GRID, height=0.1, mach=0.6)
+    params, info = (learn.load() if os.path.exists(learn.WEIGHTS) else (None, None))
+    runs = {"fp64_plain": learn.solve(case, args.target, None, args.max_seconds, precision="fp64", device=device),
+            "hybrid_plain": learn.solve(case, args.target, None, args.max_seconds, precision="hybrid", device=device)}
+    if params is not None:
+        runs["hybrid_learned"] = learn.solve(case, args.target, params, args.max_seconds, precision="hybrid",
+                                             device=device)
+    head = runs.get("hybrid_learned", runs["hybrid_plain"])
+    out = {"metric": f"seconds to a {args.target:g} density-residual drop", "unit": "s",
+           "workload": WORKLOADS["channel"], "cells": case.cells, "accelerator": info}
+    for k, r in runs.items():
+        out[k] = {"seconds": r["seconds"], "reached": r["reached"], "steps": r["steps"],
+                  "drop": r.get("drop"), **{x: r[x] for x in ("tried", "kept", "fp64_steps") if x in r}}
+    plain = runs["fp64_plain"]
+    out["speedup_vs_fp64_plain"] = (plain["seconds"] / head["seconds"]
+                                    if head["reached"] and plain["reached"] else None)
+    return out
+
+
 def run_lattice(args, world, rank, local, device, torch, cases, gbcfd):
-    lat = cases.lattice_case(device=device)
-    prec = args.precision or "mixed"
-    paths = ["mixed", "fp64"] if prec == "both" else [prec]
+    if args.lattice_div > 1:
+        full = cases.lattice_sizes(cases.lattice_seed((4, 4, 6), 16, 160), (4, 4, 6), 16, 160)
+        sizes = [[max(8, v // args.lattice_div) for v in s] for s in full]
+        lat = cases.lattice_case(sizes=sizes, seed=4, device=device)
+    else:
+        lat = cases.lattice_case(device=device)
+    prec = args.precision or "both"
+    paths = ["fp64", "mixed"] if prec == "both" else [prec]
     peak, peak_kind = hbm_peak()
     clocks = ClockSampler(local)
     clocks.start()
     results = {p: time_group_path(gbcfd, torch, lat, p, args.steps, args.warmup, world, device) for p in paths}
     clk = clocks.stop()
     head = paths[0]
-    e2e = e2e_group_path(gbcfd, torch, lat, head, args.e2e_steps, world, device)
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else (3 if head == "fp64" else 20)
+    e2e = e2e_group_path(gbcfd, torch, lat, head, e2e_steps, world, device, pipelined=head == "mixed")
     cpu = cpu_baseline_lattice() if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    cells = lat.cells
+    del lat
+    torch.cuda.empty_cache()
+    vortex = None if args.no_vortex else vortex_key(args, world, device, torch, cases, gbcfd)
+    channel = None if args.no_channel else channel_key(args, device, cases)
     if rank != 0:
         return
     r = results[head]
+    hbm = roofline(head, r, cells, args.steps, peak, peak_kind, "lattice96")
     out = {
         "metric": "cell-updates/s",
-        "value": world * lat.cells * args.steps / (r["ms"] / 1e3),
+        "value": world * cells * args.steps / (r["ms"] / 1e3),
         "unit": "cell-updates/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -645,12 +714,12 @@ def run_lattice(args, world, rank, local, device, torch, cases, gbcfd):
         "vs_baseline": None,
         "dtype": "f32+f64" if head == "mixed" else "f64",
         "data": "synthetic (seeded lattice sizes and Fourier-mode phases; the paper's meshes are not available)",
-        "config": {"workload": WORKLOADS["lattice96"], "cells": lat.cells, "blocks": r["blocks"], "precision": head,
-                   "ctas_per_sm": r["ctas_per_sm"],
+        "config": {"workload": WORKLOADS["lattice96"], "cells": cells, "blocks": r["blocks"], "precision": head,
+                   "ctas_per_sm": r["ctas_per_sm"], "tile": r.get("tile"),
                    "l2": "working set > 20 GB >> 129 MB L2, no flush needed",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roofline(head, r, lat.cells, args.steps, peak, peak_kind, "lattice96"),
-        "issue": issue_estimate(head, r, lat.cells, args.steps, clk.get("sm_mhz"), "lattice96"),
+        "roofline": fp64_alu_roofline(r, cells, args.steps, hbm, "lattice96") if head == "fp64" else hbm,
+        "issue": issue_estimate(head, r, cells, args.steps, clk.get("sm_mhz"), "lattice96"),
         "e2e": e2e,
         "gpu_launches": r["launches"],
         "clocks": clk,
@@ -660,11 +729,17 @@ def run_lattice(args, world, rank, local, device, torch, cases, gbcfd):
     }
     for p in paths[1:]:
         rp = results[p]
-        hbm = roofline(p, rp, lat.cells, args.steps, peak, peak_kind, "lattice96")
-        out[p] = {"value": world * lat.cells * args.steps / (rp["ms"] / 1e3), "unit": "cell-updates/s",
+        hp = roofline(p, rp, cells, args.steps, peak, peak_kind, "lattice96")
+        out[p] = {"value": world * cells * args.steps / (rp["ms"] / 1e3), "unit": "cell-updates/s",
                   "ms_per_step": rp["ms"] / args.steps, "dtype": "f64" if p == "fp64" else "f32+f64",
-                  "roofline": fp64_alu_roofline(rp, lat.cells, args.steps, hbm, "lattice96") if p == "fp64" else hbm,
-                  "gpu_launches": rp["launches"]}
+                  "ctas_per_sm": rp["ctas_per_sm"], "tile": rp.get("tile"),
+                  "roofline": fp64_alu_roofline(rp, cells, args.steps, hp, "lattice96") if p == "fp64" else hp,
+                  "issue": issue_estimate(p, rp, cells, args.steps, clk.get("sm_mhz"), "lattice96"),
+                  "halo_ms_per_step": rp["halo_ms"] / args.steps, "gpu_launches": rp["launches"]}
+    if vortex is not None:
+        out["vortex256"] = vortex
+    if channel is not None:
+        out["channel"] = channel
     print(json.dumps(out))
 
 
@@ -712,7 +787,7 @@ def run_accel(args, world, rank, local, device, torch, gbcfd):
     host_y = torch.empty((cells, 8), dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(min(args.e2e_steps, args.steps)):
+    for _ in range(min(args.e2e_steps or 20, args.steps)):
         x.copy_(host_x, non_blocking=True)
         acc.forward(x, y, stream)
         host_y.copy_(y, non_blocking=True)
@@ -732,7 +807,7 @@ def run_accel(args, world, rank, local, device, torch, gbcfd):
         "roofline": {"bound": "tensor", "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": None,
                      "kernel": "conv_tc_kernel (3 launches)", "flops_per_cell": ACCEL_FLOPS_PER_CELL},
-        "e2e": {"value": world * cells * min(args.e2e_steps, args.steps) / e2e_s, "unit": "cells/s",
+        "e2e": {"value": world * cells * min(args.e2e_steps or 20, args.steps) / e2e_s, "unit": "cells/s",
                 "h2d_bytes_per_step": cells * 16 * 2, "d2h_bytes_per_step": cells * 8 * 4},
         "gpu_launches": 3 * args.steps, "clocks": clk,
         "cpu_baseline": None if (world > 1 or args.no_cpu_baseline) else cpu_baseline_accel(params),
@@ -878,8 +953,8 @@ def wcns_roofline(precision, res, cells, steps, peak, peak_kind):
 
 
 def e2e_wcns(gbcfd, torch, case, precision, steps, world, device):
-    """As e2e_path, on WCNS-E-5 blocks: the headline through a 3-block pipeline
-    (gbcfd_wcns_pipe_create + gbcfd_pipe_submit / _sync), `serial_value` through the block calls."""
+    """As e2e_path, on WCNS-E-5 blocks: the value through the block calls one after the other,
+    `pipelined_value` through a 3-block pipeline (gbcfd_wcns_pipe_create + gbcfd_pipe_submit / _sync)."""
     prec = gbcfd.MIXED if precision == "mixed" else gbcfd.FP64
     host_in = torch.from_numpy(case.state).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
@@ -918,12 +993,13 @@ def e2e_wcns(gbcfd, torch, case, precision, steps, world, device):
     for b in members:
         b.close()
     nbytes = case.state.nbytes
-    return {"value": world * case.cells * steps / dt, "unit": "cell-updates/s",
-            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 40,
-            "api": "gbcfd_pipe_submit x steps + gbcfd_pipe_sync (3 WCNS member blocks)",
-            "serial_value": world * case.cells * steps / serial,
-            "serial_api": "gbcfd_wcns_set_state + _step + _get_state + _residual_norm per step",
-            "serial_d2h_bytes_per_step": nbytes + 112, "steps": steps}
+    return {"value": world * case.cells * steps / serial, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 112,
+            "api": "gbcfd_wcns_set_state + _step + _get_state + _residual_norm per step "
+                   "(time marching: each step's state uploaded and read back)",
+            "pipelined_value": world * case.cells * steps / dt,
+            "pipelined_api": "gbcfd_pipe_submit x steps + gbcfd_pipe_sync (3 WCNS member blocks; steps as independent items)",
+            "steps": steps}
 
 
 def cpu_baseline_wcns(n):
@@ -955,7 +1031,7 @@ def run_wcns(args, world, rank, local, device, torch, cases, gbcfd):
                for p in paths}
     clk = clocks.stop()
     head = paths[0]
-    e2e = e2e_wcns(gbcfd, torch, case, head, args.e2e_steps, world, device)
+    e2e = e2e_wcns(gbcfd, torch, case, head, args.e2e_steps or 20, world, device)
     cpu = cpu_baseline_wcns(args.side) if rank == 0 and world == 1 and not args.no_cpu_baseline else None
     if rank != 0:
         return

@@ -239,10 +239,25 @@ int gbcfd_group_destroy(gbcfd_group group);
  * reported per block by gbcfd_residual_norm. */
 int gbcfd_group_step(gbcfd_group group, int nsteps, void* stream);
 
-/* Autotuner: times stage-1 launches (which write only scratch and norms) for several grid
- * splits (CTAs per SM) and keeps the fastest for this group.  Synchronises the stream; drops
- * the captured graphs.  The chosen CTAs per SM are returned in *ctas_per_sm when not NULL. */
+/* Autotuner (Sec. 3.1.1 distributes uneven zones over the hardware; here the schedule of one
+ * GPU): times pairs of stage-1 and stage-2 launches (which write only the stage scratch and the
+ * norms; stage 1's output gets its halos between them) for every tile shape the
+ * stage kernel is compiled for on this path -- 32 x 8 cells, and on Cartesian Euler blocks a
+ * second height (32 x 11 on the FP64 path, 32 x 4 on the mixed path) -- and for each of them
+ * several grid splits (1x .. 16x the resident CTAs per SM, at most 16 per SM, shared between
+ * the blocks in proportion to their tile-planes), and keeps the fastest for this group.  Synchronises the
+ * stream; drops the captured graphs.  The chosen CTAs per SM and tile height (cells along y)
+ * are returned in *ctas_per_sm and *tile_rows when not NULL; gbcfd_group_tune is the same
+ * without the tile height. */
 int gbcfd_group_tune(gbcfd_group group, void* stream, int* ctas_per_sm);
+int gbcfd_group_tune_tile(gbcfd_group group, void* stream, int* ctas_per_sm, int* tile_rows);
+
+/* Set the schedule the tuner would choose: tile height tile_rows (8, or the path's second height
+ * on Cartesian Euler blocks: 11 FP64, 4 mixed; GBCFD_ERR_ARG otherwise) and ctas_per_sm CTAs per
+ * SM (1..16, split between the blocks as by the tuner).  Results do not depend on the schedule
+ * (every face flux and every cell's update is the same arithmetic); the residual norms' rounding
+ * does (their partial sums follow the grid).  Synchronises the stream; drops the captured graphs. */
+int gbcfd_group_set_schedule(gbcfd_group group, int ctas_per_sm, int tile_rows, void* stream);
 
 /* Timing marks inside each step of the group: events[0..6] are CUDA events (cudaEvent_t) the
  * caller created with timing enabled and owns.  Each step records events[0] before the time-step

@@ -110,7 +110,7 @@ static bool valid_params(const gbcfd_params* p, std::string& why) {
 static int stage_grid(const Geometry& g, int precision, int viscous, int curvi, int nsm) {
   const int occ = precision == GBCFD_MIXED ? (curvi ? stage_occupancy_f32c(viscous) : stage_occupancy_f32(viscous))
                                            : (curvi ? stage_occupancy_f64c(viscous) : stage_occupancy_f64(viscous));
-  const long long units = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY) * g.nz;
+  const long long units = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY_DEFAULT - 1) / TY_DEFAULT) * g.nz;
   long long grid = (long long)nsm * occ;
   if (grid > units) grid = units;
   return (int)std::max(1LL, grid);
@@ -175,9 +175,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// 4D map (x, y, z, variable) over a padded field; box = one tile plane with its halo, all nvar
-// variables.  x extent is the padded width nx + 4, so a box past it is zero-filled.
-static int make_map(CUtensorMap* m, void* base, const Geometry& g, int elem, int nvar = 5) {
+// 4D map (x, y, z, variable) over a padded field; box = one tile plane with its halo (rows: the
+// tile height + 4), all nvar variables.  x extent is the padded width nx + 4, so a box past it is
+// zero-filled.
+static int make_map(CUtensorMap* m, void* base, const Geometry& g, int elem, int nvar = 5,
+                    int rows = box_rows(TY_DEFAULT)) {
   auto enc = get_encode();
   if (!enc) return fail(GBCFD_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const int pitch = elem == 8 ? g.px : g.pxf;
@@ -185,7 +187,7 @@ static int make_map(CUtensorMap* m, void* base, const Geometry& g, int elem, int
                         (cuuint64_t)(g.nz + 2 * HALO), (cuuint64_t)nvar};
   cuuint64_t strides[3] = {(cuuint64_t)pitch * elem, (cuuint64_t)pitch * elem * (g.ny + 2 * HALO),
                            (cuuint64_t)pitch * elem * (g.ny + 2 * HALO) * (g.nz + 2 * HALO)};
-  cuuint32_t box[4] = {(cuuint32_t)BX, (cuuint32_t)BY, 1, (cuuint32_t)nvar};
+  cuuint32_t box[4] = {(cuuint32_t)BX, (cuuint32_t)rows, 1, (cuuint32_t)nvar};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = enc(m, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base,
                    dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -265,10 +267,32 @@ static void fill_desc(gbcfd_block_s* b) {
   D.dtl = b->dtl;
   b->desc_version++;
   D.ntx = (b->nx + TX - 1) / TX;
-  D.nty = (b->ny + TY - 1) / TY;
+  D.nty = (b->ny + TY_DEFAULT - 1) / TY_DEFAULT;
   D.units = (long long)D.ntx * D.nty * b->nz;
   D.cta0 = 0;
   D.ctas = b->grid;
+}
+
+// the block's descriptor for a stage kernel compiled with tile height ty: the default one, or a
+// copy whose tensor maps move (ty + 4)-row boxes and whose tile counts use ty
+static int write_desc(const gbcfd_block_s* b, int ty, BlockDesc* D) {
+  *D = b->desc_host;
+  if (ty == TY_DEFAULT) return GBCFD_OK;
+  const int rows = box_rows(ty);
+  int r = GBCFD_OK;
+  if (b->p.precision == GBCFD_FP64) {
+    for (int i = 0; i < 3 && !r; ++i) r = make_map(&D->tq[i], b->q[i], b->g, 8, 5, rows);
+    if (!r) D->td[0] = D->td[1] = D->tq[0];
+  } else {
+    for (int i = 0; i < 2 && !r; ++i) r = make_map(&D->tq[i], b->sh[i], b->g, 4, 5, rows);
+    for (int i = 0; i < 2 && !r; ++i) r = make_map(&D->td[i], b->d[i], b->g, 4, 5, rows);
+    if (!r) D->tq[2] = D->tq[0];
+  }
+  if (!r && b->curvi) r = make_map(&D->tm, b->metrics, b->g, b->p.precision == GBCFD_MIXED ? 4 : 8, 10, rows);
+  if (r) return r;
+  D->nty = (b->ny + ty - 1) / ty;
+  D->units = (long long)D->ntx * D->nty * b->nz;
+  return GBCFD_OK;
 }
 
 extern "C" int gbcfd_create_block(int nx, int ny, int nz, const gbcfd_params* params, void* dev_mem,
@@ -737,6 +761,7 @@ struct gbcfd_group_s {
   double* partial;
   size_t partial_n;
   int ctas_per_sm;        // grid = SMs x this (split between the blocks)
+  int ty;                 // tile height of the stage kernel the table is written for
   int grid;
   cudaStream_t cap;       // private stream the step graphs are captured on
   cudaGraphExec_t exec[2];  // one step, for each parity of the mixed path's ping-pong
@@ -745,7 +770,7 @@ struct gbcfd_group_s {
   std::vector<unsigned> versions;  // members' descriptor versions the table was written with
 };
 
-static int max_group_ctas(int nsm) { return 8 * nsm; }
+static int max_group_ctas(int nsm) { return 16 * nsm; }
 
 extern "C" int gbcfd_group_required_bytes(int n, size_t* bytes) {
   if (n < 1 || n > MAX_GROUP) return fail(GBCFD_ERR_ARG, "a group holds 1.." + std::to_string(MAX_GROUP) + " blocks");
@@ -759,15 +784,14 @@ extern "C" int gbcfd_group_required_bytes(int n, size_t* bytes) {
 }
 
 // split SMs x ctas_per_sm CTAs between the blocks in proportion to their tile-planes (each gets
-// at least one) and write the descriptor table
-static int group_split(gbcfd_group g, int ctas_per_sm, cudaStream_t s) {
+// at least one) and write the descriptor table for the stage kernel of tile height ty
+static int group_split(gbcfd_group g, int ctas_per_sm, cudaStream_t s, int ty = -1) {
   const int nsm = g->blocks[0]->nsm;
+  if (ty < 0) ty = g->ty;
   g->versions.resize(g->blocks.size());
   for (size_t i = 0; i < g->blocks.size(); ++i) {  // the members' current descriptors
-    const int cta0 = g->table_host[i].cta0, ctas = g->table_host[i].ctas;
-    g->table_host[i] = g->blocks[i]->desc_host;
-    g->table_host[i].cta0 = cta0;
-    g->table_host[i].ctas = ctas;
+    int rc = write_desc(g->blocks[i], ty, &g->table_host[i]);
+    if (rc) return rc;
     g->versions[i] = g->blocks[i]->desc_version;
   }
   const long long target = (long long)nsm * ctas_per_sm;
@@ -785,6 +809,7 @@ static int group_split(gbcfd_group g, int ctas_per_sm, cudaStream_t s) {
   if ((size_t)c0 > g->partial_n) return fail(GBCFD_ERR_ARG, "too many CTAs for the group's partial sums");
   g->grid = c0;
   g->ctas_per_sm = ctas_per_sm;
+  g->ty = ty;
   CK(cudaMemcpyAsync(g->table, g->table_host.data(), sizeof(BlockDesc) * g->table_host.size(),
                      cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));  // the host table is reused
@@ -827,6 +852,7 @@ extern "C" int gbcfd_group_create(const gbcfd_block* blocks, int n, void* dev_me
   g->exec[0] = g->exec[1] = nullptr;
   g->cap = nullptr;
   g->timed = false;
+  g->ty = TY_DEFAULT;
   for (int i = 0; i < n; ++i) g->table_host.push_back(blocks[i]->desc_host);
   const int mixed = blocks[0]->p.precision == GBCFD_MIXED, vis = blocks[0]->p.viscous, cv = blocks[0]->curvi;
   cudaError_t e = mixed ? (cv ? stage_prepare_f32c(vis) : stage_prepare_f32(vis))
@@ -837,7 +863,7 @@ extern "C" int gbcfd_group_create(const gbcfd_block* blocks, int n, void* dev_me
   const int occ = blocks[0]->p.precision == GBCFD_MIXED
                       ? (blocks[0]->curvi ? stage_occupancy_f32c(blocks[0]->p.viscous) : stage_occupancy_f32(blocks[0]->p.viscous))
                       : (blocks[0]->curvi ? stage_occupancy_f64c(blocks[0]->p.viscous) : stage_occupancy_f64(blocks[0]->p.viscous));
-  rc = group_split(g, occ, g->cap);
+  rc = group_split(g, occ, g->cap, TY_DEFAULT);
   if (rc) { cudaStreamDestroy(g->cap); delete g; return rc; }
   *out = g;
   return GBCFD_OK;
@@ -884,7 +910,7 @@ static int group_step_launches(gbcfd_group g, cudaStream_t s) {
     int rc = exchange(g->blocks.data(), n, fields[st - 1], false, s);
     if (rc) return rc;
     CK(mark(2 * st - 1));
-    CK(launch_stage(b0->p.precision, b0->p.viscous, b0->curvi, st, P, g->grid, s));
+    CK(launch_stage(b0->p.precision, b0->p.viscous, b0->curvi, st, P, g->grid, s, g->ty));
     CK(mark(2 * st));
   }
   return GBCFD_OK;
@@ -907,7 +933,8 @@ static int group_refresh(gbcfd_group g, cudaStream_t s) {
   if (!changed) return GBCFD_OK;
   for (size_t i = 0; i < g->blocks.size(); ++i) {
     const int cta0 = g->table_host[i].cta0, ctas = g->table_host[i].ctas;
-    g->table_host[i] = g->blocks[i]->desc_host;
+    int rc = write_desc(g->blocks[i], g->ty, &g->table_host[i]);
+    if (rc) return rc;
     g->table_host[i].cta0 = cta0;
     g->table_host[i].ctas = ctas;
     g->versions[i] = g->blocks[i]->desc_version;
@@ -963,7 +990,25 @@ extern "C" int gbcfd_group_set_timing(gbcfd_group g, void* const* events, int n)
   return GBCFD_OK;
 }
 
+extern "C" int gbcfd_group_set_schedule(gbcfd_group g, int ctas_per_sm, int tile_rows, void* stream) {
+  if (!g) return fail(GBCFD_ERR_ARG, "group is NULL");
+  gbcfd_block b0 = g->blocks[0];
+  int tys[4];
+  const int ntile = stage_tiles(b0->p.precision, b0->p.viscous, b0->curvi, tys);
+  if (std::find(tys, tys + ntile, tile_rows) == tys + ntile)
+    return fail(GBCFD_ERR_ARG, "tile height " + std::to_string(tile_rows) + " is not compiled for this path");
+  if (ctas_per_sm < 1 || (long long)b0->nsm * ctas_per_sm > max_group_ctas(b0->nsm))
+    return fail(GBCFD_ERR_ARG, "ctas_per_sm must be 1..16");
+  if (stage_prepare_tile(b0->p.precision, b0->p.viscous, b0->curvi, tile_rows) != cudaSuccess)
+    return fail(GBCFD_ERR_CUDA, "stage kernel set-up failed");
+  return group_split(g, ctas_per_sm, static_cast<cudaStream_t>(stream), tile_rows);
+}
+
 extern "C" int gbcfd_group_tune(gbcfd_group g, void* stream, int* ctas_per_sm) {
+  return gbcfd_group_tune_tile(g, stream, ctas_per_sm, nullptr);
+}
+
+extern "C" int gbcfd_group_tune_tile(gbcfd_group g, void* stream, int* ctas_per_sm, int* tile_rows) {
   if (!g) return fail(GBCFD_ERR_ARG, "group is NULL");
   int rc = group_check(g);
   if (rc) return rc;
@@ -971,41 +1016,62 @@ extern "C" int gbcfd_group_tune(gbcfd_group g, void* stream, int* ctas_per_sm) {
   rc = prepare_metrics(g->blocks.data(), (int)g->blocks.size(), s);
   if (rc) return rc;
   gbcfd_block b0 = g->blocks[0];
-  const int occ = b0->p.precision == GBCFD_MIXED
-                      ? (b0->curvi ? stage_occupancy_f32c(b0->p.viscous) : stage_occupancy_f32(b0->p.viscous))
-                      : (b0->curvi ? stage_occupancy_f64c(b0->p.viscous) : stage_occupancy_f64(b0->p.viscous));
-  // candidates: one resident wave (occ per SM) and finer splits of 2x and 4x that
-  const int cand[3] = {occ, 2 * occ, 4 * occ};
+  // candidates: every tile height compiled for the path, each with one resident wave (occ CTAs
+  // per SM) and finer splits of 2x .. 16x that, up to 16 CTAs per SM: uneven blocks share the
+  // grid in proportion to their tile-planes with rounding, and several waves of smaller CTAs
+  // even that out (on the 96-block lattice 8 per SM beat 1 by 30% on the FP64 path)
+  int tys[4];
+  const int ntile = stage_tiles(b0->p.precision, b0->p.viscous, b0->curvi, tys);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_c = occ;
+  int best_c = 0, best_ty = TY_DEFAULT;
   rc = exchange(g->blocks.data(), (int)g->blocks.size(), F_STATE, false, s);
-  for (int ci = 0; ci < 3 && !rc; ++ci) {
-    if ((long long)b0->nsm * cand[ci] > max_group_ctas(b0->nsm)) continue;
-    rc = group_split(g, cand[ci], s);
-    if (rc) break;
-    GroupParams P = group_params(g);
-    float t = 0.f;
-    for (int rep = 0; rep < 4 && !rc; ++rep) {  // the first launch warms up, three are timed
-      cudaEventRecord(e0, s);
-      if (launch_stage(b0->p.precision, b0->p.viscous, b0->curvi, 1, P, g->grid, s) != cudaSuccess)
-        rc = fail(GBCFD_ERR_CUDA, "tuning launch failed");
-      cudaEventRecord(e1, s);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) t += ms;
+  for (int ti = 0; ti < ntile && !rc; ++ti) {
+    const int ty = tys[ti];
+    if (stage_prepare_tile(b0->p.precision, b0->p.viscous, b0->curvi, ty) != cudaSuccess) {
+      rc = fail(GBCFD_ERR_CUDA, "stage kernel set-up failed");
+      break;
     }
-    if (!rc && t < best) { best = t; best_c = cand[ci]; }
+    const int occ = stage_occupancy_tile(b0->p.precision, b0->p.viscous, b0->curvi, ty);
+    const int cand[5] = {occ, 2 * occ, 4 * occ, 8 * occ, 16 * occ};
+    for (int ci = 0; ci < 5 && !rc; ++ci) {
+      if ((long long)b0->nsm * cand[ci] > max_group_ctas(b0->nsm)) continue;
+      rc = group_split(g, cand[ci], s, ty);
+      if (rc) break;
+      GroupParams P = group_params(g);
+      float t = 0.f;
+      // stages 1 and 2 write only the stage scratch (Q1 / Q2, or D1 / D2) and the norms, so they
+      // can run without touching the state; stage 2 reads stage 1's output with its halos
+      for (int rep = 0; rep < 3 && !rc; ++rep) {  // the first pair warms up, two are timed
+        float ms1 = 0.f, ms2 = 0.f;
+        cudaEventRecord(e0, s);
+        if (launch_stage(b0->p.precision, b0->p.viscous, b0->curvi, 1, P, g->grid, s, ty) != cudaSuccess)
+          rc = fail(GBCFD_ERR_CUDA, "tuning launch failed");
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms1, e0, e1);
+        if (!rc) rc = exchange(g->blocks.data(), (int)g->blocks.size(), F_STAGE1, false, s);
+        if (rc) break;
+        cudaEventRecord(e0, s);
+        if (launch_stage(b0->p.precision, b0->p.viscous, b0->curvi, 2, P, g->grid, s, ty) != cudaSuccess)
+          rc = fail(GBCFD_ERR_CUDA, "tuning launch failed");
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms2, e0, e1);
+        if (rep > 0) t += ms1 + ms2;
+      }
+      if (!rc && t < best) { best = t; best_c = cand[ci]; best_ty = ty; }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  rc = group_split(g, best_c, s);
+  rc = group_split(g, best_c, s, best_ty);
   if (rc) return rc;
   if (ctas_per_sm) *ctas_per_sm = best_c;
+  if (tile_rows) *tile_rows = best_ty;
   return GBCFD_OK;
 }
 
@@ -1680,9 +1746,34 @@ extern "C" int gbcfd_accel_try(gbcfd_accel a, gbcfd_block b, void* stream, int* 
 // ---- dispatch ----------------------------------------------------------------------------
 namespace gbcfd {
 cudaError_t launch_stage(int precision, int viscous, int curvi, int stage, const GroupParams& P, int grid,
-                         cudaStream_t s) {
+                         cudaStream_t s, int ty) {
+  if (ty != TY_DEFAULT) {  // the second height: Cartesian Euler blocks only
+    if (viscous || curvi) return cudaErrorInvalidValue;
+    if (precision == GBCFD_MIXED && ty == TY_ALT_F32) return launch_stage_f32_alt(stage, P, grid, s);
+    if (precision == GBCFD_FP64 && ty == TY_ALT_F64) return launch_stage_f64_alt(stage, P, grid, s);
+    return cudaErrorInvalidValue;
+  }
   if (precision == GBCFD_MIXED)
     return curvi ? launch_stage_f32c(viscous, stage, P, grid, s) : launch_stage_f32(viscous, stage, P, grid, s);
   return curvi ? launch_stage_f64c(viscous, stage, P, grid, s) : launch_stage_f64(viscous, stage, P, grid, s);
+}
+
+int stage_tiles(int precision, int viscous, int curvi, int* ty) {
+  ty[0] = TY_DEFAULT;
+  if (viscous || curvi) return 1;
+  ty[1] = precision == GBCFD_MIXED ? TY_ALT_F32 : TY_ALT_F64;
+  return 2;
+}
+
+int stage_occupancy_tile(int precision, int viscous, int curvi, int ty) {
+  if (ty != TY_DEFAULT) return precision == GBCFD_MIXED ? stage_occupancy_f32_alt() : stage_occupancy_f64_alt();
+  return precision == GBCFD_MIXED ? (curvi ? stage_occupancy_f32c(viscous) : stage_occupancy_f32(viscous))
+                                  : (curvi ? stage_occupancy_f64c(viscous) : stage_occupancy_f64(viscous));
+}
+
+cudaError_t stage_prepare_tile(int precision, int viscous, int curvi, int ty) {
+  if (ty != TY_DEFAULT) return precision == GBCFD_MIXED ? stage_prepare_f32_alt() : stage_prepare_f64_alt();
+  return precision == GBCFD_MIXED ? (curvi ? stage_prepare_f32c(viscous) : stage_prepare_f32(viscous))
+                                  : (curvi ? stage_prepare_f64c(viscous) : stage_prepare_f64(viscous));
 }
 }  // namespace gbcfd

@@ -22,7 +22,7 @@ struct MetIdx {
   int vl, vr;
 };
 
-template <typename T, bool VISC>
+template <typename T, bool VISC, int BY>
 __device__ __forceinline__ void face_flux_curvi(const T* __restrict__ ring, const T* __restrict__ mring,
                                                 int nv_ms, const int (&b)[4], const int (&tg)[8],
                                                 const MetIdx& mi, const Consts<T>& K, T* F) {
@@ -119,48 +119,52 @@ __device__ __forceinline__ void face_flux_curvi(const T* __restrict__ ring, cons
 }
 
 // metric-ring base of slot s, box row cy, column cx (field 0)
+template <int BY>
 __device__ __forceinline__ int mb(int s, int cy, int cx) { return (s * 10 * BY + cy) * BX + cx; }
 
 // faces below box cell (cy, cx) of plane k (metric slots mk = k, mk1 = k+1); fields 0-2 S_xi,
 // 3-5 S_eta, 6-8 S_zeta, 9 V
+template <int BY>
 __device__ __forceinline__ MetIdx xface_met(int mk, int mk1, int cy, int cx) {
   constexpr int MS = BY * BX;
   MetIdx m;
-  m.sf = mb(mk, cy, cx) + 0 * MS;
+  m.sf = mb<BY>(mk, cy, cx) + 0 * MS;
   // tangent 1 = y: S_eta of L=(cy,cx-1), L+y, R=(cy,cx), R+y ; tangent 2 = z: S_zeta of L, L+z, R, R+z
-  m.t1[0] = mb(mk, cy, cx - 1) + 3 * MS; m.t1[1] = mb(mk, cy + 1, cx - 1) + 3 * MS;
-  m.t1[2] = mb(mk, cy, cx) + 3 * MS;     m.t1[3] = mb(mk, cy + 1, cx) + 3 * MS;
-  m.t2[0] = mb(mk, cy, cx - 1) + 6 * MS; m.t2[1] = mb(mk1, cy, cx - 1) + 6 * MS;
-  m.t2[2] = mb(mk, cy, cx) + 6 * MS;     m.t2[3] = mb(mk1, cy, cx) + 6 * MS;
-  m.vl = mb(mk, cy, cx - 1) + 9 * MS;
-  m.vr = mb(mk, cy, cx) + 9 * MS;
+  m.t1[0] = mb<BY>(mk, cy, cx - 1) + 3 * MS; m.t1[1] = mb<BY>(mk, cy + 1, cx - 1) + 3 * MS;
+  m.t1[2] = mb<BY>(mk, cy, cx) + 3 * MS;     m.t1[3] = mb<BY>(mk, cy + 1, cx) + 3 * MS;
+  m.t2[0] = mb<BY>(mk, cy, cx - 1) + 6 * MS; m.t2[1] = mb<BY>(mk1, cy, cx - 1) + 6 * MS;
+  m.t2[2] = mb<BY>(mk, cy, cx) + 6 * MS;     m.t2[3] = mb<BY>(mk1, cy, cx) + 6 * MS;
+  m.vl = mb<BY>(mk, cy, cx - 1) + 9 * MS;
+  m.vr = mb<BY>(mk, cy, cx) + 9 * MS;
   return m;
 }
+template <int BY>
 __device__ __forceinline__ MetIdx yface_met(int mk, int mk1, int cy, int cx) {
   constexpr int MS = BY * BX;
   MetIdx m;
-  m.sf = mb(mk, cy, cx) + 3 * MS;
+  m.sf = mb<BY>(mk, cy, cx) + 3 * MS;
   // tangent 1 = z: S_zeta of L=(cy-1,cx), L+z, R, R+z ; tangent 2 = x: S_xi of L, L+x, R, R+x
-  m.t1[0] = mb(mk, cy - 1, cx) + 6 * MS; m.t1[1] = mb(mk1, cy - 1, cx) + 6 * MS;
-  m.t1[2] = mb(mk, cy, cx) + 6 * MS;     m.t1[3] = mb(mk1, cy, cx) + 6 * MS;
-  m.t2[0] = mb(mk, cy - 1, cx) + 0 * MS; m.t2[1] = mb(mk, cy - 1, cx + 1) + 0 * MS;
-  m.t2[2] = mb(mk, cy, cx) + 0 * MS;     m.t2[3] = mb(mk, cy, cx + 1) + 0 * MS;
-  m.vl = mb(mk, cy - 1, cx) + 9 * MS;
-  m.vr = mb(mk, cy, cx) + 9 * MS;
+  m.t1[0] = mb<BY>(mk, cy - 1, cx) + 6 * MS; m.t1[1] = mb<BY>(mk1, cy - 1, cx) + 6 * MS;
+  m.t1[2] = mb<BY>(mk, cy, cx) + 6 * MS;     m.t1[3] = mb<BY>(mk1, cy, cx) + 6 * MS;
+  m.t2[0] = mb<BY>(mk, cy - 1, cx) + 0 * MS; m.t2[1] = mb<BY>(mk, cy - 1, cx + 1) + 0 * MS;
+  m.t2[2] = mb<BY>(mk, cy, cx) + 0 * MS;     m.t2[3] = mb<BY>(mk, cy, cx + 1) + 0 * MS;
+  m.vl = mb<BY>(mk, cy - 1, cx) + 9 * MS;
+  m.vr = mb<BY>(mk, cy, cx) + 9 * MS;
   return m;
 }
 // z-face between plane k (slot mk, cell L) and k+1 (slot mk1, cell R) at column (cy, cx)
+template <int BY>
 __device__ __forceinline__ MetIdx zface_met(int mk, int mk1, int cy, int cx) {
   constexpr int MS = BY * BX;
   MetIdx m;
-  m.sf = mb(mk1, cy, cx) + 6 * MS;
+  m.sf = mb<BY>(mk1, cy, cx) + 6 * MS;
   // tangent 1 = x: S_xi of L, L+x, R, R+x ; tangent 2 = y: S_eta of L, L+y, R, R+y
-  m.t1[0] = mb(mk, cy, cx) + 0 * MS;  m.t1[1] = mb(mk, cy, cx + 1) + 0 * MS;
-  m.t1[2] = mb(mk1, cy, cx) + 0 * MS; m.t1[3] = mb(mk1, cy, cx + 1) + 0 * MS;
-  m.t2[0] = mb(mk, cy, cx) + 3 * MS;  m.t2[1] = mb(mk, cy + 1, cx) + 3 * MS;
-  m.t2[2] = mb(mk1, cy, cx) + 3 * MS; m.t2[3] = mb(mk1, cy + 1, cx) + 3 * MS;
-  m.vl = mb(mk, cy, cx) + 9 * MS;
-  m.vr = mb(mk1, cy, cx) + 9 * MS;
+  m.t1[0] = mb<BY>(mk, cy, cx) + 0 * MS;  m.t1[1] = mb<BY>(mk, cy, cx + 1) + 0 * MS;
+  m.t1[2] = mb<BY>(mk1, cy, cx) + 0 * MS; m.t1[3] = mb<BY>(mk1, cy, cx + 1) + 0 * MS;
+  m.t2[0] = mb<BY>(mk, cy, cx) + 3 * MS;  m.t2[1] = mb<BY>(mk, cy + 1, cx) + 3 * MS;
+  m.t2[2] = mb<BY>(mk1, cy, cx) + 3 * MS; m.t2[3] = mb<BY>(mk1, cy + 1, cx) + 3 * MS;
+  m.vl = mb<BY>(mk, cy, cx) + 9 * MS;
+  m.vr = mb<BY>(mk1, cy, cx) + 9 * MS;
   return m;
 }
 

@@ -24,11 +24,16 @@ namespace gbcfd {
 
 constexpr int HALO = 2;
 constexpr int TX = 32;        // tile width (cells, x) = one warp
-constexpr int TY = 8;         // tile height (cells, y) = number of cell-owning warps
-constexpr int NWARP = TY + 1; // + one helper warp for the tile's upper x and y faces
-constexpr int NT = 32 * NWARP;
 constexpr int BX = TX + 2 * HALO; // staged box width
-constexpr int BY = TY + 2 * HALO; // staged box height
+// Tile height (cells, y) = the number of cell-owning warps; one more helper warp computes the
+// tile's upper x and y faces.  The stage kernel is compiled for a few heights (the group tuner
+// chooses among them); single blocks use TY_DEFAULT.
+constexpr int TY_DEFAULT = 8;
+constexpr int TY_ALT_F64 = 11;  // FP64 Euler: 12 warps = 3 per sub-partition, as many as 168 registers allow
+constexpr int TY_ALT_F32 = 4;   // mixed Euler: 5 warps, four CTAs per SM
+__host__ __device__ constexpr int tile_warps(int ty) { return ty + 1; }
+__host__ __device__ constexpr int tile_threads(int ty) { return 32 * (ty + 1); }
+__host__ __device__ constexpr int box_rows(int ty) { return ty + 2 * HALO; }  // staged box height
 constexpr int NSTAGE = 2;     // TMA staging slots (prefetch distance 2 planes)
 constexpr int NRING = 4;      // primitive planes kept: k-1, k, k+1, k+2
 constexpr int MAX_GROUP = 128; // blocks per grouped launch (halo exchange, time-step minimum)
@@ -96,7 +101,7 @@ struct BlockDesc {
   float* sh[2];              // mixed: shadows
   float* d[2];               // mixed: increments
   DevCtrl* ctrl;
-  int ntx, nty;              // tiles along x and y
+  int ntx, nty;              // tiles along x and y (tile height: the launch's kernel)
   long long units;           // work units (tile-planes) = ntx * nty * nz
   int cta0, ctas;            // the CTAs of a group launch that work on this block
   void* dtl;                 // local time steps, one padded field (f64 FP64 path, f32 mixed)

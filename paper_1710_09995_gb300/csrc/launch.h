@@ -10,9 +10,22 @@ namespace gbcfd {
 // record an error for gbcfd_last_error() on this host thread and return `code`
 int set_error(int code, const std::string& msg);
 
-// fused stage kernel over a group of blocks; precision GBCFD_FP64 / GBCFD_MIXED, stage 0 = residual
+// fused stage kernel over a group of blocks; precision GBCFD_FP64 / GBCFD_MIXED, stage 0 = residual;
+// ty = the tile height the launch's descriptors were written for (TY_DEFAULT, or the path's
+// second height on Cartesian Euler blocks)
 cudaError_t launch_stage(int precision, int viscous, int curvi, int stage, const GroupParams& P, int grid,
-                         cudaStream_t s);
+                         cudaStream_t s, int ty = TY_DEFAULT);
+// the tile heights the stage kernel is compiled for on a path (TY_DEFAULT first); returns the count
+int stage_tiles(int precision, int viscous, int curvi, int* ty);
+// CTAs per SM of the stage kernel for a tile height
+int stage_occupancy_tile(int precision, int viscous, int curvi, int ty);
+cudaError_t stage_prepare_tile(int precision, int viscous, int curvi, int ty);
+cudaError_t launch_stage_f64_alt(int stage, const GroupParams& P, int grid, cudaStream_t s);
+cudaError_t launch_stage_f32_alt(int stage, const GroupParams& P, int grid, cudaStream_t s);
+cudaError_t stage_prepare_f64_alt();
+cudaError_t stage_prepare_f32_alt();
+int stage_occupancy_f64_alt();
+int stage_occupancy_f32_alt();
 cudaError_t launch_stage_f64(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s);
 cudaError_t launch_stage_f64c(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s);
 cudaError_t launch_stage_f32(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s);

@@ -70,8 +70,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 }
 
 // ---- shared-memory plan ----------------------------------------------------------------------
-template <typename T, bool VISC, bool CURVI = false>
+template <typename T, bool VISC, bool CURVI, int TYV>
 struct Plan {
+  static constexpr int TY = TYV, BY = box_rows(TYV), NWARP = tile_warps(TYV);
   static constexpr int NV = VISC ? 6 : 5;           // rho u v w p [theta]
   static constexpr int BOX = BY * BX;               // cells per staged plane
   static constexpr int RSLOT = NV * BOX;            // T per ring slot
@@ -95,7 +96,7 @@ struct Plan {
 };
 
 // stencil cell base index inside the ring: slot s, row cy, column cx (variable 0)
-template <int NV>
+template <int NV, int BY>
 __device__ __forceinline__ int rb(int s, int cy, int cx) {
   return (s * NV * BY + cy) * BX + cx;
 }
@@ -114,26 +115,26 @@ template <> struct Frame<1> { static constexpr int N = 2, T1 = 3, T2 = 1; };  //
 template <> struct Frame<2> { static constexpr int N = 3, T1 = 1, T2 = 2; };  // z: (w | u, v)
 
 // x-face below box cell (cy, cx) in ring slot s; sm / sp = slots of planes k-1 / k+1
-template <int NV>
+template <int NV, int BY>
 __device__ __forceinline__ FaceIdx xface_idx(int s, int sm, int sp, int cy, int cx) {
-  const int b = rb<NV>(s, cy, cx);
+  const int b = rb<NV, BY>(s, cy, cx);
   // tangent 1 = y (rows), tangent 2 = z (planes)
   return {{b - 2, b - 1, b, b + 1}, b - 1 + BX, b - 1 - BX, b + BX, b - BX,
-          rb<NV>(sp, cy, cx - 1), rb<NV>(sm, cy, cx - 1), rb<NV>(sp, cy, cx), rb<NV>(sm, cy, cx)};
+          rb<NV, BY>(sp, cy, cx - 1), rb<NV, BY>(sm, cy, cx - 1), rb<NV, BY>(sp, cy, cx), rb<NV, BY>(sm, cy, cx)};
 }
-template <int NV>
+template <int NV, int BY>
 __device__ __forceinline__ FaceIdx yface_idx(int s, int sm, int sp, int cy, int cx) {
-  const int b = rb<NV>(s, cy, cx);
+  const int b = rb<NV, BY>(s, cy, cx);
   // tangent 1 = z (planes), tangent 2 = x (columns)
-  return {{b - 2 * BX, b - BX, b, b + BX}, rb<NV>(sp, cy - 1, cx), rb<NV>(sm, cy - 1, cx),
-          rb<NV>(sp, cy, cx), rb<NV>(sm, cy, cx), b - BX + 1, b - BX - 1, b + 1, b - 1};
+  return {{b - 2 * BX, b - BX, b, b + BX}, rb<NV, BY>(sp, cy - 1, cx), rb<NV, BY>(sm, cy - 1, cx),
+          rb<NV, BY>(sp, cy, cx), rb<NV, BY>(sm, cy, cx), b - BX + 1, b - BX - 1, b + 1, b - 1};
 }
 // z-face between planes k (slot s1) and k+1 (slot s2); s0 = k-1, s3 = k+2
-template <int NV>
+template <int NV, int BY>
 __device__ __forceinline__ FaceIdx zface_idx(int s0, int s1, int s2, int s3, int cy, int cx) {
-  const int b1 = rb<NV>(s1, cy, cx), b2 = rb<NV>(s2, cy, cx);
+  const int b1 = rb<NV, BY>(s1, cy, cx), b2 = rb<NV, BY>(s2, cy, cx);
   // tangent 1 = x (columns), tangent 2 = y (rows)
-  return {{rb<NV>(s0, cy, cx), b1, b2, rb<NV>(s3, cy, cx)}, b1 + 1, b1 - 1, b2 + 1, b2 - 1,
+  return {{rb<NV, BY>(s0, cy, cx), b1, b2, rb<NV, BY>(s3, cy, cx)}, b1 + 1, b1 - 1, b2 + 1, b2 - 1,
           b1 + BX, b1 - BX, b2 + BX, b2 - BX};
 }
 
@@ -154,7 +155,7 @@ __device__ __forceinline__ void flux_core(const V (&w)[4][5], const V* gn, V dnt
 // stencil gather of one face, then flux_core (twice the flux).  ih = inverse spacings along
 // (normal, tangent 1, tangent 2), qih = a quarter of them (the tangential differences average
 // two central differences of two cells: 1/4 x the sum of four differences).
-template <typename T, bool VISC, int D>
+template <typename T, bool VISC, int D, int BY>
 __device__ __forceinline__ void face_flux(const T* __restrict__ ring, const FaceIdx& f, const T* ih, const T* qih,
                                           const Consts<T>& K, T* F) {
   constexpr int MS = BY * BX;
@@ -195,14 +196,14 @@ __device__ __forceinline__ const int (&tg_of(const FaceIdx& f))[8] {
 }
 
 // a cell's mean face vector per direction (lower and upper face), from the metric ring
-template <typename T>
+template <typename T, int BY>
 __device__ __forceinline__ void cell_face_means(const T* mring, int mk, int mk1, int cy, int cx, T* sb) {
   constexpr int MS = BY * BX;
 #pragma unroll
   for (int x = 0; x < 3; ++x) {
-    sb[x] = T(0.5) * (mring[mb(mk, cy, cx) + x * MS] + mring[mb(mk, cy, cx + 1) + x * MS]);
-    sb[3 + x] = T(0.5) * (mring[mb(mk, cy, cx) + (3 + x) * MS] + mring[mb(mk, cy + 1, cx) + (3 + x) * MS]);
-    sb[6 + x] = T(0.5) * (mring[mb(mk, cy, cx) + (6 + x) * MS] + mring[mb(mk1, cy, cx) + (6 + x) * MS]);
+    sb[x] = T(0.5) * (mring[mb<BY>(mk, cy, cx) + x * MS] + mring[mb<BY>(mk, cy, cx + 1) + x * MS]);
+    sb[3 + x] = T(0.5) * (mring[mb<BY>(mk, cy, cx) + (3 + x) * MS] + mring[mb<BY>(mk, cy + 1, cx) + (3 + x) * MS]);
+    sb[6 + x] = T(0.5) * (mring[mb<BY>(mk, cy, cx) + (6 + x) * MS] + mring[mb<BY>(mk1, cy, cx) + (6 + x) * MS]);
   }
 }
 
@@ -237,13 +238,15 @@ template <> __device__ __forceinline__ const PathK<double>& path_k<double>(const
 // one).  STAGE 0: residual only (one block, R to P.rout); 1..3: the stages of Eqs. 4-6.
 // registers: the register file is split over the SM's four sub-partitions (16K each) and warps
 // are spread round-robin, so two 9-warp CTAs (5 warps on one sub-partition) allow 96 registers
-// per thread on the mixed path, one CTA (3 warps) 168 on the FP64 and curvilinear paths
-template <typename T, bool VISC, int STAGE, bool CURVI>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
+// per thread on the mixed path, four 5-warp CTAs (TYV = 4) 102, one CTA of 9 or 12 warps (3 per
+// sub-partition) 168 on the FP64 and curvilinear paths
+template <typename T, bool VISC, int STAGE, bool CURVI, int TYV>
+__global__ void __launch_bounds__(tile_threads(TYV), (sizeof(T) == 4 && !CURVI) ? (TYV <= 4 ? 4 : 2) : 1)
     stage_kernel(const GroupParams P) {
   constexpr bool MIXED = sizeof(T) == 4;
   constexpr bool LOADD = MIXED && (STAGE == 2 || STAGE == 3);
-  using PL = Plan<T, VISC, CURVI>;
+  using PL = Plan<T, VISC, CURVI, TYV>;
+  constexpr int TY = TYV, BY = PL::BY, NWARP = PL::NWARP, NT = tile_threads(TYV);
   constexpr int NMS = PL::NMS;
   constexpr int NV = PL::NV;
   constexpr int MS = BY * BX;
@@ -289,9 +292,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
   unsigned mpending = 0;     // metric slots with a copy in flight (thread 0)
   bool bad = false;          // non-physical value met by this thread
   // per-thread sums for the current block: R^2 (stage 1), max rate (stage 3)
-  double nacc[5] = {0, 0, 0, 0, 0};
-  float ncomp[5] = {0, 0, 0, 0, 0};  // Kahan compensation (mixed path)
-  float nsum[5] = {0, 0, 0, 0, 0};
+  double nacc[5] = {0, 0, 0, 0, 0};  // FP64 sums of R^2 on both paths
   T rate_max = T(0);
 
   // the block of this CTA and the CTA's contiguous share of its tile-planes
@@ -318,10 +319,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
       double part[6];
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
-        part[m] = MIXED ? double(nsum[m]) - double(ncomp[m]) : nacc[m];
+        part[m] = nacc[m];
         nacc[m] = 0.0;
-        nsum[m] = 0.f;
-        ncomp[m] = 0.f;
       }
       part[5] = double(rate_max);
       rate_max = T(0);
@@ -477,15 +476,21 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
     // owning warps: cell (lane, warp) of the tile
     const int ci = x0 + lane, cj = y0 + warp;  // interior coordinates of the owned cell
     const bool live = owner && ci < g.nx && cj < g.ny;
+    // rows of a ragged tile past the block's edge: the first one still computes its lower y-face
+    // (the upper face of the block's last row), the others nothing (warp-uniform skips)
+    const bool row_in = owner && cj < g.ny, row_edge = owner && cj == g.ny;
+    // the helper's upper faces of the tile are read only where the tile does not end past the block
+    const bool up_y = y0 + TY <= g.ny;
+    const bool up_x = lane < TY && y0 + lane < g.ny && x0 + TX <= g.nx;
     const int ocy = warp + HALO, ocx = lane + HALO;
     T fzl[5], fzu[5];
-    if (owner) {
-      const FaceIdx iz = zface_idx<NV>(rslot(k0 - 2), rslot(k0 - 1), rslot(k0), rslot(k0 + 1), ocy, ocx);
+    if (row_in) {
+      const FaceIdx iz = zface_idx<NV, BY>(rslot(k0 - 2), rslot(k0 - 1), rslot(k0), rslot(k0 + 1), ocy, ocx);
       if constexpr (CURVI)
-        face_flux_curvi<T, VISC>(ring, mring, NV * MS, iz.b, tg_of(iz), zface_met(mslot(k0 - 1), mslot(k0), ocy, ocx),
+        face_flux_curvi<T, VISC, BY>(ring, mring, NV * MS, iz.b, tg_of(iz), zface_met<BY>(mslot(k0 - 1), mslot(k0), ocy, ocx),
                                  K, fzl);
       else
-        face_flux<T, VISC, 2>(ring, iz, ihz3(hx, hy, hz).v, ihz3(qhx, qhy, qhz).v, K, fzl);
+        face_flux<T, VISC, 2, BY>(ring, iz, ihz3(hx, hy, hz).v, ihz3(qhx, qhy, qhz).v, K, fzl);
     }
     __syncthreads();  // the first consume below overwrites plane k0-2, read by the z-face above
 
@@ -513,41 +518,50 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
       const int mk = mslot(k), mk1 = mslot(k + 1);
       if (owner) {
         T Fa[5], Fb[5];
-        const FaceIdx ix = xface_idx<NV>(sk, sm, sp, ocy, ocx), iy = yface_idx<NV>(sk, sm, sp, ocy, ocx);
-        if constexpr (CURVI) {
-          face_flux_curvi<T, VISC>(ring, mring, NV * MS, ix.b, tg_of(ix), xface_met(mk, mk1, ocy, ocx), K, Fa);
-          face_flux_curvi<T, VISC>(ring, mring, NV * MS, iy.b, tg_of(iy), yface_met(mk, mk1, ocy, ocx), K, Fb);
-        } else {
-          face_flux<T, VISC, 0>(ring, ix, ihx3(hx, hy, hz).v, ihx3(qhx, qhy, qhz).v, K, Fa);
-          face_flux<T, VISC, 1>(ring, iy, ihy3(hx, hy, hz).v, ihy3(qhx, qhy, qhz).v, K, Fb);
+        const FaceIdx ix = xface_idx<NV, BY>(sk, sm, sp, ocy, ocx), iy = yface_idx<NV, BY>(sk, sm, sp, ocy, ocx);
+        if (row_in) {
+          if constexpr (CURVI)
+            face_flux_curvi<T, VISC, BY>(ring, mring, NV * MS, ix.b, tg_of(ix), xface_met<BY>(mk, mk1, ocy, ocx), K, Fa);
+          else
+            face_flux<T, VISC, 0, BY>(ring, ix, ihx3(hx, hy, hz).v, ihx3(qhx, qhy, qhz).v, K, Fa);
+#pragma unroll
+          for (int m = 0; m < 5; ++m) fx[(m * TY + warp) * (TX + 1) + lane] = Fa[m];
         }
+        if (row_in || row_edge) {
+          if constexpr (CURVI)
+            face_flux_curvi<T, VISC, BY>(ring, mring, NV * MS, iy.b, tg_of(iy), yface_met<BY>(mk, mk1, ocy, ocx), K, Fb);
+          else
+            face_flux<T, VISC, 1, BY>(ring, iy, ihy3(hx, hy, hz).v, ihy3(qhx, qhy, qhz).v, K, Fb);
 #pragma unroll
-        for (int m = 0; m < 5; ++m) fx[(m * TY + warp) * (TX + 1) + lane] = Fa[m];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + warp) * TX + lane] = Fb[m];
-        const FaceIdx iz = zface_idx<NV>(sm, sk, sp, s2, ocy, ocx);
-        if constexpr (CURVI)
-          face_flux_curvi<T, VISC>(ring, mring, NV * MS, iz.b, tg_of(iz), zface_met(mk, mk1, ocy, ocx), K, fzu);
-        else
-          face_flux<T, VISC, 2>(ring, iz, ihz3(hx, hy, hz).v, ihz3(qhx, qhy, qhz).v, K, fzu);
+          for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + warp) * TX + lane] = Fb[m];
+        }
+        if (row_in) {
+          const FaceIdx iz = zface_idx<NV, BY>(sm, sk, sp, s2, ocy, ocx);
+          if constexpr (CURVI)
+            face_flux_curvi<T, VISC, BY>(ring, mring, NV * MS, iz.b, tg_of(iz), zface_met<BY>(mk, mk1, ocy, ocx), K, fzu);
+          else
+            face_flux<T, VISC, 2, BY>(ring, iz, ihz3(hx, hy, hz).v, ihz3(qhx, qhy, qhz).v, K, fzu);
+        }
       } else {
         // the tile's upper y-faces (all lanes) and upper x-faces (lanes < TY)
         T Fa[5], Fb[5];
-        const FaceIdx iy = yface_idx<NV>(sk, sm, sp, TY + HALO, lane + HALO);
-        const FaceIdx ix = xface_idx<NV>(sk, sm, sp, (lane % TY) + HALO, TX + HALO);
-        if constexpr (CURVI) {
-          face_flux_curvi<T, VISC>(ring, mring, NV * MS, iy.b, tg_of(iy),
-                                   yface_met(mk, mk1, TY + HALO, lane + HALO), K, Fa);
-          if (lane < TY)
-            face_flux_curvi<T, VISC>(ring, mring, NV * MS, ix.b, tg_of(ix),
-                                     xface_met(mk, mk1, lane + HALO, TX + HALO), K, Fb);
-        } else {
-          face_flux<T, VISC, 1>(ring, iy, ihy3(hx, hy, hz).v, ihy3(qhx, qhy, qhz).v, K, Fa);
-          if (lane < TY) face_flux<T, VISC, 0>(ring, ix, ihx3(hx, hy, hz).v, ihx3(qhx, qhy, qhz).v, K, Fb);
-        }
+        const FaceIdx iy = yface_idx<NV, BY>(sk, sm, sp, TY + HALO, lane + HALO);
+        const FaceIdx ix = xface_idx<NV, BY>(sk, sm, sp, (lane % TY) + HALO, TX + HALO);
+        if (up_y) {
+          if constexpr (CURVI)
+            face_flux_curvi<T, VISC, BY>(ring, mring, NV * MS, iy.b, tg_of(iy),
+                                     yface_met<BY>(mk, mk1, TY + HALO, lane + HALO), K, Fa);
+          else
+            face_flux<T, VISC, 1, BY>(ring, iy, ihy3(hx, hy, hz).v, ihy3(qhx, qhy, qhz).v, K, Fa);
 #pragma unroll
-        for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + TY) * TX + lane] = Fa[m];
-        if (lane < TY) {
+          for (int m = 0; m < 5; ++m) fy[(m * (TY + 1) + TY) * TX + lane] = Fa[m];
+        }
+        if (up_x) {
+          if constexpr (CURVI)
+            face_flux_curvi<T, VISC, BY>(ring, mring, NV * MS, ix.b, tg_of(ix),
+                                     xface_met<BY>(mk, mk1, lane + HALO, TX + HALO), K, Fb);
+          else
+            face_flux<T, VISC, 0, BY>(ring, ix, ihx3(hx, hy, hz).v, ihx3(qhx, qhy, qhz).v, K, Fb);
 #pragma unroll
           for (int m = 0; m < 5; ++m) fx[(m * TY + lane) * (TX + 1) + TX] = Fb[m];
         }
@@ -565,7 +579,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
             R[m] = (ddx * hx2 + ddy * hy2) + (fzu[m] - fzl[m]) * hz2;  // doubled fluxes
         }
         if constexpr (CURVI) {
-          const T iv = Fm::rcp(mring[mb(mk, ocy, ocx) + 9 * MS]);
+          const T iv = Fm::rcp(mring[mb<BY>(mk, ocy, ocx) + 9 * MS]);
 #pragma unroll
           for (int m = 0; m < 5; ++m) R[m] = R[m] * iv;
         }
@@ -582,26 +596,26 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
             const double adv = qs_[m] - double(dtc) * double(R[m]);
             if constexpr (STAGE == 1) out[m] = adv;
             else if constexpr (STAGE == 2) out[m] = 0.75 * qn_[m] + 0.25 * adv;
-            else out[m] = qn_[m] / 3.0 + (2.0 / 3.0) * adv;
+            else out[m] = fma(2.0 / 3.0, adv, (1.0 / 3.0) * qn_[m]);  // an FP64 division costs ~7 FMAs here
             qout[m * g.field + o] = out[m];
           }
           if constexpr (STAGE == 3) {
-            const double ir = 1.0 / out[0];
+            const double ir = VM<double>::rcp(out[0]);
             const double uu = out[1] * ir, vv = out[2] * ir, ww = out[3] * ir;
             const double pp = double(gm1) * (out[4] - 0.5 * out[0] * (uu * uu + vv * vv + ww * ww));
             if (!(out[0] > 0.0 && pp > 0.0)) bad = true;
             double rate;
             if constexpr (CURVI) {
               T sb[9];
-              cell_face_means(mring, mk, mk1, ocy, ocx, sb);
-              rate = cell_rate_curvi<double>(out[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], RK,
+              cell_face_means<T, BY>(mring, mk, mk1, ocy, ocx, sb);
+              rate = cell_rate_curvi<double>(out[0], uu, vv, ww, pp, sb, mring[mb<BY>(mk, ocy, ocx) + 9 * MS], RK,
                                              ph.viscous);
             } else {
               rate = cell_rate<double>(out[0], uu, vv, ww, pp, RK, ph.viscous, hx, hy, hz, hs2);
             }
             rate_max = fmax(rate_max, T(rate));
             if constexpr (!VISC)
-              if (ph.local_dt) static_cast<double*>(D->dtl)[o] = ph.cfl / rate;
+              if (ph.local_dt) static_cast<double*>(D->dtl)[o] = ph.cfl * VM<double>::rcp(rate);
           }
         } else {
           float inc[5];
@@ -630,8 +644,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
             float rate;
             if constexpr (CURVI) {
               T sb[9];
-              cell_face_means(mring, mk, mk1, ocy, ocx, sb);
-              rate = cell_rate_curvi<float>(qf[0], uu, vv, ww, pp, sb, mring[mb(mk, ocy, ocx) + 9 * MS], RK,
+              cell_face_means<T, BY>(mring, mk, mk1, ocy, ocx, sb);
+              rate = cell_rate_curvi<float>(qf[0], uu, vv, ww, pp, sb, mring[mb<BY>(mk, ocy, ocx) + 9 * MS], RK,
                                             ph.viscous);
             } else {
               rate = cell_rate<float>(qf[0], uu, vv, ww, pp, RK, ph.viscous, hx, hy, hz, hs2);
@@ -642,15 +656,16 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && !CURVI) ? 2 : 1)
           }
         }
         if constexpr (STAGE == 1) {
+          // the residual norm is reduced in FP64 on both paths: an FP32 residual's square is exact
+          // in FP64 (24-bit significand), so the mixed path's sums round only in the FP64 additions;
+          // it is widened on the integer pipe, leaving one FP64 operation per variable
 #pragma unroll
           for (int m = 0; m < 5; ++m) {
-            if constexpr (MIXED) {  // compensated FP32 accumulation, folded into FP64 below
-              const float y = float(R[m]) * float(R[m]) - ncomp[m];
-              const float t = nsum[m] + y;
-              ncomp[m] = (t - nsum[m]) - y;
-              nsum[m] = t;
+            if constexpr (MIXED) {
+              const double r = f32_to_f64_bits(float(R[m]));
+              nacc[m] = fma(r, r, nacc[m]);
             } else {
-              nacc[m] += double(R[m]) * double(R[m]);
+              nacc[m] = fma(double(R[m]), double(R[m]), nacc[m]);
             }
           }
         }

@@ -1,0 +1,11 @@
+// stage_f64t.cu -- stage-kernel instantiations: FP64 path, Cartesian Euler blocks, the second
+// tile height the group tuner may choose (TY_ALT_F64)
+#include "stage_inst.cuh"
+
+namespace gbcfd {
+cudaError_t launch_stage_f64_alt(int stage, const GroupParams& P, int grid, cudaStream_t s) {
+  return stage_dispatch_v<double, false, false, TY_ALT_F64>(stage, P, grid, s);
+}
+cudaError_t stage_prepare_f64_alt() { return stage_prepare_v<double, false, false, TY_ALT_F64>(); }
+int stage_occupancy_f64_alt() { return stage_occupancy_v<double, false, false, TY_ALT_F64>(); }
+}  // namespace gbcfd

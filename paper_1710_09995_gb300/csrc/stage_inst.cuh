@@ -10,78 +10,70 @@ namespace gbcfd {
 // the kernel's dynamic shared-memory limit, set once per device (before any graph capture)
 // (a per-device bit set atomically: host threads may set up blocks concurrently, and setting the
 // attribute twice is harmless)
-template <typename T, bool VISC, int STAGE, bool CURVI>
+template <typename T, bool VISC, int STAGE, bool CURVI, int TYV>
 cudaError_t stage_attr() {
   static std::atomic<unsigned long long> done{0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 64 && ((done.load(std::memory_order_acquire) >> dev) & 1ull)) return cudaSuccess;
-  e = cudaFuncSetAttribute(stage_kernel<T, VISC, STAGE, CURVI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)Plan<T, VISC, CURVI>::bytes);
+  e = cudaFuncSetAttribute(stage_kernel<T, VISC, STAGE, CURVI, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Plan<T, VISC, CURVI, TYV>::bytes);
   if (e == cudaSuccess && dev < 64) done.fetch_or(1ull << dev, std::memory_order_acq_rel);
   return e;
 }
 
-template <typename T, bool VISC, int STAGE, bool CURVI>
+template <typename T, bool VISC, int STAGE, bool CURVI, int TYV>
 cudaError_t stage_go(const GroupParams& P, int grid, cudaStream_t s) {
-  cudaError_t e = stage_attr<T, VISC, STAGE, CURVI>();
+  cudaError_t e = stage_attr<T, VISC, STAGE, CURVI, TYV>();
   if (e != cudaSuccess) return e;
-  stage_kernel<T, VISC, STAGE, CURVI><<<grid, NT, Plan<T, VISC, CURVI>::bytes, s>>>(P);
+  stage_kernel<T, VISC, STAGE, CURVI, TYV><<<grid, tile_threads(TYV), Plan<T, VISC, CURVI, TYV>::bytes, s>>>(P);
   return cudaGetLastError();
 }
 
-template <typename T, bool CURVI>
-cudaError_t stage_prepare(int viscous) {
-  cudaError_t e = cudaSuccess;
-  if (viscous) {
-    if (e == cudaSuccess) e = stage_attr<T, true, 0, CURVI>();
-    if (e == cudaSuccess) e = stage_attr<T, true, 1, CURVI>();
-    if (e == cudaSuccess) e = stage_attr<T, true, 2, CURVI>();
-    if (e == cudaSuccess) e = stage_attr<T, true, 3, CURVI>();
-  } else {
-    if (e == cudaSuccess) e = stage_attr<T, false, 0, CURVI>();
-    if (e == cudaSuccess) e = stage_attr<T, false, 1, CURVI>();
-    if (e == cudaSuccess) e = stage_attr<T, false, 2, CURVI>();
-    if (e == cudaSuccess) e = stage_attr<T, false, 3, CURVI>();
-  }
+template <typename T, bool VISC, bool CURVI, int TYV>
+cudaError_t stage_prepare_v() {
+  cudaError_t e = stage_attr<T, VISC, 0, CURVI, TYV>();
+  if (e == cudaSuccess) e = stage_attr<T, VISC, 1, CURVI, TYV>();
+  if (e == cudaSuccess) e = stage_attr<T, VISC, 2, CURVI, TYV>();
+  if (e == cudaSuccess) e = stage_attr<T, VISC, 3, CURVI, TYV>();
   return e;
 }
 
-template <typename T, bool CURVI>
-cudaError_t stage_dispatch(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s) {
-  if (viscous) {
-    switch (stage) {
-      case 0: return stage_go<T, true, 0, CURVI>(P, grid, s);
-      case 1: return stage_go<T, true, 1, CURVI>(P, grid, s);
-      case 2: return stage_go<T, true, 2, CURVI>(P, grid, s);
-      case 3: return stage_go<T, true, 3, CURVI>(P, grid, s);
-    }
-  } else {
-    switch (stage) {
-      case 0: return stage_go<T, false, 0, CURVI>(P, grid, s);
-      case 1: return stage_go<T, false, 1, CURVI>(P, grid, s);
-      case 2: return stage_go<T, false, 2, CURVI>(P, grid, s);
-      case 3: return stage_go<T, false, 3, CURVI>(P, grid, s);
-    }
+template <typename T, bool VISC, bool CURVI, int TYV>
+cudaError_t stage_dispatch_v(int stage, const GroupParams& P, int grid, cudaStream_t s) {
+  switch (stage) {
+    case 0: return stage_go<T, VISC, 0, CURVI, TYV>(P, grid, s);
+    case 1: return stage_go<T, VISC, 1, CURVI, TYV>(P, grid, s);
+    case 2: return stage_go<T, VISC, 2, CURVI, TYV>(P, grid, s);
+    case 3: return stage_go<T, VISC, 3, CURVI, TYV>(P, grid, s);
   }
   return cudaErrorInvalidValue;
 }
 
+template <typename T, bool VISC, bool CURVI, int TYV>
+int stage_occupancy_v() {
+  int n = 0;
+  auto k = stage_kernel<T, VISC, 1, CURVI, TYV>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Plan<T, VISC, CURVI, TYV>::bytes);
+  const cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, tile_threads(TYV), Plan<T, VISC, CURVI, TYV>::bytes);
+  return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+// the default tile height, viscous or not
+template <typename T, bool CURVI>
+cudaError_t stage_prepare(int viscous) {
+  return viscous ? stage_prepare_v<T, true, CURVI, TY_DEFAULT>() : stage_prepare_v<T, false, CURVI, TY_DEFAULT>();
+}
+template <typename T, bool CURVI>
+cudaError_t stage_dispatch(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s) {
+  return viscous ? stage_dispatch_v<T, true, CURVI, TY_DEFAULT>(stage, P, grid, s)
+                 : stage_dispatch_v<T, false, CURVI, TY_DEFAULT>(stage, P, grid, s);
+}
 template <typename T, bool CURVI>
 int stage_occupancy(int viscous) {
-  int n = 0;
-  cudaError_t e;
-  if (viscous) {
-    auto k = stage_kernel<T, true, 1, CURVI>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Plan<T, true, CURVI>::bytes);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, Plan<T, true, CURVI>::bytes);
-  } else {
-    auto k = stage_kernel<T, false, 1, CURVI>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Plan<T, false, CURVI>::bytes);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NT, Plan<T, false, CURVI>::bytes);
-  }
-  return (e == cudaSuccess && n > 0) ? n : 1;
+  return viscous ? stage_occupancy_v<T, true, CURVI, TY_DEFAULT>() : stage_occupancy_v<T, false, CURVI, TY_DEFAULT>();
 }
 
 }  // namespace gbcfd

@@ -504,16 +504,6 @@ struct Smem {
 
 
 
-// Kahan-compensated running sum (the mixed path's per-thread sums of squares)
-struct KSum {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float y = x - c, t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-};
-
 // MODE: 0 x pass (R =), 1 y pass (R +=), 2 z pass (stage update or residual output)
 template <typename T, int D, int MODE>
 __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a) {
@@ -536,8 +526,7 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
   const bool linear = a.linear != 0;
   const double dt = (MODE == 2 && a.stage > 0) ? a.ctrl->dt : 0.0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double sq[5] = {0, 0, 0, 0, 0};
-  KSum ks[5];
+  double sq[5] = {0, 0, 0, 0, 0};  // FP64 sums of R^2 (an FP32 residual's square is exact in FP64)
   constexpr int idx[5] = {0, Fr<D>::N, Fr<D>::T1, Fr<D>::T2, 4};
   struct TileInfo { int s0, Ls, a0, ob; };
   auto decode = [&](long long tile) {
@@ -733,7 +722,7 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
           if (a.stage == 0) {
             a.rout[o] = f32_to_f64_bits(tot);
           } else if (a.stage == 1) {
-            ks[q].add(tot * tot);
+            sq[q] = fma(double(tot), double(tot), sq[q]);
             a.d1[o] = -dtf * tot;
           } else if (a.stage == 2) {
             a.d2[o] = 0.25f * (a.d1[o] - dtf * tot);
@@ -748,9 +737,6 @@ __global__ void __launch_bounds__(NTW, sizeof(T) == 4 ? 3 : 2) dir_kernel(Args a
   }
   if (MODE != 2 || a.stage != 1) return;
   // residual norm of R(Q^n): per-CTA sums of squares, the last CTA folds them in CTA order
-  if (sizeof(T) == 4)
-#pragma unroll
-    for (int q = 0; q < 5; ++q) sq[q] = double(ks[q].s) - double(ks[q].c);
 #pragma unroll
   for (int q = 0; q < 5; ++q)
     for (int off = 16; off > 0; off >>= 1) sq[q] += __shfl_xor_sync(0xffffffffu, sq[q], off);

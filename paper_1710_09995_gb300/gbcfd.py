@@ -81,6 +81,8 @@ SIGNATURES = {
     "gbcfd_group_destroy": [_VP],
     "gbcfd_group_step": [_VP, ctypes.c_int, _VP],
     "gbcfd_group_tune": [_VP, _VP, ctypes.POINTER(ctypes.c_int)],
+    "gbcfd_group_tune_tile": [_VP, _VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "gbcfd_group_set_schedule": [_VP, ctypes.c_int, ctypes.c_int, _VP],
     "gbcfd_group_set_timing": [_VP, ctypes.POINTER(_VP), ctypes.c_int],
     "gbcfd_accel_required_bytes": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
     "gbcfd_accel_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t,
@@ -357,14 +359,23 @@ class Group:
         _check(lib().gbcfd_group_create(_handles(self.blocks), len(self.blocks), ctypes.c_void_p(base + off),
                                         nbytes.value, ctypes.byref(h)))
         self.handle = h
+        self.tile_rows = 8  # the default tile height until tune() or set_schedule()
 
     def step(self, nsteps=1, stream=None):
         _check(lib().gbcfd_group_step(self.handle, int(nsteps), _stream(stream)))
 
     def tune(self, stream=None) -> int:
-        c = ctypes.c_int(0)
-        _check(lib().gbcfd_group_tune(self.handle, _stream(stream), ctypes.byref(c)))
+        """choose the tile shape and grid split (gbcfd_group_tune_tile); returns the CTAs per SM,
+        the tile height is kept in `tile_rows`"""
+        c, t = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().gbcfd_group_tune_tile(self.handle, _stream(stream), ctypes.byref(c), ctypes.byref(t)))
+        self.tile_rows = t.value
         return c.value
+
+    def set_schedule(self, ctas_per_sm, tile_rows, stream=None):
+        """pin the tile height and grid split (gbcfd_group_set_schedule)"""
+        _check(lib().gbcfd_group_set_schedule(self.handle, int(ctas_per_sm), int(tile_rows), _stream(stream)))
+        self.tile_rows = int(tile_rows)
 
     def set_timing(self, events):
         """events: 7 torch.cuda.Event(enable_timing=True) recorded inside every step (or None)"""

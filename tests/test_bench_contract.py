@@ -36,3 +36,18 @@ def test_reference_arm_has_a_sample_for_every_workload():
         assert cells > 0 and text and unit in ("cell-updates/s", "cells/s")
         out = step(state)
         assert out.shape == state.shape
+
+
+def test_fp64_alu_peak_and_roofline():
+    """the FP64 path is bound by the FP64 pipe: its peak is 152 SMs x 2 FMA lanes x 2 flops x
+    2.07 GHz = 1.2586 TFLOP/s (the recipe's nominal 1.25; a DFMA probe measured 1.2556), and the
+    roofline divides the flops per cell and stage (from the committed ncu summary, or None when
+    that summary predates the kernel source) by the launch time"""
+    assert abs(bench.FP64_PEAK_TFLOPS - 1.25856) < 1e-4
+    res = {"stage_ms": {1: 1.0, 2: 1.0, 3: 1.0}}
+    hbm = {"avg_launch_ms": 1.0, "traffic": None, "frac": 0.01}
+    r = bench.fp64_alu_roofline(res, 1000, 1, hbm, workload="lattice96")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] == bench.FP64_PEAK_TFLOPS
+    if r["achieved"] is not None:
+        total = sum(r["flops_per_cell"]) * 1000
+        assert abs(r["achieved"] - round(total / 3e-3 / 1e12, 4)) < 1e-9

@@ -96,16 +96,54 @@ def test_lattice_mixed_matches_oracle(gb):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_tune_keeps_results(gb, precision):
-    """every grid split the tuner tries gives the same bits; the choice is one of its candidates"""
+    """every schedule the tuner tries gives the same bits; its choice is one of its candidates"""
     lat = small_lattice(seed=7)
     a = gb.blocks_for_lattice(lat, precision)
     b = gb.blocks_for_lattice(lat, precision)
     ga, gbb = gb.Group(a), gb.Group(b)
     c = gbb.tune()
-    assert c >= 1
+    assert c >= 1 and gbb.tile_rows in (8, ALT_TILE[precision])
     ga.step(2)
     gbb.step(2)
     assert torch.equal(gb.gather_lattice(lat, a), gb.gather_lattice(lat, b))
+
+
+ALT_TILE = {0: 11, 1: 4}  # the second tile height compiled for Cartesian Euler blocks, per path
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("tile_rows,ctas", [(8, 1), (8, 3), ("alt", 1), ("alt", 2), ("alt", 16)])
+def test_every_schedule_gives_the_same_bits(gb, precision, tile_rows, ctas):
+    """each tile shape the stage kernel is compiled for (32 x 8, and 32 x 11 FP64 / 32 x 4 mixed),
+    with several grid splits, advances the lattice (uneven blocks, ragged tiles in x and y) bit for
+    bit like gbcfd_step on the same blocks, both parities of the mixed path"""
+    ty = ALT_TILE[precision] if tile_rows == "alt" else tile_rows
+    lat = small_lattice(seed=9)
+    a = gb.blocks_for_lattice(lat, precision)
+    b = gb.blocks_for_lattice(lat, precision)
+    g = gb.Group(b)
+    g.set_schedule(ctas, ty)
+    gb.step(a, 3)
+    g.step(3)
+    ga, gbb = gb.gather_lattice(lat, a), gb.gather_lattice(lat, b)
+    assert torch.equal(ga, gbb), (ty, ctas, float((ga - gbb).abs().max()))
+    assert a[0].get_dt() == b[0].get_dt()
+    rtol = 1e-12 if precision == 0 else 1e-6
+    for x, y in zip(a, b):
+        assert np.allclose(x.residual_norm(), y.residual_norm(), rtol=rtol, atol=0)
+    g.close()
+
+
+def test_schedule_rejects_uncompiled_shapes(gb):
+    lat = small_lattice(seed=9)
+    g = gb.Group(gb.blocks_for_lattice(lat, 0))
+    with pytest.raises(RuntimeError):
+        g.set_schedule(1, 4)   # 32 x 4 is compiled for the mixed path only
+    with pytest.raises(RuntimeError):
+        g.set_schedule(0, 8)
+    with pytest.raises(RuntimeError):
+        g.set_schedule(17, 8)
+    g.close()
 
 
 def test_group_curvilinear_equals_single(gb):
