@@ -62,7 +62,7 @@ METRIC_BYTES = {"mixed": 40, "fp64": 80}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gbcfd", choices=["gbcfd", "reference"])
     ap.add_argument("--side", type=int, default=N_DEFAULT, help="cells per side of the cubic vortex block")
