@@ -262,12 +262,13 @@ def time_group_path(gbcfd, torch, lat, precision, steps, warmup, world, device):
     barrier(world)
     ms = max_over_ranks(start.elapsed_time(stop), world, device)
     norms = [b.residual_norm().tolist() for b in blocks]
-    tile_rows = g.tile_rows
+    _, tile_rows, halo_push = g.schedule()
     g.close()
     for b in blocks:
         b.close()
     return {"ms": ms, "stage_ms": stage_ms, "halo_ms": halo_ms, "launches": 7 * steps, "norms": norms[0],
-            "ctas_per_sm": ctas_per_sm, "tile": [32, tile_rows], "blocks": len(blocks)}
+            "ctas_per_sm": ctas_per_sm, "tile": [32, tile_rows],
+            "halo": "folded into stages 1-2" if halo_push else "launch per stage", "blocks": len(blocks)}
 
 
 def e2e_group_path(gbcfd, torch, lat, precision, steps, world, device, pipelined=True):
@@ -715,7 +716,7 @@ def run_lattice(args, world, rank, local, device, torch, cases, gbcfd):
         "dtype": "f32+f64" if head == "mixed" else "f64",
         "data": "synthetic (seeded lattice sizes and Fourier-mode phases; the paper's meshes are not available)",
         "config": {"workload": WORKLOADS["lattice96"], "cells": cells, "blocks": r["blocks"], "precision": head,
-                   "ctas_per_sm": r["ctas_per_sm"], "tile": r.get("tile"),
+                   "ctas_per_sm": r["ctas_per_sm"], "tile": r.get("tile"), "halo": r.get("halo"),
                    "l2": "working set > 20 GB >> 129 MB L2, no flush needed",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": fp64_alu_roofline(r, cells, args.steps, hbm, "lattice96") if head == "fp64" else hbm,
@@ -732,7 +733,7 @@ def run_lattice(args, world, rank, local, device, torch, cases, gbcfd):
         hp = roofline(p, rp, cells, args.steps, peak, peak_kind, "lattice96")
         out[p] = {"value": world * cells * args.steps / (rp["ms"] / 1e3), "unit": "cell-updates/s",
                   "ms_per_step": rp["ms"] / args.steps, "dtype": "f64" if p == "fp64" else "f32+f64",
-                  "ctas_per_sm": rp["ctas_per_sm"], "tile": rp.get("tile"),
+                  "ctas_per_sm": rp["ctas_per_sm"], "tile": rp.get("tile"), "halo": rp.get("halo"),
                   "roofline": fp64_alu_roofline(rp, cells, args.steps, hp, "lattice96") if p == "fp64" else hp,
                   "issue": issue_estimate(p, rp, cells, args.steps, clk.get("sm_mhz"), "lattice96"),
                   "halo_ms_per_step": rp["halo_ms"] / args.steps, "gpu_launches": rp["launches"]}

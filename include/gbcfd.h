@@ -245,7 +245,9 @@ int gbcfd_group_step(gbcfd_group group, int nsteps, void* stream);
  * stage kernel is compiled for on this path -- 32 x 8 cells, and on Cartesian Euler blocks a
  * second height (32 x 11 on the FP64 path, 32 x 4 on the mixed path) -- and for each of them
  * several grid splits (1x .. 16x the resident CTAs per SM, at most 16 per SM, shared between
- * the blocks in proportion to their tile-planes), and keeps the fastest for this group.  Synchronises the
+ * the blocks in proportion to their tile-planes), keeps the fastest, and then for it times the
+ * halo exchange of the stage outputs as launches against its fold into the stages (where the
+ * group allows the fold, see gbcfd_group_set_schedule) and keeps the faster.  Synchronises the
  * stream; drops the captured graphs.  The chosen CTAs per SM and tile height (cells along y)
  * are returned in *ctas_per_sm and *tile_rows when not NULL; gbcfd_group_tune is the same
  * without the tile height. */
@@ -253,11 +255,21 @@ int gbcfd_group_tune(gbcfd_group group, void* stream, int* ctas_per_sm);
 int gbcfd_group_tune_tile(gbcfd_group group, void* stream, int* ctas_per_sm, int* tile_rows);
 
 /* Set the schedule the tuner would choose: tile height tile_rows (8, or the path's second height
- * on Cartesian Euler blocks: 11 FP64, 4 mixed; GBCFD_ERR_ARG otherwise) and ctas_per_sm CTAs per
- * SM (1..16, split between the blocks as by the tuner).  Results do not depend on the schedule
- * (every face flux and every cell's update is the same arithmetic); the residual norms' rounding
- * does (their partial sums follow the grid).  Synchronises the stream; drops the captured graphs. */
-int gbcfd_group_set_schedule(gbcfd_group group, int ctas_per_sm, int tile_rows, void* stream);
+ * on Cartesian Euler blocks: 11 FP64, 4 mixed; GBCFD_ERR_ARG otherwise), ctas_per_sm CTAs per
+ * SM (1..16, split between the blocks as by the tuner), and halo_push: 0 runs the halo exchange
+ * of the stage-1 and stage-2 outputs as launches between the stages, 1 folds it into those
+ * stages (each cell near a block face also writes its output into the neighbours' halo cells
+ * that copy it, faces, edges and corners; Sec. 3.2.5 merges such small kernels), which needs
+ * Cartesian Euler blocks forming a conforming periodic lattice: every face connected to a member, the blocks of a face equal in
+ * the face's two directions, at least 2 cells per direction, face-neighbour walks that commute
+ * (GBCFD_ERR_ARG otherwise).  Results do not depend on the schedule (every face flux and every
+ * cell's update is the same arithmetic); the residual norms' rounding does (their partial sums
+ * follow the grid).  Synchronises the stream; drops the captured graphs. */
+int gbcfd_group_set_schedule(gbcfd_group group, int ctas_per_sm, int tile_rows, int halo_push, void* stream);
+
+/* The group's current schedule (from the tuner or gbcfd_group_set_schedule); NULL pointers are
+ * skipped. */
+int gbcfd_group_get_schedule(gbcfd_group group, int* ctas_per_sm, int* tile_rows, int* halo_push);
 
 /* Timing marks inside each step of the group: events[0..6] are CUDA events (cudaEvent_t) the
  * caller created with timing enabled and owns.  Each step records events[0] before the time-step

@@ -762,6 +762,8 @@ struct gbcfd_group_s {
   size_t partial_n;
   int ctas_per_sm;        // grid = SMs x this (split between the blocks)
   int ty;                 // tile height of the stage kernel the table is written for
+  int push_ok;            // the members form a conforming lattice (group_can_push)
+  int push;               // stages 1 and 2 fill the neighbours' halos themselves (a schedule choice)
   int grid;
   cudaStream_t cap;       // private stream the step graphs are captured on
   cudaGraphExec_t exec[2];  // one step, for each parity of the mixed path's ping-pong
@@ -783,6 +785,38 @@ extern "C" int gbcfd_group_required_bytes(int n, size_t* bytes) {
   return GBCFD_OK;
 }
 
+// the members' face neighbours as group indices, in every descriptor of the table
+static void set_group_nbrs(gbcfd_group g) {
+  for (size_t i = 0; i < g->blocks.size(); ++i)
+    for (int f = 0; f < 6; ++f) {
+      gbcfd_block nb = g->blocks[i]->nbr[f];
+      g->table_host[i].nbr[f] = nb ? (int)(std::find(g->blocks.begin(), g->blocks.end(), nb) - g->blocks.begin()) : -1;
+    }
+}
+
+// Whether the stage kernel may fill the halos itself (push_halo in stage.cuh): Cartesian Euler
+// blocks (the kernels compiled with the fold) forming a conforming block lattice -- every face connected to a member (periodic wrap included), the two
+// blocks of a face equal in the face's two directions, at least HALO cells in every direction,
+// and walking face neighbours along two different axes reaching the same block in either order --
+// so each halo cell has exactly one source cell, the one the halo kernel would copy.
+static bool group_can_push(const std::vector<gbcfd_block>& bl) {
+  auto nb = [](gbcfd_block b, int f) { return b ? b->nbr[f] : nullptr; };
+  if (bl[0]->p.viscous || bl[0]->curvi) return false;  // the folded kernels: Cartesian Euler blocks
+  for (gbcfd_block b : bl) {
+    if (b->nx < HALO || b->ny < HALO || b->nz < HALO) return false;
+    for (int f = 0; f < 6; ++f) {
+      gbcfd_block n = b->nbr[f];
+      if (!n || n->nbr[f ^ 1] != b) return false;
+      const int a = f >> 1;  // axis of the face: the other two sizes must match
+      if ((a != 0 && n->nx != b->nx) || (a != 1 && n->ny != b->ny) || (a != 2 && n->nz != b->nz)) return false;
+    }
+    for (int f1 = 0; f1 < 6; ++f1)
+      for (int f2 = 0; f2 < 6; ++f2)
+        if ((f1 >> 1) != (f2 >> 1) && nb(nb(b, f1), f2) != nb(nb(b, f2), f1)) return false;
+  }
+  return true;
+}
+
 // split SMs x ctas_per_sm CTAs between the blocks in proportion to their tile-planes (each gets
 // at least one) and write the descriptor table for the stage kernel of tile height ty
 static int group_split(gbcfd_group g, int ctas_per_sm, cudaStream_t s, int ty = -1) {
@@ -794,6 +828,7 @@ static int group_split(gbcfd_group g, int ctas_per_sm, cudaStream_t s, int ty = 
     if (rc) return rc;
     g->versions[i] = g->blocks[i]->desc_version;
   }
+  set_group_nbrs(g);
   const long long target = (long long)nsm * ctas_per_sm;
   long long W = 0;
   for (auto& d : g->table_host) W += d.units;
@@ -853,6 +888,8 @@ extern "C" int gbcfd_group_create(const gbcfd_block* blocks, int n, void* dev_me
   g->cap = nullptr;
   g->timed = false;
   g->ty = TY_DEFAULT;
+  g->push_ok = group_can_push(g->blocks) ? 1 : 0;
+  g->push = 0;
   for (int i = 0; i < n; ++i) g->table_host.push_back(blocks[i]->desc_host);
   const int mixed = blocks[0]->p.precision == GBCFD_MIXED, vis = blocks[0]->p.viscous, cv = blocks[0]->curvi;
   cudaError_t e = mixed ? (cv ? stage_prepare_f32c(vis) : stage_prepare_f32(vis))
@@ -890,6 +927,7 @@ static GroupParams group_params(gbcfd_group g) {
   P.pk = path_consts(P.ph);
   P.gctrl = g->gctrl;
   P.partial = g->partial;
+  P.push = g->push;
   return P;
 }
 
@@ -907,8 +945,10 @@ static int group_step_launches(gbcfd_group g, cudaStream_t s) {
   GroupParams P = group_params(g);
   const int fields[3] = {F_STATE, F_STAGE1, F_STAGE2};
   for (int st = 1; st <= 3; ++st) {
-    int rc = exchange(g->blocks.data(), n, fields[st - 1], false, s);
-    if (rc) return rc;
+    if (st == 1 || !g->push) {  // with push, stages 1 and 2 fill the halos stages 2 and 3 read
+      int rc = exchange(g->blocks.data(), n, fields[st - 1], false, s);
+      if (rc) return rc;
+    }
     CK(mark(2 * st - 1));
     CK(launch_stage(b0->p.precision, b0->p.viscous, b0->curvi, st, P, g->grid, s, g->ty));
     CK(mark(2 * st));
@@ -939,6 +979,7 @@ static int group_refresh(gbcfd_group g, cudaStream_t s) {
     g->table_host[i].ctas = ctas;
     g->versions[i] = g->blocks[i]->desc_version;
   }
+  set_group_nbrs(g);
   CK(cudaMemcpyAsync(g->table, g->table_host.data(), sizeof(BlockDesc) * g->table_host.size(),
                      cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));  // the host table is reused
@@ -990,7 +1031,8 @@ extern "C" int gbcfd_group_set_timing(gbcfd_group g, void* const* events, int n)
   return GBCFD_OK;
 }
 
-extern "C" int gbcfd_group_set_schedule(gbcfd_group g, int ctas_per_sm, int tile_rows, void* stream) {
+extern "C" int gbcfd_group_set_schedule(gbcfd_group g, int ctas_per_sm, int tile_rows, int halo_push,
+                                        void* stream) {
   if (!g) return fail(GBCFD_ERR_ARG, "group is NULL");
   gbcfd_block b0 = g->blocks[0];
   int tys[4];
@@ -999,9 +1041,23 @@ extern "C" int gbcfd_group_set_schedule(gbcfd_group g, int ctas_per_sm, int tile
     return fail(GBCFD_ERR_ARG, "tile height " + std::to_string(tile_rows) + " is not compiled for this path");
   if (ctas_per_sm < 1 || (long long)b0->nsm * ctas_per_sm > max_group_ctas(b0->nsm))
     return fail(GBCFD_ERR_ARG, "ctas_per_sm must be 1..16");
-  if (stage_prepare_tile(b0->p.precision, b0->p.viscous, b0->curvi, tile_rows) != cudaSuccess)
+  if (halo_push && !g->push_ok)
+    return fail(GBCFD_ERR_ARG, "halo push needs a conforming periodic block lattice (every face connected, "
+                               "matching face sizes, at least 2 cells per direction)");
+  if (stage_prepare_tile(b0->p.precision, b0->p.viscous, b0->curvi, tile_rows) != cudaSuccess ||
+      (halo_push && (b0->p.precision == GBCFD_MIXED ? stage_prepare_f32_push(tile_rows)
+                                                    : stage_prepare_f64_push(tile_rows)) != cudaSuccess))
     return fail(GBCFD_ERR_CUDA, "stage kernel set-up failed");
+  g->push = halo_push ? 1 : 0;
   return group_split(g, ctas_per_sm, static_cast<cudaStream_t>(stream), tile_rows);
+}
+
+extern "C" int gbcfd_group_get_schedule(gbcfd_group g, int* ctas_per_sm, int* tile_rows, int* halo_push) {
+  if (!g) return fail(GBCFD_ERR_ARG, "group is NULL");
+  if (ctas_per_sm) *ctas_per_sm = g->ctas_per_sm;
+  if (tile_rows) *tile_rows = g->ty;
+  if (halo_push) *halo_push = g->push;
+  return GBCFD_OK;
 }
 
 extern "C" int gbcfd_group_tune(gbcfd_group g, void* stream, int* ctas_per_sm) {
@@ -1028,6 +1084,7 @@ extern "C" int gbcfd_group_tune_tile(gbcfd_group g, void* stream, int* ctas_per_
   float best = 1e30f;
   int best_c = 0, best_ty = TY_DEFAULT;
   rc = exchange(g->blocks.data(), (int)g->blocks.size(), F_STATE, false, s);
+  g->push = 0;  // shapes are compared with the exchange as a launch; the fold is decided after
   for (int ti = 0; ti < ntile && !rc; ++ti) {
     const int ty = tys[ti];
     if (stage_prepare_tile(b0->p.precision, b0->p.viscous, b0->curvi, ty) != cudaSuccess) {
@@ -1065,11 +1122,40 @@ extern "C" int gbcfd_group_tune_tile(gbcfd_group g, void* stream, int* ctas_per_
       if (!rc && t < best) { best = t; best_c = cand[ci]; best_ty = ty; }
     }
   }
+  // the halo exchange of the stage output: a launch between the stages, or folded into the
+  // stages (push); timed on the chosen shape as stage 1, [exchange,] stage 2
+  g->push = 0;
+  if (!rc) rc = group_split(g, best_c, s, best_ty);
+  if (!rc && g->push_ok &&
+      (b0->p.precision == GBCFD_MIXED ? stage_prepare_f32_push(best_ty) : stage_prepare_f64_push(best_ty)) !=
+          cudaSuccess)
+    rc = fail(GBCFD_ERR_CUDA, "stage kernel set-up failed");
+  if (!rc && g->push_ok) {
+    float tp[2] = {0.f, 0.f};
+    for (int push = 0; push < 2 && !rc; ++push) {
+      g->push = push;
+      GroupParams P = group_params(g);
+      for (int rep = 0; rep < 3 && !rc; ++rep) {
+        cudaEventRecord(e0, s);
+        if (launch_stage(b0->p.precision, b0->p.viscous, b0->curvi, 1, P, g->grid, s, best_ty) != cudaSuccess)
+          rc = fail(GBCFD_ERR_CUDA, "tuning launch failed");
+        if (!rc && !push) rc = exchange(g->blocks.data(), (int)g->blocks.size(), F_STAGE1, false, s);
+        if (!rc && launch_stage(b0->p.precision, b0->p.viscous, b0->curvi, 2, P, g->grid, s, best_ty) != cudaSuccess)
+          rc = fail(GBCFD_ERR_CUDA, "tuning launch failed");
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tp[push] += ms;
+      }
+    }
+    g->push = (!rc && tp[1] < tp[0]) ? 1 : 0;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (rc) return rc;
-  rc = group_split(g, best_c, s, best_ty);
-  if (rc) return rc;
+  if (rc) { g->push = 0; return rc; }
+  for (int p = 0; p < 2; ++p)  // the step graphs hold the exchange choice
+    if (g->exec[p]) { cudaGraphExecDestroy(g->exec[p]); g->exec[p] = nullptr; }
   if (ctas_per_sm) *ctas_per_sm = best_c;
   if (tile_rows) *tile_rows = best_ty;
   return GBCFD_OK;
@@ -1747,6 +1833,11 @@ extern "C" int gbcfd_accel_try(gbcfd_accel a, gbcfd_block b, void* stream, int* 
 namespace gbcfd {
 cudaError_t launch_stage(int precision, int viscous, int curvi, int stage, const GroupParams& P, int grid,
                          cudaStream_t s, int ty) {
+  if (P.push && (stage == 1 || stage == 2)) {  // the folded halo exchange: Cartesian Euler groups
+    if (viscous || curvi) return cudaErrorInvalidValue;
+    return precision == GBCFD_MIXED ? launch_stage_f32_push(stage, ty, P, grid, s)
+                                    : launch_stage_f64_push(stage, ty, P, grid, s);
+  }
   if (ty != TY_DEFAULT) {  // the second height: Cartesian Euler blocks only
     if (viscous || curvi) return cudaErrorInvalidValue;
     if (precision == GBCFD_MIXED && ty == TY_ALT_F32) return launch_stage_f32_alt(stage, P, grid, s);

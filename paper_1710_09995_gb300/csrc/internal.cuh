@@ -105,6 +105,7 @@ struct BlockDesc {
   long long units;           // work units (tile-planes) = ntx * nty * nz
   int cta0, ctas;            // the CTAs of a group launch that work on this block
   void* dtl;                 // local time steps, one padded field (f64 FP64 path, f32 mixed)
+  int nbr[6];                // group index of the neighbour across each face (-x +x -y +y -z +z), -1 if none
   long long pad_;
 };
 
@@ -117,6 +118,9 @@ struct GroupParams {
   int cur;                   // mixed path: which of QA/QB, SA/SB holds Q^n
   Physics ph;                // shared physics (gamma, mu, Pr, cfl, eps, viscous, limiter)
   PathConsts pk;             // its constants in both precisions
+  int push;                  // 1: stages 1 and 2 also write their output into the neighbours' halo
+                             // cells (conforming periodic block lattices; no halo launch before
+                             // stages 2 and 3)
   DevCtrl* gctrl;            // group control: counter, time step (read at stage start)
   double* partial;           // [gridDim.x * NPART]
   double* rout;              // residual mode (one block): compact R[5][nz][ny][nx]

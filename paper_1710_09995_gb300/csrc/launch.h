@@ -26,6 +26,11 @@ cudaError_t stage_prepare_f64_alt();
 cudaError_t stage_prepare_f32_alt();
 int stage_occupancy_f64_alt();
 int stage_occupancy_f32_alt();
+// stages 1 and 2 with the halo exchange folded in (Cartesian Euler groups, both tile heights)
+cudaError_t launch_stage_f64_push(int stage, int ty, const GroupParams& P, int grid, cudaStream_t s);
+cudaError_t launch_stage_f32_push(int stage, int ty, const GroupParams& P, int grid, cudaStream_t s);
+cudaError_t stage_prepare_f64_push(int ty);
+cudaError_t stage_prepare_f32_push(int ty);
 cudaError_t launch_stage_f64(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s);
 cudaError_t launch_stage_f64c(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s);
 cudaError_t launch_stage_f32(int viscous, int stage, const GroupParams& P, int grid, cudaStream_t s);

@@ -69,6 +69,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return true;
 }
 
+// one destination of the halo push (push_table, push_halo below): direction (sx, sy, sz) in
+// {-1,0,1}^3 from a block to the neighbour whose halo holds copies of its cells near those faces
+struct PushDst {
+  void* base;              // the neighbour's output field of this stage (element 0 of variable 0)
+  long long field, plane;  // strides in elements
+  int pitch, oi, oj, ok;   // row pitch; (i, j, k) shift into the neighbour's index space
+};
+
 // ---- shared-memory plan ----------------------------------------------------------------------
 template <typename T, bool VISC, bool CURVI, int TYV>
 struct Plan {
@@ -92,7 +100,8 @@ struct Plan {
   static constexpr size_t red = (mring + NMS * MSLOT + 15) / 16 * 16;
   static constexpr size_t bar = red + sizeof(double) * NWARP * NPART;
   static constexpr size_t misc = bar + 8 * (NSTAGE + NMS);
-  static constexpr size_t bytes = (misc + 16 + 127) / 128 * 128;
+  static constexpr size_t push = (misc + 16 + 15) / 16 * 16;  // 27 PushDst (halo push of stages 1, 2)
+  static constexpr size_t bytes = (push + 27 * sizeof(PushDst) + 127) / 128 * 128;
 };
 
 // stencil cell base index inside the ring: slot s, row cy, column cx (variable 0)
@@ -228,6 +237,65 @@ __device__ __forceinline__ T cell_rate(T r, T u, T v, T w, T p, const RateK<T>& 
   return rate;
 }
 
+// The halo exchange folded into the stage (groups with GroupParams::push): the output of a cell
+// within HALO cells of a block face is also written into the halo cells of the neighbouring
+// blocks that hold its copy -- across the face, and across the edge and the corner for cells
+// near two or three faces (the block diagonal reached by walking the face neighbours, in any
+// order on a conforming lattice) -- the cells the halo kernel would fill from it.  No stage
+// reads the halos of the field it writes, so the next launch finds them complete.
+// One destination per direction (sx, sy, sz) in {-1,0,1}^3, built once per CTA for its block:
+// the neighbour's output field and strides, and the index shift from this block's cell to the
+// neighbour's halo cell.
+
+template <typename T, int STAGE>
+__device__ void push_table(const BlockDesc* tb, int b0, int t, PushDst* dst) {
+  const int sx = t % 3 - 1, sy = (t / 3) % 3 - 1, sz = t / 9 - 1;
+  int d = b0, oi = 0, oj = 0, ok = 0;
+  if (sx > 0) { oi -= tb[d].g.nx; d = tb[d].nbr[1]; }
+  if (sx < 0) { d = tb[d].nbr[0]; oi += tb[d].g.nx; }
+  if (sy > 0) { oj -= tb[d].g.ny; d = tb[d].nbr[3]; }
+  if (sy < 0) { d = tb[d].nbr[2]; oj += tb[d].g.ny; }
+  if (sz > 0) { ok -= tb[d].g.nz; d = tb[d].nbr[5]; }
+  if (sz < 0) { d = tb[d].nbr[4]; ok += tb[d].g.nz; }
+  const BlockDesc& D = tb[d];
+  PushDst e;
+  if constexpr (sizeof(T) == 8) {
+    e.base = D.q[STAGE % 3];
+    e.field = D.g.field;
+    e.plane = D.g.plane;
+    e.pitch = D.g.px;
+  } else {
+    e.base = D.d[STAGE - 1];
+    e.field = D.g.fieldf;
+    e.plane = D.g.planef;
+    e.pitch = D.g.pxf;
+  }
+  e.oi = oi; e.oj = oj; e.ok = ok;
+  dst[t] = e;
+}
+
+// out of line: only cells next to a block face call it
+template <typename T>
+__device__ __noinline__ void push_halo(const PushDst* dst, int nx, int ny, int nz, int ci, int cj, int ck,
+                                       T v0, T v1, T v2, T v3, T v4) {
+  const T v[5] = {v0, v1, v2, v3, v4};
+  const int lx = ci < HALO ? -1 : 0, hx = ci >= nx - HALO ? 1 : 0;
+  const int ly = cj < HALO ? -1 : 0, hy = cj >= ny - HALO ? 1 : 0;
+  const int lz = ck < HALO ? -1 : 0, hz = ck >= nz - HALO ? 1 : 0;
+  for (int sz = lz; sz <= hz; ++sz)
+    for (int sy = ly; sy <= hy; ++sy)
+      for (int sx = lx; sx <= hx; ++sx) {
+        const int t = (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);
+        if (t == 13) continue;  // the cell itself
+        const PushDst& e = dst[t];
+        const long long o = (long long)(ck + e.ok + HALO) * e.plane + (long long)(cj + e.oj + HALO) * e.pitch +
+                            (ci + e.oi + HALO);
+        T* f = static_cast<T*>(e.base);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) f[m * e.field + o] = v[m];
+      }
+}
+
 // the path's constants from the launch parameters (formed on the host)
 template <typename T> __device__ __forceinline__ const PathK<T>& path_k(const GroupParams& P);
 template <> __device__ __forceinline__ const PathK<float>& path_k<float>(const GroupParams& P) { return P.pk.f; }
@@ -240,7 +308,9 @@ template <> __device__ __forceinline__ const PathK<double>& path_k<double>(const
 // are spread round-robin, so two 9-warp CTAs (5 warps on one sub-partition) allow 96 registers
 // per thread on the mixed path, four 5-warp CTAs (TYV = 4) 102, one CTA of 9 or 12 warps (3 per
 // sub-partition) 168 on the FP64 and curvilinear paths
-template <typename T, bool VISC, int STAGE, bool CURVI, int TYV>
+// PUSH: stages 1 and 2 of a group with the halo exchange folded in (GroupParams::push); a separate
+// instantiation, so kernels without it carry none of its code
+template <typename T, bool VISC, int STAGE, bool CURVI, int TYV, bool PUSH = false>
 __global__ void __launch_bounds__(tile_threads(TYV), (sizeof(T) == 4 && !CURVI) ? (TYV <= 4 ? 4 : 2) : 1)
     stage_kernel(const GroupParams P) {
   constexpr bool MIXED = sizeof(T) == 4;
@@ -306,6 +376,11 @@ __global__ void __launch_bounds__(tile_threads(TYV), (sizeof(T) == 4 && !CURVI) 
     bsel = lo;
   }
   const BlockDesc* D = P.table + bsel;
+  PushDst* pushdst = reinterpret_cast<PushDst*>(smem + PL::push);
+  if constexpr (PUSH && (STAGE == 1 || STAGE == 2)) {
+    if (tid < 27) push_table<T, STAGE>(P.table, bsel, tid, pushdst);
+    __syncthreads();
+  }
   const int lcta = (int)blockIdx.x - D->cta0, nctas = D->ctas;
   const long long W = D->units;
   const long long u_begin = (long long)lcta * W / nctas;
@@ -599,6 +674,9 @@ __global__ void __launch_bounds__(tile_threads(TYV), (sizeof(T) == 4 && !CURVI) 
             else out[m] = fma(2.0 / 3.0, adv, (1.0 / 3.0) * qn_[m]);  // an FP64 division costs ~7 FMAs here
             qout[m * g.field + o] = out[m];
           }
+          if constexpr (PUSH && (STAGE == 1 || STAGE == 2))
+            if (ci < HALO || cj < HALO || k < HALO || ci >= g.nx - HALO || cj >= g.ny - HALO || k >= g.nz - HALO)
+              push_halo<double>(pushdst, g.nx, g.ny, g.nz, ci, cj, k, out[0], out[1], out[2], out[3], out[4]);
           if constexpr (STAGE == 3) {
             const double ir = VM<double>::rcp(out[0]);
             const double uu = out[1] * ir, vv = out[2] * ir, ww = out[3] * ir;
@@ -621,12 +699,16 @@ __global__ void __launch_bounds__(tile_threads(TYV), (sizeof(T) == 4 && !CURVI) 
           float inc[5];
 #pragma unroll
           for (int m = 0; m < 5; ++m) inc[m] = -float(dtc) * float(R[m]);
-          if constexpr (STAGE == 1) {
+          if constexpr (STAGE == 1 || STAGE == 2) {
+            float dv[5];
 #pragma unroll
-            for (int m = 0; m < 5; ++m) dout[m * g.fieldf + of] = inc[m];
-          } else if constexpr (STAGE == 2) {
-#pragma unroll
-            for (int m = 0; m < 5; ++m) dout[m * g.fieldf + of] = 0.25f * (dp_[m] + inc[m]);
+            for (int m = 0; m < 5; ++m) {
+              dv[m] = STAGE == 1 ? inc[m] : 0.25f * (dp_[m] + inc[m]);
+              dout[m * g.fieldf + of] = dv[m];
+            }
+            if (PUSH && (ci < HALO || cj < HALO || k < HALO || ci >= g.nx - HALO || cj >= g.ny - HALO ||
+                         k >= g.nz - HALO))
+              push_halo<float>(pushdst, g.nx, g.ny, g.nz, ci, cj, k, dv[0], dv[1], dv[2], dv[3], dv[4]);
           } else {
             float qf[5];
 #pragma unroll

@@ -10,25 +10,41 @@ namespace gbcfd {
 // the kernel's dynamic shared-memory limit, set once per device (before any graph capture)
 // (a per-device bit set atomically: host threads may set up blocks concurrently, and setting the
 // attribute twice is harmless)
-template <typename T, bool VISC, int STAGE, bool CURVI, int TYV>
+template <typename T, bool VISC, int STAGE, bool CURVI, int TYV, bool PUSH = false>
 cudaError_t stage_attr() {
   static std::atomic<unsigned long long> done{0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 64 && ((done.load(std::memory_order_acquire) >> dev) & 1ull)) return cudaSuccess;
-  e = cudaFuncSetAttribute(stage_kernel<T, VISC, STAGE, CURVI, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(stage_kernel<T, VISC, STAGE, CURVI, TYV, PUSH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)Plan<T, VISC, CURVI, TYV>::bytes);
   if (e == cudaSuccess && dev < 64) done.fetch_or(1ull << dev, std::memory_order_acq_rel);
   return e;
 }
 
-template <typename T, bool VISC, int STAGE, bool CURVI, int TYV>
+template <typename T, bool VISC, int STAGE, bool CURVI, int TYV, bool PUSH = false>
 cudaError_t stage_go(const GroupParams& P, int grid, cudaStream_t s) {
-  cudaError_t e = stage_attr<T, VISC, STAGE, CURVI, TYV>();
+  cudaError_t e = stage_attr<T, VISC, STAGE, CURVI, TYV, PUSH>();
   if (e != cudaSuccess) return e;
-  stage_kernel<T, VISC, STAGE, CURVI, TYV><<<grid, tile_threads(TYV), Plan<T, VISC, CURVI, TYV>::bytes, s>>>(P);
+  stage_kernel<T, VISC, STAGE, CURVI, TYV, PUSH><<<grid, tile_threads(TYV), Plan<T, VISC, CURVI, TYV>::bytes, s>>>(P);
   return cudaGetLastError();
+}
+
+// stages 1 and 2 with the halo exchange folded in (Cartesian Euler groups); stage 3 has none
+template <typename T, int TYV>
+cudaError_t stage_dispatch_push(int stage, const GroupParams& P, int grid, cudaStream_t s) {
+  switch (stage) {
+    case 1: return stage_go<T, false, 1, false, TYV, true>(P, grid, s);
+    case 2: return stage_go<T, false, 2, false, TYV, true>(P, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+template <typename T, int TYV>
+cudaError_t stage_prepare_push() {
+  cudaError_t e = stage_attr<T, false, 1, false, TYV, true>();
+  if (e == cudaSuccess) e = stage_attr<T, false, 2, false, TYV, true>();
+  return e;
 }
 
 template <typename T, bool VISC, bool CURVI, int TYV>

@@ -82,7 +82,9 @@ SIGNATURES = {
     "gbcfd_group_step": [_VP, ctypes.c_int, _VP],
     "gbcfd_group_tune": [_VP, _VP, ctypes.POINTER(ctypes.c_int)],
     "gbcfd_group_tune_tile": [_VP, _VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
-    "gbcfd_group_set_schedule": [_VP, ctypes.c_int, ctypes.c_int, _VP],
+    "gbcfd_group_set_schedule": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP],
+    "gbcfd_group_get_schedule": [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int)],
     "gbcfd_group_set_timing": [_VP, ctypes.POINTER(_VP), ctypes.c_int],
     "gbcfd_accel_required_bytes": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
     "gbcfd_accel_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t,
@@ -372,10 +374,17 @@ class Group:
         self.tile_rows = t.value
         return c.value
 
-    def set_schedule(self, ctas_per_sm, tile_rows, stream=None):
-        """pin the tile height and grid split (gbcfd_group_set_schedule)"""
-        _check(lib().gbcfd_group_set_schedule(self.handle, int(ctas_per_sm), int(tile_rows), _stream(stream)))
+    def set_schedule(self, ctas_per_sm, tile_rows, halo_push=0, stream=None):
+        """pin the tile height, grid split and halo fold (gbcfd_group_set_schedule)"""
+        _check(lib().gbcfd_group_set_schedule(self.handle, int(ctas_per_sm), int(tile_rows), int(halo_push),
+                                              _stream(stream)))
         self.tile_rows = int(tile_rows)
+
+    def schedule(self):
+        """(ctas_per_sm, tile_rows, halo_push) in force (gbcfd_group_get_schedule)"""
+        c, t, p = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().gbcfd_group_get_schedule(self.handle, ctypes.byref(c), ctypes.byref(t), ctypes.byref(p)))
+        return c.value, t.value, p.value
 
     def set_timing(self, events):
         """events: 7 torch.cuda.Event(enable_timing=True) recorded inside every step (or None)"""

@@ -141,6 +141,7 @@ def solve(case, target=1e-6, accel_params=None, max_seconds=900.0, check=200, st
         acc = gbcfd.Accel(case.nx, case.ny, case.nz, 1, device=dev)
         acc.set_params(accel_params)
     g = gbcfd.Group([blk])
+    g.tune()  # grid split for this block (the timed region starts after it)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g.step(1)
@@ -181,6 +182,7 @@ def solve(case, target=1e-6, accel_params=None, max_seconds=900.0, check=200, st
             blk = gbcfd.block_for_case(case, precision=gbcfd.FP64, device=dev)
             blk.set_state(q)
             g = gbcfd.Group([blk])
+            g.tune()
             phase, best, since = "fp64", r, 0
     torch.cuda.synchronize()
     el = time.perf_counter() - t0

@@ -112,17 +112,19 @@ ALT_TILE = {0: 11, 1: 4}  # the second tile height compiled for Cartesian Euler 
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("tile_rows,ctas", [(8, 1), (8, 3), ("alt", 1), ("alt", 2), ("alt", 16)])
-def test_every_schedule_gives_the_same_bits(gb, precision, tile_rows, ctas):
+@pytest.mark.parametrize("tile_rows,ctas,push", [(8, 1, 0), (8, 3, 1), ("alt", 1, 1), ("alt", 2, 0), ("alt", 16, 1)])
+def test_every_schedule_gives_the_same_bits(gb, precision, tile_rows, ctas, push):
     """each tile shape the stage kernel is compiled for (32 x 8, and 32 x 11 FP64 / 32 x 4 mixed),
-    with several grid splits, advances the lattice (uneven blocks, ragged tiles in x and y) bit for
-    bit like gbcfd_step on the same blocks, both parities of the mixed path"""
+    with several grid splits and with the halo exchange of the stage outputs as launches or folded
+    into the stages, advances the lattice (uneven blocks, ragged tiles in x and y) bit for bit
+    like gbcfd_step on the same blocks, both parities of the mixed path"""
     ty = ALT_TILE[precision] if tile_rows == "alt" else tile_rows
     lat = small_lattice(seed=9)
     a = gb.blocks_for_lattice(lat, precision)
     b = gb.blocks_for_lattice(lat, precision)
     g = gb.Group(b)
-    g.set_schedule(ctas, ty)
+    g.set_schedule(ctas, ty, push)
+    assert g.schedule() == (ctas, ty, push)
     gb.step(a, 3)
     g.step(3)
     ga, gbb = gb.gather_lattice(lat, a), gb.gather_lattice(lat, b)
@@ -131,6 +133,24 @@ def test_every_schedule_gives_the_same_bits(gb, precision, tile_rows, ctas):
     rtol = 1e-12 if precision == 0 else 1e-6
     for x, y in zip(a, b):
         assert np.allclose(x.residual_norm(), y.residual_norm(), rtol=rtol, atol=0)
+    g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tiny_blocks_halo_push(gb, precision):
+    """a lattice of blocks 2 to 5 cells wide: stages 1 and 2 of the group fill the neighbours'
+    halos themselves (cells near two opposite faces push both ways; edge and corner cells into
+    the diagonal blocks) and must equal gbcfd_step, whose halos come from the halo kernel, bit
+    for bit over both parities of the mixed path"""
+    lat = small_lattice(seed=11, sizes=([2, 5, 3], [3, 2], [2, 4]))
+    a = gb.blocks_for_lattice(lat, precision)
+    b = gb.blocks_for_lattice(lat, precision)
+    g = gb.Group(b)
+    g.set_schedule(1, 8, 1)
+    gb.step(a, 4)
+    g.step(4)
+    ga, gbb = gb.gather_lattice(lat, a), gb.gather_lattice(lat, b)
+    assert torch.equal(ga, gbb), float((ga - gbb).abs().max())
     g.close()
 
 
@@ -143,6 +163,14 @@ def test_schedule_rejects_uncompiled_shapes(gb):
         g.set_schedule(0, 8)
     with pytest.raises(RuntimeError):
         g.set_schedule(17, 8)
+    g.close()
+    # a block with an unconnected face (a wall) cannot take the halo fold
+    c = cases.channel_case(40, 24, 6, height=0.1, mach=0.6)
+    blk = gb.block_for_case(c, precision=0)
+    g = gb.Group([blk])
+    g.set_schedule(1, 8, 0)
+    with pytest.raises(RuntimeError):
+        g.set_schedule(1, 8, 1)
     g.close()
 
 
