@@ -347,6 +347,18 @@ int gbcfd_accel_target(gbcfd_accel accel, gbcfd_block block, float* t, void* str
  * which; norms[0], norms[1] (host, may be NULL) get the two RMS values.  Synchronises. */
 int gbcfd_accel_try(gbcfd_accel accel, gbcfd_block block, void* stream, int* accepted, double norms[2]);
 
+/* One accelerated update with smoothing: the prediction scaled by alpha (0 < alpha <= 4) is applied
+ * (Q' = Q + alpha 20 s ref y), the time steps re-evaluated, and nsteps (0..1000) plain steps run
+ * from Q' (gbcfd_step); the result is kept when RMS(R_rho) then lies below min(ratio, 1) x RMS(R_rho(Q))
+ * -- the caller passes the factor the plain iteration achieved over nsteps steps lately, so a
+ * prediction is kept only if the residual drops and it beat the plain steps -- else the state, the
+ * local time steps and the control block (time step, norms, flags) are restored bit for bit, and
+ * the steps count for nothing.  The plain steps damp the small-scale error of the prediction that
+ * the bare test of gbcfd_accel_try sees first.  *accepted, norms as gbcfd_accel_try (norms[1]: after
+ * the steps).  Synchronises. */
+int gbcfd_accel_try_smooth(gbcfd_accel accel, gbcfd_block block, double alpha, int nsteps, double ratio,
+                           void* stream, int* accepted, double norms[2]);
+
 /* ---- the paper's own scheme: WCNS-E-5 on periodic uniform Cartesian blocks -------------------
  * Sec. 2.2: the inviscid derivative at a cell centre is Eq. 2, the sixth-order combination of the
  * flux differences at the cell edges i +- 1/2, i +- 3/2, i +- 5/2, each edge flux the Roe flux

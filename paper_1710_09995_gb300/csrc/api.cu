@@ -1487,6 +1487,8 @@ struct gbcfd_accel_s {
   bf16 *x, *a1, *a2, *dy, *dz1, *dz2;
   float *z1, *z2, *y;
   double *R, *qsave, *partial, *stats;
+  void* dtlsave;              // gbcfd_accel_try_smooth: the block's local time steps before the try
+  DevCtrl* ctrlsave;          // and its control block (time step, norms, flags)
   int pgrid;
   int step_count;
 };
@@ -1523,6 +1525,9 @@ static size_t accel_carve(int nx, int ny, int nz, int batch, int nsm, size_t* of
   take(22, sizeof(double) * NPART * kAccelParts);                      // partials
   take(23, sizeof(double) * 8);                                        // stats
   take(24, sizeof(int) * 4);                                           // timeout flag
+  take(25, sizeof(double) * (size_t)make_geometry(nx, ny, nz).field);   // saved local time steps (try_smooth;
+                                                                       // >= the f32 field's bytes)
+  take(26, sizeof(DevCtrl));                                           // saved control block (try_smooth)
   return o;
 }
 
@@ -1532,7 +1537,7 @@ extern "C" int gbcfd_accel_required_bytes(int nx, int ny, int nz, int batch, siz
   int dev = 0, nsm = 0;
   int rc = device_sms(&dev, &nsm);
   if (rc) return rc;
-  size_t off[25];
+  size_t off[27];
   *bytes = accel_carve(nx, ny, nz, batch, nsm, off);
   return GBCFD_OK;
 }
@@ -1550,7 +1555,7 @@ extern "C" int gbcfd_accel_create(int nx, int ny, int nz, int batch, int zperiod
   int dev = 0, nsm = 0;
   rc = device_sms(&dev, &nsm);
   if (rc) return rc;
-  size_t off[25];
+  size_t off[27];
   accel_carve(nx, ny, nz, batch, nsm, off);
   char* base = static_cast<char*>(dev_mem);
   gbcfd_accel a = new gbcfd_accel_s();
@@ -1585,6 +1590,8 @@ extern "C" int gbcfd_accel_create(int nx, int ny, int nz, int batch, int zperiod
   a->partial = reinterpret_cast<double*>(base + off[22]);
   a->stats = reinterpret_cast<double*>(base + off[23]);
   n.flag = reinterpret_cast<int*>(base + off[24]);
+  a->dtlsave = base + off[25];
+  a->ctrlsave = reinterpret_cast<DevCtrl*>(base + off[26]);
   a->pgrid = (int)std::min<size_t>(kAccelParts, (size_t)4 * nsm);
   a->step_count = 0;
   cudaError_t e = cudaMemset(base, 0, off[11]);  // parameters, moments, packed weights: zero
@@ -1824,6 +1831,63 @@ extern "C" int gbcfd_accel_try(gbcfd_accel a, gbcfd_block b, void* stream, int* 
     CK(learn::launch_apply(v, a->y, a->qsave, a->stats, 1, s));
   }
   CK(cudaStreamSynchronize(s));
+  *accepted = keep ? 1 : 0;
+  if (norms) { norms[0] = r0; norms[1] = r1; }
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_accel_try_smooth(gbcfd_accel a, gbcfd_block b, double alpha, int nsteps, double ratio,
+                                      void* stream, int* accepted, double norms[2]) {
+  if (!a || !accepted) return fail(GBCFD_ERR_ARG, "NULL argument");
+  if (!(alpha > 0.0) || !(alpha <= 4.0)) return fail(GBCFD_ERR_ARG, "alpha must be in (0, 4]");
+  if (nsteps < 0 || nsteps > 1000) return fail(GBCFD_ERR_ARG, "nsteps must be 0..1000");
+  if (!(ratio > 0.0)) return fail(GBCFD_ERR_ARG, "ratio must be positive");
+  if (ratio > 1.0) ratio = 1.0;  // kept only if the residual drops
+  learn::BlockView v;
+  int rc = accel_view(a, b, &v);
+  if (rc) return rc;
+  if (a->batch != 1) return fail(GBCFD_ERR_ARG, "an accelerator for one volume is needed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the local time steps: one padded field in the path's flux type (f32 rows have their own pitch)
+  const size_t dtl_bytes = b->p.precision == GBCFD_MIXED ? sizeof(float) * (size_t)b->g.fieldf
+                                                         : sizeof(double) * (size_t)b->g.field;
+  // what the plain steps change besides the state: the control block and the local time steps
+  CK(cudaMemcpyAsync(a->ctrlsave, b->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToDevice, s));
+  if (b->dtl) CK(cudaMemcpyAsync(a->dtlsave, b->dtl, dtl_bytes, cudaMemcpyDeviceToDevice, s));
+  rc = accel_residual_stats(a, b, v, 0, s);
+  if (rc) return rc;
+  CK(learn::launch_features(v, a->R, a->stats, a->x, a->qsave, s));
+  rc = accel_forward(a, a->x, a->y, false, s);
+  if (rc) return rc;
+  CK(learn::launch_apply(v, a->y, a->qsave, a->stats, 0, s, alpha));
+  rc = init_rate(b, s);  // time steps of the predicted state
+  if (!rc && nsteps > 0) rc = gbcfd_step(&b, 1, nsteps, stream);
+  learn::BlockView w;  // the state's buffers after the steps (the mixed path alternates them)
+  if (!rc) rc = accel_view(a, b, &w);
+  if (!rc) rc = accel_residual_stats(a, b, w, 2, s);
+  int frc = accel_flag(a, s);
+  DevCtrl h;
+  if (!rc) {
+    CK(cudaMemcpyAsync(&h, b->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
+  }
+  double st[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(st, a->stats, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double n = (double)b->nx * b->ny * b->nz;
+  const double r0 = std::sqrt(st[1] / n), r1 = std::sqrt(st[3] / n);
+  const bool keep = !rc && !frc && h.flag == 0 && std::isfinite(r1) && r1 < ratio * r0;
+  if (!keep) {  // the state, time steps and control block back, bit for bit
+    if (rc) {   // a failure inside: the views may be stale, take the block's own
+      learn::BlockView u;
+      if (accel_view(a, b, &u) == GBCFD_OK) w = u; else w = v;
+    }
+    CK(learn::launch_apply(w, a->y, a->qsave, a->stats, 1, s));
+    if (b->dtl) CK(cudaMemcpyAsync(b->dtl, a->dtlsave, dtl_bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(b->ctrl, a->ctrlsave, sizeof(DevCtrl), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (rc) return rc;
+  if (frc) return frc;
   *accepted = keep ? 1 : 0;
   if (norms) { norms[0] = r0; norms[1] = r1; }
   return GBCFD_OK;

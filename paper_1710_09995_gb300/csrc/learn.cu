@@ -332,11 +332,11 @@ cudaError_t launch_features(const BlockView& v, const double* R, const double* s
   return cudaGetLastError();
 }
 
-// Q = Q_saved + K s ref y (or Q_saved when revert), into the padded state and its f32 shadow
+// Q = Q_saved + alpha K s ref y (or Q_saved when revert), into the padded state and its f32 shadow
 __global__ void apply_kernel(BlockView v, const float* __restrict__ y, const double* __restrict__ qsave,
-                             const double* __restrict__ stats, int revert) {
+                             const double* __restrict__ stats, int revert, double alpha) {
   const long long n = (long long)v.nx * v.ny * v.nz;
-  const double s = sqrt(stats[0] / (5.0 * (double)n));
+  const double s = alpha * sqrt(stats[0] / (5.0 * (double)n));
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(c % v.nx);
     const long long r = c / v.nx;
@@ -352,11 +352,11 @@ __global__ void apply_kernel(BlockView v, const float* __restrict__ y, const dou
   }
 }
 cudaError_t launch_apply(const BlockView& v, const float* y, const double* qsave, const double* stats, int revert,
-                         cudaStream_t s) {
+                         cudaStream_t s, double alpha) {
   const long long n = (long long)v.nx * v.ny * v.nz;
   long long grid = (n + 255) / 256;
   if (grid > 65535LL * 8) grid = 65535LL * 8;
-  apply_kernel<<<(unsigned)grid, 256, 0, s>>>(v, y, qsave, stats, revert);
+  apply_kernel<<<(unsigned)grid, 256, 0, s>>>(v, y, qsave, stats, revert, alpha);
   return cudaGetLastError();
 }
 

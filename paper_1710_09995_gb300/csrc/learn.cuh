@@ -79,7 +79,7 @@ cudaError_t launch_feature_stats(const BlockView& v, const double* R, double* pa
 cudaError_t launch_features(const BlockView& v, const double* R, const double* stats, __nv_bfloat16* x,
                             double* qsave, cudaStream_t s);
 cudaError_t launch_apply(const BlockView& v, const float* y, const double* qsave, const double* stats, int revert,
-                         cudaStream_t s);
+                         cudaStream_t s, double alpha = 1.0);
 cudaError_t launch_target(const BlockView& v, const double* qsave, const double* stats, float* t, cudaStream_t s);
 
 }  // namespace learn

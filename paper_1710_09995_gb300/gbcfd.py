@@ -99,6 +99,8 @@ SIGNATURES = {
     "gbcfd_accel_features": [_VP, _VP, _VP, _VP],
     "gbcfd_accel_target": [_VP, _VP, _VP, _VP],
     "gbcfd_accel_try": [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_int), _D],
+    "gbcfd_accel_try_smooth": [_VP, _VP, ctypes.c_double, ctypes.c_int, ctypes.c_double, _VP,
+                               ctypes.POINTER(ctypes.c_int), _D],
     "gbcfd_wcns_required_bytes": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params),
                                   ctypes.POINTER(ctypes.c_size_t)],
     "gbcfd_wcns_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params), _D, _VP, ctypes.c_size_t,
@@ -518,6 +520,15 @@ class Accel:
         norms = np.zeros(2)
         _check(lib().gbcfd_accel_try(self.handle, block.handle, _stream(stream), ctypes.byref(acc),
                                      norms.ctypes.data_as(_D)))
+        return bool(acc.value), float(norms[0]), float(norms[1])
+
+    def try_smooth(self, block, alpha, nsteps, ratio, stream=None):
+        """prediction x alpha, nsteps plain steps, kept only below min(ratio, 1) x the residual before
+        (gbcfd_accel_try_smooth); returns (accepted, rms R_rho before, after)"""
+        acc = ctypes.c_int(0)
+        norms = np.zeros(2)
+        _check(lib().gbcfd_accel_try_smooth(self.handle, block.handle, float(alpha), int(nsteps), float(ratio),
+                                            _stream(stream), ctypes.byref(acc), norms.ctypes.data_as(_D)))
         return bool(acc.value), float(norms[0]), float(norms[1])
 
     def close(self):

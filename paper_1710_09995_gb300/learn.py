@@ -121,17 +121,24 @@ def _norm(blk):
 
 
 def solve(case, target=1e-6, accel_params=None, max_seconds=900.0, check=200, stall_checks=50,
-          precision="hybrid", device=None, log=None):
+          precision="hybrid", device=None, log=None, smooth=0, alpha=0.5, alpha_min=0.125):
     """Pseudo-time iteration of a steady case to RMS(R_rho) <= target x its initial value.
 
     precision: "fp64" (the plain FP64 iteration), "mixed" (mixed path only; it stalls where the
     Runge-Kutta increments fall below the FP32 resolution of the state, around 1e-5 on the bump
     channel) or "hybrid" (mixed until the density residual has not improved by 10% over
-    `stall_checks` checks, then the FP64 path from that state).  Below its floor the mixed
+    `stall_checks` checks, or has reached the target, then the FP64 path from that state until the
+    FP64 residual confirms the target).  Below its floor the mixed
     iteration still converges the smooth part of the solution (its residual norm is FP32 noise
     there), so a late switch leaves the FP64 path little more than that noise to remove.
-    accel_params: network parameters; when given, every `check` steps a prediction is tried
-    (kept only if the residual drops; a kept one is followed by another try).
+    accel_params: network parameters; when given, every `check` steps a prediction is tried (in the
+    mixed phase of a hybrid solve; its FP64 finish runs the plain iteration).
+    smooth = 0: the bare test (gbcfd_accel_try: kept only if the residual of the predicted state is
+    lower; a kept one is followed by another try).  smooth = m > 0: the prediction scaled by alpha
+    is followed by m plain steps and kept only if the residual then lies below min(1, rate^m) times
+    its value before, rate the plain iteration's per-step factor over the last `check` steps
+    (gbcfd_accel_try_smooth); alpha grows (x1.5, up to 1) after a kept try and halves (down to
+    alpha_min) after a rejected one.
     Returns a dict with the wall time, steps, predictions tried/kept and the history."""
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     prec = gbcfd.FP64 if precision == "fp64" else gbcfd.MIXED
@@ -151,11 +158,25 @@ def solve(case, target=1e-6, accel_params=None, max_seconds=900.0, check=200, st
     best, since = 1.0, 0
     phase = "fp64" if prec == gbcfd.FP64 else "mixed"
     r = 1.0
+    r_prev = 1.0
     while True:
         g.step(check)
         steps += check
         r = _norm(blk) / r0
-        if acc is not None:
+        r_plain = r  # the stall test watches the plain steps' norm, not a kept try's fresh residual
+        try_now = acc is not None and (precision != "hybrid" or phase == "mixed")  # the FP64 finish runs plain
+        if try_now and smooth > 0:
+            rate = (r / r_prev) ** (1.0 / check) if r_prev > 0 and r > 0 else 1.0
+            ok, _, r1 = acc.try_smooth(blk, alpha, smooth, min(1.0, rate ** smooth))
+            tried += 1
+            if ok:
+                kept += 1
+                steps += smooth
+                r = r1 / r0
+                alpha = min(1.0, 1.5 * alpha)
+            else:
+                alpha = max(alpha_min, 0.5 * alpha)
+        elif try_now:
             while True:
                 ok, _, r1 = acc.try_update(blk)
                 tried += 1
@@ -165,17 +186,21 @@ def solve(case, target=1e-6, accel_params=None, max_seconds=900.0, check=200, st
                 r = r1 / r0
                 if r <= target:
                     break
+        r_prev = r
         el = time.perf_counter() - t0
         hist.append((round(el, 3), steps, r, phase))
         if log and len(hist) % 50 == 0:
             log(f"{phase} {steps} steps {el:.1f} s drop {r:.3e} kept {kept}/{tried}")
-        if r <= target or el > max_seconds or not math.isfinite(r):
+        # a hybrid solve is done only when the FP64 path confirms the drop: reaching it on the mixed
+        # path's FP32 residual switches to the FP64 path like a stall does
+        mixed_phase = precision == "hybrid" and phase == "mixed"
+        if (r <= target and not mixed_phase) or el > max_seconds or not math.isfinite(r):
             break
-        if r < 0.9 * best:
-            best, since = r, 0
+        if r_plain < 0.9 * best:
+            best, since = r_plain, 0
         else:
             since += 1
-        if precision == "hybrid" and phase == "mixed" and since >= stall_checks:
+        if mixed_phase and (since >= stall_checks or r <= target):
             q = blk.get_state()
             g.close()
             blk.close()
@@ -187,7 +212,8 @@ def solve(case, target=1e-6, accel_params=None, max_seconds=900.0, check=200, st
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     out = {"seconds": el, "steps": steps, "drop": r, "reached": bool(r <= target), "tried": tried, "kept": kept,
-           "precision": precision, "accelerated": acc is not None, "history": hist[:: max(1, len(hist) // 60)]}
+           "precision": precision, "accelerated": acc is not None, "smooth": smooth,
+           "history": hist[:: max(1, len(hist) // 60)]}
     g.close()
     blk.close()
     return out

@@ -264,3 +264,31 @@ def test_try_keeps_or_restores(gb, precision):
         assert torch.equal(blk.get_state(), twin.get_state())
     gb.step([blk], 2)
     assert np.all(np.isfinite(blk.residual_norm()))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("nsteps", [3, 4])
+def test_try_smooth_keeps_or_restores(gb, precision, nsteps):
+    """a smoothed try (prediction x alpha, then plain steps) that misses its bar leaves the block bit
+    for bit as it was -- state, norms, time steps -- so it steps on exactly like its untouched twin
+    (odd step counts swap the mixed path's state buffers inside the try); one that meets it is kept
+    exactly when the residual fell below the bar"""
+    c = channel(seed=5)
+    blk = gb.block_for_case(c, precision=precision)
+    twin = gb.block_for_case(c, precision=precision)
+    gb.step([blk], 3)
+    gb.step([twin], 3)
+    a = gb.Accel(c.nx, c.ny, c.nz)
+    a.set_params(random_params(8, scale=0.05))
+    before, n_before, dt_before = blk.get_state().clone(), blk.residual_norm(), blk.get_dt()
+    kept, r0, r1 = a.try_smooth(blk, 0.5, nsteps, 1e-9)  # a bar no try can meet
+    assert not kept and np.isfinite(r1)
+    assert torch.equal(blk.get_state(), before)
+    assert np.array_equal(blk.residual_norm(), n_before) and blk.get_dt() == dt_before
+    gb.step([blk], 2)
+    gb.step([twin], 2)
+    assert torch.equal(blk.get_state(), twin.get_state())
+    kept, r0, r1 = a.try_smooth(blk, 0.5, nsteps, 1.0)
+    assert kept == (r1 < r0)
+    gb.step([blk], 2)
+    assert np.all(np.isfinite(blk.residual_norm()))
