@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--no-channel", action="store_true",
                     help="lattice96: skip the bump channel's time-to-drop key (the longest part of the run)")
     ap.add_argument("--no-vortex", action="store_true", help="lattice96: skip the 256^3 vortex key")
+    ap.add_argument("--schedule", default=None,
+                    help="lattice96: pin the groups' schedule 'ctas_per_sm,tile_rows,halo_push' instead of tuning "
+                         "(profiling runs: no tuner launches before the steps)")
     ap.add_argument("--lattice-div", type=int, default=1,
                     help="lattice96: divide every block side by this (same recipe, fewer cells: profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -231,14 +234,23 @@ def time_path(gbcfd, torch, case, precision, steps, warmup, world, device):
     return {"ms": ms, "stage_ms": stage_ms, "halo_ms": halo_ms, "launches": 6 * steps, "norms": norms.tolist()}
 
 
-def time_group_path(gbcfd, torch, lat, precision, steps, warmup, world, device):
+def schedule_group(g, schedule):
+    """the tuner's choice, or the pinned 'ctas_per_sm,tile_rows,halo_push'; returns CTAs per SM"""
+    if not schedule:
+        return g.tune()
+    c, t, p = (int(x) for x in schedule.split(","))
+    g.set_schedule(c, t, p)
+    return c
+
+
+def time_group_path(gbcfd, torch, lat, precision, steps, warmup, world, device, schedule=None):
     """The lattice as one group: per step one CUDA graph (time step, then halo exchange and one
     stage launch for all blocks, three times).  Seven events recorded inside the graph time each
     stage kernel; the stream is synchronised after every step to read them (the host gap this
     leaves is inside the timed region)."""
     blocks = gbcfd.blocks_for_lattice(lat, gbcfd.MIXED if precision == "mixed" else gbcfd.FP64, device)
     g = gbcfd.Group(blocks)
-    ctas_per_sm = g.tune()
+    ctas_per_sm = schedule_group(g, schedule)
     marks = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
     g.set_timing(marks)
     stream = torch.cuda.current_stream()
@@ -271,7 +283,7 @@ def time_group_path(gbcfd, torch, lat, precision, steps, warmup, world, device):
             "halo": "folded into stages 1-2" if halo_push else "launch per stage", "blocks": len(blocks)}
 
 
-def e2e_group_path(gbcfd, torch, lat, precision, steps, world, device, pipelined=True):
+def e2e_group_path(gbcfd, torch, lat, precision, steps, world, device, pipelined=True, schedule=None):
     """Through the C ABI with pinned host buffers, every step uploading each block's state,
     advancing the group one SSP-RK3 step and reading back every block's state and residual norms:
     the value is per-block set_state, one group step and per-block get_state / residual_norm calls,
@@ -286,7 +298,7 @@ def e2e_group_path(gbcfd, torch, lat, precision, steps, world, device, pipelined
     # serial calls
     blocks = gbcfd.blocks_for_lattice(lat, prec, device)
     g = gbcfd.Group(blocks)
-    g.tune()
+    schedule_group(g, schedule)
     host_in = [h.pin_memory() for h in parts]
     host_out = [torch.empty_like(h).pin_memory() for h in host_in]
 
@@ -326,7 +338,7 @@ def e2e_group_path(gbcfd, torch, lat, precision, steps, world, device, pipelined
     groups = []
     for _ in range(3):
         gg = gbcfd.Group(gbcfd.blocks_for_lattice(lat, prec, device))
-        gg.tune()
+        schedule_group(gg, schedule)
         groups.append(gg)
     pipe = gbcfd.Pipe(groups)
     outs = [torch.empty_like(item).pin_memory() for _ in range(2)]
@@ -687,11 +699,13 @@ def run_lattice(args, world, rank, local, device, torch, cases, gbcfd):
     peak, peak_kind = hbm_peak()
     clocks = ClockSampler(local)
     clocks.start()
-    results = {p: time_group_path(gbcfd, torch, lat, p, args.steps, args.warmup, world, device) for p in paths}
+    results = {p: time_group_path(gbcfd, torch, lat, p, args.steps, args.warmup, world, device, args.schedule)
+               for p in paths}
     clk = clocks.stop()
     head = paths[0]
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else (3 if head == "fp64" else 20)
-    e2e = e2e_group_path(gbcfd, torch, lat, head, e2e_steps, world, device, pipelined=head == "mixed")
+    e2e = e2e_group_path(gbcfd, torch, lat, head, e2e_steps, world, device, pipelined=head == "mixed",
+                         schedule=args.schedule)
     cpu = cpu_baseline_lattice() if rank == 0 and world == 1 and not args.no_cpu_baseline else None
     cells = lat.cells
     del lat
