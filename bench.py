@@ -964,7 +964,21 @@ def wcns_roofline(precision, res, cells, steps, peak, peak_kind):
             "avg_launch_ms": round(res["kernel_ms"][name] / (3 * steps), 4),
             "share_of_step": round(res["kernel_ms"][name] / max(res["ms"], 1e-9), 4),
             "kernels_ms_per_step": {n: round(v / steps, 4) for n, v in res["kernel_ms"].items()},
-            "dominant_ms_per_stage": [round(v / steps, 4) for v in res["kernel_stage_ms"][name]]}
+            "dominant_ms_per_stage": [round(v / steps, 4) for v in res["kernel_stage_ms"][name]],
+            "step": wcns_step_roofline(precision, res, cells, steps, peak)}
+
+
+def wcns_step_roofline(precision, res, cells, steps, peak):
+    """the whole WCNS step against HBM: the method's FP64-state minimum (ALGO_BYTES, 320 B per
+    cell-step, as for the block path) and the bytes the path's five kernels move by design (every
+    kernel of every stage, wcns_kernel_bytes) over the step's wall time"""
+    sec = res["ms"] / 1e3
+    algo = sum(ALGO_BYTES) * cells * steps
+    design = sum(sum(wcns_kernel_bytes(precision, st).values()) for st in (1, 2, 3)) * cells * steps
+    return {"achieved": round(algo / sec / 1e9, 1), "frac": round(algo / sec / 1e9 / peak, 4),
+            "algorithmic_bytes_per_cell_step": sum(ALGO_BYTES),
+            "design_bytes_per_cell_step": design / (cells * steps),
+            "design_achieved": round(design / sec / 1e9, 1), "design_frac": round(design / sec / 1e9 / peak, 4)}
 
 
 def e2e_wcns(gbcfd, torch, case, precision, steps, world, device):

@@ -51,3 +51,17 @@ def test_fp64_alu_peak_and_roofline():
     if r["achieved"] is not None:
         total = sum(r["flops_per_cell"]) * 1000
         assert abs(r["achieved"] - round(total / 3e-3 / 1e12, 4)) < 1e-9
+
+
+def test_wcns_step_roofline():
+    """the WCNS step's figure divides the method's 320 B per cell-step, and the bytes its five
+    kernels move by design, by the step's wall time"""
+    cells, steps, ms = 1000, 2, 4.0
+    res = {"ms": ms}
+    r = bench.wcns_step_roofline("mixed", res, cells, steps, 1000.0)
+    assert r["algorithmic_bytes_per_cell_step"] == 320
+    assert abs(r["achieved"] - round(320 * cells * steps / 4e-3 / 1e9, 1)) < 1e-9
+    design = sum(sum(bench.wcns_kernel_bytes("mixed", st).values()) for st in (1, 2, 3))
+    assert r["design_bytes_per_cell_step"] == design
+    # mixed: prim 44/64/64, viscres 32, x 56, y 60, z 60/80/160 bytes per cell
+    assert design == (20 + 24) + (40 + 24) * 2 + 3 * (32 + 56 + 60 + 40) + 20 + 40 + 120
