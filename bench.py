@@ -459,17 +459,25 @@ def roofline(precision, res, cells, steps, peak, peak_kind, workload="vortex256"
 
 def fp64_alu_roofline(res, cells, steps, hbm, workload="vortex256"):
     """FP64-pipe roofline of the FP64 stage kernel: its FP64 flops per cell (2 DFMA + DADD + DMUL,
-    counted by ncu per stage) over the launch time, against the part's FP64 peak"""
+    counted by ncu per stage) over the launch time, against the part's FP64 peak; and the share of
+    the pipe's lane slots its FP64 instructions fill (DADD + DMUL + DFMA per cell against 152 SMs x
+    2 lanes x the clock)"""
     flops = profiled_numbers("fp64", "fp64 flops per cell and stage", workload)
     out = {"bound": "alu", "kernel": "stage_kernel", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
            "peak_kind": "FP64 FMA lanes x clock (152 SMs x 2 x 2 flops x 2.07 GHz; 1.2556 measured)",
            "avg_launch_ms": hbm["avg_launch_ms"],
            "traffic": hbm["traffic"], "hbm_frac": hbm["frac"]}
+    ops = profiled_numbers("fp64", "fp64 ops per cell and stage", workload)
     if flops:
+        sec = sum(res["stage_ms"].values()) / 1e3
         total = sum(flops[s - 1] * cells * steps for s in (1, 2, 3))
-        achieved = total / (sum(res["stage_ms"].values()) / 1e3) / 1e12
+        achieved = total / sec / 1e12
         out.update({"achieved": round(achieved, 4), "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
                     "flops_per_cell": flops})
+        if ops:  # a DADD or DMUL fills an FMA lane slot for one flop: the pipe's own utilisation
+            nops = sum(ops[s - 1] * cells * steps for s in (1, 2, 3))
+            out.update({"lane_slot_frac": round(nops / sec / (FP64_PEAK_TFLOPS / 2 * 1e12), 4),
+                        "ops_per_cell": ops})
     else:
         out.update({"achieved": None, "frac": None})
     return out

@@ -51,6 +51,10 @@ def test_fp64_alu_peak_and_roofline():
     if r["achieved"] is not None:
         total = sum(r["flops_per_cell"]) * 1000
         assert abs(r["achieved"] - round(total / 3e-3 / 1e12, 4)) < 1e-9
+    if r.get("lane_slot_frac") is not None:  # one lane slot per DADD, DMUL or DFMA
+        nops = sum(r["ops_per_cell"]) * 1000
+        assert abs(r["lane_slot_frac"] - round(nops / 3e-3 / (bench.FP64_PEAK_TFLOPS / 2 * 1e12), 4)) < 1e-9
+        assert r["lane_slot_frac"] > r["frac"]
 
 
 def test_wcns_step_roofline():
