@@ -370,8 +370,10 @@ int gbcfd_accel_try_smooth(gbcfd_accel accel, gbcfd_block block, double alpha, i
  * with candidates u_i + g_k/2 + s_k/8 (g_k, s_k the stencil's first and second differences),
  * smoothness g_k^2 + s_k^2, weights C_k / (1e-6 + smoothness)^2 normalised, C = (1/16, 10/16,
  * 5/16); the right state at i + 1/2 from the mirrored stencil.  Time stepping as gbcfd_step
- * (Eqs. 4-6, lambda = -dt, the global CFL step of Q^n).  Every direction is periodic (the block
- * is its own neighbour; its 5-cell halo is filled by index wrap) and the grid uniform.
+ * (Eqs. 4-6, lambda = -dt, the global CFL step of Q^n).  A block on its own is periodic in every
+ * direction (its own neighbour; its 5-cell halo is filled by index wrap); blocks connected face
+ * to face (gbcfd_wcns_connect) form a periodic multi-block lattice advanced together by
+ * gbcfd_wcns_step_many (Sec. 2.2's multi-block interfaces, uniform Cartesian grids).
  * params: as for blocks; `limiter` 0 takes the nonlinear weights, 1 the optimal linear ones
  * (linear fifth-order interpolation); `precision` GBCFD_MIXED evaluates the interpolation, the
  * fluxes and the derivatives in FP32 (state and update in FP64); `local_dt` must be 0. */
@@ -401,8 +403,31 @@ int gbcfd_wcns_get_state(gbcfd_wcns block, double* q, void* stream);
 /* R(Q) of Eq. 3 for the current state into r[5][nz][ny][nx] float64 (device pointer). */
 int gbcfd_wcns_compute_residual(gbcfd_wcns block, double* r, void* stream);
 
-/* nsteps SSP-RK3 steps; asynchronous, device errors reported by gbcfd_wcns_residual_norm. */
+/* nsteps SSP-RK3 steps; asynchronous, device errors reported by gbcfd_wcns_residual_norm.
+ * GBCFD_ERR_STATE for a block connected to other blocks (they advance with
+ * gbcfd_wcns_step_many; gbcfd_wcns_compute_residual refuses such a block too). */
 int gbcfd_wcns_step(gbcfd_wcns block, int nsteps, void* stream);
+
+/* Connect face `face` of block a (0..5 = -x, +x, -y, +y, -z, +z) to block b: a's cells beyond
+ * that face are b's first cells across b's opposite face, and the link is recorded both ways
+ * (a == b makes that direction periodic).  The two blocks must match in the face's two
+ * directions and share parameters and cell sizes (GBCFD_ERR_ARG otherwise).  Destroying a block
+ * removes the links to it. */
+int gbcfd_wcns_connect(gbcfd_wcns a, int face, gbcfd_wcns b);
+
+/* nsteps SSP-RK3 steps of the n (1..32) blocks blocks[0..n-1] together, on one stream: every
+ * stage first forms each block's primitives over its 5-cell halo from the stage inputs of the
+ * blocks that own the halo cells (face neighbours walked along z, y and x, so edges and corners
+ * come from the diagonal blocks and neighbours thinner than the halo are crossed), then each
+ * block's viscous and direction passes; the time step is cfl / the largest CFL rate of Q^n over
+ * all the blocks, the same in every block.  Results equal one periodic block holding the whole
+ * lattice (the same arithmetic on the same values).  Requirements (GBCFD_ERR_ARG otherwise):
+ * every face of every block connected to a block of the list (a lone unconnected block counts
+ * as periodic), the blocks form a conforming lattice (face walks along two different axes reach
+ * the same block in either order), and share device, parameters and cell sizes; every block has
+ * a state (GBCFD_ERR_STATE).  Asynchronous; each block's norms and time step are read with
+ * gbcfd_wcns_residual_norm / gbcfd_wcns_get_dt. */
+int gbcfd_wcns_step_many(const gbcfd_wcns* blocks, int n, int nsteps, void* stream);
 
 /* RMS per component of R(Q^n) of the last step's stage 1, to out[5] on the host (synchronises;
  * GBCFD_ERR_NONPHYSICAL if rho <= 0 or p <= 0 was met since the last call). */

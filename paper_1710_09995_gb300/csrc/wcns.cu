@@ -126,8 +126,49 @@ __device__ __forceinline__ void load_conserved<float>(const Args& a, long long c
   for (int m = 0; m < 5; ++m) U[m] = a.din ? a.sh[m * a.n + c] + a.din[m * a.n + c] : a.sh[m * a.n + c];
 }
 
+// blocks advanced together (gbcfd_wcns_step_many): each member's stage-input arrays, sizes and
+// face neighbours (indices into the table; the faces of a conforming periodic lattice, Sec. 2.2's
+// multi-block interfaces), so that a member's halo cells are read from the block that owns them
+constexpr int MAXW = 32;
+struct WSrc {
+  const double* q[3];       // FP64: Q^n, Q1, Q2.  mixed: q[0] = Q^n
+  const float* sh;          // mixed: S^n
+  const float* d[2];        // mixed: D1, D2
+  DevCtrl* ctrl;
+  int nx, ny, nz, pad;
+  int nbr[6];               // -x, +x, -y, +y, -z, +z
+};
+struct WTab {
+  WSrc e[MAXW];
+  int n, self;              // members; the launching block's own index
+};
+static_assert(sizeof(Args) + sizeof(int) + sizeof(WTab) <= 4096, "prim_multi_kernel's parameters exceed 4 KB");
+
+// the conserved state of cell c of member s of the table at a stage (as load_conserved)
 template <typename T>
-__global__ void __launch_bounds__(NTW) prim_kernel(Args a, int with_rate) {
+__device__ __forceinline__ void load_member(const WSrc& s, int stage, long long c, T* U);
+template <>
+__device__ __forceinline__ void load_member<double>(const WSrc& s, int stage, long long c, double* U) {
+  const long long n = (long long)s.nx * s.ny * s.nz;
+  const double* q = stage <= 1 ? s.q[0] : s.q[stage - 1];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) U[m] = q[m * n + c];
+}
+template <>
+__device__ __forceinline__ void load_member<float>(const WSrc& s, int stage, long long c, float* U) {
+  const long long n = (long long)s.nx * s.ny * s.nz;
+  const float* din = stage == 2 ? s.d[0] : (stage == 3 ? s.d[1] : nullptr);
+#pragma unroll
+  for (int m = 0; m < 5; ++m) U[m] = din ? s.sh[m * n + c] + din[m * n + c] : s.sh[m * n + c];
+}
+
+// primitives of the padded box (and, with_rate, the CFL rate of Q^n over the interior).  The
+// source of padded cell (i, j, k): one block wraps its own indices (periodic); a member of a
+// table walks face neighbours along z, then y, then x, so edge and corner halos come from the
+// diagonal block (in a conforming lattice every order of the walk reaches the same block), and
+// a neighbour thinner than the halo is crossed to the next one.
+template <typename T, bool MULTI>
+__device__ __forceinline__ void prim_body(const Args& a, int with_rate, const WTab* tab) {
   __shared__ double wmax[NTW / 32];
   __shared__ int last;
   const Box& b = a.b;
@@ -142,14 +183,36 @@ __global__ void __launch_bounds__(NTW) prim_kernel(Args a, int with_rate) {
   for (int row = blockIdx.x; row < wy * wz; row += gridDim.x) {  // rows (j, k) of the padded box
     const int jj = row % wy, kk = row / wy;
     const int j = jj - H, k = kk - H;
-    const int sj = wrap(j, b.ny), sk = wrap(k, b.nz);
-    const long long src = ((long long)sk * b.ny + sj) * b.nx;
+    int sj, sk, rb = 0;
+    if constexpr (MULTI) {  // the row's block: walk z, then y
+      rb = tab->self;
+      sk = k;
+      while (sk < 0) { rb = tab->e[rb].nbr[4]; sk += tab->e[rb].nz; }
+      while (sk >= tab->e[rb].nz) { sk -= tab->e[rb].nz; rb = tab->e[rb].nbr[5]; }
+      sj = j;
+      while (sj < 0) { rb = tab->e[rb].nbr[2]; sj += tab->e[rb].ny; }
+      while (sj >= tab->e[rb].ny) { sj -= tab->e[rb].ny; rb = tab->e[rb].nbr[3]; }
+    } else {
+      sj = wrap(j, b.ny);
+      sk = wrap(k, b.nz);
+    }
     T* dst = W + ((long long)kk * wy + jj) * b.px;
-    const bool inner_row = j == sj && k == sk;
+    const bool inner_row = j == sj && k == sk && (!MULTI || rb == tab->self);
     for (int ii = threadIdx.x; ii < wx; ii += NTW) {
-      const int i = ii - H, si = wrap(i, b.nx);
+      const int i = ii - H;
       T U[5];
-      load_conserved<T>(a, src + si, U);
+      int si;
+      if constexpr (MULTI) {
+        int cb = rb;
+        si = i;
+        while (si < 0) { cb = tab->e[cb].nbr[0]; si += tab->e[cb].nx; }
+        while (si >= tab->e[cb].nx) { si -= tab->e[cb].nx; cb = tab->e[cb].nbr[1]; }
+        const WSrc& e = tab->e[cb];
+        load_member<T>(e, a.stage, ((long long)sk * e.ny + sj) * e.nx + si, U);
+      } else {
+        si = wrap(i, b.nx);
+        load_conserved<T>(a, ((long long)sk * b.ny + sj) * b.nx + si, U);
+      }
       const T rho = U[0], ir = T(1) / rho;
       const T u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
       const T p = gm1 * (U[4] - half * rho * (u * u + v * v + w * w));
@@ -195,6 +258,27 @@ __global__ void __launch_bounds__(NTW) prim_kernel(Args a, int with_rate) {
     a.ctrl->rate = m;
     a.ctrl->dt = a.cfl / m;
     a.ctrl->counter = 0u;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTW) prim_kernel(Args a, int with_rate) {
+  prim_body<T, false>(a, with_rate, nullptr);
+}
+template <typename T>
+__global__ void __launch_bounds__(NTW) prim_multi_kernel(Args a, int with_rate, const __grid_constant__ WTab tab) {
+  prim_body<T, true>(a, with_rate, &tab);
+}
+
+// the common time step of blocks advanced together: cfl / the largest of their rates, written
+// to every member (after each member's stage-1 primitive pass has reduced its own rate)
+__global__ void wcns_group_dt_kernel(const __grid_constant__ WTab tab, double cfl) {
+  if (threadIdx.x != 0) return;
+  double m = 0.0;
+  for (int b = 0; b < tab.n; ++b) m = fmax(m, tab.e[b].ctrl->rate);
+  for (int b = 0; b < tab.n; ++b) {
+    tab.e[b].ctrl->rate = m;
+    tab.e[b].ctrl->dt = cfl / m;
   }
 }
 
@@ -826,6 +910,7 @@ struct gbcfd_wcns_s {
   int dir_grid, occ, rocc;
   cudaEvent_t events[18];  // timing marks (gbcfd_wcns_set_timing), 6 per stage
   int timing;
+  gbcfd_wcns nbr[6];       // face neighbours (gbcfd_wcns_connect); none: the block wraps periodically
 };
 
 namespace {
@@ -958,15 +1043,12 @@ Args make_args(gbcfd_wcns w) {
   return a;
 }
 
+// the passes after the primitives: viscous residual, then x, y and z (marks 1..5 of ev)
 template <typename T>
-cudaError_t launch_pass(gbcfd_wcns w, Args a, int with_rate, const cudaEvent_t* ev, cudaStream_t s) {
+cudaError_t launch_rest(gbcfd_wcns w, const Args& a, const cudaEvent_t* ev, cudaStream_t s) {
   auto mark = [&](int m) {
     if (ev) cudaEventRecord(ev[m], s);
   };
-  const int pgrid = std::min(w->rows, w->nsm * 8);
-  mark(0);
-  prim_kernel<T><<<pgrid, NTW, 0, s>>>(a, with_rate);
-  mark(1);
   if (a.viscous) viscres_kernel<T><<<w->nsm * w->rocc, NTW, RSmem<T>::bytes, s>>>(a);
   mark(2);
   const size_t sm = Smem<T>::bytes;
@@ -980,8 +1062,17 @@ cudaError_t launch_pass(gbcfd_wcns w, Args a, int with_rate, const cudaEvent_t* 
   return cudaGetLastError();
 }
 
-// one Runge-Kutta stage (1..3) or the residual (stage 0, written to rout)
-int run_stage(gbcfd_wcns w, int stage, double* rout, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_pass(gbcfd_wcns w, Args a, int with_rate, const cudaEvent_t* ev, cudaStream_t s) {
+  if (ev) cudaEventRecord(ev[0], s);
+  const int pgrid = std::min(w->rows, w->nsm * 8);
+  prim_kernel<T><<<pgrid, NTW, 0, s>>>(a, with_rate);
+  if (ev) cudaEventRecord(ev[1], s);
+  return launch_rest<T>(w, a, ev, s);
+}
+
+// the kernel arguments of one Runge-Kutta stage (1..3) or of the residual (stage 0, into rout)
+Args stage_args(gbcfd_wcns w, int stage, double* rout) {
   Args a = make_args(w);
   a.stage = stage;
   a.rout = rout;
@@ -996,10 +1087,41 @@ int run_stage(gbcfd_wcns w, int stage, double* rout, cudaStream_t s) {
     a.qs = stage <= 1 ? w->q[0] : w->q[stage - 1];
     a.qout = stage == 3 ? w->q[0] : (stage >= 1 ? w->q[stage] : nullptr);
   }
+  return a;
+}
+
+// one Runge-Kutta stage (1..3) or the residual (stage 0, written to rout)
+int run_stage(gbcfd_wcns w, int stage, double* rout, cudaStream_t s) {
+  const Args a = stage_args(w, stage, rout);
   const cudaEvent_t* ev = (w->timing && stage >= 1) ? w->events + 6 * (stage - 1) : nullptr;
   const cudaError_t e = w->mixed ? launch_pass<float>(w, a, stage == 1, ev, s) : launch_pass<double>(w, a, stage == 1, ev, s);
   if (e != cudaSuccess) return cuda_err(e, "WCNS stage launch");
   return GBCFD_OK;
+}
+
+// one Runge-Kutta stage of blocks advanced together: every member's primitives first (a member's
+// halo reads its neighbours' stage inputs, which no launch of this stage has written yet), the
+// common time step after stage 1's, then each member's viscous and direction passes
+template <typename T>
+cudaError_t run_stage_many(const gbcfd_wcns* blocks, int n, WTab& tab, int stage, cudaStream_t s) {
+  for (int i = 0; i < n; ++i) {
+    const gbcfd_wcns w = blocks[i];
+    tab.self = i;
+    const int pgrid = std::min(w->rows, w->nsm * 8);
+    prim_multi_kernel<T><<<pgrid, NTW, 0, s>>>(stage_args(w, stage, nullptr), stage == 1, tab);
+  }
+  if (stage == 1) wcns_group_dt_kernel<<<1, 32, 0, s>>>(tab, blocks[0]->p.cfl);
+  for (int i = 0; i < n; ++i) {
+    const cudaError_t e = launch_rest<T>(blocks[i], stage_args(blocks[i], stage, nullptr), nullptr, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+bool connected_to_others(gbcfd_wcns w) {
+  for (int f = 0; f < 6; ++f)
+    if (w->nbr[f] && w->nbr[f] != w) return true;
+  return false;
 }
 
 }  // namespace
@@ -1092,6 +1214,8 @@ extern "C" int gbcfd_wcns_create(int nx, int ny, int nz, const gbcfd_params* par
 extern "C" int gbcfd_wcns_destroy(gbcfd_wcns w) {
   if (!w) return set_error(GBCFD_ERR_ARG, "NULL block");
   cudaDeviceSynchronize();
+  for (int f = 0; f < 6; ++f)  // the neighbours forget this block
+    if (w->nbr[f] && w->nbr[f] != w && w->nbr[f]->nbr[f ^ 1] == w) w->nbr[f]->nbr[f ^ 1] = nullptr;
   delete w;
   return GBCFD_OK;
 }
@@ -1132,6 +1256,8 @@ extern "C" int gbcfd_wcns_get_state(gbcfd_wcns w, double* q, void* stream) {
 extern "C" int gbcfd_wcns_compute_residual(gbcfd_wcns w, double* r, void* stream) {
   if (!w || !r) return set_error(GBCFD_ERR_ARG, "NULL argument");
   if (!w->has_state) return set_error(GBCFD_ERR_STATE, "no state set");
+  if (connected_to_others(w))
+    return set_error(GBCFD_ERR_STATE, "the block is connected to other blocks: they advance with gbcfd_wcns_step_many");
   return run_stage(w, 0, r, static_cast<cudaStream_t>(stream));
 }
 
@@ -1139,11 +1265,79 @@ extern "C" int gbcfd_wcns_step(gbcfd_wcns w, int nsteps, void* stream) {
   if (!w) return set_error(GBCFD_ERR_ARG, "NULL block");
   if (nsteps < 0) return set_error(GBCFD_ERR_ARG, "nsteps must be >= 0");
   if (!w->has_state) return set_error(GBCFD_ERR_STATE, "no state set");
+  if (connected_to_others(w))
+    return set_error(GBCFD_ERR_STATE, "the block is connected to other blocks: they advance with gbcfd_wcns_step_many");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int n = 0; n < nsteps; ++n)
     for (int st = 1; st <= 3; ++st) {
       const int rc = run_stage(w, st, nullptr, s);
       if (rc != GBCFD_OK) return rc;
+    }
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_wcns_connect(gbcfd_wcns a, int face, gbcfd_wcns b) {
+  if (!a || !b) return set_error(GBCFD_ERR_ARG, "NULL block");
+  if (face < 0 || face > 5) return set_error(GBCFD_ERR_ARG, "face must be 0..5 (-x, +x, -y, +y, -z, +z)");
+  const int ax = face >> 1;
+  if ((ax != 0 && a->nx != b->nx) || (ax != 1 && a->ny != b->ny) || (ax != 2 && a->nz != b->nz))
+    return set_error(GBCFD_ERR_ARG, "the two blocks' faces differ in size");
+  if (a->mixed != b->mixed || memcmp(&a->p, &b->p, sizeof(gbcfd_params)) != 0 || memcmp(a->h, b->h, sizeof(a->h)) != 0)
+    return set_error(GBCFD_ERR_ARG, "connected blocks must share parameters and cell sizes");
+  a->nbr[face] = b;
+  b->nbr[face ^ 1] = a;
+  return GBCFD_OK;
+}
+
+extern "C" int gbcfd_wcns_step_many(const gbcfd_wcns* blocks, int n, int nsteps, void* stream) {
+  if (!blocks) return set_error(GBCFD_ERR_ARG, "NULL block list");
+  if (n < 1 || n > MAXW) return set_error(GBCFD_ERR_ARG, "gbcfd_wcns_step_many takes 1 to 32 blocks");
+  if (nsteps < 0) return set_error(GBCFD_ERR_ARG, "nsteps must be >= 0");
+  WTab tab;
+  memset(&tab, 0, sizeof(tab));
+  tab.n = n;
+  for (int i = 0; i < n; ++i) {
+    const gbcfd_wcns w = blocks[i];
+    if (!w) return set_error(GBCFD_ERR_ARG, "NULL block");
+    for (int k = 0; k < i; ++k)
+      if (blocks[k] == w) return set_error(GBCFD_ERR_ARG, "a block is listed twice");
+    if (!w->has_state) return set_error(GBCFD_ERR_STATE, "no state set");
+    if (w->device != blocks[0]->device || w->mixed != blocks[0]->mixed ||
+        memcmp(&w->p, &blocks[0]->p, sizeof(gbcfd_params)) != 0 || memcmp(w->h, blocks[0]->h, sizeof(w->h)) != 0)
+      return set_error(GBCFD_ERR_ARG, "the blocks must share device, parameters and cell sizes");
+    WSrc& e = tab.e[i];
+    for (int q = 0; q < 3; ++q) e.q[q] = w->q[q];
+    e.sh = w->sh;
+    e.d[0] = w->d[0];
+    e.d[1] = w->d[1];
+    e.ctrl = w->ctrl;
+    e.nx = w->nx; e.ny = w->ny; e.nz = w->nz;
+  }
+  // every face connected within the list, the two blocks of a face equal across it, and face
+  // walks along two different axes reaching the same block in either order (a conforming periodic
+  // lattice: every halo cell has one owner)
+  for (int i = 0; i < n; ++i)
+    for (int f = 0; f < 6; ++f) {
+      const gbcfd_wcns nb = blocks[i]->nbr[f] ? blocks[i]->nbr[f] : (n == 1 ? blocks[i] : nullptr);
+      int j = -1;
+      for (int k = 0; k < n && nb; ++k)
+        if (blocks[k] == nb) j = k;
+      if (j < 0)
+        return set_error(GBCFD_ERR_ARG, "face " + std::to_string(f) + " of block " + std::to_string(i) +
+                                            " is not connected to a block of the list");
+      tab.e[i].nbr[f] = j;
+    }
+  for (int i = 0; i < n; ++i)
+    for (int f1 = 0; f1 < 6; ++f1)
+      for (int f2 = 0; f2 < 6; ++f2)
+        if ((f1 >> 1) != (f2 >> 1) && tab.e[tab.e[i].nbr[f1]].nbr[f2] != tab.e[tab.e[i].nbr[f2]].nbr[f1])
+          return set_error(GBCFD_ERR_ARG, "the blocks do not form a conforming lattice (face walks do not commute)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int step = 0; step < nsteps; ++step)
+    for (int st = 1; st <= 3; ++st) {
+      const cudaError_t e = blocks[0]->mixed ? run_stage_many<float>(blocks, n, tab, st, s)
+                                             : run_stage_many<double>(blocks, n, tab, st, s);
+      if (e != cudaSuccess) return cuda_err(e, "WCNS stage launch");
     }
   return GBCFD_OK;
 }
@@ -1255,6 +1449,7 @@ extern "C" int gbcfd_wcns_pipe_create(const gbcfd_wcns* blocks, int n, gbcfd_pip
     for (int k = 0; k < i; ++k)
       if (blocks[k] == w) return set_error(GBCFD_ERR_ARG, "a block is listed twice");
     if (w->nx != a->nx || w->ny != a->ny || w->nz != a->nz) return set_error(GBCFD_ERR_ARG, "members differ in size");
+    if (connected_to_others(w)) return set_error(GBCFD_ERR_ARG, "pipeline members are single periodic blocks");
     if (memcmp(&w->p, &a->p, sizeof(gbcfd_params)) != 0 || memcmp(w->h, a->h, sizeof(a->h)) != 0)
       return set_error(GBCFD_ERR_ARG, "members differ in parameters or cell sizes");
     m[i] = PipeMember{w, bytes, wp_upload, wp_run, wp_download, wp_flags, nullptr};

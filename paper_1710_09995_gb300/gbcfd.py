@@ -110,6 +110,8 @@ SIGNATURES = {
     "gbcfd_wcns_get_state": [_VP, _VP, _VP],
     "gbcfd_wcns_compute_residual": [_VP, _VP, _VP],
     "gbcfd_wcns_step": [_VP, ctypes.c_int, _VP],
+    "gbcfd_wcns_connect": [_VP, ctypes.c_int, _VP],
+    "gbcfd_wcns_step_many": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP],
     "gbcfd_wcns_residual_norm": [_VP, _D, _VP],
     "gbcfd_wcns_get_dt": [_VP, _D, _VP],
     "gbcfd_wcns_set_timing": [_VP, ctypes.POINTER(_VP), ctypes.c_int],
@@ -595,6 +597,11 @@ class WcnsBlock:
         _check(lib().gbcfd_wcns_residual_norm(self.handle, out.ctypes.data_as(_D), _stream(stream)))
         return out
 
+    def connect(self, face, other):
+        """face 0..5 (-x, +x, -y, +y, -z, +z) of this block to the opposite face of `other`
+        (gbcfd_wcns_connect); blocks connected to others advance with wcns_step_many"""
+        _check(lib().gbcfd_wcns_connect(self.handle, int(face), other.handle))
+
     def get_dt(self, stream=None) -> float:
         out = ctypes.c_double(0.0)
         _check(lib().gbcfd_wcns_get_dt(self.handle, ctypes.byref(out), _stream(stream)))
@@ -624,6 +631,55 @@ class WcnsBlock:
             self.close()
         except Exception:
             pass
+
+
+def wcns_step_many(blocks, nsteps=1, stream=None):
+    """nsteps SSP-RK3 steps of connected WCNS blocks together (gbcfd_wcns_step_many)"""
+    arr = (_VP * len(blocks))(*[b.handle for b in blocks])
+    _check(lib().gbcfd_wcns_step_many(arr, len(blocks), int(nsteps), _stream(stream)))
+
+
+def wcns_blocks_for_split(case, cuts, precision=FP64, linear=False, device=None):
+    """A periodic uniform Cartesian case split into a lattice of WCNS blocks: cuts = the block
+    sizes along x, y and z (each list sums to the case's size).  The blocks hold their part of
+    the state and are connected face to face with periodic wrap; returned with k slowest, then j,
+    then i (the order gather_wcns_split expects)."""
+    assert case.nodes is None, "WCNS blocks are uniform Cartesian"
+    sx, sy, sz = (list(map(int, c)) for c in cuts)
+    assert (sum(sx), sum(sy), sum(sz)) == (case.nx, case.ny, case.nz)
+    prm = params(case.gamma, case.mu, case.Pr, case.cfl, case.eps, case.viscous, int(bool(linear)), precision)
+    ox, oy, oz = np.cumsum([0] + sx), np.cumsum([0] + sy), np.cumsum([0] + sz)
+    nxb, nyb, nzb = len(sx), len(sy), len(sz)
+    blocks = []
+    for k in range(nzb):
+        for j in range(nyb):
+            for i in range(nxb):
+                b = WcnsBlock(sx[i], sy[j], sz[k], prm, case.spacing, device)
+                part = case.state[:, oz[k]:oz[k + 1], oy[j]:oy[j + 1], ox[i]:ox[i + 1]]
+                b.set_state(torch.from_numpy(np.ascontiguousarray(part)).to(b.memory.device))
+                blocks.append(b)
+    at = lambda i, j, k: blocks[((k % nzb) * nyb + (j % nyb)) * nxb + (i % nxb)]
+    for k in range(nzb):
+        for j in range(nyb):
+            for i in range(nxb):
+                at(i, j, k).connect(1, at(i + 1, j, k))
+                at(i, j, k).connect(3, at(i, j + 1, k))
+                at(i, j, k).connect(5, at(i, j, k + 1))
+    return blocks
+
+
+def gather_wcns_split(case, cuts, blocks):
+    """the global state [5][nz][ny][nx] (float64, on the blocks' device) of a split lattice"""
+    sx, sy, sz = (list(map(int, c)) for c in cuts)
+    ox, oy, oz = np.cumsum([0] + sx), np.cumsum([0] + sy), np.cumsum([0] + sz)
+    out = torch.empty((5, case.nz, case.ny, case.nx), dtype=torch.float64, device=blocks[0].memory.device)
+    n = 0
+    for k in range(len(sz)):
+        for j in range(len(sy)):
+            for i in range(len(sx)):
+                out[:, oz[k]:oz[k + 1], oy[j]:oy[j + 1], ox[i]:ox[i + 1]] = blocks[n].get_state()
+                n += 1
+    return out
 
 
 def wcns_block_for_case(case, precision=FP64, linear=False, device=None) -> WcnsBlock:

@@ -186,3 +186,74 @@ def test_nonphysical_state_is_reported(gb, precision):
         blk.residual_norm()
     assert e.value.code == gb.ERR_NONPHYSICAL
     blk.residual_norm()  # the flag was cleared by the first report
+
+
+# ---- multi-block lattices (gbcfd_wcns_connect / gbcfd_wcns_step_many) -------------------------
+def combined_rms(blocks, cells):
+    """the RMS over the whole lattice from the blocks' own RMS norms"""
+    s = sum(b.cells * b.residual_norm() ** 2 for b in blocks)
+    return np.sqrt(s / cells)
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+@pytest.mark.parametrize("viscous", [False, True])
+def test_split_lattice_equals_one_block(gb, precision, viscous):
+    """a periodic box split into uneven blocks -- one 3 cells wide, thinner than the 5-cell halo,
+    so halos cross it into the next block; edges and corners from the diagonal blocks -- advances
+    bit for bit like the single periodic block (and, in FP64, matches the oracle)"""
+    c = ragged(viscous, seed=5, nx=70, ny=19, nz=21, amp=0.05)
+    cuts = ([23, 3, 44], [7, 12], [2, 19])
+    prec = getattr(gb, precision)
+    one = gb.wcns_block_for_case(c, precision=prec)
+    one.step(3)
+    blocks = gb.wcns_blocks_for_split(c, cuts, precision=prec)
+    gb.wcns_step_many(blocks, 3)
+    got = gb.gather_wcns_split(c, cuts, blocks)
+    ref = one.get_state()
+    assert torch.equal(got, ref), float((got - ref).abs().max())
+    assert all(b.get_dt() == one.get_dt() for b in blocks)
+    assert np.allclose(combined_rms(blocks, c.cells), one.residual_norm(), rtol=1e-12, atol=0)
+    if precision == "FP64":
+        want, _, _ = oracle.wcns_step(oparams(c), c.state, c.spacing, 3)
+        assert max(per_var(got.cpu().numpy(), want)) <= 1e-12
+
+
+def test_split_vortex_128_two_by_two_by_two(gb):
+    """a larger uneven 2 x 2 x 2 split of the Navier-Stokes vortex (128 x 128 x 8 cells), mixed
+    precision, 4 steps: equal to the single block bit for bit"""
+    c = cases.isentropic_vortex(n=128, nz=8, L=10.0, viscous=True, Re=1e4)
+    cuts = ([40, 88], [101, 27], [3, 5])
+    one = gb.wcns_block_for_case(c, precision=gb.MIXED)
+    one.step(4)
+    blocks = gb.wcns_blocks_for_split(c, cuts, precision=gb.MIXED)
+    gb.wcns_step_many(blocks, 4)
+    assert torch.equal(gb.gather_wcns_split(c, cuts, blocks), one.get_state())
+
+
+def test_lone_block_step_many_equals_step(gb):
+    c = ragged(True, seed=2, nx=33, ny=9, nz=7)
+    a = gb.wcns_block_for_case(c, precision=gb.FP64)
+    b = gb.wcns_block_for_case(c, precision=gb.FP64)
+    a.step(2)
+    gb.wcns_step_many([b], 2)
+    assert torch.equal(a.get_state(), b.get_state())
+    assert a.get_dt() == b.get_dt()
+    assert np.array_equal(a.residual_norm(), b.residual_norm())
+
+
+def test_step_many_errors(gb):
+    c = ragged(False, seed=4, nx=24, ny=10, nz=6)
+    cuts = ([10, 14], [10], [6])
+    blocks = gb.wcns_blocks_for_split(c, cuts, precision=gb.FP64)
+    with pytest.raises(gb.GbcfdError) as e:
+        blocks[0].step(1)  # connected to another block
+    assert e.value.code == gb.ERR_STATE
+    with pytest.raises(gb.GbcfdError) as e:
+        gb.wcns_step_many(blocks[:1], 1)  # its +x neighbour is not in the list
+    assert e.value.code == gb.ERR_ARG
+    with pytest.raises(gb.GbcfdError):
+        gb.wcns_step_many([blocks[0], blocks[0]], 1)
+    other = gb.WcnsBlock(10, 9, 6, gb.params(), c.spacing)
+    with pytest.raises(gb.GbcfdError):
+        blocks[0].connect(1, other)  # faces of different sizes
+    gb.wcns_step_many(blocks, 1)  # the lattice itself still steps
