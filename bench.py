@@ -959,6 +959,32 @@ def time_wcns(gbcfd, torch, case, precision, steps, warmup, world, device):
     return {"ms": ms, "kernel_ms": kern, "kernel_stage_ms": per_stage, "launches": nlaunch, "norms": norms.tolist()}
 
 
+def time_wcns_split(gbcfd, torch, case, precision, steps, warmup, world, device):
+    """the same case as a periodic lattice of 2 x 2 x 2 uneven WCNS blocks advanced together
+    (gbcfd_wcns_step_many): the wall time of a step through the multi-block path"""
+    n = case.nx
+    cuts = ([n * 5 // 16, n - n * 5 // 16], [n * 11 // 16, n - n * 11 // 16], [case.nz // 2, case.nz - case.nz // 2])
+    blocks = gbcfd.wcns_blocks_for_split(case, cuts, precision=gbcfd.MIXED if precision == "mixed" else gbcfd.FP64,
+                                         device=device)
+    stream = torch.cuda.current_stream()
+    gbcfd.wcns_step_many(blocks, warmup, stream)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    start.record(stream)
+    gbcfd.wcns_step_many(blocks, steps, stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(start.elapsed_time(stop), world, device)
+    for b in blocks:
+        b.close()
+    return {"value": world * case.cells * steps / (ms / 1e3), "unit": "cell-updates/s",
+            "ms_per_step": ms / steps, "steps": steps, "blocks": [list(c) for c in cuts],
+            "api": "gbcfd_wcns_connect + gbcfd_wcns_step_many (8 blocks, 5-cell halos across block faces)"}
+
+
 def wcns_roofline(precision, res, cells, steps, peak, peak_kind):
     """HBM roofline of the WCNS path's dominant kernel: its algorithmic bytes per launch over its
     mean launch time (CUDA events around every launch of the timed region)"""
@@ -1066,6 +1092,7 @@ def run_wcns(args, world, rank, local, device, torch, cases, gbcfd):
     steps = {p: (args.steps if p == "mixed" else min(args.steps, 10)) for p in paths}
     results = {p: time_wcns(gbcfd, torch, case, p, steps[p], args.warmup if p == "mixed" else 1, world, device)
                for p in paths}
+    split = time_wcns_split(gbcfd, torch, case, paths[0], steps[paths[0]], args.warmup, world, device)
     clk = clocks.stop()
     head = paths[0]
     e2e = e2e_wcns(gbcfd, torch, case, head, args.e2e_steps or 20, world, device)
@@ -1084,7 +1111,7 @@ def run_wcns(args, world, rank, local, device, torch, cases, gbcfd):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": wcns_roofline(head, r, case.cells, steps[head], peak, peak_kind),
         "e2e": e2e, "gpu_launches": r["launches"], "clocks": clk, "cpu_baseline": cpu,
-        "residual_norm": r["norms"],
+        "residual_norm": r["norms"], "multiblock_2x2x2": split,
     }
     for p in paths[1:]:
         rp = results[p]

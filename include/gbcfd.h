@@ -425,8 +425,11 @@ int gbcfd_wcns_connect(gbcfd_wcns a, int face, gbcfd_wcns b);
  * every face of every block connected to a block of the list (a lone unconnected block counts
  * as periodic), the blocks form a conforming lattice (face walks along two different axes reach
  * the same block in either order), and share device, parameters and cell sizes; every block has
- * a state (GBCFD_ERR_STATE).  Asynchronous; each block's norms and time step are read with
- * gbcfd_wcns_residual_norm / gbcfd_wcns_get_dt. */
+ * a state (GBCFD_ERR_STATE).  Asynchronous with respect to the host: the blocks' kernels run on
+ * up to 8 internal streams of the device that fork from and join into `stream` at every stage
+ * (so the blocks overlap on the GPU; `stream` sees the whole step in order, also when captured
+ * into a graph).  Each block's norms and time step are read with gbcfd_wcns_residual_norm /
+ * gbcfd_wcns_get_dt. */
 int gbcfd_wcns_step_many(const gbcfd_wcns* blocks, int n, int nsteps, void* stream);
 
 /* RMS per component of R(Q^n) of the last step's stage 1, to out[5] on the host (synchronises;

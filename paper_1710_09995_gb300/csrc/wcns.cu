@@ -1099,23 +1099,82 @@ int run_stage(gbcfd_wcns w, int stage, double* rout, cudaStream_t s) {
   return GBCFD_OK;
 }
 
+// side streams of the current device for blocks advanced together: the kernels of different
+// blocks overlap (each block alone fills the GPU only partly, and its launches' tails leave SMs
+// idle); created once per device, shared by all calls (events order the work of each call)
+constexpr int NSIDE = 8;
+struct SidePool {
+  int device;
+  cudaStream_t st[NSIDE];
+  cudaEvent_t done[NSIDE], fork;
+};
+cudaError_t side_pool(SidePool** out) {
+  static std::mutex mu;
+  static std::vector<SidePool*> pools;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (SidePool* p : pools)
+    if (p->device == dev) {
+      *out = p;
+      return cudaSuccess;
+    }
+  SidePool* p = new SidePool();
+  p->device = dev;
+  for (int k = 0; k < NSIDE && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&p->st[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) return e;  // (a failed pool is not kept; its handles leak)
+  pools.push_back(p);
+  *out = p;
+  return cudaSuccess;
+}
+
+// the side streams k < m wait for the work issued so far on s
+cudaError_t fork(SidePool* p, int m, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(p->fork, s);
+  for (int k = 0; k < m && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->st[k], p->fork, 0);
+  return e;
+}
+// s waits for the work issued so far on the side streams k < m
+cudaError_t join(SidePool* p, int m, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < m && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(p->done[k], p->st[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->done[k], 0);
+  }
+  return e;
+}
+
 // one Runge-Kutta stage of blocks advanced together: every member's primitives first (a member's
-// halo reads its neighbours' stage inputs, which no launch of this stage has written yet), the
-// common time step after stage 1's, then each member's viscous and direction passes
+// halo reads its neighbours' stage inputs, and on the mixed path stage 3 rewrites the shadow S^n
+// its neighbours' halos read, so no member's passes start before all primitives are formed), the
+// common time step after stage 1's, then each member's viscous and direction passes.  Members run
+// on side streams (block i on stream i mod 8) between a fork from and a join into s.
 template <typename T>
-cudaError_t run_stage_many(const gbcfd_wcns* blocks, int n, WTab& tab, int stage, cudaStream_t s) {
-  for (int i = 0; i < n; ++i) {
+cudaError_t run_stage_many(const gbcfd_wcns* blocks, int n, WTab& tab, int stage, SidePool* pool, cudaStream_t s) {
+  const int m = std::min(n, NSIDE);
+  cudaError_t e = fork(pool, m, s);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
     const gbcfd_wcns w = blocks[i];
     tab.self = i;
     const int pgrid = std::min(w->rows, w->nsm * 8);
-    prim_multi_kernel<T><<<pgrid, NTW, 0, s>>>(stage_args(w, stage, nullptr), stage == 1, tab);
+    prim_multi_kernel<T><<<pgrid, NTW, 0, pool->st[i % NSIDE]>>>(stage_args(w, stage, nullptr), stage == 1, tab);
+    e = cudaGetLastError();
   }
-  if (stage == 1) wcns_group_dt_kernel<<<1, 32, 0, s>>>(tab, blocks[0]->p.cfl);
-  for (int i = 0; i < n; ++i) {
-    const cudaError_t e = launch_rest<T>(blocks[i], stage_args(blocks[i], stage, nullptr), nullptr, s);
-    if (e != cudaSuccess) return e;
+  if (e == cudaSuccess) e = join(pool, m, s);
+  if (e == cudaSuccess && stage == 1) {
+    wcns_group_dt_kernel<<<1, 32, 0, s>>>(tab, blocks[0]->p.cfl);
+    e = cudaGetLastError();
   }
-  return cudaGetLastError();
+  if (e == cudaSuccess) e = fork(pool, m, s);
+  for (int i = 0; i < n && e == cudaSuccess; ++i)
+    e = launch_rest<T>(blocks[i], stage_args(blocks[i], stage, nullptr), nullptr, pool->st[i % NSIDE]);
+  if (e == cudaSuccess) e = join(pool, m, s);
+  return e;
 }
 
 bool connected_to_others(gbcfd_wcns w) {
@@ -1333,10 +1392,13 @@ extern "C" int gbcfd_wcns_step_many(const gbcfd_wcns* blocks, int n, int nsteps,
         if ((f1 >> 1) != (f2 >> 1) && tab.e[tab.e[i].nbr[f1]].nbr[f2] != tab.e[tab.e[i].nbr[f2]].nbr[f1])
           return set_error(GBCFD_ERR_ARG, "the blocks do not form a conforming lattice (face walks do not commute)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SidePool* pool = nullptr;
+  cudaError_t pe = side_pool(&pool);
+  if (pe != cudaSuccess) return cuda_err(pe, "side streams");
   for (int step = 0; step < nsteps; ++step)
     for (int st = 1; st <= 3; ++st) {
-      const cudaError_t e = blocks[0]->mixed ? run_stage_many<float>(blocks, n, tab, st, s)
-                                             : run_stage_many<double>(blocks, n, tab, st, s);
+      const cudaError_t e = blocks[0]->mixed ? run_stage_many<float>(blocks, n, tab, st, pool, s)
+                                             : run_stage_many<double>(blocks, n, tab, st, pool, s);
       if (e != cudaSuccess) return cuda_err(e, "WCNS stage launch");
     }
   return GBCFD_OK;
