@@ -121,7 +121,7 @@ def _norm(blk):
 
 
 def solve(case, target=1e-6, accel_params=None, max_seconds=900.0, check=200, stall_checks=50,
-          precision="hybrid", device=None, log=None, smooth=0, alpha=0.5, alpha_min=0.125):
+          precision="hybrid", device=None, log=None, smooth=0, alpha=0.5, alpha_min=0.125, alpha_max=1.0):
     """Pseudo-time iteration of a steady case to RMS(R_rho) <= target x its initial value.
 
     precision: "fp64" (the plain FP64 iteration), "mixed" (mixed path only; it stalls where the
@@ -137,8 +137,9 @@ def solve(case, target=1e-6, accel_params=None, max_seconds=900.0, check=200, st
     lower; a kept one is followed by another try).  smooth = m > 0: the prediction scaled by alpha
     is followed by m plain steps and kept only if the residual then lies below min(1, rate^m) times
     its value before, rate the plain iteration's per-step factor over the last `check` steps
-    (gbcfd_accel_try_smooth); alpha grows (x1.5, up to 1) after a kept try and halves (down to
-    alpha_min) after a rejected one.
+    (gbcfd_accel_try_smooth); alpha grows (x1.5, up to alpha_max <= 4: beyond 1 the prediction is
+    extrapolated along its own direction) after a kept try and halves (down to alpha_min) after a
+    rejected one.
     Returns a dict with the wall time, steps, predictions tried/kept and the history."""
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     prec = gbcfd.FP64 if precision == "fp64" else gbcfd.MIXED
@@ -173,7 +174,7 @@ def solve(case, target=1e-6, accel_params=None, max_seconds=900.0, check=200, st
                 kept += 1
                 steps += smooth
                 r = r1 / r0
-                alpha = min(1.0, 1.5 * alpha)
+                alpha = min(alpha_max, 1.5 * alpha)
             else:
                 alpha = max(alpha_min, 0.5 * alpha)
         elif try_now:
