@@ -393,43 +393,127 @@ cudaError_t launch_init_rate_curvi(const Geometry& g, const Physics& ph, const d
 //              inflow takes the free stream, supersonic outflow the interior), both layers
 // On the mixed path the state is f32; for stages 2 and 3 the field is the f32 increment D over
 // the f32 state S^n (the stencil adds them): the ghost increment is f32(Q_ghost - S_ghost).
-__device__ __forceinline__ void bc_load(const BcBlock& B, long long o, long long of, double* q) {
+// The ghost-cell arithmetic runs in the precision of the field it fills: FP64 for the FP64 state,
+// FP32 for the mixed path's f32 state and increments (the values the FP32 fluxes read; FP64 here
+// would leave these small launches waiting on the FP64 pipe, 2 lanes per SM).
+template <typename T> struct BcMath;
+template <> struct BcMath<double> {
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
+};
+template <> struct BcMath<float> {
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
+};
+
+template <typename T>
+__device__ __forceinline__ void bc_load(const BcBlock& B, long long o, long long of, T* q) {
   if (B.mode == BC_F64) {
     const double* f = static_cast<const double*>(B.field);
-    for (int v = 0; v < 5; ++v) q[v] = f[v * B.g.field + o];
+    for (int v = 0; v < 5; ++v) q[v] = T(f[v * B.g.field + o]);
   } else if (B.mode == BC_F32) {
     const float* f = static_cast<const float*>(B.field);
-    for (int v = 0; v < 5; ++v) q[v] = double(f[v * B.g.fieldf + of]);
-  } else {
+    for (int v = 0; v < 5; ++v) q[v] = T(f[v * B.g.fieldf + of]);
+  } else {  // the stage input S + D, formed in f32 as the stage kernel forms it
     const float* f = static_cast<const float*>(B.field);
-    for (int v = 0; v < 5; ++v) q[v] = double(B.shadow[v * B.g.fieldf + of] + f[v * B.g.fieldf + of]);
+    for (int v = 0; v < 5; ++v) q[v] = T(B.shadow[v * B.g.fieldf + of] + f[v * B.g.fieldf + of]);
   }
 }
-__device__ __forceinline__ void bc_store(const BcBlock& B, long long o, long long of, const double* w) {
-  const double gm = B.gamma;
-  double q[5];
+template <typename T>
+__device__ __forceinline__ void bc_store(const BcBlock& B, long long o, long long of, const T* w) {
+  const T gm = T(B.gamma);
+  T q[5];
   q[0] = w[0];
   q[1] = w[0] * w[1];
   q[2] = w[0] * w[2];
   q[3] = w[0] * w[3];
-  q[4] = w[4] / (gm - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+  q[4] = w[4] / (gm - T(1)) + T(0.5) * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
   if (B.mode == BC_F64) {
     double* f = static_cast<double*>(B.field);
-    for (int v = 0; v < 5; ++v) f[v * B.g.field + o] = q[v];
+    for (int v = 0; v < 5; ++v) f[v * B.g.field + o] = double(q[v]);
   } else if (B.mode == BC_F32) {
     float* f = static_cast<float*>(B.field);
     for (int v = 0; v < 5; ++v) f[v * B.g.fieldf + of] = float(q[v]);
   } else {
     float* f = static_cast<float*>(B.field);
-    for (int v = 0; v < 5; ++v) f[v * B.g.fieldf + of] = float(q[v] - double(B.shadow[v * B.g.fieldf + of]));
+    for (int v = 0; v < 5; ++v) f[v * B.g.fieldf + of] = float(q[v] - T(B.shadow[v * B.g.fieldf + of]));
   }
 }
-__device__ __forceinline__ void bc_prim(double gm, const double* q, double* w) {
+template <typename T>
+__device__ __forceinline__ void bc_prim(T gm, const T* q, T* w) {
   w[0] = q[0];
   w[1] = q[1] / q[0];
   w[2] = q[2] / q[0];
   w[3] = q[3] / q[0];
-  w[4] = (gm - 1.0) * (q[4] - 0.5 * q[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]));
+  w[4] = (gm - T(1)) * (q[4] - T(0.5) * q[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]));
+}
+
+// one ghost cell: layer m (0 nearest the face) beyond face `hi` of direction d, at (a, b) along the
+// other two directions
+template <typename T>
+__device__ __forceinline__ void bc_cell(const BcBlock& B, int d, int d1, int d2, const int* n, int a, int b, int m,
+                                        int hi, int kind) {
+  using M = BcMath<T>;
+  const Geometry& g = B.g;
+  int idx[3], gi[3], ii[3];
+  idx[d1] = a; idx[d2] = b; idx[d] = hi ? n[d] : 0;  // the boundary face is this cell's lower face
+  for (int x = 0; x < 3; ++x) { gi[x] = idx[x]; ii[x] = idx[x]; }
+  gi[d] = hi ? n[d] + m : -1 - m;
+  // unit normal (towards +d) of the boundary face
+  T nrm[3] = {T(0), T(0), T(0)};
+  if (B.metrics) {
+    T S[3];
+    if (B.mode == BC_F64) {
+      const double* Mt = static_cast<const double*>(B.metrics);
+      const long long oc = gidx(g, idx[0], idx[1], idx[2]);
+      for (int x = 0; x < 3; ++x) S[x] = T(Mt[(3 * d + x) * g.field + oc]);
+    } else {
+      const float* Mt = static_cast<const float*>(B.metrics);
+      const long long oc = gidxf(g, idx[0], idx[1], idx[2]);
+      for (int x = 0; x < 3; ++x) S[x] = T(Mt[(3 * d + x) * g.fieldf + oc]);
+    }
+    const T len = M::sqrt_(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    for (int x = 0; x < 3; ++x) nrm[x] = S[x] / len;
+  } else {
+    nrm[d] = T(1);
+  }
+  T q[5], wi[5], wb[5], inf[5];
+  for (int v = 0; v < 5; ++v) inf[v] = T(B.inf[v]);
+  const T gm = T(B.gamma);
+  if (kind == BC_SLIP_WALL) {
+    ii[d] = hi ? n[d] - 1 - m : m;  // the mirror image inside
+    bc_load<T>(B, gidx(g, ii[0], ii[1], ii[2]), gidxf(g, ii[0], ii[1], ii[2]), q);
+    bc_prim<T>(gm, q, wi);
+    const T un = wi[1] * nrm[0] + wi[2] * nrm[1] + wi[3] * nrm[2];
+    wb[0] = wi[0];
+    for (int x = 0; x < 3; ++x) wb[1 + x] = wi[1 + x] - T(2) * un * nrm[x];
+    wb[4] = wi[4];
+  } else {
+    ii[d] = hi ? n[d] - 1 : 0;  // the interior cell next to the face
+    bc_load<T>(B, gidx(g, ii[0], ii[1], ii[2]), gidxf(g, ii[0], ii[1], ii[2]), q);
+    bc_prim<T>(gm, q, wi);
+    const T out[3] = {hi ? nrm[0] : -nrm[0], hi ? nrm[1] : -nrm[1], hi ? nrm[2] : -nrm[2]};
+    const T ci = M::sqrt_(gm * wi[4] / wi[0]), cinf = M::sqrt_(gm * inf[4] / inf[0]);
+    const T uni = wi[1] * out[0] + wi[2] * out[1] + wi[3] * out[2];
+    const T uninf = inf[1] * out[0] + inf[2] * out[1] + inf[3] * out[2];
+    if (uninf <= -cinf) {
+      for (int v = 0; v < 5; ++v) wb[v] = inf[v];
+    } else if (uni >= ci) {
+      for (int v = 0; v < 5; ++v) wb[v] = wi[v];
+    } else {
+      const T rp = uni + T(2) * ci / (gm - T(1)), rm = uninf - T(2) * cinf / (gm - T(1));
+      const T unb = T(0.5) * (rp + rm), cb = T(0.25) * (gm - T(1)) * (rp - rm);
+      T src[5];  // the upwind side's state (selected by value: no local-memory array)
+      for (int v = 0; v < 5; ++v) src[v] = unb < T(0) ? inf[v] : wi[v];
+      const T un_src = src[1] * out[0] + src[2] * out[1] + src[3] * out[2];
+      const T ent = src[4] / M::pow_(src[0], gm);
+      const T rho = M::pow_(cb * cb / (gm * ent), T(1) / (gm - T(1)));
+      wb[0] = rho;
+      for (int x = 0; x < 3; ++x) wb[1 + x] = src[1 + x] + (unb - un_src) * out[x];
+      wb[4] = rho * cb * cb / gm;
+    }
+  }
+  bc_store<T>(B, gidx(g, gi[0], gi[1], gi[2]), gidxf(g, gi[0], gi[1], gi[2]), wb);
 }
 
 __global__ void bc_kernel(const BcBlock B) {
@@ -447,63 +531,8 @@ __global__ void bc_kernel(const BcBlock B) {
     const int m = (int)(r % HALO), hi = (int)(r / HALO);
     const int kind = B.kind[2 * d + hi];
     if (kind == BC_NONE) continue;
-    int idx[3], gi[3], ii[3];
-    idx[d1] = a; idx[d2] = b; idx[d] = hi ? n[d] : 0;  // the boundary face is this cell's lower face
-    for (int x = 0; x < 3; ++x) { gi[x] = idx[x]; ii[x] = idx[x]; }
-    gi[d] = hi ? n[d] + m : -1 - m;
-    // unit normal (towards +d) of the boundary face
-    double nrm[3] = {0.0, 0.0, 0.0};
-    if (B.metrics) {
-      double S[3];
-      if (B.mode == BC_F64) {
-        const double* M = static_cast<const double*>(B.metrics);
-        const long long oc = gidx(g, idx[0], idx[1], idx[2]);
-        for (int x = 0; x < 3; ++x) S[x] = M[(3 * d + x) * g.field + oc];
-      } else {
-        const float* M = static_cast<const float*>(B.metrics);
-        const long long oc = gidxf(g, idx[0], idx[1], idx[2]);
-        for (int x = 0; x < 3; ++x) S[x] = double(M[(3 * d + x) * g.fieldf + oc]);
-      }
-      const double len = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
-      for (int x = 0; x < 3; ++x) nrm[x] = S[x] / len;
-    } else {
-      nrm[d] = 1.0;
-    }
-    double q[5], wi[5], wb[5];
-    if (kind == BC_SLIP_WALL) {
-      ii[d] = hi ? n[d] - 1 - m : m;  // the mirror image inside
-      bc_load(B, gidx(g, ii[0], ii[1], ii[2]), gidxf(g, ii[0], ii[1], ii[2]), q);
-      bc_prim(B.gamma, q, wi);
-      const double un = wi[1] * nrm[0] + wi[2] * nrm[1] + wi[3] * nrm[2];
-      wb[0] = wi[0];
-      for (int x = 0; x < 3; ++x) wb[1 + x] = wi[1 + x] - 2.0 * un * nrm[x];
-      wb[4] = wi[4];
-    } else {
-      ii[d] = hi ? n[d] - 1 : 0;  // the interior cell next to the face
-      bc_load(B, gidx(g, ii[0], ii[1], ii[2]), gidxf(g, ii[0], ii[1], ii[2]), q);
-      bc_prim(B.gamma, q, wi);
-      const double gm = B.gamma;
-      const double out[3] = {hi ? nrm[0] : -nrm[0], hi ? nrm[1] : -nrm[1], hi ? nrm[2] : -nrm[2]};
-      const double ci = sqrt(gm * wi[4] / wi[0]), cinf = sqrt(gm * B.inf[4] / B.inf[0]);
-      const double uni = wi[1] * out[0] + wi[2] * out[1] + wi[3] * out[2];
-      const double uninf = B.inf[1] * out[0] + B.inf[2] * out[1] + B.inf[3] * out[2];
-      if (uninf <= -cinf) {
-        for (int v = 0; v < 5; ++v) wb[v] = B.inf[v];
-      } else if (uni >= ci) {
-        for (int v = 0; v < 5; ++v) wb[v] = wi[v];
-      } else {
-        const double rp = uni + 2.0 * ci / (gm - 1.0), rm = uninf - 2.0 * cinf / (gm - 1.0);
-        const double unb = 0.5 * (rp + rm), cb = 0.25 * (gm - 1.0) * (rp - rm);
-        const double* src = unb < 0.0 ? B.inf : wi;
-        const double un_src = src[1] * out[0] + src[2] * out[1] + src[3] * out[2];
-        const double ent = src[4] / pow(src[0], gm);
-        const double rho = pow(cb * cb / (gm * ent), 1.0 / (gm - 1.0));
-        wb[0] = rho;
-        for (int x = 0; x < 3; ++x) wb[1 + x] = src[1 + x] + (unb - un_src) * out[x];
-        wb[4] = rho * cb * cb / gm;
-      }
-    }
-    bc_store(B, gidx(g, gi[0], gi[1], gi[2]), gidxf(g, gi[0], gi[1], gi[2]), wb);
+    if (B.mode == BC_F64) bc_cell<double>(B, d, d1, d2, n, a, b, m, hi, kind);
+    else bc_cell<float>(B, d, d1, d2, n, a, b, m, hi, kind);
   }
 }
 
