@@ -1387,6 +1387,11 @@ extern "C" int gbcfd_wcns_step_many(const gbcfd_wcns* blocks, int n, int nsteps,
       tab.e[i].nbr[f] = j;
     }
   for (int i = 0; i < n; ++i)
+    for (int f = 0; f < 6; ++f)  // links both ways (a face re-connected elsewhere leaves a stale one)
+      if (tab.e[tab.e[i].nbr[f]].nbr[f ^ 1] != i)
+        return set_error(GBCFD_ERR_ARG, "face " + std::to_string(f) + " of block " + std::to_string(i) +
+                                            " is not connected back by its neighbour");
+  for (int i = 0; i < n; ++i)
     for (int f1 = 0; f1 < 6; ++f1)
       for (int f2 = 0; f2 < 6; ++f2)
         if ((f1 >> 1) != (f2 >> 1) && tab.e[tab.e[i].nbr[f1]].nbr[f2] != tab.e[tab.e[i].nbr[f2]].nbr[f1])

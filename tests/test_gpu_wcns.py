@@ -257,3 +257,9 @@ def test_step_many_errors(gb):
     with pytest.raises(gb.GbcfdError):
         blocks[0].connect(1, other)  # faces of different sizes
     gb.wcns_step_many(blocks, 1)  # the lattice itself still steps
+    # re-connecting a face elsewhere leaves the old neighbour's link stale: refused
+    third = gb.wcns_blocks_for_split(c, ([24], [10], [6]), precision=gb.FP64)[0]
+    blocks[0].connect(1, third)
+    with pytest.raises(gb.GbcfdError) as e:
+        gb.wcns_step_many(blocks + [third], 1)
+    assert e.value.code == gb.ERR_ARG
