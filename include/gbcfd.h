@@ -422,8 +422,8 @@ int gbcfd_wcns_connect(gbcfd_wcns a, int face, gbcfd_wcns b);
  * block's viscous and direction passes; the time step is cfl / the largest CFL rate of Q^n over
  * all the blocks, the same in every block.  Results equal one periodic block holding the whole
  * lattice (the same arithmetic on the same values).  Requirements (GBCFD_ERR_ARG otherwise):
- * every face of every block connected to a block of the list (a lone unconnected block counts
- * as periodic), the blocks form a conforming lattice (face walks along two different axes reach
+ * every face of every block connected to a block of the list and connected back by it (a lone
+ * unconnected block counts as periodic), the blocks form a conforming lattice (face walks along two different axes reach
  * the same block in either order), and share device, parameters and cell sizes; every block has
  * a state (GBCFD_ERR_STATE).  Asynchronous with respect to the host: the blocks' kernels run on
  * up to 8 internal streams of the device that fork from and join into `stream` at every stage
