@@ -451,6 +451,21 @@ int gbcfd_wcns_set_timing(gbcfd_wcns block, void* const* events, int n);
  * bitwise the results of those calls on one block.  Waits for the device before returning. */
 int gbcfd_wcns_pipe_create(const gbcfd_wcns* blocks, int n, gbcfd_pipe* out);
 
+/* Throughput of one arithmetic operation on the current GPU, in operations per second, to
+ * *ops_per_second: op GBCFD_OP_DFMA (FP64 fused multiply-add; x 2 = FP64 flop/s, the FP64 stage
+ * kernels' bound), GBCFD_OP_FFMA (FP32 fused multiply-add), GBCFD_OP_DIV (FP64 1/x by IEEE
+ * division), GBCFD_OP_RCP_NEWTON (the FP64 path's reciprocal: hardware estimate and one
+ * third-order Newton step), GBCFD_OP_RSQRT (FP64 1/sqrt(x)).  8 independent chains per thread,
+ * 8 CTAs of 256 threads per SM; a warm-up launch, then one launch timed with CUDA events on
+ * `stream` (synchronises; tens of milliseconds).  scratch: caller device memory of at least
+ * 8 x (SMs x 8) bytes the kernel may write.  GBCFD_ERR_ARG for an unknown op or NULL pointers. */
+#define GBCFD_OP_DFMA 0
+#define GBCFD_OP_FFMA 1
+#define GBCFD_OP_DIV 2
+#define GBCFD_OP_RCP_NEWTON 3
+#define GBCFD_OP_RSQRT 4
+int gbcfd_op_rate(int op, void* scratch, double* ops_per_second, void* stream);
+
 /* Message of the last error on the calling host thread ("" if none). */
 const char* gbcfd_last_error(void);
 

@@ -115,6 +115,7 @@ SIGNATURES = {
     "gbcfd_wcns_residual_norm": [_VP, _D, _VP],
     "gbcfd_wcns_get_dt": [_VP, _D, _VP],
     "gbcfd_wcns_set_timing": [_VP, ctypes.POINTER(_VP), ctypes.c_int],
+    "gbcfd_op_rate": [ctypes.c_int, _VP, _D, _VP],
     "gbcfd_last_error": [],
 }
 
@@ -295,6 +296,21 @@ def time_step_noalloc(q, prm: Params, spacing, out=None, stream=None):
     sp = (ctypes.c_double * 3)(*spacing)
     _check(lib().gbcfd_time_step_noalloc(_ptr(q), nx, ny, nz, ctypes.byref(prm), sp, _ptr(out), _stream(stream)))
     return out
+
+
+OP_DFMA, OP_FFMA, OP_DIV, OP_RCP_NEWTON, OP_RSQRT = 0, 1, 2, 3, 4
+
+
+def op_rate(op, device=None, stream=None) -> float:
+    """operations per second of one arithmetic operation on the GPU (gbcfd_op_rate): OP_DFMA,
+    OP_FFMA, OP_DIV (FP64 1/x by IEEE division), OP_RCP_NEWTON (the FP64 path's reciprocal),
+    OP_RSQRT (FP64)"""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    scratch = torch.empty(8 * nsm, dtype=torch.float64, device=dev)
+    out = ctypes.c_double(0.0)
+    _check(lib().gbcfd_op_rate(int(op), _ptr(scratch), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 class Pipe:
