@@ -421,7 +421,7 @@ def e2e_path(gbcfd, torch, case, precision, steps, world, device):
 
 
 # GB300 FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x
-# 2.07 GHz (the recipe's nominal 1.25 TFLOP/s; a DFMA-chain probe measured 1.2556)
+# 2.07 GHz (the recipe's nominal 1.25 TFLOP/s; gbcfd_op_rate's DFMA chains measure 1.2524)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 ISSUE_PER_CLK = 152 * 4 * 32  # SMs x schedulers x lanes: thread instructions issued per clock
 
@@ -466,7 +466,7 @@ def fp64_alu_roofline(res, cells, steps, hbm, workload="vortex256"):
     2 lanes x the clock)"""
     flops = profiled_numbers("fp64", "fp64 flops per cell and stage", workload)
     out = {"bound": "alu", "kernel": "stage_kernel", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
-           "peak_kind": "FP64 FMA lanes x clock (152 SMs x 2 x 2 flops x 2.07 GHz; 1.2556 measured)",
+           "peak_kind": "FP64 FMA lanes x clock (152 SMs x 2 x 2 flops x 2.07 GHz; 1.2524 measured by gbcfd_op_rate)",
            "avg_launch_ms": hbm["avg_launch_ms"],
            "traffic": hbm["traffic"], "hbm_frac": hbm["frac"]}
     ops = profiled_numbers("fp64", "fp64 ops per cell and stage", workload)

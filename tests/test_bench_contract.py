@@ -40,7 +40,7 @@ def test_reference_arm_has_a_sample_for_every_workload():
 
 def test_fp64_alu_peak_and_roofline():
     """the FP64 path is bound by the FP64 pipe: its peak is 152 SMs x 2 FMA lanes x 2 flops x
-    2.07 GHz = 1.2586 TFLOP/s (the recipe's nominal 1.25; a DFMA probe measured 1.2556), and the
+    2.07 GHz = 1.2586 TFLOP/s (the recipe's nominal 1.25; gbcfd_op_rate measures 1.2524), and the
     roofline divides the flops per cell and stage (from the committed ncu summary, or None when
     that summary predates the kernel source) by the launch time"""
     assert abs(bench.FP64_PEAK_TFLOPS - 1.25856) < 1e-4
