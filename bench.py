@@ -182,7 +182,7 @@ def hbm_peak():
 def kernel_source_hash(curvi=False):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1710_09995_gb300", "csrc")
-    for name in ("stage.cuh", "physics.cuh", "internal.cuh") + (("curvi.cuh",) if curvi else ()):
+    for name in ("stage.cuh", "physics.cuh", "internal.cuh", "vmath.cuh", "stage_inst.cuh") + (("curvi.cuh",) if curvi else ()):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
