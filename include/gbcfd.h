@@ -455,7 +455,9 @@ int gbcfd_wcns_pipe_create(const gbcfd_wcns* blocks, int n, gbcfd_pipe* out);
  * *ops_per_second: op GBCFD_OP_DFMA (FP64 fused multiply-add; x 2 = FP64 flop/s, the FP64 stage
  * kernels' bound), GBCFD_OP_FFMA (FP32 fused multiply-add), GBCFD_OP_DIV (FP64 1/x by IEEE
  * division), GBCFD_OP_RCP_NEWTON (the FP64 path's reciprocal: hardware estimate and one
- * third-order Newton step), GBCFD_OP_RSQRT (FP64 1/sqrt(x)).  8 independent chains per thread,
+ * third-order Newton step), GBCFD_OP_RSQRT (FP64 1/sqrt(x)), GBCFD_OP_DADD and GBCFD_OP_DMUL (FP64
+ * add and multiply of registers), GBCFD_OP_DFMA_CONST (FP64 FMA whose multiplier and addend are
+ * literal constants).  8 independent chains per thread,
  * 8 CTAs of 256 threads per SM; a warm-up launch, then one launch timed with CUDA events on
  * `stream` (synchronises; tens of milliseconds).  scratch: caller device memory of at least
  * 8 x (SMs x 8) bytes the kernel may write.  GBCFD_ERR_ARG for an unknown op or NULL pointers. */
@@ -464,6 +466,9 @@ int gbcfd_wcns_pipe_create(const gbcfd_wcns* blocks, int n, gbcfd_pipe* out);
 #define GBCFD_OP_DIV 2
 #define GBCFD_OP_RCP_NEWTON 3
 #define GBCFD_OP_RSQRT 4
+#define GBCFD_OP_DADD 5
+#define GBCFD_OP_DMUL 6
+#define GBCFD_OP_DFMA_CONST 7
 int gbcfd_op_rate(int op, void* scratch, double* ops_per_second, void* stream);
 
 /* Message of the last error on the calling host thread ("" if none). */

@@ -47,6 +47,9 @@ __global__ void __launch_bounds__(PROBE_THREADS) op_rate_kernel(double* sink, in
         if constexpr (OP == GBCFD_OP_DIV) a[i] = 1.0 / a[i];                     // x, 1/x, x, ...
         if constexpr (OP == GBCFD_OP_RCP_NEWTON) a[i] = VM<double>::rcp(a[i]);
         if constexpr (OP == GBCFD_OP_RSQRT) a[i] = rsqrt(a[i]);                  // tends to 1
+        if constexpr (OP == GBCFD_OP_DADD) a[i] = a[i] + c;                      // register operands
+        if constexpr (OP == GBCFD_OP_DMUL) a[i] = a[i] * m;
+        if constexpr (OP == GBCFD_OP_DFMA_CONST) a[i] = fma(a[i], 0.999999999, 1e-9);  // constant-bank operands
       }
     double s = 0.0;
 #pragma unroll
@@ -71,14 +74,15 @@ using namespace gbcfd;
 
 extern "C" int gbcfd_op_rate(int op, void* scratch, double* ops_per_second, void* stream) {
   if (!scratch || !ops_per_second) return set_error(GBCFD_ERR_ARG, "NULL argument");
-  if (op < GBCFD_OP_DFMA || op > GBCFD_OP_RSQRT) return set_error(GBCFD_ERR_ARG, "unknown operation");
+  if (op < GBCFD_OP_DFMA || op > GBCFD_OP_DFMA_CONST) return set_error(GBCFD_ERR_ARG, "unknown operation");
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return probe_err(e, "no CUDA device");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int grid = 8 * nsm;
-  const int iters = op == GBCFD_OP_FFMA ? 65536 : (op == GBCFD_OP_DFMA ? 4096 : 1024);
+  const int iters = op == GBCFD_OP_FFMA ? 65536
+                    : ((op == GBCFD_OP_DIV || op == GBCFD_OP_RCP_NEWTON || op == GBCFD_OP_RSQRT) ? 1024 : 4096);
   double* sink = static_cast<double*>(scratch);
   auto go = [&]() -> cudaError_t {
     switch (op) {
@@ -86,7 +90,10 @@ extern "C" int gbcfd_op_rate(int op, void* scratch, double* ops_per_second, void
       case GBCFD_OP_FFMA: return op_rate_go<GBCFD_OP_FFMA>(sink, grid, iters, s);
       case GBCFD_OP_DIV: return op_rate_go<GBCFD_OP_DIV>(sink, grid, iters, s);
       case GBCFD_OP_RCP_NEWTON: return op_rate_go<GBCFD_OP_RCP_NEWTON>(sink, grid, iters, s);
-      default: return op_rate_go<GBCFD_OP_RSQRT>(sink, grid, iters, s);
+      case GBCFD_OP_RSQRT: return op_rate_go<GBCFD_OP_RSQRT>(sink, grid, iters, s);
+      case GBCFD_OP_DADD: return op_rate_go<GBCFD_OP_DADD>(sink, grid, iters, s);
+      case GBCFD_OP_DMUL: return op_rate_go<GBCFD_OP_DMUL>(sink, grid, iters, s);
+      default: return op_rate_go<GBCFD_OP_DFMA_CONST>(sink, grid, iters, s);
     }
   };
   cudaEvent_t e0, e1;

@@ -298,7 +298,7 @@ def time_step_noalloc(q, prm: Params, spacing, out=None, stream=None):
     return out
 
 
-OP_DFMA, OP_FFMA, OP_DIV, OP_RCP_NEWTON, OP_RSQRT = 0, 1, 2, 3, 4
+OP_DFMA, OP_FFMA, OP_DIV, OP_RCP_NEWTON, OP_RSQRT, OP_DADD, OP_DMUL, OP_DFMA_CONST = 0, 1, 2, 3, 4, 5, 6, 7
 
 
 def op_rate(op, device=None, stream=None) -> float:

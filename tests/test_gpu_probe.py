@@ -30,6 +30,15 @@ def test_op_rates(gb):
     assert 0 < rsq < dfma and 0 < div < dfma
 
 
+def test_fp64_instruction_forms(gb):
+    """an FP64 FMA of three registers issues faster than an FP64 add or multiply, or an FMA with
+    constant-bank operands (measured 598 against 504 G/s)"""
+    dfma = gb.op_rate(gb.OP_DFMA)
+    for op in (gb.OP_DADD, gb.OP_DMUL, gb.OP_DFMA_CONST):
+        r = gb.op_rate(op)
+        assert 0.5 * dfma < r <= 1.02 * dfma, (op, r, dfma)
+
+
 def test_op_rate_rejects_unknown_op(gb):
     with pytest.raises(gb.GbcfdError):
-        gb.op_rate(7)
+        gb.op_rate(8)
