@@ -476,7 +476,7 @@ def fp64_alu_roofline(res, cells, steps, hbm, workload="vortex256"):
         achieved = total / sec / 1e12
         out.update({"achieved": round(achieved, 4), "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
                     "flops_per_cell": flops})
-        if ops:  # a DADD or DMUL fills an FMA lane slot for one flop: the pipe's own utilisation
+        if ops:  # FP64 instructions per FMA issue slot (a DADD or DMUL counted as one; they issue at 84% of an FMA's rate)
             nops = sum(ops[s - 1] * cells * steps for s in (1, 2, 3))
             out.update({"lane_slot_frac": round(nops / sec / (FP64_PEAK_TFLOPS / 2 * 1e12), 4),
                         "ops_per_cell": ops})
