@@ -1,12 +1,16 @@
-// wcns.cu -- the paper's own spatial scheme on periodic uniform Cartesian blocks: WCNS-E-5
-// (arXiv 1710.09995 Sec. 2.2, Eq. 2) with fourth-order central viscous derivatives, advanced by
-// the third-order Runge-Kutta stages of Eqs. 4-6 (lambda = -dt), and its C ABI (gbcfd_wcns_*).
+// wcns.cu -- the paper's own spatial scheme on uniform Cartesian blocks, periodic alone or
+// connected into a periodic multi-block lattice: WCNS-E-5 (arXiv 1710.09995 Sec. 2.2, Eq. 2) with
+// fourth-order central viscous derivatives, advanced by the third-order Runge-Kutta stages of
+// Eqs. 4-6 (lambda = -dt), and its C ABI (gbcfd_wcns_*).
 //
-// Per Runge-Kutta stage (all launches on the caller's stream):
+// Per Runge-Kutta stage (all launches on the caller's stream; blocks advanced together run on
+// side streams forked from and joined into it):
 //   prim_kernel  the stage input -> primitives W = (rho, u, v, w, p, theta) of every cell of a box
 //                padded by 5 cells (periodic images by index wrap: the halo exchange of a
 //                self-connected block); stage 1 also reduces the CFL rate of Q^n to the step's
-//                time step.
+//                time step.  prim_multi_kernel, for blocks advanced together, reads each halo
+//                cell from the block that owns it (the members' table walked face to face) and
+//                wcns_group_dt_kernel then gives every member the common time step.
 //   viscres_kernel  (Navier-Stokes) the viscous residual Rv = -(D4_x Fv + D4_y Gv + D4_z Hv) at the
 //                interior cells in one pass: tiles marching in z form the gradient tensor (D4 of
 //                u, v, w, theta) once per cell of the tile's union box from a TMA-fed ring of
